@@ -1,0 +1,195 @@
+"""FP64 CPU oracle for force-interpolation AdResS — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference leg of
+``bench.py`` may import this package.  The product path (the CUDA library and its
+binding) never imports it and shares no code with it.
+
+The arithmetic lives in ``adress_oracle.c`` (plain C, double precision), compiled
+here with gcc into ``oracle/_build/libadress_oracle.so`` and called through ctypes.
+Arrays are numpy float64 ``(N, 3)`` row-major.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "adress_oracle.c")
+_HDR = os.path.join(_HERE, "adress_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libadress_oracle.so")
+
+ORC_OK, ORC_ERR_BOND = 0, 1
+
+
+class orc_sys(C.Structure):
+    _fields_ = [
+        ("M", C.c_int), ("na", C.c_int),
+        ("mass", C.POINTER(C.c_double)),
+        ("L", C.c_double * 3),
+        ("xc", C.c_double), ("d_at", C.c_double), ("d_hy", C.c_double),
+        ("eps", C.c_double), ("sig", C.c_double), ("rc_at", C.c_double),
+        ("nb", C.c_int), ("bonds", C.POINTER(C.c_int)),
+        ("fene_k", C.c_double), ("fene_r0", C.c_double),
+        ("intra_wca", C.c_int),
+        ("cgF", C.POINTER(C.c_double)), ("cgV", C.POINTER(C.c_double)),
+        ("cg_n", C.c_int), ("cg_dr", C.c_double), ("rc_cg", C.c_double),
+        ("tf", C.POINTER(C.c_double)), ("tf_n", C.c_int), ("tf_dx", C.c_double),
+        ("kT", C.c_double), ("gamma", C.c_double), ("dt", C.c_double),
+        ("seed", C.c_uint64), ("replica", C.c_int64),
+    ]
+
+
+def build(force: bool = False, extra_flags: tuple = ()) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no fast-math).  Returns the .so path."""
+    out = _LIB if not extra_flags else os.path.join(
+        _BUILD, "libadress_oracle_" + "_".join(f.strip("-").replace("=", "") for f in extra_flags) + ".so")
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", *extra_flags,
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+_lib = None
+
+
+def _load(path: str | None = None):
+    global _lib
+    if path is not None:
+        lib = C.CDLL(path)
+    else:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+    d, i64, u64 = C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)
+    S = C.POINTER(orc_sys)
+    lib.orc_philox4x64.argtypes = [u64, u64, u64]
+    lib.orc_weight.argtypes = [S, C.c_double]
+    lib.orc_weight.restype = C.c_double
+    lib.orc_com_lambda.argtypes = [S, d, d, d, d]
+    lib.orc_forces.argtypes = [S, d, C.c_int, d, d, d]
+    lib.orc_forces.restype = C.c_int
+    lib.orc_run.argtypes = [S, d, d, d, C.c_int64, C.c_int, C.c_int]
+    lib.orc_run.restype = C.c_int
+    lib.orc_langevin_force.argtypes = [S, d, C.c_int64, d]
+    lib.orc_kinetic.argtypes = [S, d, d]
+    lib.orc_density.argtypes = [S, d, C.c_int, i64, C.c_int, i64]
+    lib.orc_tf_update.argtypes = [S, d, C.c_int, i64, C.c_int, C.c_double, C.c_double]
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(a, ct=C.c_double):
+    return a.ctypes.data_as(C.POINTER(ct)) if a is not None else None
+
+
+class Oracle:
+    """Holds one system description and exposes the oracle's functions on numpy arrays.
+
+    `system` is any object with the fields of ``paper_1806_10841_gb300.inputs.System``.
+    """
+
+    def __init__(self, system, *, replica: int = 0, lib_path: str | None = None):
+        s = system
+        self.lib = _load(lib_path)
+        self.M, self.na = int(s.M), int(s.na)
+        self.N = self.M * self.na
+        self._keep = dict(
+            mass=np.ascontiguousarray(s.mass, dtype=np.float64),
+            bonds=np.ascontiguousarray(np.asarray(s.bonds, dtype=np.int32).reshape(-1)),
+            cgF=np.ascontiguousarray(s.cg_F, dtype=np.float64),
+            cgV=np.ascontiguousarray(s.cg_V, dtype=np.float64),
+            tf=np.ascontiguousarray(s.tf if s.tf is not None else np.zeros(0), dtype=np.float64),
+        )
+        k = self._keep
+        self.sys = orc_sys(
+            M=self.M, na=self.na, mass=_ptr(k["mass"]), L=(C.c_double * 3)(*s.box),
+            xc=s.xc, d_at=s.d_at, d_hy=s.d_hy, eps=s.eps, sig=s.sigma, rc_at=s.rc_at,
+            nb=len(k["bonds"]) // 2, bonds=_ptr(k["bonds"], C.c_int),
+            fene_k=s.fene_k, fene_r0=s.fene_r0, intra_wca=int(s.intra_wca),
+            cgF=_ptr(k["cgF"]), cgV=_ptr(k["cgV"]), cg_n=len(k["cgF"]) - 1, cg_dr=s.cg_dr,
+            rc_cg=s.rc_cg, tf=_ptr(k["tf"]), tf_n=len(k["tf"]), tf_dx=s.tf_dx,
+            kT=s.kT, gamma=s.gamma, dt=s.dt, seed=int(s.seed), replica=int(replica))
+
+    def set_tf(self, tf):
+        self._keep["tf"] = np.ascontiguousarray(tf, dtype=np.float64)
+        self.sys.tf = _ptr(self._keep["tf"])
+        self.sys.tf_n = len(self._keep["tf"])
+
+    def weight(self, d: float) -> float:
+        return self.lib.orc_weight(C.byref(self.sys), float(d))
+
+    def com_lambda(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        R = np.empty((self.M, 3))
+        dxc = np.empty(self.M)
+        w = np.empty(self.M)
+        self.lib.orc_com_lambda(C.byref(self.sys), _ptr(x), _ptr(R), _ptr(dxc), _ptr(w))
+        return R, dxc, w
+
+    def forces(self, x, method: int = 1, w_override=None):
+        """Conservative forces (N,3) and energies {E_at, E_cg, E_bond, virial}."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        f = np.empty((self.N, 3))
+        e = np.zeros(4)
+        wo = None if w_override is None else np.ascontiguousarray(w_override, dtype=np.float64)
+        st = self.lib.orc_forces(C.byref(self.sys), _ptr(x), int(method), _ptr(wo), _ptr(f), _ptr(e))
+        if st != ORC_OK:
+            raise RuntimeError(f"oracle forces failed with status {st}")
+        return f, dict(E_at=e[0], E_cg=e[1], E_bond=e[2], virial=e[3])
+
+    def run(self, x, v, f, step0: int, nsteps: int, method: int = 1):
+        """Advance (x, v, f) by nsteps of Langevin velocity Verlet; returns new copies."""
+        x = np.array(x, dtype=np.float64, order="C")
+        v = np.array(v, dtype=np.float64, order="C")
+        f = np.array(f, dtype=np.float64, order="C")
+        st = self.lib.orc_run(C.byref(self.sys), _ptr(x), _ptr(v), _ptr(f), int(step0), int(nsteps),
+                              int(method))
+        if st != ORC_OK:
+            raise RuntimeError(f"oracle run failed with status {st}")
+        return x, v, f
+
+    def langevin_force(self, v, step: int):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        f = np.zeros((self.N, 3))
+        self.lib.orc_langevin_force(C.byref(self.sys), _ptr(v), int(step), _ptr(f))
+        return f
+
+    def kinetic(self, v):
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.zeros(4)
+        self.lib.orc_kinetic(C.byref(self.sys), _ptr(v), _ptr(out))
+        return out[0], out[1:].copy()
+
+    def density(self, x, nd: int, nx: int):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        cd = np.zeros(nd, dtype=np.int64)
+        cx = np.zeros(nx, dtype=np.int64)
+        self.lib.orc_density(C.byref(self.sys), _ptr(x), nd, _ptr(cd, C.c_int64), nx, _ptr(cx, C.c_int64))
+        return cd, cx
+
+    def tf_update(self, tf, counts_d, nsamples: float, alpha: float):
+        tf = np.array(tf, dtype=np.float64, order="C")
+        cd = np.ascontiguousarray(counts_d, dtype=np.int64)
+        self.lib.orc_tf_update(C.byref(self.sys), _ptr(tf), len(tf), _ptr(cd, C.c_int64), len(cd),
+                               float(nsamples), float(alpha))
+        return tf
+
+
+def philox4x64(ctr, key):
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib.orc_philox4x64(_ptr(c, C.c_uint64), _ptr(k, C.c_uint64), _ptr(out, C.c_uint64))
+    return out

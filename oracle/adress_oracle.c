@@ -1,0 +1,420 @@
+/*
+ * FP64 CPU oracle for one force-interpolation AdResS molecular-dynamics step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark may load this code; the product path never does.  It shares no
+ * code, header, table generator or helper with the CUDA library.
+ *
+ * Every function is the plain definition, in double precision, in the order the
+ * method states it:
+ *   - resolution function lambda(R_alpha) of the molecule centre of mass, 1 in the
+ *     AT region, 0 in the CG region, squared cosine through the hybrid layer
+ *     (Sec. "Force interpolation"; Sec. "Potential energy interpolation" names the
+ *     squared cosine);
+ *   - force interpolation between molecules alpha and beta (Eq. 1):
+ *       F_ab = l_a l_b F^AT_ab + (1 - l_a l_b) F^CG_ab,
+ *     F^AT the sum of atom-atom forces, F^CG a COM-COM force (Sec. "Force
+ *     interpolation");
+ *   - intramolecular bonded terms, never interpolated (same section);
+ *   - the thermodynamic force in the hybrid layer and its iterative construction from
+ *     the density profile (Sec. "Free energy corrections and the thermodynamic force");
+ *   - a Langevin thermostat (force interpolation needs thermostatting, Sec.
+ *     "Potential energy interpolation") with velocity-Verlet integration.
+ * Parity unpinned: the thermodynamic-force update rule (orc_tf_update) beyond its
+ * identity and closed-form cases; the paper gives no formula for it.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "adress_oracle.h"
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ---------------------------------------------------------------------------------
+ * Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11): ten rounds of two 64x64->128 multiplies with
+ * the published multipliers, key bumped by the published Weyl constants between rounds.
+ * ------------------------------------------------------------------------------- */
+static void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+  unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+  *lo = (uint64_t)p;
+  *hi = (uint64_t)(p >> 64);
+}
+
+void orc_philox4x64(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+  uint64_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint64_t k[2] = {key_in[0], key_in[1]};
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k[0] += W0;
+      k[1] += W1;
+    }
+    uint64_t hi0, lo0, hi1, lo1;
+    mulhilo64(M0, c[0], &hi0, &lo0);
+    mulhilo64(M1, c[2], &hi1, &lo1);
+    uint64_t n0 = hi1 ^ c[1] ^ k[0];
+    uint64_t n1 = lo1;
+    uint64_t n2 = hi0 ^ c[3] ^ k[1];
+    uint64_t n3 = lo0;
+    c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+  }
+  memcpy(out, c, sizeof(c));
+}
+
+/* Uniform double in [0,1) from the top 53 bits. */
+static double u01(uint64_t r) { return (double)(r >> 11) * (1.0 / 9007199254740992.0); }
+
+/* --------------------------------------------------------------------------------- */
+
+static double minimg(double d, double L) { return d - L * nearbyint(d / L); }
+
+double orc_weight(const orc_sys* s, double d) {
+  /* lambda = 1 inside the AT half-width, squared cosine across the hybrid layer,
+   * 0 beyond it; a zero-width layer is a step with no division. */
+  if (d < s->d_at) return 1.0;
+  if (d >= s->d_at + s->d_hy) return 0.0;
+  double c = cos(0.5 * M_PI * (d - s->d_at) / s->d_hy);
+  return c * c;
+}
+
+static double mol_mass(const orc_sys* s) {
+  double m = 0;
+  for (int k = 0; k < s->na; ++k) m += s->mass[k];
+  return m;
+}
+
+/* Centre of mass of every molecule (minimum-image unwrap relative to its first atom,
+ * result wrapped into [0,L)), signed x-distance to the slab centre, |d| and lambda. */
+void orc_com_lambda(const orc_sys* s, const double* x, double* R, double* dx_c, double* w) {
+  const double Mt = mol_mass(s);
+  for (int a = 0; a < s->M; ++a) {
+    const double* x0 = x + 3 * (size_t)a * s->na;
+    double acc[3] = {0, 0, 0};
+    for (int k = 0; k < s->na; ++k) {
+      const double* xi = x0 + 3 * k;
+      for (int d = 0; d < 3; ++d) acc[d] += s->mass[k] * (x0[d] + minimg(xi[d] - x0[d], s->L[d]));
+    }
+    for (int d = 0; d < 3; ++d) {
+      double r = acc[d] / Mt;
+      r -= s->L[d] * floor(r / s->L[d]);
+      if (r >= s->L[d]) r -= s->L[d];
+      R[3 * a + d] = r;
+    }
+    double dxc = minimg(R[3 * a] - s->xc, s->L[0]);
+    if (dx_c) dx_c[a] = dxc;
+    if (w) w[a] = orc_weight(s, fabs(dxc));
+  }
+}
+
+/* --- pair potentials (force returned as F/r so that f_vec = (F/r) * r_vec) --------- */
+
+static double wca_fr(const orc_sys* s, double r2, double* V) {
+  double sr2 = s->sig * s->sig / r2;
+  double sr6 = sr2 * sr2 * sr2;
+  *V = 4.0 * s->eps * (sr6 * sr6 - sr6) + s->eps;
+  return 24.0 * s->eps * (2.0 * sr6 * sr6 - sr6) / r2;
+}
+
+/* Linear interpolation in the CG table: returns F(r) (positive = repulsive), sets V. */
+static double cg_table(const orc_sys* s, double r, double* V) {
+  double u = r / s->cg_dr;
+  int k = (int)u;
+  if (k >= s->cg_n) { *V = 0; return 0; }
+  double t = u - k;
+  *V = s->cgV[k] * (1.0 - t) + s->cgV[k + 1] * t;
+  return s->cgF[k] * (1.0 - t) + s->cgF[k + 1] * t;
+}
+
+/* Thermodynamic force table, nodes d_k = k*tf_dx, linear interpolation, 0 outside. */
+static double tf_table(const orc_sys* s, double d) {
+  if (!s->tf || s->tf_n <= 0) return 0.0;
+  double u = d / s->tf_dx;
+  int k = (int)u;
+  if (k + 1 < s->tf_n) {
+    double t = u - k;
+    return s->tf[k] * (1.0 - t) + s->tf[k + 1] * t;
+  }
+  if (k + 1 == s->tf_n && u == (double)k) return s->tf[k];
+  return 0.0;
+}
+
+/* Accumulators: e[0]=E_AT (weighted), e[1]=E_CG (weighted), e[2]=E_bond,
+ * e[3]=virial sum r.f (nonbonded + bonded). */
+
+/* Interaction of molecules a and b (a != b), Eq. 1, added to both (Newton's 3rd law). */
+static void pair_ab(const orc_sys* s, const double* x, const double* R, const double* w, int a,
+                    int b, double* f, double* e) {
+  const double wab = w[a] * w[b];
+  const int na = s->na;
+  if (wab > 0.0) {
+    const double rc2 = s->rc_at * s->rc_at;
+    for (int i = a * na; i < (a + 1) * na; ++i)
+      for (int j = b * na; j < (b + 1) * na; ++j) {
+        double r[3], r2 = 0;
+        for (int d = 0; d < 3; ++d) {
+          r[d] = minimg(x[3 * i + d] - x[3 * j + d], s->L[d]);
+          r2 += r[d] * r[d];
+        }
+        if (r2 >= rc2) continue;
+        double V, fr = wca_fr(s, r2, &V);
+        for (int d = 0; d < 3; ++d) {
+          f[3 * i + d] += wab * fr * r[d];
+          f[3 * j + d] -= wab * fr * r[d];
+        }
+        e[0] += wab * V;
+        e[3] += wab * fr * r2;
+      }
+  }
+  if (wab < 1.0) {
+    double Rab[3], r2 = 0;
+    for (int d = 0; d < 3; ++d) {
+      Rab[d] = minimg(R[3 * a + d] - R[3 * b + d], s->L[d]);
+      r2 += Rab[d] * Rab[d];
+    }
+    if (r2 < s->rc_cg * s->rc_cg) {
+      double r = sqrt(r2), V, F = cg_table(s, r, &V);
+      double c = (1.0 - wab) * F / r;
+      const double Mt = mol_mass(s);
+      /* the COM force reaches each atom in proportion m_i / M (dR/dx_i = m_i/M) */
+      for (int k = 0; k < na; ++k)
+        for (int d = 0; d < 3; ++d) {
+          f[3 * (a * na + k) + d] += s->mass[k] / Mt * c * Rab[d];
+          f[3 * (b * na + k) + d] -= s->mass[k] / Mt * c * Rab[d];
+        }
+      e[1] += (1.0 - wab) * V;
+      e[3] += c * r2;
+    }
+  }
+}
+
+/* Bonded terms of molecule a: FENE (+ optional WCA) on every listed pair, unweighted. */
+static int bonded_mol(const orc_sys* s, const double* x, int a, double* f, double* e) {
+  const int na = s->na;
+  const double R02 = s->fene_r0 * s->fene_r0;
+  for (int q = 0; q < s->nb; ++q) {
+    int i = a * na + s->bonds[2 * q], j = a * na + s->bonds[2 * q + 1];
+    double r[3], r2 = 0;
+    for (int d = 0; d < 3; ++d) {
+      r[d] = minimg(x[3 * i + d] - x[3 * j + d], s->L[d]);
+      r2 += r[d] * r[d];
+    }
+    if (r2 >= R02) return ORC_ERR_BOND;
+    double g = 1.0 - r2 / R02;
+    double fr = -s->fene_k / g;
+    double V = -0.5 * s->fene_k * R02 * log(g);
+    if (s->intra_wca && r2 < s->rc_at * s->rc_at) {
+      double Vw, frw = wca_fr(s, r2, &Vw);
+      fr += frw;
+      V += Vw;
+    }
+    for (int d = 0; d < 3; ++d) {
+      f[3 * i + d] += fr * r[d];
+      f[3 * j + d] -= fr * r[d];
+    }
+    e[2] += V;
+    e[3] += fr * r2;
+  }
+  return ORC_OK;
+}
+
+/* Thermodynamic force on hybrid-layer molecules, along x, away from the centre when
+ * positive, spread over the atoms by mass fraction. */
+static void tf_forces(const orc_sys* s, const double* dxc, double* f) {
+  const double Mt = mol_mass(s);
+  for (int a = 0; a < s->M; ++a) {
+    double d = fabs(dxc[a]);
+    if (d < s->d_at || d >= s->d_at + s->d_hy) continue;
+    double F = tf_table(s, d) * (dxc[a] < 0 ? -1.0 : 1.0);
+    for (int k = 0; k < s->na; ++k) f[3 * (a * s->na + k)] += s->mass[k] / Mt * F;
+  }
+}
+
+/* Largest atom-to-COM distance over all molecules. */
+static double max_extent(const orc_sys* s, const double* x, const double* R) {
+  double m = 0;
+  for (int a = 0; a < s->M; ++a)
+    for (int k = 0; k < s->na; ++k) {
+      double r2 = 0;
+      for (int d = 0; d < 3; ++d) {
+        double t = minimg(x[3 * (a * s->na + k) + d] - R[3 * a + d], s->L[d]);
+        r2 += t * t;
+      }
+      if (r2 > m) m = r2;
+    }
+  return sqrt(m);
+}
+
+/* Conservative forces (no thermostat).  method 0: every molecule pair a<b;
+ * method 1: a linked-cell scan over COM cells no smaller than the largest pair reach.
+ * w_override (may be NULL) replaces lambda for every molecule. */
+int orc_forces(const orc_sys* s, const double* x, int method, const double* w_override, double* f,
+               double* e) {
+  const int M = s->M;
+  double* R = (double*)malloc(sizeof(double) * 3 * M);
+  double* dxc = (double*)malloc(sizeof(double) * M);
+  double* w = (double*)malloc(sizeof(double) * M);
+  orc_com_lambda(s, x, R, dxc, w);
+  if (w_override) memcpy(w, w_override, sizeof(double) * M);
+  memset(f, 0, sizeof(double) * 3 * (size_t)M * s->na);
+  double acc[4] = {0, 0, 0, 0};
+  int st = ORC_OK;
+
+  if (method == 0) {
+    for (int a = 0; a < M; ++a)
+      for (int b = a + 1; b < M; ++b) pair_ab(s, x, R, w, a, b, f, acc);
+  } else {
+    double ext = max_extent(s, x, R);
+    double reach = s->rc_cg > s->rc_at + 2 * ext ? s->rc_cg : s->rc_at + 2 * ext;
+    int nc[3];
+    for (int d = 0; d < 3; ++d) {
+      nc[d] = (int)floor(s->L[d] / reach);
+      if (nc[d] < 1) nc[d] = 1;
+    }
+    int ncell = nc[0] * nc[1] * nc[2];
+    int* head = (int*)malloc(sizeof(int) * ncell);
+    int* next = (int*)malloc(sizeof(int) * M);
+    int* cell = (int*)malloc(sizeof(int) * M);
+    for (int c = 0; c < ncell; ++c) head[c] = -1;
+    for (int a = M - 1; a >= 0; --a) {
+      int ci[3];
+      for (int d = 0; d < 3; ++d) {
+        ci[d] = (int)(R[3 * a + d] / s->L[d] * nc[d]);
+        if (ci[d] >= nc[d]) ci[d] = nc[d] - 1;
+      }
+      cell[a] = (ci[0] * nc[1] + ci[1]) * nc[2] + ci[2];
+      next[a] = head[cell[a]];
+      head[cell[a]] = a;
+    }
+    for (int a = 0; a < M; ++a) {
+      int c = cell[a];
+      int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
+      int seen[27], ns = 0;
+      for (int ox = -1; ox <= 1; ++ox)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int oz = -1; oz <= 1; ++oz) {
+            int nx = ((cx + ox) % nc[0] + nc[0]) % nc[0];
+            int ny = ((cy + oy) % nc[1] + nc[1]) % nc[1];
+            int nz = ((cz + oz) % nc[2] + nc[2]) % nc[2];
+            int nbc = (nx * nc[1] + ny) * nc[2] + nz, dup = 0;
+            for (int q = 0; q < ns; ++q) dup |= (seen[q] == nbc);
+            if (dup) continue;
+            seen[ns++] = nbc;
+            for (int b = head[nbc]; b >= 0; b = next[b])
+              if (b > a) pair_ab(s, x, R, w, a, b, f, acc);
+          }
+    }
+    free(head); free(next); free(cell);
+  }
+  for (int a = 0; a < M && st == ORC_OK; ++a) st = bonded_mol(s, x, a, f, acc);
+  tf_forces(s, dxc, f);
+  if (e) memcpy(e, acc, sizeof(acc));
+  free(R); free(dxc); free(w);
+  return st;
+}
+
+/* Langevin friction and noise for atom gid at time level `step`:
+ *   F_L = -gamma m v + sqrt(24 gamma kT m / dt) (u - 1/2),
+ * u uniform in [0,1) from Philox4x64-10 with key (seed, step), counter (gid, replica, 0, 0). */
+static void langevin(const orc_sys* s, const double* v, int64_t step, double* f) {
+  const int N = s->M * s->na;
+  for (int i = 0; i < N; ++i) {
+    double m = s->mass[i % s->na];
+    double amp = sqrt(24.0 * s->gamma * s->kT * m / s->dt);
+    uint64_t ctr[4] = {(uint64_t)i, (uint64_t)s->replica, 0, 0}, key[2] = {s->seed, (uint64_t)step};
+    uint64_t r[4];
+    orc_philox4x64(ctr, key, r);
+    for (int d = 0; d < 3; ++d) f[3 * i + d] += -s->gamma * m * v[3 * i + d] + amp * (u01(r[d]) - 0.5);
+  }
+}
+
+/* Velocity Verlet with the thermostat force evaluated with the half-step velocity:
+ *   v += dt/2 f/m;  x += dt v;  wrap;  f = F(x) + F_L(v; step+1);  v += dt/2 f/m.
+ * (x, v, f) hold time level `step0` on entry and step0+nsteps on return. */
+int orc_run(const orc_sys* s, double* x, double* v, double* f, int64_t step0, int nsteps, int method) {
+  const int N = s->M * s->na;
+  for (int n = 0; n < nsteps; ++n) {
+    for (int i = 0; i < N; ++i) {
+      double m = s->mass[i % s->na];
+      for (int d = 0; d < 3; ++d) {
+        v[3 * i + d] += 0.5 * s->dt * f[3 * i + d] / m;
+        double y = x[3 * i + d] + s->dt * v[3 * i + d];
+        if (y < 0) y += s->L[d];
+        if (y >= s->L[d]) y -= s->L[d];
+        x[3 * i + d] = y;
+      }
+    }
+    int st = orc_forces(s, x, method, NULL, f, NULL);
+    if (st != ORC_OK) return st;
+    if (s->gamma != 0.0) langevin(s, v, step0 + n + 1, f);
+    for (int i = 0; i < N; ++i) {
+      double m = s->mass[i % s->na];
+      for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * s->dt * f[3 * i + d] / m;
+    }
+  }
+  return ORC_OK;
+}
+
+/* Thermostat force alone (for tests): f += F_L(v; step). */
+void orc_langevin_force(const orc_sys* s, const double* v, int64_t step, double* f) {
+  langevin(s, v, step, f);
+}
+
+/* Kinetic energy and total momentum: out = {KE, Px, Py, Pz}. */
+void orc_kinetic(const orc_sys* s, const double* v, double* out) {
+  const int N = s->M * s->na;
+  double ke = 0, p[3] = {0, 0, 0};
+  for (int i = 0; i < N; ++i) {
+    double m = s->mass[i % s->na];
+    for (int d = 0; d < 3; ++d) {
+      ke += 0.5 * m * v[3 * i + d] * v[3 * i + d];
+      p[d] += m * v[3 * i + d];
+    }
+  }
+  out[0] = ke; out[1] = p[0]; out[2] = p[1]; out[3] = p[2];
+}
+
+/* COM density histograms: counts_d[k] over |x_com - xc| in bins of tf_dx (folded about
+ * the centre, nd bins), counts_x[k] over x_com in bins of Lx/nx.  Counts are added. */
+void orc_density(const orc_sys* s, const double* x, int nd, int64_t* counts_d, int nx,
+                 int64_t* counts_x) {
+  double* R = (double*)malloc(sizeof(double) * 3 * s->M);
+  double* dxc = (double*)malloc(sizeof(double) * s->M);
+  orc_com_lambda(s, x, R, dxc, NULL);
+  for (int a = 0; a < s->M; ++a) {
+    int kd = (int)floor(fabs(dxc[a]) / s->tf_dx);
+    if (counts_d && kd < nd) counts_d[kd] += 1;
+    int kx = (int)floor(R[3 * a] / s->L[0] * nx);
+    if (kx >= nx) kx = nx - 1;
+    if (counts_x) counts_x[kx] += 1;
+  }
+  free(R); free(dxc);
+}
+
+/* Thermodynamic-force iteration: tf_k <- tf_k - alpha * g_k for hybrid-layer nodes,
+ * where rho_k = counts_d[k] / (nsamples * 2 tf_dx Ly Lz) is the folded COM density in
+ * bin [k dx, (k+1) dx), g_k = (rho_k - rho_{k-1}) / dx is its gradient at node d_k
+ * (g_0 = 0 by symmetry, g at the last node one-sided), smoothed by a three-point moving
+ * average.  Parity unpinned beyond zero-gradient and linear-profile cases. */
+void orc_tf_update(const orc_sys* s, double* tf, int n, const int64_t* counts_d, int nd,
+                   double nsamples, double alpha) {
+  double* rho = (double*)calloc(n + 1, sizeof(double));
+  double* g = (double*)calloc(n, sizeof(double));
+  double vol = nsamples * 2.0 * s->tf_dx * s->L[1] * s->L[2];
+  for (int k = 0; k < n && k < nd; ++k) rho[k] = counts_d[k] / vol;
+  for (int k = 1; k < n; ++k) g[k] = (k < nd ? (rho[k] - rho[k - 1]) : 0.0) / s->tf_dx;
+  for (int k = 0; k < n; ++k) {
+    double sum = 0;
+    int cnt = 0;
+    for (int q = k - 1; q <= k + 1; ++q)
+      if (q >= 0 && q < n) { sum += g[q]; ++cnt; }
+    double dk = k * s->tf_dx;
+    if (dk >= s->d_at && dk <= s->d_at + s->d_hy) tf[k] -= alpha * sum / cnt;
+  }
+  free(rho); free(g);
+}

@@ -1,0 +1,45 @@
+/*
+ * FP64 CPU oracle for force-interpolation AdResS (test infrastructure only; see
+ * adress_oracle.c).  Positions, velocities and forces are (N, 3) row-major doubles,
+ * atoms of molecule a at a*na .. a*na+na-1.
+ */
+#ifndef ADRESS_ORACLE_H
+#define ADRESS_ORACLE_H
+#include <stdint.h>
+
+enum { ORC_OK = 0, ORC_ERR_BOND = 1 };
+
+typedef struct {
+  int M, na;
+  const double* mass; /* na per-site masses */
+  double L[3];
+  double xc, d_at, d_hy; /* slab centre, AT half-width, hybrid width */
+  double eps, sig, rc_at; /* WCA between atoms of different molecules */
+  int nb;
+  const int* bonds; /* 2*nb local atom indices */
+  double fene_k, fene_r0;
+  int intra_wca;
+  const double *cgF, *cgV; /* CG table, cg_n+1 nodes at k*cg_dr */
+  int cg_n;
+  double cg_dr, rc_cg;
+  const double* tf; /* thermodynamic force, tf_n nodes at k*tf_dx */
+  int tf_n;
+  double tf_dx;
+  double kT, gamma, dt;
+  uint64_t seed;
+  int64_t replica;
+} orc_sys;
+
+void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+double orc_weight(const orc_sys* s, double d);
+void orc_com_lambda(const orc_sys* s, const double* x, double* R, double* dx_c, double* w);
+int orc_forces(const orc_sys* s, const double* x, int method, const double* w_override, double* f,
+               double* e);
+int orc_run(const orc_sys* s, double* x, double* v, double* f, int64_t step0, int nsteps, int method);
+void orc_langevin_force(const orc_sys* s, const double* v, int64_t step, double* f);
+void orc_kinetic(const orc_sys* s, const double* v, double* out);
+void orc_density(const orc_sys* s, const double* x, int nd, int64_t* counts_d, int nx,
+                 int64_t* counts_x);
+void orc_tf_update(const orc_sys* s, double* tf, int n, const int64_t* counts_d, int nd,
+                   double nsamples, double alpha);
+#endif
