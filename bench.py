@@ -1,0 +1,392 @@
+"""Benchmark of the AdResS force-interpolation step on the 800k-atom tetrahedral fluid.
+
+A bench step is one thermodynamic-force iteration block: 100 Langevin velocity-Verlet
+MD steps (list rebuilds on the device as needed), a COM density sample every 10 MD
+steps, and one thermodynamic-force update from that profile.  Metric: atom-steps/s =
+atoms x MD steps / device seconds.  L2 is flushed (a 512 MB write) between timed
+bench steps, outside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+
+Under torchrun each rank runs an independent replica (replicas only; no collective on
+the data path) and value is the sum over ranks of atoms x steps / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MD_PER_BLOCK = 100
+SAMPLE_EVERY = 10
+TF_ALPHA = 0.5
+METRIC = "AdResS atom-steps/s"
+CONFIG_NAME = "tetrahedral AdResS fluid, 200k molecules / 800k atoms, 200x100x100 sigma, AT 40 + 2x10 hybrid"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pair_statistics(s, x):
+    """Unique interactions of the force evaluation (algorithmic work per launch), counted
+    on the host from the positions with numpy (cell grid over molecule centres)."""
+    L = np.array(s.box)
+    M, na = s.M, s.na
+    xm = x.reshape(M, na, 3)
+    d0 = xm - xm[:, :1]
+    d0 -= L * np.rint(d0 / L)
+    R = np.mod(xm[:, 0] + (s.mass[None, :, None] * d0).sum(1) / s.mass.sum(), L)
+    dxc = R[:, 0] - s.xc
+    dxc -= L[0] * np.rint(dxc / L[0])
+    d = np.abs(dxc)
+    w = np.where(d < s.d_at, 1.0, np.where(d >= s.d_at + s.d_hy, 0.0,
+                                           np.cos(0.5 * np.pi * (d - s.d_at) / max(s.d_hy, 1e-30)) ** 2))
+    reach = max(s.rc_cg, s.rc_at + 2 * 0.75)
+    nc = np.maximum(1, np.floor(L / reach)).astype(int)
+    cell = np.minimum((R / L * nc).astype(int), nc - 1)
+    lin = (cell[:, 0] * nc[1] + cell[:, 1]) * nc[2] + cell[:, 2]
+    order = np.argsort(lin, kind="stable")
+    lin_s = lin[order]
+    starts = np.searchsorted(lin_s, np.arange(nc.prod() + 1))
+    n_at = n_cg = 0
+    offs = [(i, j, k) for i in (-1, 0, 1) for j in (-1, 0, 1) for k in (-1, 0, 1)]
+    for o in offs:
+        nb = (cell + np.array(o)) % nc
+        nl = (nb[:, 0] * nc[1] + nb[:, 1]) * nc[2] + nb[:, 2]
+        cnt = starts[nl + 1] - starts[nl]
+        mx = cnt.max()
+        for q in range(mx):
+            has = cnt > q
+            a = np.nonzero(has)[0]
+            b = order[starts[nl[a]] + q]
+            keep = b > a
+            a, b = a[keep], b[keep]
+            dR = R[a] - R[b]
+            dR -= L * np.rint(dR / L)
+            r2 = (dR ** 2).sum(1)
+            wab = w[a] * w[b]
+            n_cg += int(((r2 < s.rc_cg ** 2) & (wab < 1)).sum())
+            sel = wab > 0
+            a2, b2 = a[sel], b[sel]
+            for i in range(na):
+                for j in range(na):
+                    dd = xm[a2, i] - xm[b2, j]
+                    dd -= L * np.rint(dd / L)
+                    n_at += int(((dd ** 2).sum(1) < s.rc_at ** 2).sum())
+    return {"at_pairs": n_at, "cg_pairs": n_cg, "bonds": M * len(s.bonds), "atoms": M * na,
+            "hr_molecules": int((w > 0).sum())}
+
+
+FLOPS = {"at_pair": 35, "cg_pair": 55, "bond": 40}  # FP32 flops per interaction
+
+
+def reference_arm(args, world, rank):
+    """The FP64 CPU oracle on the host cores (a bounded sample of the same workload)."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1806_10841_gb300 import inputs
+
+    s = inputs.c2_800k()
+    x, v = inputs.tetra_state(s)
+    o = oracle.Oracle(s)
+    f, _ = o.forces(x)
+    for k in range(args.warmup):
+        x, v, f = o.run(x, v, f, k, 1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        x, v, f = o.run(x, v, f, args.warmup + k, 1)
+    dt = time.perf_counter() - t0
+    value = s.N * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "atom-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CONFIG_NAME, "md_steps_per_bench_step": 1, "atoms": s.N},
+            "cpu_baseline": {"value": value, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} MD steps of the full 800k-atom system (1 per bench step)"},
+            "e2e": {"value": value, "unit": "atom-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(s, x, v):
+    import oracle
+
+    o = oracle.Oracle(s)
+    f, _ = o.forces(x)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        x, v, f = o.run(x, v, f, n, 1)
+        n += 1
+        if time.perf_counter() - t0 > 10.0 or n >= 8:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": s.N * n / dt, "unit": "atom-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} MD steps (incl. force, bonded, thermostat) of the full 800k-atom system, single thread"}
+
+
+def run_block(sim, nsteps=MD_PER_BLOCK):
+    for _ in range(nsteps // SAMPLE_EVERY):
+        sim.step(SAMPLE_EVERY)
+        sim.density_accumulate()
+    sim.tf_update(TF_ALPHA)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 GPU comparison arm")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, world, rank)
+
+    import torch
+
+    from paper_1806_10841_gb300 import adress, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    s = inputs.c2_800k(seed=20180628 + rank)
+    x0, v0 = inputs.tetra_state(s)
+
+    def make(prec):
+        sim = adress.AdResS(s, precision=prec, device=f"cuda:{local}", replica=rank)
+        sim.set_state(x0, v0)
+        sim.compute_forces(energies=False)
+        sim.check()
+        return sim
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(sim, k, w):
+        stream = sim.stream
+        for _ in range(w):
+            run_block(sim)
+        sim.check()
+        evs = []
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with Clocks(local) as clk:
+            for _ in range(k):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                run_block(sim)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        sim.check()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return sum(ms) / 1e3, ms, clk.summary()
+
+    sim = make(args.precision)
+    total_s, ms, clocks = timed(sim, args.steps, args.warmup)
+    if dist:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    atom_steps = s.N * MD_PER_BLOCK * args.steps * world
+    value = atom_steps / total_s
+
+    # ---- live kernel timing (CUDA events on the library's stream) + roofline ----
+    kt = sim.time_kernels(reps=20)
+    stats = pair_statistics(s, sim.get_state()[0]) if rank == 0 else None
+    # ---- e2e through the public API: pinned host state in, state + KE out, every step ----
+    hx = torch.from_numpy(np.ascontiguousarray(x0.T)).pin_memory()
+    hv = torch.from_numpy(np.ascontiguousarray(v0.T)).pin_memory()
+    hf = torch.empty(sim.f.shape, dtype=sim.f.dtype).pin_memory()
+    hf.copy_(sim.f.cpu())
+    ox = torch.empty_like(hx).pin_memory()
+    ov = torch.empty_like(hv).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(sim.stream):
+            sim.x.copy_(hx, non_blocking=True)
+            sim.v.copy_(hv, non_blocking=True)
+            sim.f.copy_(hf, non_blocking=True)
+        sim.build_lists()
+        run_block(sim)
+        with torch.cuda.stream(sim.stream):
+            ox.copy_(sim.x, non_blocking=True)
+            ov.copy_(sim.v, non_blocking=True)
+        ke, _ = sim.kinetic()
+    sim.check()
+    e2e_s = time.perf_counter() - t0
+    h2d = hx.numel() * 8 + hv.numel() * 8 + hf.numel() * hf.element_size()
+    d2h = ox.numel() * 8 + ov.numel() * 8 + 4 * 8
+
+    compare = None
+    if not args.no_compare and rank == 0:
+        other = "fp64" if args.precision == "fp32" else "fp32"
+        sim.close()
+        sim2 = make(other)
+        t2, _, _ = timed(sim2, max(2, args.steps // 2), 2)
+        compare = {"precision": other,
+                   "value": s.N * MD_PER_BLOCK * max(2, args.steps // 2) / t2,
+                   "unit": "atom-steps/s"}
+        # force error of both GPU paths against the FP64 oracle on the initial state
+        import oracle
+
+        f_ref, _ = oracle.Oracle(s).forces(x0)
+        errs = {}
+        for prec, sm in ((other, sim2),):
+            sm.set_state(x0, v0)
+            fg, _ = sm.forces()
+            errs[prec] = math.sqrt(((fg - f_ref) ** 2).sum() / (f_ref ** 2).sum())
+        sim2.close()
+        sim3 = make(args.precision)
+        fg, _ = sim3.forces()
+        errs[args.precision] = math.sqrt(((fg - f_ref) ** 2).sum() / (f_ref ** 2).sum())
+        sim3.close()
+        compare["force_rel_rms_vs_fp64_oracle"] = errs
+    else:
+        sim.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    pk, src = peaks()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    flops = (stats["at_pairs"] * FLOPS["at_pair"] + stats["cg_pairs"] * FLOPS["cg_pair"]
+             + stats["bonds"] * FLOPS["bond"])
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s from unit counts and the sampled clock
+    achieved = flops / (kt["forces"] * 1e-3) / 1e12
+    # integration kernel: algorithmic bytes per atom (x, v read+write fp64; f read; offsets write)
+    fbytes = 4 if args.precision == "fp32" else 8
+    int_bytes = s.N * (24 * 4 + 3 * fbytes + (16 if args.precision == "fp32" else 32)) + s.M * 64
+    int_gbs = int_bytes / (kt["integrate_com"] * 1e-3) / 1e9
+    roofline = {"bound": "alu", "kernel": "k_forces (Eq. 1 pair + bonded + TF + Langevin + kick)",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": None, "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sampled)",
+                "algorithmic_flops_per_launch": flops, "ms_per_launch": kt["forces"]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "atom-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_s / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 forces / f64 state" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded lattice + jitter, random orientations, Maxwell-Boltzmann)",
+        "config": {"workload": CONFIG_NAME, "atoms": s.N, "molecules": s.M,
+                   "md_steps_per_bench_step": MD_PER_BLOCK, "density_samples_per_bench_step": MD_PER_BLOCK // SAMPLE_EVERY,
+                   "tf_updates_per_bench_step": 1, "l2": "flushed (512 MB write) between timed bench steps",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": s.N * MD_PER_BLOCK * e2e_steps / e2e_s, "unit": "atom-steps/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": args.steps * (MD_PER_BLOCK * 3 + MD_PER_BLOCK // SAMPLE_EVERY * 2 + 1),
+        "roofline": roofline,
+        "kernel_ms": kt,
+        "integrate_kernel": {"bound": "hbm", "achieved_gbs": int_gbs, "peak_gbs": pk.get("hbm_gbs"),
+                             "frac": int_gbs / pk.get("hbm_gbs", 6800.0), "algorithmic_bytes": int_bytes},
+        "peaks_source": src,
+        "clocks": clocks,
+        "pair_stats": stats,
+        "compare": compare,
+        "per_step_ms": ms,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(s, x0, v0)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

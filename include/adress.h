@@ -1,0 +1,187 @@
+/*
+ * adress.h — C ABI of the GB300 (sm_103a) force-interpolation AdResS step.
+ *
+ * One AdResS molecular-dynamics step of the paper's force-interpolation scheme
+ * (ESPResSo++ 2.0, Sec. "Force interpolation", Eq. 1):
+ *   F_ab = l(R_a) l(R_b) F^AT_ab + (1 - l(R_a) l(R_b)) F^CG_ab,
+ * where l is the resolution function of the molecule centre of mass R (1 in the
+ * atomistic region, 0 in the coarse-grained region, squared cosine across the hybrid
+ * layer), F^AT the sum of atom-atom forces between the two molecules and F^CG a
+ * COM-COM force.  Intramolecular bonds are not interpolated (same section); a
+ * thermodynamic force acts in the hybrid layer (Sec. "Free energy corrections and the
+ * thermodynamic force"); force interpolation needs a thermostat (Sec. "Potential energy
+ * interpolation"), here Langevin inside velocity Verlet.
+ *
+ * Conventions for every call:
+ *  - All state arrays are caller-owned DEVICE memory in structure-of-arrays layout
+ *    [3][N] (x components of all atoms, then y, then z); atoms of molecule a are
+ *    a*na .. a*na+na-1.  The library never frees caller memory.
+ *  - The handle owns its lists, tables, scratch buffers and CUDA graphs; it allocates
+ *    them with cudaMalloc in adress_init / adress_build_lists and frees them in
+ *    adress_destroy.
+ *  - Work is enqueued on the stream given to adress_init and runs asynchronously,
+ *    except for calls that return host data (they synchronise that stream).
+ *  - Device-side faults of the method (list overflow, a broken FENE bond, a
+ *    non-finite force, a molecule wider than the list allows) are recorded in a
+ *    device error word and returned by the next synchronising call (adress_check).
+ *  - No call traps, aborts or throws.  Errors are returned as adress_status and
+ *    described by adress_last_error.
+ */
+#ifndef ADRESS_H
+#define ADRESS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adress_ctx* adress_handle;
+
+typedef enum {
+  ADRESS_OK = 0,
+  ADRESS_ERR_ARG = 1,           /* invalid argument or configuration */
+  ADRESS_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  ADRESS_ERR_LIST_OVERFLOW = 3, /* more neighbours than the list capacity */
+  ADRESS_ERR_NONFINITE = 4,     /* a non-finite force or velocity */
+  ADRESS_ERR_BOND_BROKEN = 5,   /* a FENE bond reached its maximum extension */
+  ADRESS_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+  ADRESS_ERR_STATE = 7,         /* call out of order (e.g. no state bound) */
+  ADRESS_ERR_EXTENT = 8         /* a molecule is wider than the list cutoff allows */
+} adress_status;
+
+typedef enum {
+  ADRESS_FP64 = 0,      /* every step in double precision */
+  ADRESS_FP32_MIXED = 1 /* pair, bonded and thermodynamic forces in float; positions,
+                           velocities, energies, virial and density profile in double */
+} adress_precision;
+
+/* System description.  Host arrays are copied by adress_init. */
+typedef struct {
+  int32_t n_mols;        /* M molecules (>= 2) */
+  int32_t atoms_per_mol; /* na, 1..4, identical topology for every molecule */
+  const double* mass;    /* host [na] per-site masses (> 0) */
+  double box[3];         /* periodic box edges L */
+  /* resolution function l(d) of d = |x_com - x_center| (minimum image along x):
+   * 1 for d < d_at_half, cos^2(pi/2 (d - d_at_half)/d_hy) for d < d_at_half + d_hy,
+   * 0 beyond (Sec. "Force interpolation"; squared cosine named in Sec. "Potential
+   * energy interpolation") */
+  double x_center, d_at_half, d_hy;
+  /* atomistic model: WCA between atoms of different molecules,
+   * V = 4 eps[(s/r)^12 - (s/r)^6] + eps for r < rc_at */
+  double wca_eps, wca_sigma, rc_at;
+  /* bonded model (never interpolated): FENE V = -K R0^2/2 ln(1 - r^2/R0^2) on the
+   * listed intramolecular pairs, plus WCA on the same pairs when intra_wca != 0 */
+  int32_t n_bonds;
+  const int32_t* bonds; /* host [2*n_bonds] local atom indices */
+  double fene_k, fene_r0;
+  int32_t intra_wca;
+  /* CG model: COM-COM force F(r) (positive = repulsive) and energy V(r) tabulated on
+   * r_k = k*cg_dr, k = 0..cg_n, linear interpolation, zero for r >= rc_cg */
+  const double* cg_F; /* host [cg_n+1] */
+  const double* cg_V; /* host [cg_n+1] */
+  int32_t cg_n;
+  double cg_dr, rc_cg;
+  /* thermodynamic force F_th(d), nodes d_k = k*tf_dx, linear interpolation; it acts
+   * along x (away from the centre when positive) on molecules with
+   * d_at_half <= d < d_at_half + d_hy, spread over atoms by mass fraction */
+  const double* tf; /* host [tf_n], may be NULL when tf_n == 0 */
+  int32_t tf_n;
+  double tf_dx;
+  /* Langevin thermostat in velocity Verlet: F_L = -gamma m v + sqrt(24 gamma kT m/dt)(u-1/2),
+   * u from Philox4x64-10 with key (seed, time level) and counter (atom, replica, 0, 0) */
+  double kT, gamma, dt;
+  uint64_t seed;
+  int64_t replica;
+  /* neighbour lists over molecule centres: cutoff max(rc_cg, rc_at + 2 r_ext) + skin */
+  double skin, r_ext;
+  int32_t max_neighbors; /* initial list capacity per molecule; 0 = automatic */
+  int32_t precision;     /* adress_precision */
+} adress_config;
+
+/* Validate `cfg`, copy its tables, allocate the handle's device buffers on the current
+ * device and bind `stream` (a cudaStream_t; NULL = legacy default stream).
+ * On failure *out is NULL and the status says why. */
+adress_status adress_init(const adress_config* cfg, void* stream, adress_handle* out);
+
+/* Borrow the caller's device state: x, v double [3][N]; f [3][N] of double
+ * (ADRESS_FP64) or float (ADRESS_FP32_MIXED).  Pointers must stay valid until the next
+ * bind or adress_destroy.  Rebinding invalidates captured step graphs. */
+adress_status adress_bind_state(adress_handle h, double* x, double* v, void* f);
+
+/* Map the bound positions to centres of mass and resolution values, then rebuild the
+ * Morton-ordered cell list, the class work lists (high-resolution candidates first,
+ * then coarse-grained molecules) and the Verlet lists.  Synchronises: grows the list
+ * capacity and rebuilds when a molecule has more neighbours than it holds. */
+adress_status adress_build_lists(adress_handle h);
+
+/* Conservative forces of the bound positions (Eq. 1 + bonded + thermodynamic force,
+ * no thermostat) into f, with a fresh list build.  If energies != NULL (host, 4
+ * doubles) synchronises and writes {E_AT, E_CG, E_bond, virial}: E_AT = sum over
+ * molecule pairs of l_a l_b V^AT, E_CG = sum of (1 - l_a l_b) V^CG, virial = sum r.f over
+ * pair and bond terms. */
+adress_status adress_compute_forces(adress_handle h, double* energies);
+
+/* Advance the bound state (x, v, f at time level n) by nsteps Langevin velocity-Verlet
+ * steps:  v += dt/2 f/m;  x += dt v (wrapped);  f = F(x) + F_L(v; n+1);  v += dt/2 f/m.
+ * Lists are rebuilt on the device when a molecule centre moved more than skin/2 or a
+ * molecule grew wider than the list allows.  Runs as replays of a captured CUDA graph
+ * whose rebuild is a conditional node.  Asynchronous; errors surface at adress_check. */
+adress_status adress_step(adress_handle h, int32_t nsteps);
+
+/* Time level of the bound state (keys the thermostat noise). */
+adress_status adress_set_step(adress_handle h, int64_t step);
+adress_status adress_get_step(adress_handle h, int64_t* step); /* synchronises */
+
+/* Centres of mass and resolution values of the bound positions: com device double [3][M]
+ * (wrapped into the box), w device double [M].  Asynchronous. */
+adress_status adress_com_lambda(adress_handle h, double* com, double* w);
+
+/* Kinetic energy and momentum of the bound velocities: out host [4] = {KE, Px, Py, Pz}.
+ * Synchronises. */
+adress_status adress_kinetic(adress_handle h, double* out);
+
+/* Add the COM histogram of the bound positions, folded about the slab centre, bins of
+ * width tf_dx over d = |x_com - x_center| (Sec. "Free energy corrections and the
+ * thermodynamic force": the density profile the thermodynamic force is built from).
+ * Asynchronous. */
+adress_status adress_density_accumulate(adress_handle h);
+/* Copy the accumulated counts (host int64 [n], n <= tf_n) and the sample count.
+ * Synchronises. */
+adress_status adress_density_get(adress_handle h, int64_t* counts, int32_t n, int64_t* nsamples);
+adress_status adress_density_reset(adress_handle h);
+
+/* One thermodynamic-force iteration from the accumulated profile, on the device:
+ * rho_k = counts_k / (nsamples 2 tf_dx Ly Lz), g_k = (rho_k - rho_{k-1})/tf_dx (g_0 = 0),
+ * three-point moving average, tf_k -= alpha * g_k on nodes with
+ * d_at_half <= k tf_dx <= d_at_half + d_hy; then resets the histogram.  Asynchronous. */
+adress_status adress_tf_update(adress_handle h, double alpha);
+adress_status adress_set_tf(adress_handle h, const double* tf_host, int32_t n);
+adress_status adress_get_tf(adress_handle h, double* tf_host, int32_t n); /* synchronises */
+
+/* List statistics (host int64 [8]): {n_high_resolution_items, n_cg_items, rebuilds,
+ * max_neighbours_at_last_build, capacity, n_cells, 0, 0}.  Synchronises. */
+adress_status adress_list_stats(adress_handle h, int64_t* out);
+
+/* Kernel timing for roofline accounting: runs `reps` steps as separate launches
+ * (integrate+COM, rebuild decision, forced list rebuild, forces+thermostat+kick) on the
+ * handle's stream with CUDA events around each kernel, advancing the state by `reps`
+ * steps exactly as adress_step does (with a rebuild every step).  ms_out host [3] =
+ * average milliseconds per launch of {integrate+COM, list rebuild, forces}.
+ * Synchronises. */
+adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out);
+
+/* Synchronise the stream and return (then clear) the first device-side error. */
+adress_status adress_check(adress_handle h);
+
+/* Message for the last failing call on h (or for init failures when h == NULL). */
+const char* adress_last_error(adress_handle h);
+const char* adress_status_string(adress_status s);
+
+/* Free everything the handle owns.  Synchronises its stream first. */
+void adress_destroy(adress_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADRESS_H */

@@ -96,7 +96,9 @@ def _ptr(a, ct=C.c_double):
 class Oracle:
     """Holds one system description and exposes the oracle's functions on numpy arrays.
 
-    `system` is any object with the fields of ``paper_1806_10841_gb300.inputs.System``.
+    `system` is any object with the fields M, na, box, mass, bonds, xc, d_at, d_hy, eps,
+    sigma, rc_at, fene_k, fene_r0, intra_wca, cg_F, cg_V, cg_dr, rc_cg, tf, tf_dx, kT,
+    gamma, dt and seed (the seeded input generator's system description).
     """
 
     def __init__(self, system, *, replica: int = 0, lib_path: str | None = None):

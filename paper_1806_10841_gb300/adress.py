@@ -1,0 +1,270 @@
+"""Python binding of the C ABI in ``include/adress.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_build/libadress_gb300.so``; this
+module only fills the configuration struct, owns the state tensors (PyTorch device
+memory) and forwards calls.  There is no CPU fallback: a missing library is an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libadress_gb300.so")
+
+ADRESS_FP64, ADRESS_FP32_MIXED = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "neighbour list overflow",
+          4: "non-finite force", 5: "FENE bond broken", 6: "device wait timed out",
+          7: "invalid state", 8: "molecule wider than the list cutoff allows"}
+
+# Every symbol include/adress.h declares (checked by the CPU test suite).
+EXPORTS = ["adress_init", "adress_bind_state", "adress_build_lists", "adress_compute_forces",
+           "adress_step", "adress_set_step", "adress_get_step", "adress_com_lambda", "adress_kinetic",
+           "adress_density_accumulate", "adress_density_get", "adress_density_reset",
+           "adress_tf_update", "adress_set_tf", "adress_get_tf", "adress_list_stats", "adress_time_kernels",
+           "adress_check",
+           "adress_last_error", "adress_status_string", "adress_destroy"]
+
+
+class AdressError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class adress_config(C.Structure):
+    _fields_ = [
+        ("n_mols", C.c_int32), ("atoms_per_mol", C.c_int32),
+        ("mass", C.POINTER(C.c_double)),
+        ("box", C.c_double * 3),
+        ("x_center", C.c_double), ("d_at_half", C.c_double), ("d_hy", C.c_double),
+        ("wca_eps", C.c_double), ("wca_sigma", C.c_double), ("rc_at", C.c_double),
+        ("n_bonds", C.c_int32), ("bonds", C.POINTER(C.c_int32)),
+        ("fene_k", C.c_double), ("fene_r0", C.c_double),
+        ("intra_wca", C.c_int32),
+        ("cg_F", C.POINTER(C.c_double)), ("cg_V", C.POINTER(C.c_double)),
+        ("cg_n", C.c_int32), ("cg_dr", C.c_double), ("rc_cg", C.c_double),
+        ("tf", C.POINTER(C.c_double)), ("tf_n", C.c_int32), ("tf_dx", C.c_double),
+        ("kT", C.c_double), ("gamma", C.c_double), ("dt", C.c_double),
+        ("seed", C.c_uint64), ("replica", C.c_int64),
+        ("skin", C.c_double), ("r_ext", C.c_double),
+        ("max_neighbors", C.c_int32), ("precision", C.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    H, vp, d = C.c_void_p, C.c_void_p, C.POINTER(C.c_double)
+    i64p = C.POINTER(C.c_int64)
+    sig = {
+        "adress_init": ([C.POINTER(adress_config), vp, C.POINTER(H)], C.c_int),
+        "adress_bind_state": ([H, vp, vp, vp], C.c_int),
+        "adress_build_lists": ([H], C.c_int),
+        "adress_compute_forces": ([H, d], C.c_int),
+        "adress_step": ([H, C.c_int32], C.c_int),
+        "adress_set_step": ([H, C.c_int64], C.c_int),
+        "adress_get_step": ([H, i64p], C.c_int),
+        "adress_com_lambda": ([H, vp, vp], C.c_int),
+        "adress_kinetic": ([H, d], C.c_int),
+        "adress_density_accumulate": ([H], C.c_int),
+        "adress_density_get": ([H, i64p, C.c_int32, i64p], C.c_int),
+        "adress_density_reset": ([H], C.c_int),
+        "adress_tf_update": ([H, C.c_double], C.c_int),
+        "adress_set_tf": ([H, d, C.c_int32], C.c_int),
+        "adress_get_tf": ([H, d, C.c_int32], C.c_int),
+        "adress_list_stats": ([H, i64p], C.c_int),
+        "adress_time_kernels": ([H, C.c_int32, C.POINTER(C.c_float)], C.c_int),
+        "adress_check": ([H], C.c_int),
+        "adress_last_error": ([H], C.c_char_p),
+        "adress_status_string": ([C.c_int], C.c_char_p),
+        "adress_destroy": ([H], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class AdResS:
+    """One AdResS system on one GPU.
+
+    State tensors live on the device in structure-of-arrays layout ``[3, N]``:
+    ``x``, ``v`` float64 and ``f`` float64 (``precision='fp64'``) or float32
+    (``precision='fp32'``, the mixed path).
+    """
+
+    def __init__(self, system, *, precision: str = "fp32", device: str = "cuda:0", stream=None,
+                 max_neighbors: int = 0, replica: int = 0):
+        import torch
+
+        self.torch = torch
+        self.lib = load_library()
+        self.system = system
+        self.precision = precision
+        self.device = torch.device(device)
+        s = system
+        self.M, self.na = int(s.M), int(s.na)
+        self.N = self.M * self.na
+        self._keep = dict(
+            mass=np.ascontiguousarray(s.mass, dtype=np.float64),
+            bonds=np.ascontiguousarray(np.asarray(s.bonds, dtype=np.int32).reshape(-1)),
+            cgF=np.ascontiguousarray(s.cg_F, dtype=np.float64),
+            cgV=np.ascontiguousarray(s.cg_V, dtype=np.float64),
+            tf=np.ascontiguousarray(s.tf if s.tf is not None else np.zeros(0), dtype=np.float64),
+        )
+        k = self._keep
+        self.tf_n = len(k["tf"])
+        cfg = adress_config(
+            n_mols=self.M, atoms_per_mol=self.na, mass=_dptr(k["mass"]), box=(C.c_double * 3)(*s.box),
+            x_center=s.xc, d_at_half=s.d_at, d_hy=s.d_hy, wca_eps=s.eps, wca_sigma=s.sigma,
+            rc_at=s.rc_at, n_bonds=len(k["bonds"]) // 2,
+            bonds=k["bonds"].ctypes.data_as(C.POINTER(C.c_int32)), fene_k=s.fene_k,
+            fene_r0=s.fene_r0, intra_wca=int(s.intra_wca), cg_F=_dptr(k["cgF"]), cg_V=_dptr(k["cgV"]),
+            cg_n=len(k["cgF"]) - 1, cg_dr=s.cg_dr, rc_cg=s.rc_cg,
+            tf=_dptr(k["tf"]) if self.tf_n else None, tf_n=self.tf_n, tf_dx=s.tf_dx,
+            kT=s.kT, gamma=s.gamma, dt=s.dt, seed=int(s.seed), replica=int(replica), skin=s.skin,
+            r_ext=s.r_ext, max_neighbors=int(max_neighbors),
+            precision=ADRESS_FP64 if precision == "fp64" else ADRESS_FP32_MIXED)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.h = C.c_void_p()
+            st = self.lib.adress_init(C.byref(cfg), C.c_void_p(self.stream.cuda_stream), C.byref(self.h))
+            if st != 0:
+                raise AdressError(st, self.lib.adress_last_error(None).decode())
+            fdt = torch.float64 if precision == "fp64" else torch.float32
+            self.x = torch.zeros((3, self.N), dtype=torch.float64, device=self.device)
+            self.v = torch.zeros((3, self.N), dtype=torch.float64, device=self.device)
+            self.f = torch.zeros((3, self.N), dtype=fdt, device=self.device)
+            self._call("adress_bind_state", C.c_void_p(self.x.data_ptr()), C.c_void_p(self.v.data_ptr()),
+                       C.c_void_p(self.f.data_ptr()))
+
+    # -- plumbing -------------------------------------------------------------------
+    def _call(self, name, *args):
+        st = getattr(self.lib, name)(self.h, *args)
+        if st != 0:
+            raise AdressError(st, self.lib.adress_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.adress_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state ------------------------------------------------------------------------
+    def set_state(self, x, v=None, f=None):
+        """x, v, f: (N, 3) numpy arrays (host) or [3, N] tensors."""
+        t = self.torch
+        for dst, src in ((self.x, x), (self.v, v), (self.f, f)):
+            if src is None:
+                continue
+            if isinstance(src, np.ndarray):
+                src = t.from_numpy(np.ascontiguousarray(np.asarray(src).T))
+            with t.cuda.stream(self.stream):
+                dst.copy_(src.to(dst.dtype), non_blocking=False)
+        self.stream.synchronize()
+
+    def get_state(self):
+        self.stream.synchronize()
+        return (self.x.T.cpu().numpy().copy(), self.v.T.cpu().numpy().copy(),
+                self.f.T.to(self.torch.float64).cpu().numpy().copy())
+
+    # -- C ABI calls --------------------------------------------------------------------
+    def build_lists(self):
+        self._call("adress_build_lists")
+
+    def compute_forces(self, energies: bool = True):
+        e = np.zeros(4)
+        self._call("adress_compute_forces", _dptr(e) if energies else None)
+        return dict(E_at=e[0], E_cg=e[1], E_bond=e[2], virial=e[3]) if energies else None
+
+    def forces(self):
+        """Conservative forces (N, 3) float64 on the host plus energies."""
+        e = self.compute_forces(True)
+        self.stream.synchronize()
+        return self.f.T.to(self.torch.float64).cpu().numpy().copy(), e
+
+    def step(self, nsteps: int):
+        self._call("adress_step", C.c_int32(int(nsteps)))
+
+    def set_step(self, step: int):
+        self._call("adress_set_step", C.c_int64(int(step)))
+
+    def get_step(self) -> int:
+        v = C.c_int64()
+        self._call("adress_get_step", C.byref(v))
+        return v.value
+
+    def com_lambda(self):
+        t = self.torch
+        com = t.empty((3, self.M), dtype=t.float64, device=self.device)
+        w = t.empty((self.M,), dtype=t.float64, device=self.device)
+        self._call("adress_com_lambda", C.c_void_p(com.data_ptr()), C.c_void_p(w.data_ptr()))
+        self.stream.synchronize()
+        return com.T.cpu().numpy().copy(), w.cpu().numpy().copy()
+
+    def kinetic(self):
+        out = np.zeros(4)
+        self._call("adress_kinetic", _dptr(out))
+        return out[0], out[1:].copy()
+
+    def density_accumulate(self):
+        self._call("adress_density_accumulate")
+
+    def density_get(self):
+        counts = np.zeros(self.tf_n, dtype=np.int64)
+        ns = C.c_int64()
+        self._call("adress_density_get", counts.ctypes.data_as(C.POINTER(C.c_int64)), self.tf_n, C.byref(ns))
+        return counts, ns.value
+
+    def density_reset(self):
+        self._call("adress_density_reset")
+
+    def tf_update(self, alpha: float):
+        self._call("adress_tf_update", C.c_double(alpha))
+
+    def set_tf(self, tf):
+        tf = np.ascontiguousarray(tf, dtype=np.float64)
+        self._call("adress_set_tf", _dptr(tf), len(tf))
+
+    def get_tf(self):
+        tf = np.zeros(self.tf_n)
+        self._call("adress_get_tf", _dptr(tf), self.tf_n)
+        return tf
+
+    def list_stats(self):
+        out = np.zeros(8, dtype=np.int64)
+        self._call("adress_list_stats", out.ctypes.data_as(C.POINTER(C.c_int64)))
+        keys = ["n_hr", "n_cg", "rebuilds", "max_nn", "capacity", "n_cells"]
+        return {k: int(out[i]) for i, k in enumerate(keys)}
+
+    def time_kernels(self, reps: int = 20):
+        """Average ms per launch of (integrate+COM, list rebuild, forces); advances the state."""
+        out = (C.c_float * 3)()
+        self._call("adress_time_kernels", C.c_int32(int(reps)), out)
+        return dict(integrate_com=out[0], rebuild=out[1], forces=out[2])
+
+    def check(self):
+        self._call("adress_check")

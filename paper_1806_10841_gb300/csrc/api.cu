@@ -1,0 +1,646 @@
+// Host side of the C ABI declared in include/adress.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace adress;
+
+struct adress_ctx {
+  Sys sys{};
+  Bufs buf{};
+  int precision = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+  int device = 0;
+  std::string err;
+  bool bound = false;
+  bool lists_built = false;
+  std::vector<void*> allocs;
+  int nparts = 0;
+  // captured step graphs: one with kGraphSteps steps, one with a single step
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  int64_t rebuild_host = 0;
+};
+
+static thread_local std::string g_init_error;
+static constexpr int kGraphSteps = 10;
+
+static adress_status fail(adress_ctx* h, adress_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_init_error = msg;
+  return s;
+}
+
+#define CUDA_OR_FAIL(h, call)                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail((h), ADRESS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+template <class T>
+static cudaError_t dalloc(adress_ctx* h, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  *p = (T*)q;
+  return cudaSuccess;
+}
+
+static void free_graphs(adress_ctx* h) {
+  for (int k = 0; k < 2; ++k) {
+    if (h->exec[k]) cudaGraphExecDestroy(h->exec[k]);
+    if (h->graph[k]) cudaGraphDestroy(h->graph[k]);
+    h->exec[k] = nullptr;
+    h->graph[k] = nullptr;
+  }
+}
+
+static uint64_t morton3(uint64_t x, uint64_t y, uint64_t z) {
+  uint64_t c = 0;
+  for (int bit = 0; bit < 21; ++bit) {
+    c |= ((x >> bit) & 1ull) << (3 * bit + 2);
+    c |= ((y >> bit) & 1ull) << (3 * bit + 1);
+    c |= ((z >> bit) & 1ull) << (3 * bit);
+  }
+  return c;
+}
+
+static int auto_capacity(const Sys& s) {
+  const double vol = s.L[0] * s.L[1] * s.L[2];
+  const double expect = 4.0 / 3.0 * M_PI * s.r_list * s.r_list * s.r_list * s.M / vol;
+  int cap = (int)ceil(2.0 * expect + 16.0);
+  cap = (cap + 3) & ~3;
+  return std::min(cap, std::max(4, s.M - 1));
+}
+
+extern "C" {
+
+const char* adress_status_string(adress_status s) {
+  switch (s) {
+    case ADRESS_OK: return "ok";
+    case ADRESS_ERR_ARG: return "invalid argument";
+    case ADRESS_ERR_CUDA: return "CUDA error";
+    case ADRESS_ERR_LIST_OVERFLOW: return "neighbour list overflow";
+    case ADRESS_ERR_NONFINITE: return "non-finite force";
+    case ADRESS_ERR_BOND_BROKEN: return "FENE bond broken";
+    case ADRESS_ERR_TIMEOUT: return "device wait timed out";
+    case ADRESS_ERR_STATE: return "invalid state";
+    case ADRESS_ERR_EXTENT: return "molecule wider than the list cutoff allows";
+  }
+  return "unknown status";
+}
+
+const char* adress_last_error(adress_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+adress_status adress_init(const adress_config* c, void* stream, adress_handle* out) {
+  if (!out) return fail(nullptr, ADRESS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!c) return fail(nullptr, ADRESS_ERR_ARG, "config is NULL");
+  if (c->n_mols < 2) return fail(nullptr, ADRESS_ERR_ARG, "n_mols must be >= 2");
+  if (c->atoms_per_mol < 1 || c->atoms_per_mol > kMaxNA)
+    return fail(nullptr, ADRESS_ERR_ARG, "atoms_per_mol must be in 1..4");
+  if ((long long)c->n_mols * c->atoms_per_mol > (1ll << 30))
+    return fail(nullptr, ADRESS_ERR_ARG, "too many atoms");
+  if (!c->mass) return fail(nullptr, ADRESS_ERR_ARG, "mass is NULL");
+  for (int k = 0; k < c->atoms_per_mol; ++k)
+    if (!(c->mass[k] > 0)) return fail(nullptr, ADRESS_ERR_ARG, "masses must be > 0");
+  for (int d = 0; d < 3; ++d)
+    if (!(c->box[d] > 0)) return fail(nullptr, ADRESS_ERR_ARG, "box edges must be > 0");
+  if (c->n_bonds < 0 || c->n_bonds > kMaxBonds || (c->n_bonds > 0 && !c->bonds))
+    return fail(nullptr, ADRESS_ERR_ARG, "n_bonds must be 0..6 with a bond array");
+  for (int q = 0; q < 2 * c->n_bonds; ++q)
+    if (c->bonds[q] < 0 || c->bonds[q] >= c->atoms_per_mol)
+      return fail(nullptr, ADRESS_ERR_ARG, "bond index out of range");
+  if (c->n_bonds > 0 && !(c->fene_r0 > 0)) return fail(nullptr, ADRESS_ERR_ARG, "fene_r0 must be > 0");
+  if (!c->cg_F || !c->cg_V || c->cg_n < 1 || !(c->cg_dr > 0))
+    return fail(nullptr, ADRESS_ERR_ARG, "CG table missing");
+  if (c->rc_cg > c->cg_n * c->cg_dr * (1 + 1e-12))
+    return fail(nullptr, ADRESS_ERR_ARG, "rc_cg beyond the CG table");
+  if (c->tf_n < 0 || (c->tf_n > 0 && (!c->tf || !(c->tf_dx > 0))))
+    return fail(nullptr, ADRESS_ERR_ARG, "thermodynamic-force table invalid");
+  if (!(c->d_at_half >= 0) || !(c->d_hy >= 0)) return fail(nullptr, ADRESS_ERR_ARG, "slab widths must be >= 0");
+  if (!(c->dt > 0) || c->gamma < 0 || c->kT < 0) return fail(nullptr, ADRESS_ERR_ARG, "dt, gamma, kT invalid");
+  if (c->precision != ADRESS_FP64 && c->precision != ADRESS_FP32_MIXED)
+    return fail(nullptr, ADRESS_ERR_ARG, "unknown precision");
+  if (!(c->skin >= 0) || !(c->r_ext >= 0) || !(c->rc_at > 0) || !(c->rc_cg > 0))
+    return fail(nullptr, ADRESS_ERR_ARG, "cutoffs invalid");
+
+  adress_ctx* h = new adress_ctx();
+  h->precision = c->precision;
+  h->stream = (cudaStream_t)stream;
+  cudaGetDevice(&h->device);
+  Sys& s = h->sys;
+  s.M = c->n_mols;
+  s.NA = c->atoms_per_mol;
+  s.N = s.M * s.NA;
+  double Mtot = 0;
+  for (int k = 0; k < s.NA; ++k) Mtot += c->mass[k];
+  s.Mtot = Mtot;
+  for (int k = 0; k < kMaxNA; ++k) {
+    double m = k < s.NA ? c->mass[k] : 1.0;
+    s.mass[k] = m;
+    s.inv_mass[k] = 1.0 / m;
+    s.frac[k] = k < s.NA ? m / Mtot : 0.0;
+  }
+  for (int d = 0; d < 3; ++d) {
+    s.L[d] = c->box[d];
+    s.halfL[d] = 0.5 * c->box[d];
+    s.fx_inv[d] = 4294967296.0 / c->box[d];
+    s.fx_scale[d] = (float)(c->box[d] / 4294967296.0);
+    s.Lf[d] = (float)c->box[d];
+  }
+  s.xc = c->x_center;
+  s.d_at = c->d_at_half;
+  s.d_hy = c->d_hy;
+  s.d_hr = c->d_at_half + c->d_hy + 0.5 * c->skin;
+  s.pi_half_over_dhy = c->d_hy > 0 ? 0.5 * M_PI / c->d_hy : 0.0;
+  s.eps = c->wca_eps;
+  s.sig2 = c->wca_sigma * c->wca_sigma;
+  s.rc_at = c->rc_at;
+  s.rc_at2 = c->rc_at * c->rc_at;
+  s.nb = c->n_bonds;
+  for (int q = 0; q < 2 * kMaxBonds; ++q) s.bonds[q] = q < 2 * c->n_bonds ? c->bonds[q] : 0;
+  s.fene_k = c->fene_k;
+  s.fene_r02 = c->fene_r0 * c->fene_r0;
+  s.intra_wca = c->intra_wca;
+  s.cg_n = c->cg_n;
+  s.cg_inv_dr = 1.0 / c->cg_dr;
+  s.rc_cg = c->rc_cg;
+  s.rc_cg2 = c->rc_cg * c->rc_cg;
+  s.tf_n = c->tf_n;
+  s.tf_dx = c->tf_n > 0 ? c->tf_dx : 1.0;
+  s.tf_inv_dx = 1.0 / s.tf_dx;
+  s.kT = c->kT;
+  s.gamma = c->gamma;
+  s.dt = c->dt;
+  s.seed = c->seed;
+  s.replica = c->replica;
+  s.skin = c->skin;
+  s.r_ext = c->r_ext;
+  s.r_list = std::max(c->rc_cg, c->rc_at + 2.0 * c->r_ext) + c->skin;
+  s.r_list2 = s.r_list * s.r_list;
+  s.reach_at2 = (c->rc_at + 2.0 * c->r_ext) * (c->rc_at + 2.0 * c->r_ext);
+  for (int d = 0; d < 3; ++d) {
+    if (c->box[d] < 2.0 * s.r_list) {
+      delete h;
+      return fail(nullptr, ADRESS_ERR_ARG, "box edge shorter than twice the list cutoff");
+    }
+    s.nc[d] = std::max(1, (int)floor(c->box[d] / s.r_list));
+  }
+  if ((long long)s.nc[0] * s.nc[1] * s.nc[2] > 4096ll * 2048ll || s.M > 4096 * 2048 - 1) {
+    delete h;
+    return fail(nullptr, ADRESS_ERR_ARG, "too many cells or molecules for the device scans (max 8388607)");
+  }
+  if (c->tf_n > 4096) {
+    delete h;
+    return fail(nullptr, ADRESS_ERR_ARG, "tf_n must be <= 4096");
+  }
+  s.ncell = s.nc[0] * s.nc[1] * s.nc[2];
+  s.cap = c->max_neighbors > 0 ? std::min(c->max_neighbors, s.M - 1) : auto_capacity(s);
+
+  // ---- device buffers ----
+  Bufs& b = h->buf;
+  const int M = s.M, N = s.N;
+  h->nparts = std::max(force_warps(s), ceil_div(N, 256));
+  cudaError_t e = cudaSuccess;
+#define A(ptr, n)                                  \
+  do {                                             \
+    if (e == cudaSuccess) e = dalloc(h, &(ptr), (n)); \
+  } while (0)
+  A(b.com_fx, M);
+  A(b.com_ref, M);
+  A(b.com64, M);
+  A(b.dxc64, M);
+  A(b.molf, M);
+  if (h->precision == ADRESS_FP64) {
+    A(b.off64, N);
+  } else {
+    A(b.off32, N);
+  }
+  A(b.mcell, M);
+  A(b.cell_count, s.ncell);
+  A(b.cell_fill, s.ncell);
+  A(b.cell_start, s.ncell + 1);
+  A(b.sorted, M);
+  A(b.flag, M);
+  A(b.pos, M + 1);
+  A(b.items, M);
+  A(b.nn, M);
+  A(b.nbr, (size_t)s.cap * M);
+  A(b.scan_tmp, 4096);
+  int* cell_rank = nullptr;
+  int* rank_cell = nullptr;
+  A(cell_rank, s.ncell);
+  A(rank_cell, s.ncell);
+  b.cell_rank = cell_rank;
+  b.rank_cell = rank_cell;
+  double* cgF = nullptr;
+  double* cgV = nullptr;
+  float2* cgFV = nullptr;
+  A(cgF, s.cg_n + 1);
+  A(cgV, s.cg_n + 1);
+  A(cgFV, s.cg_n + 1);
+  b.cgF64 = cgF;
+  b.cgV64 = cgV;
+  b.cgFV32 = cgFV;
+  A(b.tf64, std::max(1, s.tf_n));
+  A(b.tf32, std::max(1, s.tf_n));
+  A(b.part, (size_t)h->nparts * 4);
+  A(b.result, 8);
+  A(b.hist, std::max(1, s.tf_n));
+  A(b.nsamples, 1);
+  A(b.ctrl, 1);
+#undef A
+  if (e != cudaSuccess) {
+    adress_destroy(h);
+    return fail(nullptr, ADRESS_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+
+  // ---- Morton ranks of cells ----
+  std::vector<std::pair<uint64_t, int>> codes(s.ncell);
+  for (int x = 0; x < s.nc[0]; ++x)
+    for (int y = 0; y < s.nc[1]; ++y)
+      for (int z = 0; z < s.nc[2]; ++z) {
+        int lin = (x * s.nc[1] + y) * s.nc[2] + z;
+        codes[lin] = {morton3(x, y, z), lin};
+      }
+  std::sort(codes.begin(), codes.end());
+  std::vector<int> rank(s.ncell), rcell(s.ncell);
+  for (int r = 0; r < s.ncell; ++r) {
+    rank[codes[r].second] = r;
+    rcell[r] = codes[r].second;
+  }
+  std::vector<float2> fv(s.cg_n + 1);
+  for (int k = 0; k <= s.cg_n; ++k) fv[k] = make_float2((float)c->cg_F[k], (float)c->cg_V[k]);
+  std::vector<double> tf(std::max(1, s.tf_n), 0.0);
+  std::vector<float> tff(std::max(1, s.tf_n), 0.f);
+  for (int k = 0; k < s.tf_n; ++k) {
+    tf[k] = c->tf[k];
+    tff[k] = (float)c->tf[k];
+  }
+  cudaStream_t st = h->stream;
+#define H2D(dst, src, bytes)                                                                  \
+  do {                                                                                        \
+    if (e == cudaSuccess) e = cudaMemcpyAsync((void*)(dst), (src), (bytes), cudaMemcpyHostToDevice, st); \
+  } while (0)
+  H2D(cell_rank, rank.data(), sizeof(int) * s.ncell);
+  H2D(rank_cell, rcell.data(), sizeof(int) * s.ncell);
+  H2D(cgF, c->cg_F, sizeof(double) * (s.cg_n + 1));
+  H2D(cgV, c->cg_V, sizeof(double) * (s.cg_n + 1));
+  H2D(cgFV, fv.data(), sizeof(float2) * (s.cg_n + 1));
+  H2D(b.tf64, tf.data(), sizeof(double) * tf.size());
+  H2D(b.tf32, tff.data(), sizeof(float) * tff.size());
+#undef H2D
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.hist, 0, sizeof(unsigned long long) * std::max(1, s.tf_n), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.nsamples, 0, sizeof(long long), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.com_ref, 0, sizeof(int4) * M, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("init upload: ") + cudaGetErrorString(e);
+    adress_destroy(h);
+    return fail(nullptr, ADRESS_ERR_CUDA, msg);
+  }
+  *out = h;
+  return ADRESS_OK;
+}
+
+adress_status adress_bind_state(adress_handle h, double* x, double* v, void* f) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (!x || !v || !f) return fail(h, ADRESS_ERR_ARG, "state pointers must be non-NULL");
+  h->buf.x = x;
+  h->buf.v = v;
+  h->buf.f = f;
+  h->bound = true;
+  h->lists_built = false;
+  free_graphs(h);
+  return ADRESS_OK;
+}
+
+static adress_status read_ctrl(adress_handle h, Ctrl* c) {
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(c, h->buf.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
+// Map positions, rebuild lists; grow the capacity and redo while a list overflows.
+static adress_status build_lists_sync(adress_handle h) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream));
+    CUDA_OR_FAIL(h, launch_decide(h->sys, h->buf, 1, 0, 0, 0, h->stream));
+    CUDA_OR_FAIL(h, launch_rebuild(h->sys, h->buf, h->stream));
+    Ctrl c;
+    adress_status st = read_ctrl(h, &c);
+    if (st != ADRESS_OK) return st;
+    if (c.err == ADRESS_ERR_LIST_OVERFLOW || c.max_nn > h->sys.cap) {
+      int cap = ((int)ceil(c.max_nn * 1.5) + 8 + 3) & ~3;
+      cap = std::min(cap, h->sys.M - 1);
+      void* old = h->buf.nbr;
+      int* nbr = nullptr;
+      CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+      CUDA_OR_FAIL(h, dalloc(h, &nbr, (size_t)cap * h->sys.M));
+      h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), old));
+      cudaFree(old);
+      h->buf.nbr = nbr;
+      h->sys.cap = cap;
+      free_graphs(h);
+      int zero = 0;
+      CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->buf.ctrl->err, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      continue;
+    }
+    if (c.err != 0) return fail(h, (adress_status)c.err, std::string("list build: ") +
+                                                          adress_status_string((adress_status)c.err));
+    h->lists_built = true;
+    return ADRESS_OK;
+  }
+  return fail(h, ADRESS_ERR_LIST_OVERFLOW, "neighbour list capacity could not be grown enough");
+}
+
+adress_status adress_build_lists(adress_handle h) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
+  return build_lists_sync(h);
+}
+
+adress_status adress_compute_forces(adress_handle h, double* energies) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
+  adress_status st = build_lists_sync(h);
+  if (st != ADRESS_OK) return st;
+  CUDA_OR_FAIL(h, launch_forces(h->sys, h->buf, h->precision, 0, energies != nullptr, h->stream));
+  if (energies) {
+    CUDA_OR_FAIL(h, launch_energy_reduce(h->sys, h->buf, force_warps(h->sys), 4, h->stream));
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(energies, h->buf.result, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  }
+  return ADRESS_OK;
+}
+
+// Capture `nsteps` steps into a graph: per step  [integrate+COM] -> [decide: sets the
+// conditional] -> IF(rebuild){lists} -> [forces + thermostat + second half kick].
+static adress_status capture_steps(adress_handle h, int nsteps, cudaGraph_t* gout, cudaGraphExec_t* xout) {
+  cudaGraph_t g = nullptr;
+  CUDA_OR_FAIL(h, cudaGraphCreate(&g, 0));
+  std::vector<cudaGraphNode_t> deps;
+  cudaStream_t cs = h->cap_stream;
+  auto grab = [&](std::vector<cudaGraphNode_t>& into) -> cudaError_t {
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &d, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    into.assign(d, d + nd);
+    return cudaSuccess;
+  };
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, g, 0, 0);
+    if (e != cudaSuccess) break;
+    e = cudaStreamBeginCaptureToGraph(cs, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    cudaError_t le = launch_com(h->sys, h->buf, h->precision, 1, cs);
+    if (le == cudaSuccess) le = launch_decide(h->sys, h->buf, 0, 1, cond, 1, cs);
+    std::vector<cudaGraphNode_t> tail;
+    cudaError_t ge = grab(tail);
+    cudaGraph_t gg = g;
+    e = cudaStreamEndCapture(cs, &gg);
+    if (e == cudaSuccess) e = le;
+    if (e == cudaSuccess) e = ge;
+    if (e != cudaSuccess) break;
+
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode;
+    e = cudaGraphAddNode(&cnode, g, tail.data(), nullptr, tail.size(), &cp);
+    if (e != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    le = launch_rebuild(h->sys, h->buf, cs);
+    cudaGraph_t bb = body;
+    e = cudaStreamEndCapture(cs, &bb);
+    if (e == cudaSuccess) e = le;
+    if (e != cudaSuccess) break;
+
+    e = cudaStreamBeginCaptureToGraph(cs, g, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    le = launch_forces(h->sys, h->buf, h->precision, 1, 0, cs);
+    ge = grab(deps);
+    gg = g;
+    e = cudaStreamEndCapture(cs, &gg);
+    if (e == cudaSuccess) e = le;
+    if (e == cudaSuccess) e = ge;
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(h, ADRESS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(h, ADRESS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  *gout = g;
+  *xout = x;
+  return ADRESS_OK;
+}
+
+adress_status adress_step(adress_handle h, int32_t nsteps) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (nsteps < 0) return fail(h, ADRESS_ERR_ARG, "nsteps < 0");
+  if (!h->bound || !h->lists_built) return fail(h, ADRESS_ERR_STATE, "bind state and build lists first");
+  if (nsteps == 0) return ADRESS_OK;
+  const int sizes[2] = {kGraphSteps, 1};
+  for (int k = 0; k < 2; ++k)
+    if (!h->exec[k]) {
+      adress_status st = capture_steps(h, sizes[k], &h->graph[k], &h->exec[k]);
+      if (st != ADRESS_OK) return st;
+    }
+  int left = nsteps;
+  while (left >= kGraphSteps) {
+    CUDA_OR_FAIL(h, cudaGraphLaunch(h->exec[0], h->stream));
+    left -= kGraphSteps;
+  }
+  while (left-- > 0) CUDA_OR_FAIL(h, cudaGraphLaunch(h->exec[1], h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_set_step(adress_handle h, int64_t step) {
+  if (!h) return ADRESS_ERR_ARG;
+  long long v = step;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->buf.ctrl->step, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_get_step(adress_handle h, int64_t* step) {
+  if (!h || !step) return ADRESS_ERR_ARG;
+  Ctrl c;
+  adress_status st = read_ctrl(h, &c);
+  if (st == ADRESS_OK) *step = c.step;
+  return st;
+}
+
+adress_status adress_com_lambda(adress_handle h, double* com, double* w) {
+  if (!h || !com || !w) return ADRESS_ERR_ARG;
+  if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
+  CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream));
+  CUDA_OR_FAIL(h, launch_export_com(h->sys, h->buf, com, w, h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_kinetic(adress_handle h, double* out) {
+  if (!h || !out) return ADRESS_ERR_ARG;
+  if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
+  CUDA_OR_FAIL(h, launch_kinetic(h->sys, h->buf, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(out, h->buf.result, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_density_accumulate(adress_handle h) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
+  CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream));
+  CUDA_OR_FAIL(h, launch_density(h->sys, h->buf, h->precision, h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_density_get(adress_handle h, int64_t* counts, int32_t n, int64_t* nsamples) {
+  if (!h || (!counts && n > 0) || n < 0 || n > h->sys.tf_n) return ADRESS_ERR_ARG;
+  if (n > 0)
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(counts, h->buf.hist, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, h->stream));
+  long long ns = 0;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(&ns, h->buf.nsamples, sizeof(ns), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  if (nsamples) *nsamples = ns;
+  return ADRESS_OK;
+}
+
+adress_status adress_density_reset(adress_handle h) {
+  if (!h) return ADRESS_ERR_ARG;
+  CUDA_OR_FAIL(h, cudaMemsetAsync(h->buf.hist, 0, sizeof(unsigned long long) * std::max(1, h->sys.tf_n), h->stream));
+  CUDA_OR_FAIL(h, cudaMemsetAsync(h->buf.nsamples, 0, sizeof(long long), h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_tf_update(adress_handle h, double alpha) {
+  if (!h) return ADRESS_ERR_ARG;
+  CUDA_OR_FAIL(h, launch_tf_update(h->sys, h->buf, alpha, h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_set_tf(adress_handle h, const double* tf, int32_t n) {
+  if (!h || n != h->sys.tf_n || (n > 0 && !tf)) return ADRESS_ERR_ARG;
+  if (n == 0) return ADRESS_OK;
+  std::vector<float> f(n);
+  for (int k = 0; k < n; ++k) f[k] = (float)tf[k];
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->buf.tf64, tf, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->buf.tf32, f.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_get_tf(adress_handle h, double* tf, int32_t n) {
+  if (!h || n != h->sys.tf_n || (n > 0 && !tf)) return ADRESS_ERR_ARG;
+  if (n == 0) return ADRESS_OK;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(tf, h->buf.tf64, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_list_stats(adress_handle h, int64_t* out) {
+  if (!h || !out) return ADRESS_ERR_ARG;
+  Ctrl c;
+  adress_status st = read_ctrl(h, &c);
+  if (st != ADRESS_OK) return st;
+  out[0] = c.n_hr;
+  out[1] = c.n_cg;
+  out[2] = c.rebuilds;
+  out[3] = c.max_nn;
+  out[4] = h->sys.cap;
+  out[5] = h->sys.ncell;
+  out[6] = 0;
+  out[7] = 0;
+  return ADRESS_OK;
+}
+
+adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out) {
+  if (!h || !ms_out || reps < 1) return ADRESS_ERR_ARG;
+  if (!h->bound || !h->lists_built) return fail(h, ADRESS_ERR_STATE, "bind state and build lists first");
+  cudaEvent_t ev[5];
+  for (int k = 0; k < 5; ++k) CUDA_OR_FAIL(h, cudaEventCreate(&ev[k]));
+  double acc[3] = {0, 0, 0};
+  adress_status st = ADRESS_OK;
+  for (int r = 0; r < reps && st == ADRESS_OK; ++r) {
+    cudaError_t e = cudaEventRecord(ev[0], h->stream);
+    if (e == cudaSuccess) e = launch_com(h->sys, h->buf, h->precision, 1, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+    if (e == cudaSuccess) e = launch_decide(h->sys, h->buf, 1, 1, 0, 0, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+    if (e == cudaSuccess) e = launch_rebuild(h->sys, h->buf, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
+    if (e == cudaSuccess) e = launch_forces(h->sys, h->buf, h->precision, 1, 0, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+    float t0 = 0, t1 = 0, t2 = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[2], ev[3]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t2, ev[3], ev[4]);
+    if (e != cudaSuccess) st = fail(h, ADRESS_ERR_CUDA, std::string("kernel timing: ") + cudaGetErrorString(e));
+    acc[0] += t0;
+    acc[1] += t1;
+    acc[2] += t2;
+  }
+  for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+  if (st != ADRESS_OK) return st;
+  for (int k = 0; k < 3; ++k) ms_out[k] = (float)(acc[k] / reps);
+  return ADRESS_OK;
+}
+
+adress_status adress_check(adress_handle h) {
+  if (!h) return ADRESS_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(h, ADRESS_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+  Ctrl c;
+  adress_status st = read_ctrl(h, &c);
+  if (st != ADRESS_OK) return st;
+  if (c.err != 0) {
+    int zero = 0;
+    CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->buf.ctrl->err, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    char msg[160];
+    snprintf(msg, sizeof(msg), "device error: %s (info %d)", adress_status_string((adress_status)c.err),
+             c.err_info);
+    return fail(h, (adress_status)c.err, msg);
+  }
+  return ADRESS_OK;
+}
+
+void adress_destroy(adress_handle h) {
+  if (!h) return;
+  if (h->stream || h->bound) cudaStreamSynchronize(h->stream);
+  free_graphs(h);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,293 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: per-atom force relative RMS  sqrt(sum|F - F_ref|^2 / sum|F_ref|^2)
+<= 1e-10 for the FP64 path and <= 2e-5 for the FP32 mixed path; integer outputs
+(density histogram) bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_10841_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 2e-5}
+ETOL = {"fp64": 1e-10, "fp32": 2e-5}
+
+
+def rel_rms(a, b):
+    return math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
+
+
+def make(name):
+    if name == "c1_literal":
+        s = inputs.c1_literal()
+        x, v = inputs.tetra_state(s, min_contact=0.0)
+    elif name == "c1_stable":
+        s = inputs.c1_stable()
+        x, v = inputs.tetra_state(s)
+    elif name == "hybrid_216":
+        s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, seed=5)
+        x, v = inputs.tetra_state(s)
+    elif name == "scaled_20k":
+        s = inputs.scaled_c2(20_000)
+        x, v = inputs.tetra_state(s)
+    elif name == "c2_800k":
+        s = inputs.c2_800k()
+        x, v = inputs.tetra_state(s)
+    else:
+        raise KeyError(name)
+    return s, x, v
+
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        s, x, v = make(name)
+        f, e = oracle.Oracle(s).forces(x)
+        _cache[name] = (s, x, v, f, e)
+    return _cache[name]
+
+
+def gpu(s, precision, **kw):
+    from paper_1806_10841_gb300 import adress
+
+    return adress.AdResS(s, precision=precision, **kw)
+
+
+def check_forces(s, x, f_ref, e_ref, precision):
+    sim = gpu(s, precision)
+    sim.set_state(x)
+    f, e = sim.forces()
+    sim.check()
+    r = rel_rms(f, f_ref)
+    assert r <= TOL[precision], f"{precision}: force rel RMS {r:.3e}"
+    scale = abs(e_ref["E_at"]) + abs(e_ref["E_cg"]) + abs(e_ref["E_bond"])
+    for k in ("E_at", "E_cg", "E_bond"):
+        assert abs(e[k] - e_ref[k]) <= ETOL[precision] * scale, (k, e[k], e_ref[k])
+    assert abs(e["virial"] - e_ref["virial"]) <= ETOL[precision] * (abs(e_ref["virial"]) + scale)
+    sim.close()
+    return r
+
+
+# ---- step-0 forces ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["c1_literal", "c1_stable", "hybrid_216", "scaled_20k"])
+def test_forces_fp64(name):
+    s, x, v, f, e = case(name)
+    check_forces(s, x, f, e, "fp64")
+
+
+@pytest.mark.parametrize("name", ["c1_stable", "hybrid_216", "scaled_20k"])
+def test_forces_fp32(name):
+    s, x, v, f, e = case(name)
+    check_forces(s, x, f, e, "fp32")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_forces_full_size_800k_atoms(precision):
+    """The benchmark's workload (200k tetrahedra, 800k atoms), every atom compared."""
+    s, x, v, f, e = case("c2_800k")
+    check_forces(s, x, f, e, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_com_and_resolution(precision):
+    s, x, v, f, e = case("hybrid_216")
+    R, dxc, w = oracle.Oracle(s).com_lambda(x)
+    sim = gpu(s, precision)
+    sim.set_state(x)
+    com, wg = sim.com_lambda()
+    d = com - R
+    d -= np.array(s.box) * np.rint(d / np.array(s.box))
+    assert np.abs(d).max() < 1e-12
+    assert np.abs(wg - w).max() < (1e-14 if precision == "fp64" else 2e-6)
+    assert ((w > 0) & (w < 1)).any() and (w == 1).any() and (w == 0).any()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_thermodynamic_force_table(precision):
+    s, x, v, _, _ = case("hybrid_216")
+    o = oracle.Oracle(s)
+    tf = 0.8 * np.sin(np.arange(len(s.tf)) * 0.7)
+    o.set_tf(tf)
+    f_ref, e_ref = o.forces(x)
+    sim = gpu(s, precision)
+    sim.set_tf(tf)
+    assert np.array_equal(sim.get_tf(), tf)
+    sim.set_state(x)
+    f, _ = sim.forces()
+    assert rel_rms(f, f_ref) <= TOL[precision]
+
+
+# ---- limits of Eq. 1 and conservation -------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("geom", ["all_at", "all_cg", "step", "two_cells"])
+def test_edge_geometries(precision, geom):
+    if geom == "all_at":
+        s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 1e3, 1.0, seed=6)
+    elif geom == "all_cg":
+        s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 0.0, 0.0, seed=7)
+    elif geom == "step":
+        s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 8.0, 0.0, seed=8)
+    else:  # 2 cells along y and z: the 27-cell stencil must not double count
+        s = inputs.tetra_system(64, (17.2, 6.0, 6.0), 5.0, 2.0, seed=9)
+    x, v = inputs.tetra_state(s)
+    f_ref, e_ref = oracle.Oracle(s).forces(x)
+    check_forces(s, x, f_ref, e_ref, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_point_particles(precision):
+    """One atom per molecule: AT and CG act between the same points."""
+    s = inputs.tetra_system(400, (20.0, 10.0, 10.0), 6.0, 2.0, seed=10)
+    s.na, s.mass, s.bonds = 1, np.ones(1), np.zeros((0, 2), np.int32)
+    rng = np.random.default_rng(10)
+    g = np.stack(np.meshgrid(np.arange(10), np.arange(5), np.arange(8), indexing="ij"), -1).reshape(-1, 3)
+    x = (g + 0.5) * np.array([2.0, 2.0, 1.25]) + rng.uniform(-0.1, 0.1, g.shape)
+    f_ref, e_ref = oracle.Oracle(s).forces(x)
+    check_forces(s, x, f_ref, e_ref, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_newton_third_law(precision):
+    s, x, v, f, e = case("hybrid_216")
+    sim = gpu(s, precision)
+    sim.set_state(x)
+    fg, _ = sim.forces()
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    assert np.abs(fg.sum(0)).max() <= tol * np.abs(fg).sum()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_deterministic(precision):
+    s, x, v, f, e = case("scaled_20k")
+    sim = gpu(s, precision)
+    sim.set_state(x, v)
+    f1, _ = sim.forces()
+    f2, _ = sim.forces()
+    assert np.array_equal(f1, f2)
+    sim.set_state(x, v, f1)
+    sim.step(20)
+    a = sim.get_state()
+    sim.set_state(x, v, f1)
+    sim.set_step(0)
+    sim.build_lists()
+    sim.step(20)
+    b = sim.get_state()
+    for p, q in zip(a, b):
+        assert np.array_equal(p, q)
+
+
+# ---- trajectories -----------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_trajectory_divergence_100_steps(precision):
+    """Langevin velocity Verlet with identical Philox noise: the GPU trajectory follows the
+    oracle's; the divergence curve stays below a precision-dependent envelope."""
+    s, x, v, f0, _ = case("c1_stable")
+    o = oracle.Oracle(s)
+    sim = gpu(s, precision)
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    _, _, fg = sim.get_state()
+    xo, vo, fo = x, v, f0
+    L = np.array(s.box)
+    curve = []
+    for k in range(10):
+        sim.step(10)
+        xo, vo, fo = o.run(xo, vo, fo, 10 * k, 10)
+        xg, vg, fg = sim.get_state()
+        dx = xg - xo
+        dx -= L * np.rint(dx / L)
+        curve.append((np.abs(dx).max(), np.abs(vg - vo).max()))
+    sim.check()
+    assert sim.get_step() == 100
+    env = {"fp64": (1e-11, 1e-9), "fp32": (1e-5, 1e-3)}[precision]
+    print(precision, "divergence curve", [f"{a:.1e}" for a, _ in curve])
+    assert curve[0][0] < env[0] / 10
+    assert curve[-1][0] < env[0] * 100 and curve[-1][1] < env[1] * 100
+    stats = sim.list_stats()
+    assert stats["rebuilds"] >= 2 and stats["n_hr"] + stats["n_cg"] == s.M
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_kinetic_energy_and_momentum(precision):
+    s, x, v, f, e = case("scaled_20k")
+    o = oracle.Oracle(s)
+    sim = gpu(s, precision)
+    sim.set_state(x, v)
+    ke, p = sim.kinetic()
+    ke_ref, p_ref = o.kinetic(v)
+    assert ke == pytest.approx(ke_ref, rel=1e-13)
+    assert np.allclose(p, p_ref, atol=1e-10)
+
+
+# ---- density profile and thermodynamic-force iteration -------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_density_histogram_bit_exact_and_tf_update(precision):
+    s, x, v, f, e = case("scaled_20k")
+    o = oracle.Oracle(s)
+    sim = gpu(s, precision)
+    sim.set_state(x)
+    sim.density_accumulate()
+    sim.density_accumulate()
+    counts, ns = sim.density_get()
+    ref_d, _ = o.density(x, len(s.tf), 10)
+    assert ns == 2
+    assert np.array_equal(counts, 2 * ref_d)
+    tf0 = 0.1 * np.cos(np.arange(len(s.tf)))
+    sim.set_tf(tf0)
+    sim.tf_update(alpha=3.0)
+    tf_gpu = sim.get_tf()
+    tf_ref = o.tf_update(tf0, 2 * ref_d, nsamples=2, alpha=3.0)
+    assert np.allclose(tf_gpu, tf_ref, rtol=1e-13, atol=1e-15)
+    counts, ns = sim.density_get()
+    assert ns == 0 and not counts.any()
+
+
+# ---- host-visible error paths (no GPU fault: device flags read back by the host) ----------
+
+def test_list_capacity_grows_automatically():
+    s, x, v, f, e = case("hybrid_216")
+    sim = gpu(s, "fp64", max_neighbors=4)
+    sim.set_state(x)
+    fg, _ = sim.forces()
+    assert rel_rms(fg, f) <= TOL["fp64"]
+    st = sim.list_stats()
+    assert st["capacity"] >= st["max_nn"] > 4
+
+
+def test_broken_bond_is_reported():
+    from paper_1806_10841_gb300 import adress
+
+    s, x, v, f, e = case("hybrid_216")
+    x = x.copy()
+    x[1] = x[0] + np.array([1.6, 0.0, 0.0])  # beyond R0 = 1.5
+    x[1] = np.mod(x[1], s.box)
+    sim = gpu(s, "fp32")
+    sim.set_state(x)
+    sim.compute_forces(energies=False)
+    with pytest.raises(adress.AdressError) as ei:
+        sim.check()
+    assert ei.value.status == 5
+    sim.check()  # cleared
+
+
+def test_invalid_configs_are_rejected():
+    from paper_1806_10841_gb300 import adress
+
+    s = inputs.tetra_system(8, (4.0, 4.0, 4.0), 1.0, 1.0)  # box shorter than twice r_list
+    with pytest.raises(adress.AdressError) as ei:
+        gpu(s, "fp32")
+    assert ei.value.status == 1
+    s = inputs.tetra_system(1, (20.0, 20.0, 20.0), 1.0, 1.0)
+    with pytest.raises(adress.AdressError):
+        gpu(s, "fp64")
