@@ -215,6 +215,10 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 GPU comparison arm")
+    ap.add_argument("--profile", type=int, default=0,
+                    help="profiling driver: set up, run this many MD steps, exit (no timing output)")
+    ap.add_argument("--molecules", type=int, default=200_000,
+                    help="system size for --profile (same density, shape and slab proportions)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -234,6 +238,20 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
+
+    if args.profile:
+        s = inputs.c2_800k() if args.molecules == 200_000 else inputs.scaled_c2(args.molecules)
+        x0, v0 = inputs.tetra_state(s)
+        sim = adress.AdResS(s, precision=args.precision, device=f"cuda:{local}")
+        sim.set_state(x0, v0)
+        sim.compute_forces(energies=False)
+        sim.step(args.profile)
+        sim.density_accumulate()
+        sim.tf_update(TF_ALPHA)
+        sim.check()
+        print(json.dumps({"profile_steps": args.profile, "atoms": s.N, "lists": sim.list_stats()}))
+        sim.close()
+        return 0
 
     s = inputs.c2_800k(seed=20180628 + rank)
     x0, v0 = inputs.tetra_state(s)

@@ -126,7 +126,10 @@ adress_status adress_compute_forces(adress_handle h, double* energies);
  * steps:  v += dt/2 f/m;  x += dt v (wrapped);  f = F(x) + F_L(v; n+1);  v += dt/2 f/m.
  * Lists are rebuilt on the device when a molecule centre moved more than skin/2 or a
  * molecule grew wider than the list allows.  Runs as replays of a captured CUDA graph
- * whose rebuild is a conditional node.  Asynchronous; errors surface at adress_check. */
+ * whose rebuild is a conditional node.  Asynchronous; errors surface at adress_check.
+ * With the environment variable ADRESS_EAGER=1 set before adress_init, kernels are
+ * launched one by one and the rebuild is decided on the host (synchronising every step);
+ * per-kernel profilers cannot see kernels inside graphs that hold conditional nodes. */
 adress_status adress_step(adress_handle h, int32_t nsteps);
 
 /* Time level of the bound state (keys the thermostat noise). */

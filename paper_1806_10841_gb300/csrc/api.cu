@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/adress.h.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -27,7 +28,7 @@ struct adress_ctx {
   // captured step graphs: one with kGraphSteps steps, one with a single step
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  int64_t rebuild_host = 0;
+  bool eager = false;  // ADRESS_EAGER=1: launch kernel by kernel (for per-kernel profilers)
 };
 
 static thread_local std::string g_init_error;
@@ -138,6 +139,10 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   adress_ctx* h = new adress_ctx();
   h->precision = c->precision;
   h->stream = (cudaStream_t)stream;
+  {
+    const char* ev = getenv("ADRESS_EAGER");
+    h->eager = ev && ev[0] == '1';
+  }
   cudaGetDevice(&h->device);
   Sys& s = h->sys;
   s.M = c->n_mols;
@@ -467,6 +472,18 @@ adress_status adress_step(adress_handle h, int32_t nsteps) {
   if (nsteps < 0) return fail(h, ADRESS_ERR_ARG, "nsteps < 0");
   if (!h->bound || !h->lists_built) return fail(h, ADRESS_ERR_STATE, "bind state and build lists first");
   if (nsteps == 0) return ADRESS_OK;
+  if (h->eager) {
+    for (int k = 0; k < nsteps; ++k) {
+      CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 1, h->stream));
+      CUDA_OR_FAIL(h, launch_decide(h->sys, h->buf, 0, 1, 0, 0, h->stream));
+      Ctrl c;
+      adress_status st = read_ctrl(h, &c);
+      if (st != ADRESS_OK) return st;
+      if (c.rebuild) CUDA_OR_FAIL(h, launch_rebuild(h->sys, h->buf, h->stream));
+      CUDA_OR_FAIL(h, launch_forces(h->sys, h->buf, h->precision, 1, 0, h->stream));
+    }
+    return ADRESS_OK;
+  }
   const int sizes[2] = {kGraphSteps, 1};
   for (int k = 0; k < 2; ++k)
     if (!h->exec[k]) {

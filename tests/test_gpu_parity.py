@@ -268,10 +268,10 @@ def test_list_capacity_grows_automatically():
 def test_broken_bond_is_reported():
     from paper_1806_10841_gb300 import adress
 
-    s, x, v, f, e = case("hybrid_216")
-    x = x.copy()
-    x[1] = x[0] + np.array([1.6, 0.0, 0.0])  # beyond R0 = 1.5
-    x[1] = np.mod(x[1], s.box)
+    s = inputs.scaled_c2(2000)
+    s.r_ext = 1.2  # wide enough lists that the stretched molecule is still listed
+    x, v = inputs.tetra_state(s)
+    x[1] = np.mod(x[0] + np.array([1.6, 0.0, 0.0]), s.box)  # beyond R0 = 1.5
     sim = gpu(s, "fp32")
     sim.set_state(x)
     sim.compute_forces(energies=False)
