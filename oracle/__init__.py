@@ -72,7 +72,9 @@ def _load(path: str | None = None):
         lib = C.CDLL(build())
     d, i64, u64 = C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_uint64)
     S = C.POINTER(orc_sys)
-    lib.orc_philox4x64.argtypes = [u64, u64, u64]
+    u32 = C.POINTER(C.c_uint32)
+    lib.orc_philox4x32.argtypes = [u32, u32, u32]
+    lib.orc_uniform3.argtypes = [C.c_uint64, C.c_int64, C.c_int64, C.c_int64, d]
     lib.orc_weight.argtypes = [S, C.c_double]
     lib.orc_weight.restype = C.c_double
     lib.orc_com_lambda.argtypes = [S, d, d, d, d]
@@ -188,10 +190,17 @@ class Oracle:
         return tf
 
 
-def philox4x64(ctr, key):
+def philox4x32(ctr, key):
     lib = _load()
-    c = np.ascontiguousarray(ctr, dtype=np.uint64)
-    k = np.ascontiguousarray(key, dtype=np.uint64)
-    out = np.zeros(4, dtype=np.uint64)
-    lib.orc_philox4x64(_ptr(c, C.c_uint64), _ptr(k, C.c_uint64), _ptr(out, C.c_uint64))
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.orc_philox4x32(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(out, C.c_uint32))
     return out
+
+
+def uniform3(seed: int, replica: int, gid: int, step: int):
+    lib = _load()
+    u = np.zeros(3)
+    lib.orc_uniform3(int(seed), int(replica), int(gid), int(step), _ptr(u))
+    return u

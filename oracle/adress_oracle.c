@@ -35,40 +35,44 @@
 #endif
 
 /* ---------------------------------------------------------------------------------
- * Philox4x64-10 counter-based generator (Salmon, Moraes, Dror, Shaw, "Parallel random
- * numbers: as easy as 1, 2, 3", SC'11): ten rounds of two 64x64->128 multiplies with
- * the published multipliers, key bumped by the published Weyl constants between rounds.
+ * Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, "Parallel random
+ * numbers: as easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the
+ * published multipliers, key bumped by the published Weyl constants between rounds.
  * ------------------------------------------------------------------------------- */
-static void mulhilo64(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
-  unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
-  *lo = (uint64_t)p;
-  *hi = (uint64_t)(p >> 64);
-}
-
-void orc_philox4x64(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-  uint64_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
-  uint64_t k[2] = {key_in[0], key_in[1]};
+void orc_philox4x32(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+  uint32_t k[2] = {key_in[0], key_in[1]};
   for (int round = 0; round < 10; ++round) {
     if (round > 0) {
       k[0] += W0;
       k[1] += W1;
     }
-    uint64_t hi0, lo0, hi1, lo1;
-    mulhilo64(M0, c[0], &hi0, &lo0);
-    mulhilo64(M1, c[2], &hi1, &lo1);
-    uint64_t n0 = hi1 ^ c[1] ^ k[0];
-    uint64_t n1 = lo1;
-    uint64_t n2 = hi0 ^ c[3] ^ k[1];
-    uint64_t n3 = lo0;
+    uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k[0];
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k[1];
+    uint32_t n3 = (uint32_t)p0;
     c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
   }
   memcpy(out, c, sizeof(c));
 }
 
-/* Uniform double in [0,1) from the top 53 bits. */
-static double u01(uint64_t r) { return (double)(r >> 11) * (1.0 / 9007199254740992.0); }
+/* Three uniforms in [0,1) for atom `gid` at time level `step`: two generator blocks with
+ * counters (gid, step_lo, step_hi, 2 replica) and (gid, step_lo, step_hi, 2 replica + 1),
+ * key (seed_lo, seed_hi); component d takes 32 high bits from the first block and 21 low
+ * bits from the top of the second: u = (hi << 21 | lo >> 11) 2^-53. */
+void orc_uniform3(uint64_t seed, int64_t replica, int64_t gid, int64_t step, double u[3]) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t c0[4] = {(uint32_t)gid, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)(2 * replica)};
+  uint32_t c1[4] = {(uint32_t)gid, (uint32_t)step, (uint32_t)((uint64_t)step >> 32), (uint32_t)(2 * replica + 1)};
+  uint32_t hi[4], lo[4];
+  orc_philox4x32(c0, key, hi);
+  orc_philox4x32(c1, key, lo);
+  for (int d = 0; d < 3; ++d)
+    u[d] = (double)(((uint64_t)hi[d] << 21) | (lo[d] >> 11)) * (1.0 / 9007199254740992.0);
+}
 
 /* --------------------------------------------------------------------------------- */
 
@@ -320,16 +324,15 @@ int orc_forces(const orc_sys* s, const double* x, int method, const double* w_ov
 
 /* Langevin friction and noise for atom gid at time level `step`:
  *   F_L = -gamma m v + sqrt(24 gamma kT m / dt) (u - 1/2),
- * u uniform in [0,1) from Philox4x64-10 with key (seed, step), counter (gid, replica, 0, 0). */
+ * u uniform in [0,1) from orc_uniform3 (Philox4x32-10). */
 static void langevin(const orc_sys* s, const double* v, int64_t step, double* f) {
   const int N = s->M * s->na;
   for (int i = 0; i < N; ++i) {
     double m = s->mass[i % s->na];
     double amp = sqrt(24.0 * s->gamma * s->kT * m / s->dt);
-    uint64_t ctr[4] = {(uint64_t)i, (uint64_t)s->replica, 0, 0}, key[2] = {s->seed, (uint64_t)step};
-    uint64_t r[4];
-    orc_philox4x64(ctr, key, r);
-    for (int d = 0; d < 3; ++d) f[3 * i + d] += -s->gamma * m * v[3 * i + d] + amp * (u01(r[d]) - 0.5);
+    double u[3];
+    orc_uniform3(s->seed, s->replica, i, step, u);
+    for (int d = 0; d < 3; ++d) f[3 * i + d] += -s->gamma * m * v[3 * i + d] + amp * (u[d] - 0.5);
   }
 }
 

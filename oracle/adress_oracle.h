@@ -30,7 +30,8 @@ typedef struct {
   int64_t replica;
 } orc_sys;
 
-void orc_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]);
+void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void orc_uniform3(uint64_t seed, int64_t replica, int64_t gid, int64_t step, double u[3]);
 double orc_weight(const orc_sys* s, double d);
 void orc_com_lambda(const orc_sys* s, const double* x, double* R, double* dx_c, double* w);
 int orc_forces(const orc_sys* s, const double* x, int method, const double* w_override, double* f,

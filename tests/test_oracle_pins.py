@@ -2,12 +2,13 @@
 
 Each test checks the oracle against something other than itself: closed forms,
 finite-difference gradients of its own energies (force = -grad V), library routines
-(numpy's Philox, numpy.interp, numpy.histogram), the reductions of Eq. 1 at lambda = 1
+(numpy.interp, numpy.histogram), the published Philox4x32-10 known-answer vectors, the reductions of Eq. 1 at lambda = 1
 and lambda = 0, Newton's third law (which force interpolation preserves exactly),
 energy conservation of velocity Verlet in the pure-AT limit, and the Langevin
 equipartition / friction limits.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -31,29 +32,43 @@ def point_system(n, box, d_at, d_hy, **kw):
     return s
 
 
-# --- Philox4x64-10 against numpy's independent implementation ----------------------
+# --- Philox4x32-10 against its published known-answer vectors ----------------------
 
-@pytest.mark.parametrize("ctr,key", [
-    ((1, 0, 0, 0), (0, 0)),
-    ((9, 0, 0, 0), (5, 7)),
-    ((123456789, 3, 0, 0), (20180628, 1000)),
-    ((2**64 - 1, 7, 11, 13), (2**64 - 3, 2**63 + 5)),
-    ((0, 1, 0, 0), (42, 0)),
-])
-def test_philox_matches_numpy(ctr, key):
-    # numpy's Philox produces block philox(counter + 1) first (carry across words)
-    c = list(ctr)
-    prev = c[:]
-    i = 0
-    while True:
-        prev[i] = (prev[i] - 1) % 2**64
-        if prev[i] != 2**64 - 1:
-            break
-        i += 1
-    g = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=np.array(prev, dtype=np.uint64))
-    ref = g.random_raw(4)
-    got = oracle.philox4x64(ctr, key)
-    assert list(map(int, got)) == list(map(int, ref))
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def kat_vectors():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(t, 16) for t in line.split()]
+        rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,expect", kat_vectors())
+def test_philox4x32_known_answers(ctr, key, expect):
+    assert list(map(int, oracle.philox4x32(ctr, key))) == expect
+
+
+def test_uniform3_bits_and_distribution():
+    """Each component joins 32 bits of the first block and the top 21 bits of the second;
+    draws are uniform on [0,1) and independent across atoms, steps and replicas."""
+    seed, rep, gid, step = 0x1234567890ABCDEF, 3, 77, 2**33 + 5
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    hi = oracle.philox4x32([gid, step & 0xFFFFFFFF, step >> 32, 2 * rep], key)
+    lo = oracle.philox4x32([gid, step & 0xFFFFFFFF, step >> 32, 2 * rep + 1], key)
+    u = oracle.uniform3(seed, rep, gid, step)
+    for d in range(3):
+        assert u[d] == ((int(hi[d]) << 21) | (int(lo[d]) >> 11)) * 2.0 ** -53
+    draws = np.array([oracle.uniform3(7, 0, g, s) for g in range(200) for s in range(20)]).ravel()
+    assert draws.min() >= 0 and draws.max() < 1
+    hist, _ = np.histogram(draws, bins=20, range=(0, 1))
+    chi2 = ((hist - draws.size / 20) ** 2 / (draws.size / 20)).sum()
+    assert chi2 < 45  # 19 degrees of freedom, p ~ 1e-3
+    assert abs(np.corrcoef(draws[:-1], draws[1:])[0, 1]) < 0.05
+    assert not np.array_equal(oracle.uniform3(7, 0, 5, 1), oracle.uniform3(7, 1, 5, 1))
 
 
 # --- resolution function ------------------------------------------------------------
