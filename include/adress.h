@@ -125,8 +125,11 @@ adress_status adress_compute_forces(adress_handle h, double* energies);
 /* Advance the bound state (x, v, f at time level n) by nsteps Langevin velocity-Verlet
  * steps:  v += dt/2 f/m;  x += dt v (wrapped);  f = F(x) + F_L(v; n+1);  v += dt/2 f/m.
  * Lists are rebuilt on the device when a molecule centre moved more than skin/2 or a
- * molecule grew wider than the list allows.  Runs as replays of a captured CUDA graph
- * whose rebuild is a conditional node.  Asynchronous; errors surface at adress_check.
+ * molecule grew wider than the list allows.  Runs as a captured CUDA graph (cached per
+ * step count, up to 100 steps per graph): one prologue kernel (half kick, drift,
+ * mapping), one fused kernel per further step (forces, thermostat, both half kicks,
+ * drift, next mapping), one last kernel (forces, thermostat, second half kick); after each
+ * mapping a decide kernel sets the conditional node that runs the list rebuild.  Asynchronous; errors surface at adress_check.
  * With the environment variable ADRESS_EAGER=1 set before adress_init, kernels are
  * launched one by one and the rebuild is decided on the host (synchronising every step);
  * per-kernel profilers cannot see kernels inside graphs that hold conditional nodes. */
@@ -166,12 +169,11 @@ adress_status adress_get_tf(adress_handle h, double* tf_host, int32_t n); /* syn
  * max_neighbours_at_last_build, capacity, n_cells, 0, 0}.  Synchronises. */
 adress_status adress_list_stats(adress_handle h, int64_t* out);
 
-/* Kernel timing for roofline accounting: runs `reps` steps as separate launches
- * (integrate+COM, rebuild decision, forced list rebuild, forces+thermostat+kick) on the
- * handle's stream with CUDA events around each kernel, advancing the state by `reps`
- * steps exactly as adress_step does (with a rebuild every step).  ms_out host [3] =
- * average milliseconds per launch of {integrate+COM, list rebuild, forces}.
- * Synchronises. */
+/* Kernel timing for roofline accounting: advances the state by reps + 1 steps with the
+ * kernels adress_step uses, launched one by one on the handle's stream with CUDA events
+ * around each (prologue, then reps fused steps each followed by a forced list rebuild,
+ * then the last step).  ms_out host [4] = milliseconds of {prologue (half kick + drift +
+ * mapping), list rebuild (average), fused step (average), last step}.  Synchronises. */
 adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out);
 
 /* Synchronise the stream and return (then clear) the first device-side error. */

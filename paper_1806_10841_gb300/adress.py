@@ -261,10 +261,10 @@ class AdResS:
         return {k: int(out[i]) for i, k in enumerate(keys)}
 
     def time_kernels(self, reps: int = 20):
-        """Average ms per launch of (integrate+COM, list rebuild, forces); advances the state."""
-        out = (C.c_float * 3)()
+        """ms per launch of the step kernels (advances the state by reps + 1 steps)."""
+        out = (C.c_float * 4)()
         self._call("adress_time_kernels", C.c_int32(int(reps)), out)
-        return dict(integrate_com=out[0], rebuild=out[1], forces=out[2])
+        return dict(prologue=out[0], rebuild=out[1], step=out[2], last=out[3])
 
     def check(self):
         self._call("adress_check")

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -25,14 +26,13 @@ struct adress_ctx {
   bool lists_built = false;
   std::vector<void*> allocs;
   int nparts = 0;
-  // captured step graphs: one with kGraphSteps steps, one with a single step
-  cudaGraph_t graph[2] = {nullptr, nullptr};
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  // captured step graphs keyed by their number of steps
+  std::map<int, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   bool eager = false;  // ADRESS_EAGER=1: launch kernel by kernel (for per-kernel profilers)
 };
 
 static thread_local std::string g_init_error;
-static constexpr int kGraphSteps = 10;
+static constexpr int kMaxGraphSteps = 100;  // longest captured step graph
 
 static adress_status fail(adress_ctx* h, adress_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -58,12 +58,22 @@ static cudaError_t dalloc(adress_ctx* h, T** p, size_t n) {
 }
 
 static void free_graphs(adress_ctx* h) {
-  for (int k = 0; k < 2; ++k) {
-    if (h->exec[k]) cudaGraphExecDestroy(h->exec[k]);
-    if (h->graph[k]) cudaGraphDestroy(h->graph[k]);
-    h->exec[k] = nullptr;
-    h->graph[k] = nullptr;
+  for (auto& kv : h->graphs) {
+    if (kv.second.second) cudaGraphExecDestroy(kv.second.second);
+    if (kv.second.first) cudaGraphDestroy(kv.second.first);
   }
+  h->graphs.clear();
+}
+
+// Host twin of the device fixed-point map: floor(x 2^32 / L) from the bits of x.
+static unsigned fixed32_host(double x, unsigned long long K, int q) {
+  unsigned long long bits;
+  memcpy(&bits, &x, sizeof(bits));
+  const int e = (int)((bits >> 52) & 0x7ff);
+  const unsigned long long M = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = q - 44 - (e - 1023);
+  const unsigned long long hi = (unsigned long long)(((unsigned __int128)M * K) >> 64);
+  return (e == 0 || sh >= 64 || sh < 0) ? 0u : (unsigned)(hi >> sh);
 }
 
 static uint64_t morton3(uint64_t x, uint64_t y, uint64_t z) {
@@ -156,14 +166,27 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
     s.mass[k] = m;
     s.inv_mass[k] = 1.0 / m;
     s.frac[k] = k < s.NA ? m / Mtot : 0.0;
+    s.hdt_m[k] = 0.5 * c->dt / m;
+    s.amp[k] = sqrt(24.0 * c->gamma * c->kT * m / c->dt);
+    s.gm[k] = c->gamma * m;
+    s.ampf[k] = (float)s.amp[k];
+    s.gmf[k] = (float)s.gm[k];
   }
+  s.fp64 = c->precision == ADRESS_FP64;
   for (int d = 0; d < 3; ++d) {
     s.L[d] = c->box[d];
     s.halfL[d] = 0.5 * c->box[d];
+    memcpy(&s.Lbits[d], &c->box[d], sizeof(double));
     s.fx_inv[d] = 4294967296.0 / c->box[d];
     s.fx_scale[d] = (float)(c->box[d] / 4294967296.0);
     s.Lf[d] = (float)c->box[d];
+    int q = 63;
+    while (ldexp(1.0, q) / c->box[d] < 9223372036854775808.0) ++q;  // 2^q / L >= 2^63
+    while (ldexp(1.0, q) / c->box[d] >= 18446744073709551616.0) --q;
+    s.fxq[d] = q;
+    s.fxK[d] = (unsigned long long)(ldexp(1.0, q) / c->box[d]);
   }
+  s.xc32 = fixed32_host(c->x_center - c->box[0] * floor(c->x_center / c->box[0]), s.fxK[0], s.fxq[0]);
   s.xc = c->x_center;
   s.d_at = c->d_at_half;
   s.d_hy = c->d_hy;
@@ -189,6 +212,8 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   s.gamma = c->gamma;
   s.dt = c->dt;
   s.seed = c->seed;
+  s.seed_lo = (unsigned)(c->seed & 0xffffffffull);
+  s.seed_hi = (unsigned)(c->seed >> 32);
   s.replica = c->replica;
   s.skin = c->skin;
   s.r_ext = c->r_ext;
@@ -202,7 +227,8 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
     }
     s.nc[d] = std::max(1, (int)floor(c->box[d] / s.r_list));
   }
-  if ((long long)s.nc[0] * s.nc[1] * s.nc[2] > 4096ll * 2048ll || s.M > 4096 * 2048 - 1) {
+  if ((long long)s.nc[0] * s.nc[1] * s.nc[2] > 4096ll * 2048ll || s.M > 4096 * 2048 - 1 ||
+      ceil_div((long long)s.M * kGroup, kForceBlock) > kMaxMapBlocks) {
     delete h;
     return fail(nullptr, ADRESS_ERR_ARG, "too many cells or molecules for the device scans (max 8388607)");
   }
@@ -211,6 +237,24 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
     return fail(nullptr, ADRESS_ERR_ARG, "tf_n must be <= 4096");
   }
   s.ncell = s.nc[0] * s.nc[1] * s.nc[2];
+  for (int k = 0; k < kMaxNA; ++k) {
+    s.dt_m[k] = c->dt / s.mass[k];
+    s.f.frac[k] = (float)s.frac[k];
+  }
+  s.f.eps = (float)s.eps;
+  s.f.sig2 = (float)s.sig2;
+  s.f.rc_at = (float)s.rc_at;
+  s.f.rc_at2 = (float)s.rc_at2;
+  s.f.rc_cg2 = (float)s.rc_cg2;
+  s.f.cg_inv_dr = (float)s.cg_inv_dr;
+  s.f.fene_k = (float)s.fene_k;
+  s.f.fene_r02 = (float)s.fene_r02;
+  s.f.d_at = (float)s.d_at;
+  s.f.d_hyend = (float)(s.d_at + s.d_hy);
+  s.f.pi_half_over_dhy = (float)s.pi_half_over_dhy;
+  s.f.tf_inv_dx = (float)s.tf_inv_dx;
+  s.f.near_at = 1e-4f * (1.f + s.f.d_at);
+  s.f.near_hyend = 1e-4f * (1.f + s.f.d_hyend);
   s.cap = c->max_neighbors > 0 ? std::min(c->max_neighbors, s.M - 1) : auto_capacity(s);
 
   // ---- device buffers ----
@@ -222,15 +266,17 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   do {                                             \
     if (e == cudaSuccess) e = dalloc(h, &(ptr), (n)); \
   } while (0)
-  A(b.com_fx, M);
   A(b.com_ref, M);
-  A(b.com64, M);
-  A(b.dxc64, M);
-  A(b.molf, M);
-  if (h->precision == ADRESS_FP64) {
-    A(b.off64, N);
-  } else {
-    A(b.off32, N);
+  for (int p = 0; p < 2; ++p) {
+    A(b.com_fx[p], M);
+    if (h->precision == ADRESS_FP64) {
+      A(b.com64[p], M);
+      A(b.dxc64[p], M);
+      A(b.off64[p], N);
+    } else {
+      A(b.molf[p], M);
+      A(b.off32[p], N);
+    }
   }
   A(b.mcell, M);
   A(b.cell_count, s.ncell);
@@ -265,6 +311,8 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   A(b.hist, std::max(1, s.tf_n));
   A(b.nsamples, 1);
   A(b.ctrl, 1);
+  A(b.blk_ext, ceil_div((long long)M * kGroup, kForceBlock));
+  A(b.blk_n, 1);
 #undef A
   if (e != cudaSuccess) {
     adress_destroy(h);
@@ -310,6 +358,7 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   if (e == cudaSuccess) e = cudaMemsetAsync(b.hist, 0, sizeof(unsigned long long) * std::max(1, s.tf_n), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.nsamples, 0, sizeof(long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.com_ref, 0, sizeof(int4) * M, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.blk_n, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -383,7 +432,7 @@ adress_status adress_compute_forces(adress_handle h, double* energies) {
   if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
   adress_status st = build_lists_sync(h);
   if (st != ADRESS_OK) return st;
-  CUDA_OR_FAIL(h, launch_forces(h->sys, h->buf, h->precision, 0, energies != nullptr, h->stream));
+  CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 0, energies != nullptr, h->stream));
   if (energies) {
     CUDA_OR_FAIL(h, launch_energy_reduce(h->sys, h->buf, force_warps(h->sys), 4, h->stream));
     CUDA_OR_FAIL(h, cudaMemcpyAsync(energies, h->buf.result, 4 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -393,8 +442,11 @@ adress_status adress_compute_forces(adress_handle h, double* energies) {
   return ADRESS_OK;
 }
 
-// Capture `nsteps` steps into a graph: per step  [integrate+COM] -> [decide: sets the
-// conditional] -> IF(rebuild){lists} -> [forces + thermostat + second half kick].
+// Capture `nsteps` steps into one graph:
+//   prologue (half kick + drift + mapping) -> decide -> IF(rebuild){lists}
+//   { fused step -> decide -> IF(rebuild){lists} } x (nsteps - 1)
+//   last step (thermostat + second half kick, v and f stored)
+// `decide` sets the conditional of the IF node that follows it.
 static adress_status capture_steps(adress_handle h, int nsteps, cudaGraph_t* gout, cudaGraphExec_t* xout) {
   cudaGraph_t g = nullptr;
   CUDA_OR_FAIL(h, cudaGraphCreate(&g, 0));
@@ -417,7 +469,8 @@ static adress_status capture_steps(adress_handle h, int nsteps, cudaGraph_t* gou
     e = cudaStreamBeginCaptureToGraph(cs, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
                                       cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
-    cudaError_t le = launch_com(h->sys, h->buf, h->precision, 1, cs);
+    cudaError_t le = k == 0 ? launch_com(h->sys, h->buf, h->precision, 1, cs)
+                            : launch_step(h->sys, h->buf, h->precision, 2, 0, cs);
     if (le == cudaSuccess) le = launch_decide(h->sys, h->buf, 0, 1, cond, 1, cs);
     std::vector<cudaGraphNode_t> tail;
     cudaError_t ge = grab(tail);
@@ -442,15 +495,16 @@ static adress_status capture_steps(adress_handle h, int nsteps, cudaGraph_t* gou
     e = cudaStreamEndCapture(cs, &bb);
     if (e == cudaSuccess) e = le;
     if (e != cudaSuccess) break;
-
-    e = cudaStreamBeginCaptureToGraph(cs, g, &cnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) break;
-    le = launch_forces(h->sys, h->buf, h->precision, 1, 0, cs);
-    ge = grab(deps);
-    gg = g;
-    e = cudaStreamEndCapture(cs, &gg);
-    if (e == cudaSuccess) e = le;
-    if (e == cudaSuccess) e = ge;
+    deps.assign(1, cnode);
+  }
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCaptureToGraph(cs, g, deps.data(), nullptr, deps.size(), cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t le = launch_step(h->sys, h->buf, h->precision, 1, 0, cs);
+      cudaGraph_t gg = g;
+      e = cudaStreamEndCapture(cs, &gg);
+      if (e == cudaSuccess) e = le;
+    }
   }
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
@@ -474,28 +528,31 @@ adress_status adress_step(adress_handle h, int32_t nsteps) {
   if (nsteps == 0) return ADRESS_OK;
   if (h->eager) {
     for (int k = 0; k < nsteps; ++k) {
-      CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 1, h->stream));
+      if (k == 0) CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 1, h->stream));
+      else CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 2, 0, h->stream));
       CUDA_OR_FAIL(h, launch_decide(h->sys, h->buf, 0, 1, 0, 0, h->stream));
       Ctrl c;
       adress_status st = read_ctrl(h, &c);
       if (st != ADRESS_OK) return st;
       if (c.rebuild) CUDA_OR_FAIL(h, launch_rebuild(h->sys, h->buf, h->stream));
-      CUDA_OR_FAIL(h, launch_forces(h->sys, h->buf, h->precision, 1, 0, h->stream));
     }
+    CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 1, 0, h->stream));
     return ADRESS_OK;
   }
-  const int sizes[2] = {kGraphSteps, 1};
-  for (int k = 0; k < 2; ++k)
-    if (!h->exec[k]) {
-      adress_status st = capture_steps(h, sizes[k], &h->graph[k], &h->exec[k]);
-      if (st != ADRESS_OK) return st;
-    }
   int left = nsteps;
-  while (left >= kGraphSteps) {
-    CUDA_OR_FAIL(h, cudaGraphLaunch(h->exec[0], h->stream));
-    left -= kGraphSteps;
+  while (left > 0) {
+    const int n = std::min(left, kMaxGraphSteps);
+    auto it = h->graphs.find(n);
+    if (it == h->graphs.end()) {
+      cudaGraph_t g;
+      cudaGraphExec_t x;
+      adress_status st = capture_steps(h, n, &g, &x);
+      if (st != ADRESS_OK) return st;
+      it = h->graphs.emplace(n, std::make_pair(g, x)).first;
+    }
+    CUDA_OR_FAIL(h, cudaGraphLaunch(it->second.second, h->stream));
+    left -= n;
   }
-  while (left-- > 0) CUDA_OR_FAIL(h, cudaGraphLaunch(h->exec[1], h->stream));
   return ADRESS_OK;
 }
 
@@ -519,7 +576,8 @@ adress_status adress_com_lambda(adress_handle h, double* com, double* w) {
   if (!h || !com || !w) return ADRESS_ERR_ARG;
   if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
   CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream));
-  CUDA_OR_FAIL(h, launch_export_com(h->sys, h->buf, com, w, h->stream));
+  CUDA_OR_FAIL(h, launch_decide(h->sys, h->buf, 0, 0, 0, 0, h->stream));
+  CUDA_OR_FAIL(h, launch_export_com(h->sys, h->buf, h->precision, com, w, h->stream));
   return ADRESS_OK;
 }
 
@@ -536,6 +594,7 @@ adress_status adress_density_accumulate(adress_handle h) {
   if (!h) return ADRESS_ERR_ARG;
   if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
   CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream));
+  CUDA_OR_FAIL(h, launch_decide(h->sys, h->buf, 0, 0, 0, 0, h->stream));
   CUDA_OR_FAIL(h, launch_density(h->sys, h->buf, h->precision, h->stream));
   return ADRESS_OK;
 }
@@ -602,33 +661,35 @@ adress_status adress_list_stats(adress_handle h, int64_t* out) {
 adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out) {
   if (!h || !ms_out || reps < 1) return ADRESS_ERR_ARG;
   if (!h->bound || !h->lists_built) return fail(h, ADRESS_ERR_STATE, "bind state and build lists first");
-  cudaEvent_t ev[5];
-  for (int k = 0; k < 5; ++k) CUDA_OR_FAIL(h, cudaEventCreate(&ev[k]));
-  double acc[3] = {0, 0, 0};
-  adress_status st = ADRESS_OK;
-  for (int r = 0; r < reps && st == ADRESS_OK; ++r) {
-    cudaError_t e = cudaEventRecord(ev[0], h->stream);
-    if (e == cudaSuccess) e = launch_com(h->sys, h->buf, h->precision, 1, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-    if (e == cudaSuccess) e = launch_decide(h->sys, h->buf, 1, 1, 0, 0, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
-    if (e == cudaSuccess) e = launch_rebuild(h->sys, h->buf, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
-    if (e == cudaSuccess) e = launch_forces(h->sys, h->buf, h->precision, 1, 0, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4], h->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
-    float t0 = 0, t1 = 0, t2 = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[2], ev[3]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t2, ev[3], ev[4]);
-    if (e != cudaSuccess) st = fail(h, ADRESS_ERR_CUDA, std::string("kernel timing: ") + cudaGetErrorString(e));
-    acc[0] += t0;
-    acc[1] += t1;
-    acc[2] += t2;
+  cudaEvent_t ev[4];
+  for (int k = 0; k < 4; ++k) CUDA_OR_FAIL(h, cudaEventCreate(&ev[k]));
+  double acc[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaSuccess;
+  cudaStream_t st = h->stream;
+  auto timed = [&](int which, auto&& launch) {
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float t = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+    acc[which] += t;
+  };
+  timed(0, [&] { return launch_com(h->sys, h->buf, h->precision, 1, st); });
+  if (e == cudaSuccess) e = launch_decide(h->sys, h->buf, 1, 1, 0, 0, st);
+  timed(1, [&] { return launch_rebuild(h->sys, h->buf, st); });
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    timed(2, [&] { return launch_step(h->sys, h->buf, h->precision, 2, 0, st); });
+    if (e == cudaSuccess) e = launch_decide(h->sys, h->buf, 1, 1, 0, 0, st);
+    timed(1, [&] { return launch_rebuild(h->sys, h->buf, st); });
   }
-  for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
-  if (st != ADRESS_OK) return st;
-  for (int k = 0; k < 3; ++k) ms_out[k] = (float)(acc[k] / reps);
+  timed(3, [&] { return launch_step(h->sys, h->buf, h->precision, 1, 0, st); });
+  for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+  if (e != cudaSuccess) return fail(h, ADRESS_ERR_CUDA, std::string("kernel timing: ") + cudaGetErrorString(e));
+  ms_out[0] = (float)acc[0];
+  ms_out[1] = (float)(acc[1] / (reps + 1));
+  ms_out[2] = (float)(acc[2] / reps);
+  ms_out[3] = (float)acc[3];
   return ADRESS_OK;
 }
 

@@ -14,8 +14,6 @@ constexpr int kGroup = 4;  // threads per molecule in the force kernel
 
 // Device control block: list-validity trackers, error word, counters.
 struct Ctrl {
-  unsigned int maxdisp2;  // float bits of the largest squared COM displacement since the last build
-  unsigned int maxext;    // float bits of the largest atom-to-COM distance this step
   int rebuild;            // decision for the current step
   int err;                // first device error (adress_status), 0 = none
   int n_hr;               // high-resolution work items (first in `items`)
@@ -25,19 +23,27 @@ struct Ctrl {
   float ext_now;
   int max_nn;
   int err_info;
-  int pad;
+  int parity;  // which half of the double-buffered molecule arrays is current
 };
 
 // Per-system constants, passed by value to every kernel.
 struct Sys {
   int M, NA, N;
+  int fp64;  // 1: FP64 path, 0: FP32 mixed path
   double L[3], halfL[3];
-  double fx_inv[3];    // 2^32 / L  (fixed-point COM)
-  float fx_scale[3];   // L / 2^32
+  long long Lbits[3];           // bit patterns of L (wrap tests on the integer pipe)
+  double fx_inv[3];             // 2^32 / L  (fixed-point COM)
+  float fx_scale[3];            // L / 2^32
+  unsigned long long fxK[3];    // floor(2^fxq / L), in [2^63, 2^64)
+  int fxq[3];
+  unsigned xc32;                // slab centre in 32-bit fixed point
   float Lf[3];
   double xc, d_at, d_hy, d_hr;  // d_hr: high-resolution candidate bound at list build
   double pi_half_over_dhy;
   double mass[kMaxNA], inv_mass[kMaxNA], frac[kMaxNA], Mtot;
+  double hdt_m[kMaxNA];          // dt / (2 m)
+  double amp[kMaxNA], gm[kMaxNA];  // Langevin: sqrt(24 gamma kT m / dt), gamma m
+  float ampf[kMaxNA], gmf[kMaxNA];
   double eps, sig2, rc_at2;
   int nb;
   int bonds[2 * kMaxBonds];
@@ -49,12 +55,20 @@ struct Sys {
   double tf_inv_dx, tf_dx;
   double kT, gamma, dt;
   unsigned long long seed;
+  unsigned seed_lo, seed_hi;
   long long replica;
   double skin, r_ext, r_list, r_list2, reach_at2;  // reach_at: rc_at + 2 r_ext
   double rc_at, rc_cg;
   int nc[3];
   int ncell;
   int cap;  // neighbour-list capacity per molecule
+  double dt_m[kMaxNA];  // dt / m (both half kicks of a fused step)
+  // float copies of the parameters the FP32 path uses (no run-time double->float work)
+  struct {
+    float eps, sig2, rc_at, rc_at2, rc_cg2, cg_inv_dr, fene_k, fene_r02;
+    float d_at, d_hyend, pi_half_over_dhy, tf_inv_dx, near_at, near_hyend;
+    float frac[kMaxNA];
+  } f;
 };
 
 // Device buffers owned by the handle.
@@ -63,15 +77,15 @@ struct Bufs {
   double* x;
   double* v;
   void* f;
-  // per molecule
-  int4* com_fx;    // fixed-point COM (uint32 bits) + float bits of w
-  int4* com_ref;   // fixed-point COM at the last list build
-  double4_32a* com64;  // FP64 COM + w
-  double* dxc64;   // signed x distance to the slab centre
-  float2* molf;    // (dxc, w) in float
-  // per atom
-  double4_32a* off64;  // COM-relative atom offsets
-  float4* off32;
+  // per molecule, double-buffered: [parity] is the mapping of the current positions
+  int4* com_fx[2];         // fixed-point COM (uint32 bits) + float bits of w
+  int4* com_ref;           // fixed-point COM at the last list build
+  double4_32a* com64[2];   // FP64 path: COM + w
+  double* dxc64[2];        // FP64 path: signed x distance to the slab centre
+  float2* molf[2];         // FP32 path: (signed x distance, 1 if in the hybrid layer)
+  // per atom, double-buffered
+  double4_32a* off64[2];   // COM-relative atom offsets (FP64 path)
+  float4* off32[2];        // (FP32 path)
   // lists
   int* mcell;       // Morton rank of each molecule's cell
   int* cell_count;  // [ncell]
@@ -95,6 +109,8 @@ struct Bufs {
   // reductions
   double* part;      // per-warp partials
   double* result;    // reduced results [8]
+  float2* blk_ext;           // per-block (max extent, max displacement^2) of the last mapping
+  int* blk_n;                // number of valid entries in blk_ext
   unsigned long long* hist;  // density histogram [tf_n]
   long long* nsamples;
   Ctrl* ctrl;
@@ -109,27 +125,6 @@ __device__ __forceinline__ double minimg_cmp(double d, double L, double halfL) {
   if (d > halfL) d -= L;
   else if (d < -halfL) d += L;
   return d;
-}
-
-// ---- Philox4x64-10 (Salmon et al., SC'11): published multipliers and Weyl constants ----
-__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
-                                              unsigned long long k1) {
-  const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
-  const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += W0;
-      k1 += W1;
-    }
-    unsigned long long lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
-    unsigned long long lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
-    unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0;
-    c[1] = lo1;
-    c[2] = n2;
-    c[3] = lo0;
-  }
 }
 
 // ---- precision policies --------------------------------------------------------------
@@ -151,17 +146,19 @@ cudaError_t launch_com(const Sys& s, const Bufs& b, int precision, int integrate
 cudaError_t launch_decide(const Sys& s, const Bufs& b, int force, int advance_step,
                           cudaGraphConditionalHandle h, int use_handle, cudaStream_t st);
 cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st);
-cudaError_t launch_forces(const Sys& s, const Bufs& b, int precision, int step_mode, int energy,
-                          cudaStream_t st);
+// mode: 0 conservative forces, 1 last step of a run (thermostat + second half kick),
+// 2 fused step (thermostat + both half kicks + drift + next mapping)
+cudaError_t launch_step(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st);
 cudaError_t launch_energy_reduce(const Sys& s, const Bufs& b, int nparts, int nvals, cudaStream_t st);
 cudaError_t launch_kinetic(const Sys& s, const Bufs& b, cudaStream_t st);
 cudaError_t launch_density(const Sys& s, const Bufs& b, int precision, cudaStream_t st);
 cudaError_t launch_tf_update(const Sys& s, const Bufs& b, double alpha, cudaStream_t st);
-cudaError_t launch_export_com(const Sys& s, const Bufs& b, double* com, double* w, cudaStream_t st);
+cudaError_t launch_export_com(const Sys& s, const Bufs& b, int precision, double* com, double* w, cudaStream_t st);
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 constexpr int kForceBlock = 128;
+constexpr int kMaxMapBlocks = 1 << 16;  // per-block extent records (M <= 2^21 molecules)
 // Warps launched by the force kernel (one energy partial each).
 inline int force_warps(const Sys& s) { return ceil_div((long long)s.M * kGroup, kForceBlock) * (kForceBlock / 32); }
 

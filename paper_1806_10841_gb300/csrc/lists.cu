@@ -29,7 +29,7 @@ __global__ void k_rb_zero(Sys s, Bufs b) {
 __global__ void k_rb_count(Sys s, Bufs b) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= s.M) return;
-  const int4 C = b.com_fx[a];
+  const int4 C = b.com_fx[b.ctrl->parity][a];
   const int cx = cell_of((unsigned)C.x, s.nc[0]), cy = cell_of((unsigned)C.y, s.nc[1]),
             cz = cell_of((unsigned)C.z, s.nc[2]);
   const int r = b.cell_rank[(cx * s.nc[1] + cy) * s.nc[2] + cz];
@@ -165,7 +165,9 @@ __global__ void k_rb_sort(Sys s, Bufs b) {
 __global__ void k_rb_flag(Sys s, Bufs b) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= s.M) return;
-  b.flag[k] = fabs(b.dxc64[b.sorted[k]]) < s.d_hr ? 1 : 0;
+  const int a = b.sorted[k], cur = b.ctrl->parity;
+  const double d = s.fp64 ? fabs(b.dxc64[cur][a]) : (double)fabsf(b.molf[cur][a].x);
+  b.flag[k] = d < s.d_hr + (s.fp64 ? 0.0 : 1e-3) ? 1 : 0;
 }
 
 __global__ void k_rb_items(Sys s, Bufs b) {
@@ -188,7 +190,8 @@ __global__ void __launch_bounds__(128) k_rb_nbr(Sys s, Bufs b) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= s.M) return;
   const int a = b.items[t];
-  const int4 C = b.com_fx[a];
+  const int4* com = b.com_fx[b.ctrl->parity];
+  const int4 C = com[a];
   b.com_ref[a] = C;
   const int c0 = cell_of((unsigned)C.x, s.nc[0]), c1 = cell_of((unsigned)C.y, s.nc[1]),
             c2 = cell_of((unsigned)C.z, s.nc[2]);
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(128) k_rb_nbr(Sys s, Bufs b) {
         for (int p = b.cell_start[r]; p < pe; ++p) {
           const int m = b.sorted[p];
           if (m == a) continue;
-          const int4 D = b.com_fx[m];
+          const int4 D = com[m];
           const float d0 = (float)(int)((unsigned)C.x - (unsigned)D.x) * s.fx_scale[0];
           const float d1 = (float)(int)((unsigned)C.y - (unsigned)D.y) * s.fx_scale[1];
           const float d2 = (float)(int)((unsigned)C.z - (unsigned)D.z) * s.fx_scale[2];

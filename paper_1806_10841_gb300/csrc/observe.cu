@@ -1,0 +1,255 @@
+// Control and observables: the list-rebuild decision (which also flips the current half of
+// the double-buffered molecule arrays), deterministic FP64 reductions, the COM density
+// profile and the thermodynamic-force iteration, and the FP64 export of centres of mass.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace adress {
+
+// Runs after every kernel that maps positions (into the non-current half), as one block:
+// reduces the mapping's per-block records to the largest molecule extent and the largest
+// centre displacement since the last list build, then decides whether to rebuild the
+// lists: when a centre moved more than skin/2 (it could have changed class or found a new
+// partner) or when the widest molecule makes max(rc_cg, rc_at + 2 ext) + 2 disp exceed the
+// list cutoff.  Flips the current half of the molecule arrays.
+__global__ void __launch_bounds__(1024) k_decide(Sys s, Bufs b, int force, int advance,
+                                                 cudaGraphConditionalHandle h, int use_h) {
+  __shared__ float sm[2][32];
+  const int n = *b.blk_n;
+  float e = 0.f, d = 0.f;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const float2 r = b.blk_ext[k];
+    e = fmaxf(e, r.x);
+    d = fmaxf(d, r.y);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
+    d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sm[0][threadIdx.x >> 5] = e;
+    sm[1][threadIdx.x >> 5] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+    e = fmaxf(e, sm[0][k]);
+    d = fmaxf(d, sm[1][k]);
+  }
+  Ctrl* c = b.ctrl;
+  const float ext = fmaxf(e, sm[0][0]);
+  const float md = sqrtf(fmaxf(d, sm[1][0]));
+  const double cut = fmax(s.rc_cg, s.rc_at + 2.0 * (double)ext);
+  int rb = force || (md > 0.5 * s.skin) || (cut + 2.0 * md > s.r_list);
+  if (cut > s.r_list) set_error(c, ADRESS_ERR_EXTENT, (int)(ext * 1000));
+  c->rebuild = rb;
+  c->ext_now = ext;
+  if (rb) c->rebuilds += 1;
+  if (advance) c->step += 1;
+  c->parity ^= 1;  // the mapping just written becomes current
+  if (use_h) cudaGraphSetConditional(h, (unsigned int)rb);
+}
+
+// ---- deterministic FP64 reductions: per-block partials, then one fixed-order block ----
+
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&v)[NV], double* part, int slot) {
+  __shared__ double sm[32][NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int j = 0; j < NV; ++j) sm[w][j] = v[j];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+      double acc = 0.0;
+      for (int q = 0; q < nw; ++q) acc += sm[q][j];
+      part[(size_t)slot * NV + j] = acc;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_reduce_parts(const double* part, int nparts, int nv,
+                                                       double* out) {
+  __shared__ double sm[32][8];
+  double acc[8];
+  for (int j = 0; j < nv; ++j) acc[j] = 0.0;
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x)
+    for (int j = 0; j < nv; ++j) acc[j] += part[(size_t)p * nv + j];
+  for (int j = 0; j < nv; ++j)
+    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+  if ((threadIdx.x & 31) == 0)
+    for (int j = 0; j < nv; ++j) sm[threadIdx.x >> 5][j] = acc[j];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int j = 0; j < nv; ++j) {
+      double t = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sm[q][j];
+      out[j] = t;
+    }
+}
+
+template <int NA>
+__global__ void __launch_bounds__(256) k_kinetic(Sys s, Bufs b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (i < s.N) {
+    const double m = s.mass[i % NA];
+    for (int d = 0; d < 3; ++d) {
+      double u = b.v[(size_t)d * s.N + i];
+      v[0] += 0.5 * m * u * u;
+      v[1 + d] = m * u;
+    }
+  }
+  block_partials<4>(v, b.part, blockIdx.x);
+}
+
+// Centre-of-mass x in double exactly as R = sum_k m_k (x_0 + minimg(x_k - x_0)) / M, wrapped.
+template <int NA>
+__device__ double com_x64(const Sys& s, const double* x, int a) {
+  const double x0 = x[a * NA];
+  double acc = 0.0;
+  for (int k = 0; k < NA; ++k) acc += s.mass[k] * (x0 + minimg_cmp(x[a * NA + k] - x0, s.L[0], s.halfL[0]));
+  double r = acc / s.Mtot;
+  r -= s.L[0] * floor(r / s.L[0]);
+  if (r >= s.L[0]) r -= s.L[0];
+  return r;
+}
+
+// COM histogram folded about the slab centre: bin floor(|dxc| / tf_dx), integer atomics.
+// The FP32 path takes |dxc| from its float mapping and recomputes it in double for the
+// few molecules within 1e-4 of a bin edge, so the bin is the one the double value gives.
+template <int NA>
+__global__ void k_density(Sys s, Bufs b) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a == 0) atomicAdd((unsigned long long*)b.nsamples, 1ull);
+  if (a >= s.M) return;
+  const int cur = b.ctrl->parity;
+  double d;
+  if (s.fp64) {
+    d = fabs(b.dxc64[cur][a]);
+  } else {
+    d = (double)fabsf(b.molf[cur][a].x);
+    const double u = d / s.tf_dx, fr = u - floor(u);
+    if (fr < 1e-4 || fr > 1.0 - 1e-4) d = fabs(minimg_cmp(com_x64<NA>(s, b.x, a) - s.xc, s.L[0], s.halfL[0]));
+  }
+  const int k = (int)floor(d / s.tf_dx);
+  if (k < s.tf_n) atomicAdd(&b.hist[k], 1ull);
+}
+
+// Thermodynamic-force iteration on the accumulated profile (one block, tf_n nodes):
+// rho_k = counts_k / (nsamples 2 dx Ly Lz), g_k = (rho_k - rho_{k-1})/dx, g_0 = 0,
+// three-point moving average, tf_k -= alpha g_k on hybrid-layer nodes, then reset.
+__global__ void k_tf_update(Sys s, Bufs b, double alpha) {
+  extern __shared__ double g[];
+  const int n = s.tf_n;
+  const double ns = (double)(*b.nsamples);
+  const double vol = ns * 2.0 * s.tf_dx * s.L[1] * s.L[2];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double gk = 0.0;
+    if (k > 0 && ns > 0) gk = ((double)b.hist[k] / vol - (double)b.hist[k - 1] / vol) / s.tf_dx;
+    g[k] = gk;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double sum = 0.0;
+    int cnt = 0;
+    for (int q = k - 1; q <= k + 1; ++q)
+      if (q >= 0 && q < n) {
+        sum += g[q];
+        ++cnt;
+      }
+    const double dk = k * s.tf_dx;
+    if (ns > 0 && dk >= s.d_at && dk <= s.d_at + s.d_hy) {
+      double t = b.tf64[k] - alpha * sum / cnt;
+      b.tf64[k] = t;
+      b.tf32[k] = (float)t;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) b.hist[k] = 0ull;
+  if (threadIdx.x == 0) *b.nsamples = 0;
+}
+
+// FP64 centres of mass of the current positions (computed from x as the definition
+// states) and the resolution values the force kernels use.
+template <int NA>
+__global__ void k_export_com(Sys s, Bufs b, double* com, double* w) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= s.M) return;
+  const size_t N = (size_t)s.N;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < 3; ++d) {
+    const double x0 = b.x[d * N + a * NA];
+    for (int k = 0; k < NA; ++k)
+      acc[d] += s.mass[k] * (x0 + minimg_cmp(b.x[d * N + a * NA + k] - x0, s.L[d], s.halfL[d]));
+    double r = acc[d] / s.Mtot;
+    r -= s.L[d] * floor(r / s.L[d]);
+    if (r >= s.L[d]) r -= s.L[d];
+    com[(size_t)d * s.M + a] = r;
+  }
+  const int cur = b.ctrl->parity;
+  w[a] = s.fp64 ? b.com64[cur][a].w : (double)__int_as_float(b.com_fx[cur][a].w);
+}
+
+// ---- launchers -----------------------------------------------------------------------
+
+cudaError_t launch_decide(const Sys& s, const Bufs& b, int force, int advance,
+                          cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
+  k_decide<<<1, 1024, 0, st>>>(s, b, force, advance, h, use_h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_reduce(const Sys& s, const Bufs& b, int nparts, int nvals, cudaStream_t st) {
+  k_reduce_parts<<<1, 1024, 0, st>>>(b.part, nparts, nvals, b.result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kinetic(const Sys& s, const Bufs& b, cudaStream_t st) {
+  const int blocks = ceil_div(s.N, 256);
+  switch (s.NA) {
+    case 1: k_kinetic<1><<<blocks, 256, 0, st>>>(s, b); break;
+    case 2: k_kinetic<2><<<blocks, 256, 0, st>>>(s, b); break;
+    case 3: k_kinetic<3><<<blocks, 256, 0, st>>>(s, b); break;
+    default: k_kinetic<4><<<blocks, 256, 0, st>>>(s, b); break;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_energy_reduce(s, b, blocks, 4, st);
+}
+
+cudaError_t launch_density(const Sys& s, const Bufs& b, int, cudaStream_t st) {
+  const int blocks = ceil_div(s.M, 256);
+  switch (s.NA) {
+    case 1: k_density<1><<<blocks, 256, 0, st>>>(s, b); break;
+    case 2: k_density<2><<<blocks, 256, 0, st>>>(s, b); break;
+    case 3: k_density<3><<<blocks, 256, 0, st>>>(s, b); break;
+    default: k_density<4><<<blocks, 256, 0, st>>>(s, b); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tf_update(const Sys& s, const Bufs& b, double alpha, cudaStream_t st) {
+  if (s.tf_n <= 0) return cudaSuccess;
+  k_tf_update<<<1, 256, sizeof(double) * s.tf_n, st>>>(s, b, alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_com(const Sys& s, const Bufs& b, int, double* com, double* w, cudaStream_t st) {
+  const int blocks = ceil_div(s.M, 256);
+  switch (s.NA) {
+    case 1: k_export_com<1><<<blocks, 256, 0, st>>>(s, b, com, w); break;
+    case 2: k_export_com<2><<<blocks, 256, 0, st>>>(s, b, com, w); break;
+    case 3: k_export_com<3><<<blocks, 256, 0, st>>>(s, b, com, w); break;
+    default: k_export_com<4><<<blocks, 256, 0, st>>>(s, b, com, w); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace adress
