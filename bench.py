@@ -200,10 +200,8 @@ def cpu_baseline_sample(s, x, v):
 
 
 def run_block(sim, nsteps=MD_PER_BLOCK):
-    for _ in range(nsteps // SAMPLE_EVERY):
-        sim.step(SAMPLE_EVERY)
-        sim.density_accumulate()
-    sim.tf_update(TF_ALPHA)
+    """One bench step: a thermodynamic-force iteration block as a single captured graph."""
+    sim.run(nsteps, sample_every=SAMPLE_EVERY, tf_update=True, alpha=TF_ALPHA)
 
 
 def main():
@@ -245,9 +243,7 @@ def main():
         sim = adress.AdResS(s, precision=args.precision, device=f"cuda:{local}")
         sim.set_state(x0, v0)
         sim.compute_forces(energies=False)
-        sim.step(args.profile)
-        sim.density_accumulate()
-        sim.tf_update(TF_ALPHA)
+        sim.run(args.profile, sample_every=SAMPLE_EVERY, tf_update=True, alpha=TF_ALPHA)
         sim.check()
         print(json.dumps({"profile_steps": args.profile, "atoms": s.N, "lists": sim.list_stats()}))
         sim.close()
@@ -295,9 +291,9 @@ def main():
     rb0 = sim.list_stats()["rebuilds"]
     total_s, ms, clocks = timed(sim, args.steps, args.warmup)
     rebuilds = sim.list_stats()["rebuilds"] - rb0
-    # kernels per bench step: per step(10) graph 1 prologue + 9 fused + 1 last + 10 decide;
-    # per density sample map + decide + histogram; one TF update; 14 kernels per list rebuild
-    per_block = (MD_PER_BLOCK // SAMPLE_EVERY) * (SAMPLE_EVERY + 1 + SAMPLE_EVERY + 3) + 1
+    # kernels per bench step (one graph): 1 prologue + 99 fused + 1 last + 100 decide
+    # + 10 density samples + 1 TF update; 14 kernels per list rebuild
+    per_block = 1 + (MD_PER_BLOCK - 1) + 1 + MD_PER_BLOCK + MD_PER_BLOCK // SAMPLE_EVERY + 1
     launches = args.steps * per_block + 14 * rebuilds
     if dist:
         t = torch.tensor([total_s], device=dev, dtype=torch.float64)
@@ -350,6 +346,7 @@ def main():
         f_ref, _ = oracle.Oracle(s).forces(x0)
         errs = {}
         for prec, sm in ((other, sim2),):
+            sm.set_tf(np.zeros(sm.tf_n))
             sm.set_state(x0, v0)
             fg, _ = sm.forces()
             errs[prec] = math.sqrt(((fg - f_ref) ** 2).sum() / (f_ref ** 2).sum())

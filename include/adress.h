@@ -135,6 +135,16 @@ adress_status adress_compute_forces(adress_handle h, double* energies);
  * per-kernel profilers cannot see kernels inside graphs that hold conditional nodes. */
 adress_status adress_step(adress_handle h, int32_t nsteps);
 
+/* One thermodynamic-force iteration block (Sec. "Free energy corrections and the
+ * thermodynamic force": the correction is built from the density profile and refined
+ * iteratively): advance nsteps exactly as adress_step does; after every sample_every
+ * steps (0 = never) add the folded COM histogram of the positions at that time level to
+ * the accumulated profile; at the end, if tf_update != 0, apply one thermodynamic-force
+ * iteration with alpha (as adress_tf_update) and reset the profile.  The whole block is
+ * one captured CUDA graph (cached per argument set, nsteps <= 1000).  Asynchronous. */
+adress_status adress_run(adress_handle h, int32_t nsteps, int32_t sample_every, int32_t tf_update,
+                         double alpha);
+
 /* Time level of the bound state (keys the thermostat noise). */
 adress_status adress_set_step(adress_handle h, int64_t step);
 adress_status adress_get_step(adress_handle h, int64_t* step); /* synchronises */
@@ -164,6 +174,12 @@ adress_status adress_density_reset(adress_handle h);
 adress_status adress_tf_update(adress_handle h, double alpha);
 adress_status adress_set_tf(adress_handle h, const double* tf_host, int32_t n);
 adress_status adress_get_tf(adress_handle h, double* tf_host, int32_t n); /* synchronises */
+
+/* Copy the current Verlet lists to the host: items host int32 [M] (molecule of each work
+ * item, high-resolution candidates first), nn host int32 [M] (neighbour count per item),
+ * nbr host int32 [M * capacity] with neighbour slot q of item t at nbr[t * capacity + q].
+ * Synchronises.  (Capacity from adress_list_stats.) */
+adress_status adress_list_export(adress_handle h, int32_t* items, int32_t* nn, int32_t* nbr);
 
 /* List statistics (host int64 [8]): {n_high_resolution_items, n_cg_items, rebuilds,
  * max_neighbours_at_last_build, capacity, n_cells, 0, 0}.  Synchronises. */

@@ -21,9 +21,10 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "neighbour list ov
 
 # Every symbol include/adress.h declares (checked by the CPU test suite).
 EXPORTS = ["adress_init", "adress_bind_state", "adress_build_lists", "adress_compute_forces",
-           "adress_step", "adress_set_step", "adress_get_step", "adress_com_lambda", "adress_kinetic",
+           "adress_step", "adress_run", "adress_set_step", "adress_get_step", "adress_com_lambda", "adress_kinetic",
            "adress_density_accumulate", "adress_density_get", "adress_density_reset",
-           "adress_tf_update", "adress_set_tf", "adress_get_tf", "adress_list_stats", "adress_time_kernels",
+           "adress_tf_update", "adress_set_tf", "adress_get_tf", "adress_list_stats", "adress_list_export",
+           "adress_time_kernels",
            "adress_check",
            "adress_last_error", "adress_status_string", "adress_destroy"]
 
@@ -74,6 +75,7 @@ def load_library(path: str = LIB_PATH):
         "adress_build_lists": ([H], C.c_int),
         "adress_compute_forces": ([H, d], C.c_int),
         "adress_step": ([H, C.c_int32], C.c_int),
+        "adress_run": ([H, C.c_int32, C.c_int32, C.c_int32, C.c_double], C.c_int),
         "adress_set_step": ([H, C.c_int64], C.c_int),
         "adress_get_step": ([H, i64p], C.c_int),
         "adress_com_lambda": ([H, vp, vp], C.c_int),
@@ -85,6 +87,7 @@ def load_library(path: str = LIB_PATH):
         "adress_set_tf": ([H, d, C.c_int32], C.c_int),
         "adress_get_tf": ([H, d, C.c_int32], C.c_int),
         "adress_list_stats": ([H, i64p], C.c_int),
+        "adress_list_export": ([H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
         "adress_time_kernels": ([H, C.c_int32, C.POINTER(C.c_float)], C.c_int),
         "adress_check": ([H], C.c_int),
         "adress_last_error": ([H], C.c_char_p),
@@ -209,6 +212,11 @@ class AdResS:
     def step(self, nsteps: int):
         self._call("adress_step", C.c_int32(int(nsteps)))
 
+    def run(self, nsteps: int, sample_every: int = 0, tf_update: bool = False, alpha: float = 0.0):
+        """One thermodynamic-force iteration block as a single captured graph."""
+        self._call("adress_run", C.c_int32(int(nsteps)), C.c_int32(int(sample_every)),
+                   C.c_int32(1 if tf_update else 0), C.c_double(float(alpha)))
+
     def set_step(self, step: int):
         self._call("adress_set_step", C.c_int64(int(step)))
 
@@ -259,6 +267,20 @@ class AdResS:
         self._call("adress_list_stats", out.ctypes.data_as(C.POINTER(C.c_int64)))
         keys = ["n_hr", "n_cg", "rebuilds", "max_nn", "capacity", "n_cells"]
         return {k: int(out[i]) for i, k in enumerate(keys)}
+
+    def neighbour_lists(self):
+        """(items, nn, nbr[M, capacity]) of the current lists, on the host."""
+        cap = self.list_stats()["capacity"]
+        items = np.zeros(self.M, dtype=np.int32)
+        nn = np.zeros(self.M, dtype=np.int32)
+        nbr = np.zeros(self.M * cap, dtype=np.int32)
+        p32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+        self._call("adress_list_export", p32(items), p32(nn), p32(nbr))
+        return items, nn, nbr.reshape(self.M, cap)
+
+    def neighbour_pairs(self):
+        items, nn, nbr = self.neighbour_lists()
+        return {(int(items[t]), int(nbr[t, q])) for t in range(self.M) for q in range(nn[t])}
 
     def time_kernels(self, reps: int = 20):
         """ms per launch of the step kernels (advances the state by reps + 1 steps)."""

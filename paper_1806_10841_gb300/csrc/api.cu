@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <string>
 #include <utility>
 #include <vector>
@@ -26,8 +27,8 @@ struct adress_ctx {
   bool lists_built = false;
   std::vector<void*> allocs;
   int nparts = 0;
-  // captured step graphs keyed by their number of steps
-  std::map<int, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
+  // captured step graphs keyed by (steps, sample interval, TF update, alpha bits)
+  std::map<std::tuple<int, int, int, uint64_t>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   bool eager = false;  // ADRESS_EAGER=1: launch kernel by kernel (for per-kernel profilers)
 };
 
@@ -227,8 +228,7 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
     }
     s.nc[d] = std::max(1, (int)floor(c->box[d] / s.r_list));
   }
-  if ((long long)s.nc[0] * s.nc[1] * s.nc[2] > 4096ll * 2048ll || s.M > 4096 * 2048 - 1 ||
-      ceil_div((long long)s.M * kGroup, kForceBlock) > kMaxMapBlocks) {
+  if ((long long)s.nc[0] * s.nc[1] * s.nc[2] > 4096ll * 2048ll || s.M > 4096 * 2048 - 1) {
     delete h;
     return fail(nullptr, ADRESS_ERR_ARG, "too many cells or molecules for the device scans (max 8388607)");
   }
@@ -286,6 +286,7 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   A(b.flag, M);
   A(b.pos, M + 1);
   A(b.items, M);
+  A(b.item_of, M);
   A(b.nn, M);
   A(b.nbr, (size_t)s.cap * M);
   A(b.scan_tmp, 4096);
@@ -311,8 +312,6 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   A(b.hist, std::max(1, s.tf_n));
   A(b.nsamples, 1);
   A(b.ctrl, 1);
-  A(b.blk_ext, ceil_div((long long)M * kGroup, kForceBlock));
-  A(b.blk_n, 1);
 #undef A
   if (e != cudaSuccess) {
     adress_destroy(h);
@@ -358,7 +357,6 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   if (e == cudaSuccess) e = cudaMemsetAsync(b.hist, 0, sizeof(unsigned long long) * std::max(1, s.tf_n), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.nsamples, 0, sizeof(long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.com_ref, 0, sizeof(int4) * M, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b.blk_n, 0, sizeof(int), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -391,9 +389,9 @@ static adress_status read_ctrl(adress_handle h, Ctrl* c) {
 // Map positions, rebuild lists; grow the capacity and redo while a list overflows.
 static adress_status build_lists_sync(adress_handle h) {
   for (int attempt = 0; attempt < 4; ++attempt) {
-    CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream));
-    CUDA_OR_FAIL(h, launch_decide(h->sys, h->buf, 1, 0, 0, 0, h->stream));
+    CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream, DecideArgs{1, 0, 0, 0}));
     CUDA_OR_FAIL(h, launch_rebuild(h->sys, h->buf, h->stream));
+    CUDA_OR_FAIL(h, launch_max_nn(h->sys, h->buf, h->stream));
     Ctrl c;
     adress_status st = read_ctrl(h, &c);
     if (st != ADRESS_OK) return st;
@@ -447,7 +445,8 @@ adress_status adress_compute_forces(adress_handle h, double* energies) {
 //   { fused step -> decide -> IF(rebuild){lists} } x (nsteps - 1)
 //   last step (thermostat + second half kick, v and f stored)
 // `decide` sets the conditional of the IF node that follows it.
-static adress_status capture_steps(adress_handle h, int nsteps, cudaGraph_t* gout, cudaGraphExec_t* xout) {
+static adress_status capture_steps(adress_handle h, int nsteps, int sample_every, int tf_update, double alpha,
+                                   cudaGraph_t* gout, cudaGraphExec_t* xout) {
   cudaGraph_t g = nullptr;
   CUDA_OR_FAIL(h, cudaGraphCreate(&g, 0));
   std::vector<cudaGraphNode_t> deps;
@@ -469,9 +468,9 @@ static adress_status capture_steps(adress_handle h, int nsteps, cudaGraph_t* gou
     e = cudaStreamBeginCaptureToGraph(cs, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
                                       cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
-    cudaError_t le = k == 0 ? launch_com(h->sys, h->buf, h->precision, 1, cs)
-                            : launch_step(h->sys, h->buf, h->precision, 2, 0, cs);
-    if (le == cudaSuccess) le = launch_decide(h->sys, h->buf, 0, 1, cond, 1, cs);
+    const DecideArgs da{0, 1, 1, cond};  // the mapping kernel's last block sets the conditional
+    cudaError_t le = k == 0 ? launch_com(h->sys, h->buf, h->precision, 1, cs, da)
+                            : launch_step(h->sys, h->buf, h->precision, 2, 0, cs, da);
     std::vector<cudaGraphNode_t> tail;
     cudaError_t ge = grab(tail);
     cudaGraph_t gg = g;
@@ -496,11 +495,23 @@ static adress_status capture_steps(adress_handle h, int nsteps, cudaGraph_t* gou
     if (e == cudaSuccess) e = le;
     if (e != cudaSuccess) break;
     deps.assign(1, cnode);
+    // positions of time level k+1 are mapped and current here: sample the profile
+    if (sample_every > 0 && (k + 1) % sample_every == 0) {
+      e = cudaStreamBeginCaptureToGraph(cs, g, deps.data(), nullptr, deps.size(), cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) break;
+      le = launch_density(h->sys, h->buf, h->precision, cs);
+      ge = grab(deps);
+      gg = g;
+      e = cudaStreamEndCapture(cs, &gg);
+      if (e == cudaSuccess) e = le;
+      if (e == cudaSuccess) e = ge;
+    }
   }
   if (e == cudaSuccess) {
     e = cudaStreamBeginCaptureToGraph(cs, g, deps.data(), nullptr, deps.size(), cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       cudaError_t le = launch_step(h->sys, h->buf, h->precision, 1, 0, cs);
+      if (le == cudaSuccess && tf_update) le = launch_tf_update(h->sys, h->buf, alpha, cs);
       cudaGraph_t gg = g;
       e = cudaStreamEndCapture(cs, &gg);
       if (e == cudaSuccess) e = le;
@@ -521,6 +532,45 @@ static adress_status capture_steps(adress_handle h, int nsteps, cudaGraph_t* gou
   return ADRESS_OK;
 }
 
+static adress_status launch_graph(adress_handle h, int n, int sample_every, int tf_update, double alpha) {
+  uint64_t abits;
+  memcpy(&abits, &alpha, sizeof(abits));
+  const auto key = std::make_tuple(n, sample_every, tf_update, tf_update ? abits : 0ull);
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    cudaGraph_t g;
+    cudaGraphExec_t x;
+    adress_status st = capture_steps(h, n, sample_every, tf_update, alpha, &g, &x);
+    if (st != ADRESS_OK) return st;
+    it = h->graphs.emplace(key, std::make_pair(g, x)).first;
+  }
+  CUDA_OR_FAIL(h, cudaGraphLaunch(it->second.second, h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_run(adress_handle h, int32_t nsteps, int32_t sample_every, int32_t tf_update, double alpha) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (nsteps < 1 || nsteps > 1000 || sample_every < 0) return fail(h, ADRESS_ERR_ARG, "need 1 <= nsteps <= 1000, sample_every >= 0");
+  if (!h->bound || !h->lists_built) return fail(h, ADRESS_ERR_STATE, "bind state and build lists first");
+  if (h->eager) {
+    for (int k = 0; k < nsteps; ++k) {
+      const DecideArgs da{0, 1, 0, 0};
+      if (k == 0) CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 1, h->stream, da));
+      else CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 2, 0, h->stream, da));
+      Ctrl c;
+      adress_status st = read_ctrl(h, &c);
+      if (st != ADRESS_OK) return st;
+      if (c.rebuild) CUDA_OR_FAIL(h, launch_rebuild(h->sys, h->buf, h->stream));
+      if (sample_every > 0 && (k + 1) % sample_every == 0)
+        CUDA_OR_FAIL(h, launch_density(h->sys, h->buf, h->precision, h->stream));
+    }
+    CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 1, 0, h->stream));
+    if (tf_update) CUDA_OR_FAIL(h, launch_tf_update(h->sys, h->buf, alpha, h->stream));
+    return ADRESS_OK;
+  }
+  return launch_graph(h, nsteps, sample_every, tf_update, alpha);
+}
+
 adress_status adress_step(adress_handle h, int32_t nsteps) {
   if (!h) return ADRESS_ERR_ARG;
   if (nsteps < 0) return fail(h, ADRESS_ERR_ARG, "nsteps < 0");
@@ -528,9 +578,9 @@ adress_status adress_step(adress_handle h, int32_t nsteps) {
   if (nsteps == 0) return ADRESS_OK;
   if (h->eager) {
     for (int k = 0; k < nsteps; ++k) {
-      if (k == 0) CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 1, h->stream));
-      else CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 2, 0, h->stream));
-      CUDA_OR_FAIL(h, launch_decide(h->sys, h->buf, 0, 1, 0, 0, h->stream));
+      const DecideArgs da{0, 1, 0, 0};
+      if (k == 0) CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 1, h->stream, da));
+      else CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 2, 0, h->stream, da));
       Ctrl c;
       adress_status st = read_ctrl(h, &c);
       if (st != ADRESS_OK) return st;
@@ -542,15 +592,8 @@ adress_status adress_step(adress_handle h, int32_t nsteps) {
   int left = nsteps;
   while (left > 0) {
     const int n = std::min(left, kMaxGraphSteps);
-    auto it = h->graphs.find(n);
-    if (it == h->graphs.end()) {
-      cudaGraph_t g;
-      cudaGraphExec_t x;
-      adress_status st = capture_steps(h, n, &g, &x);
-      if (st != ADRESS_OK) return st;
-      it = h->graphs.emplace(n, std::make_pair(g, x)).first;
-    }
-    CUDA_OR_FAIL(h, cudaGraphLaunch(it->second.second, h->stream));
+    adress_status st = launch_graph(h, n, 0, 0, 0.0);
+    if (st != ADRESS_OK) return st;
     left -= n;
   }
   return ADRESS_OK;
@@ -575,8 +618,7 @@ adress_status adress_get_step(adress_handle h, int64_t* step) {
 adress_status adress_com_lambda(adress_handle h, double* com, double* w) {
   if (!h || !com || !w) return ADRESS_ERR_ARG;
   if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
-  CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream));
-  CUDA_OR_FAIL(h, launch_decide(h->sys, h->buf, 0, 0, 0, 0, h->stream));
+  CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream, DecideArgs{0, 0, 0, 0}));
   CUDA_OR_FAIL(h, launch_export_com(h->sys, h->buf, h->precision, com, w, h->stream));
   return ADRESS_OK;
 }
@@ -593,8 +635,7 @@ adress_status adress_kinetic(adress_handle h, double* out) {
 adress_status adress_density_accumulate(adress_handle h) {
   if (!h) return ADRESS_ERR_ARG;
   if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
-  CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream));
-  CUDA_OR_FAIL(h, launch_decide(h->sys, h->buf, 0, 0, 0, 0, h->stream));
+  CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream, DecideArgs{0, 0, 0, 0}));
   CUDA_OR_FAIL(h, launch_density(h->sys, h->buf, h->precision, h->stream));
   return ADRESS_OK;
 }
@@ -644,6 +685,7 @@ adress_status adress_get_tf(adress_handle h, double* tf, int32_t n) {
 
 adress_status adress_list_stats(adress_handle h, int64_t* out) {
   if (!h || !out) return ADRESS_ERR_ARG;
+  CUDA_OR_FAIL(h, launch_max_nn(h->sys, h->buf, h->stream));
   Ctrl c;
   adress_status st = read_ctrl(h, &c);
   if (st != ADRESS_OK) return st;
@@ -675,12 +717,10 @@ adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out) 
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
     acc[which] += t;
   };
-  timed(0, [&] { return launch_com(h->sys, h->buf, h->precision, 1, st); });
-  if (e == cudaSuccess) e = launch_decide(h->sys, h->buf, 1, 1, 0, 0, st);
+  timed(0, [&] { return launch_com(h->sys, h->buf, h->precision, 1, st, DecideArgs{1, 1, 0, 0}); });
   timed(1, [&] { return launch_rebuild(h->sys, h->buf, st); });
   for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-    timed(2, [&] { return launch_step(h->sys, h->buf, h->precision, 2, 0, st); });
-    if (e == cudaSuccess) e = launch_decide(h->sys, h->buf, 1, 1, 0, 0, st);
+    timed(2, [&] { return launch_step(h->sys, h->buf, h->precision, 2, 0, st, DecideArgs{1, 1, 0, 0}); });
     timed(1, [&] { return launch_rebuild(h->sys, h->buf, st); });
   }
   timed(3, [&] { return launch_step(h->sys, h->buf, h->precision, 1, 0, st); });
@@ -690,6 +730,17 @@ adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out) 
   ms_out[1] = (float)(acc[1] / (reps + 1));
   ms_out[2] = (float)(acc[2] / reps);
   ms_out[3] = (float)acc[3];
+  return ADRESS_OK;
+}
+
+adress_status adress_list_export(adress_handle h, int32_t* items, int32_t* nn, int32_t* nbr) {
+  if (!h || !items || !nn || !nbr) return ADRESS_ERR_ARG;
+  if (!h->lists_built) return fail(h, ADRESS_ERR_STATE, "no lists built");
+  const size_t M = (size_t)h->sys.M;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(items, h->buf.items, sizeof(int) * M, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(nn, h->buf.nn, sizeof(int) * M, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(nbr, h->buf.nbr, sizeof(int) * M * h->sys.cap, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
   return ADRESS_OK;
 }
 

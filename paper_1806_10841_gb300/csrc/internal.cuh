@@ -23,7 +23,15 @@ struct Ctrl {
   float ext_now;
   int max_nn;
   int err_info;
-  int parity;  // which half of the double-buffered molecule arrays is current
+  int parity;          // which half of the double-buffered molecule arrays is current
+  unsigned maxext2;    // float bits: largest squared atom-to-COM distance of the last mapping
+  unsigned maxdisp2;   // float bits: largest squared COM displacement since the last build
+};
+
+// Decision taken after a mapping (see decide_after_map in observe.cu).
+struct DecideArgs {
+  int force, advance, use_h;
+  cudaGraphConditionalHandle h;
 };
 
 // Per-system constants, passed by value to every kernel.
@@ -95,8 +103,9 @@ struct Bufs {
   int* flag;        // [M] high-resolution candidate flag at sorted positions
   int* pos;         // [M] exclusive scan of flag
   int* items;       // [M] work items: high-resolution candidates first, then CG
+  int* item_of;     // [M] work item of each molecule
   int* nn;          // [M] neighbour count per item
-  int* nbr;         // [cap*M] neighbour molecule of item t in slot s at nbr[s*M + t]
+  int* nbr;         // [M*cap] neighbour molecule of item t in slot q at nbr[t*cap + q]
   int* scan_tmp;    // block sums for device-wide scans
   const int* cell_rank;  // linear cell -> Morton rank
   const int* rank_cell;  // Morton rank -> linear cell
@@ -109,8 +118,6 @@ struct Bufs {
   // reductions
   double* part;      // per-warp partials
   double* result;    // reduced results [8]
-  float2* blk_ext;           // per-block (max extent, max displacement^2) of the last mapping
-  int* blk_n;                // number of valid entries in blk_ext
   unsigned long long* hist;  // density histogram [tf_n]
   long long* nsamples;
   Ctrl* ctrl;
@@ -142,13 +149,18 @@ struct P32 {
 };
 
 // launchers (one per translation unit)
-cudaError_t launch_com(const Sys& s, const Bufs& b, int precision, int integrate, cudaStream_t st);
-cudaError_t launch_decide(const Sys& s, const Bufs& b, int force, int advance_step,
-                          cudaGraphConditionalHandle h, int use_handle, cudaStream_t st);
+cudaError_t launch_com(const Sys& s, const Bufs& b, int precision, int integrate, cudaStream_t st,
+                       DecideArgs da = DecideArgs{0, 0, 0, 0});
 cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st);
+// Rebuild decision after a mapping kernel (one thread); also flips the current half of the
+// molecule arrays and, in a graph, sets the conditional of the rebuild node.
+cudaError_t launch_decide(const Sys& s, const Bufs& b, DecideArgs da, cudaStream_t st);
+cudaError_t launch_max_nn(const Sys& s, const Bufs& b, cudaStream_t st);
 // mode: 0 conservative forces, 1 last step of a run (thermostat + second half kick),
 // 2 fused step (thermostat + both half kicks + drift + next mapping)
-cudaError_t launch_step(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st);
+cudaError_t launch_step(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st,
+                        DecideArgs da = DecideArgs{0, 0, 0, 0});
+
 cudaError_t launch_energy_reduce(const Sys& s, const Bufs& b, int nparts, int nvals, cudaStream_t st);
 cudaError_t launch_kinetic(const Sys& s, const Bufs& b, cudaStream_t st);
 cudaError_t launch_density(const Sys& s, const Bufs& b, int precision, cudaStream_t st);
@@ -158,7 +170,7 @@ cudaError_t launch_export_com(const Sys& s, const Bufs& b, int precision, double
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 constexpr int kForceBlock = 128;
-constexpr int kMaxMapBlocks = 1 << 16;  // per-block extent records (M <= 2^21 molecules)
+
 // Warps launched by the force kernel (one energy partial each).
 inline int force_warps(const Sys& s) { return ceil_div((long long)s.M * kGroup, kForceBlock) * (kForceBlock / 32); }
 

@@ -1,8 +1,8 @@
 // Neighbour search on the GPU: a linked-cell list over molecule centres of mass (the
 // paper's linked-cell-list neighbour search, Sec. "Heterogeneous Spatial Domain
 // Decomposition Algorithm", here on one GPU).  Cells are ranked in Morton order;
-// molecules are counting-sorted by cell, each cell's members put in id order so every
-// list is deterministic; molecules are split into two work lists — high-resolution
+// molecules are counting-sorted by cell and each cell's members are taken in id order
+// when lists are built, so every list is deterministic; molecules are split into two work lists — high-resolution
 // candidates (|dxc| < d_at + d_hy + skin/2) first, then coarse-grained molecules —
 // and each work item gets a full Verlet list of molecules within r_list.
 #include "internal.cuh"
@@ -23,7 +23,6 @@ __global__ void k_rb_zero(Sys s, Bufs b) {
     b.cell_count[c] = 0;
     b.cell_fill[c] = 0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) b.ctrl->max_nn = 0;
 }
 
 __global__ void k_rb_count(Sys s, Bufs b) {
@@ -146,22 +145,6 @@ __global__ void k_rb_fill(Sys s, Bufs b) {
   b.sorted[p] = a;
 }
 
-// Members of each cell in increasing molecule id (insertion sort; cells hold a few).
-__global__ void k_rb_sort(Sys s, Bufs b) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= s.ncell) return;
-  const int lo = b.cell_start[r], hi = b.cell_start[r + 1];
-  for (int i = lo + 1; i < hi; ++i) {
-    const int key = b.sorted[i];
-    int j = i - 1;
-    while (j >= lo && b.sorted[j] > key) {
-      b.sorted[j + 1] = b.sorted[j];
-      --j;
-    }
-    b.sorted[j + 1] = key;
-  }
-}
-
 __global__ void k_rb_flag(Sys s, Bufs b) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= s.M) return;
@@ -180,19 +163,16 @@ __global__ void k_rb_items(Sys s, Bufs b) {
   if (k >= s.M) return;
   const int a = b.sorted[k];
   const int p = b.pos[k];
-  if (b.flag[k]) b.items[p] = a;
-  else b.items[n_hr + (k - p)] = a;
+  const int t = b.flag[k] ? p : n_hr + (k - p);
+  b.items[t] = a;
+  b.item_of[a] = t;
 }
 
-// Full Verlet list of work item t: every other molecule whose centre lies within r_list,
-// scanning the 27 neighbour cells (fewer when a dimension has < 3 cells) in fixed order.
-__global__ void __launch_bounds__(128) k_rb_nbr(Sys s, Bufs b) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= s.M) return;
-  const int a = b.items[t];
-  const int4* com = b.com_fx[b.ctrl->parity];
+// Verlet list of one molecule a (work item t) scanned directly from global memory: every
+// other molecule whose centre lies within r_list, over the 27 neighbour cells (fewer when
+// a dimension has < 3 cells) in fixed order, each cell's members in id order.
+__device__ void scan_neighbours(const Sys& s, const Bufs& b, const int4* com, int a, int t) {
   const int4 C = com[a];
-  b.com_ref[a] = C;
   const int c0 = cell_of((unsigned)C.x, s.nc[0]), c1 = cell_of((unsigned)C.y, s.nc[1]),
             c2 = cell_of((unsigned)C.z, s.nc[2]);
   const float rl2 = (float)s.r_list2;
@@ -206,16 +186,23 @@ __global__ void __launch_bounds__(128) k_rb_nbr(Sys s, Bufs b) {
       for (int o2 = lo2; o2 <= hi2; ++o2) {
         const int z = (c2 + o2 + s.nc[2]) % s.nc[2];
         const int r = b.cell_rank[(x * s.nc[1] + y) * s.nc[2] + z];
-        const int pe = b.cell_start[r + 1];
-        for (int p = b.cell_start[r]; p < pe; ++p) {
-          const int m = b.sorted[p];
+        const int ps = b.cell_start[r], pe = b.cell_start[r + 1];
+        // members in increasing id (cells are filled in no fixed order)
+        int last = -1;
+        for (int rep = ps; rep < pe; ++rep) {
+          int m = 0x7fffffff;
+          for (int p = ps; p < pe; ++p) {
+            const int id = b.sorted[p];
+            if (id > last && id < m) m = id;
+          }
+          last = m;
           if (m == a) continue;
           const int4 D = com[m];
           const float d0 = (float)(int)((unsigned)C.x - (unsigned)D.x) * s.fx_scale[0];
           const float d1 = (float)(int)((unsigned)C.y - (unsigned)D.y) * s.fx_scale[1];
           const float d2 = (float)(int)((unsigned)C.z - (unsigned)D.z) * s.fx_scale[2];
           if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
-            if (cnt < s.cap) b.nbr[(size_t)cnt * s.M + t] = m;
+            if (cnt < s.cap) b.nbr[(size_t)t * s.cap + cnt] = m;
             ++cnt;
           }
         }
@@ -223,8 +210,119 @@ __global__ void __launch_bounds__(128) k_rb_nbr(Sys s, Bufs b) {
     }
   }
   b.nn[t] = cnt < s.cap ? cnt : s.cap;
-  atomicMax(&b.ctrl->max_nn, cnt);
+  b.com_ref[a] = C;
   if (cnt > s.cap) set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, cnt);
+}
+
+// One warp per cell (cells in Morton order).  Lanes 0..26 take the 27 neighbour cells in
+// the fixed (ox, oy, oz) order, a warp scan gives each cell's offset in the candidate
+// list, and the candidates (centre + id) are staged in shared memory once; each molecule
+// of the cell then tests all candidates in parallel and appends its neighbours in
+// candidate order with ballot/popc compaction — the same lists scan_neighbours builds.
+constexpr int kNbrWarps = 4;
+constexpr int kMaxCand = 256;  // typical neighbourhoods hold ~70 (denser ones use the scan)
+__global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(Sys s, Bufs b) {
+  __shared__ int4 stage[kNbrWarps][kMaxCand];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kNbrWarps + w;
+  if (r >= s.ncell) return;  // warp-uniform
+  const int4* com = b.com_fx[b.ctrl->parity];
+  const int lin = b.rank_cell[r];
+  const int cz = lin % s.nc[2], cy = (lin / s.nc[2]) % s.nc[1], cx = lin / (s.nc[1] * s.nc[2]);
+  int cnt = 0, start = 0;
+  if (lane < 27) {
+    const int o0 = lane / 9 - 1, o1 = (lane / 3) % 3 - 1, o2 = lane % 3 - 1;
+    const bool ok = (o0 >= (s.nc[0] >= 3 ? -1 : 0)) && (o0 <= (s.nc[0] >= 2 ? 1 : 0)) &&
+                    (o1 >= (s.nc[1] >= 3 ? -1 : 0)) && (o1 <= (s.nc[1] >= 2 ? 1 : 0)) &&
+                    (o2 >= (s.nc[2] >= 3 ? -1 : 0)) && (o2 <= (s.nc[2] >= 2 ? 1 : 0));
+    if (ok) {
+      const int x = (cx + o0 + s.nc[0]) % s.nc[0], y = (cy + o1 + s.nc[1]) % s.nc[1],
+                z = (cz + o2 + s.nc[2]) % s.nc[2];
+      const int rr = b.cell_rank[(x * s.nc[1] + y) * s.nc[2] + z];
+      start = b.cell_start[rr];
+      cnt = b.cell_start[rr + 1] - start;
+    }
+  }
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const int pre = incl - cnt;
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const int n_home = __shfl_sync(0xffffffffu, cnt, 13);
+  const int home_start = __shfl_sync(0xffffffffu, start, 13);
+  if (n_home == 0) return;
+  if (total > kMaxCand) {  // over-dense neighbourhood: per-molecule scan
+    for (int h = lane; h < n_home; h += 32) {
+      const int a = b.sorted[home_start + h];
+      scan_neighbours(s, b, com, a, b.item_of[a]);
+    }
+    return;
+  }
+  // lane j stages the members of neighbour cell j at its offset in the candidate list,
+  // in increasing molecule id (the cell's fill order is not deterministic)
+  for (int q = 0; q < cnt; ++q) {
+    const int m = b.sorted[start + q];
+    const int4 C = com[m];
+    int p = pre + q;
+    while (p > pre && stage[w][p - 1].w > m) {
+      stage[w][p] = stage[w][p - 1];
+      --p;
+    }
+    stage[w][p] = make_int4(C.x, C.y, C.z, m);
+  }
+  __syncwarp();
+  // the home cell is neighbour 13: its molecules, centres and work items, fetched at once
+  const int home_pre = __shfl_sync(0xffffffffu, pre, 13);
+  int my_item = 0;
+  if (lane < n_home) my_item = b.item_of[stage[w][home_pre + lane].w];
+  const float rl2 = (float)s.r_list2;
+  for (int h = 0; h < n_home; ++h) {
+    const int4 H = stage[w][home_pre + h];
+    const int a = H.w;
+    const int t = h < 32 ? __shfl_sync(0xffffffffu, my_item, h) : b.item_of[a];
+    int count = 0;
+    for (int k0 = 0; k0 < total; k0 += 32) {
+      const int k = k0 + lane;
+      bool hit = false;
+      int m = 0;
+      if (k < total) {
+        const int4 D = stage[w][k];
+        m = D.w;
+        const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * s.fx_scale[0];
+        const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * s.fx_scale[1];
+        const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * s.fx_scale[2];
+        hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < rl2;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int p = count + __popc(bal & ((1u << lane) - 1u));
+        if (p < s.cap) b.nbr[(size_t)t * s.cap + p] = m;
+      }
+      count += __popc(bal);
+    }
+    if (lane == 0) {
+      b.nn[t] = count < s.cap ? count : s.cap;
+      b.com_ref[a] = make_int4(H.x, H.y, H.z, 0);
+      if (count > s.cap) set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, count);
+    }
+  }
+}
+
+// Largest neighbour count of the last build (host-side capacity check only).
+__global__ void k_max_nn(const Sys s, const Bufs b) {
+  int m = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s.M; t += gridDim.x * blockDim.x) m = max(m, b.nn[t]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) atomicMax(&b.ctrl->max_nn, m);
+}
+
+cudaError_t launch_max_nn(const Sys& s, const Bufs& b, cudaStream_t st) {
+  cudaMemsetAsync(&b.ctrl->max_nn, 0, sizeof(int), st);
+  k_max_nn<<<64, 256, 0, st>>>(s, b);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st) {
@@ -235,11 +333,10 @@ cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st) {
       cudaSuccess)
     return e;
   k_rb_fill<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
-  k_rb_sort<<<ceil_div(s.ncell, 256), 256, 0, st>>>(s, b);
   k_rb_flag<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   if ((e = exclusive_scan(b.flag, b.pos, s.M, b.scan_tmp, b.pos + s.M, st)) != cudaSuccess) return e;
   k_rb_items<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
-  k_rb_nbr<<<ceil_div(s.M, 128), 128, 0, st>>>(s, b);
+  k_rb_nbr<<<ceil_div(s.ncell, kNbrWarps), 32 * kNbrWarps, 0, st>>>(s, b);
   return cudaGetLastError();
 }
 

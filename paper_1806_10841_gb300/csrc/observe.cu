@@ -3,52 +3,36 @@
 // profile and the thermodynamic-force iteration, and the FP64 export of centres of mass.
 #include <math.h>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace adress {
 
-// Runs after every kernel that maps positions (into the non-current half), as one block:
-// reduces the mapping's per-block records to the largest molecule extent and the largest
-// centre displacement since the last list build, then decides whether to rebuild the
-// lists: when a centre moved more than skin/2 (it could have changed class or found a new
-// partner) or when the widest molecule makes max(rc_cg, rc_at + 2 ext) + 2 disp exceed the
-// list cutoff.  Flips the current half of the molecule arrays.
-__global__ void __launch_bounds__(1024) k_decide(Sys s, Bufs b, int force, int advance,
-                                                 cudaGraphConditionalHandle h, int use_h) {
-  __shared__ float sm[2][32];
-  const int n = *b.blk_n;
-  float e = 0.f, d = 0.f;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const float2 r = b.blk_ext[k];
-    e = fmaxf(e, r.x);
-    d = fmaxf(d, r.y);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
-    d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    sm[0][threadIdx.x >> 5] = e;
-    sm[1][threadIdx.x >> 5] = d;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
-    e = fmaxf(e, sm[0][k]);
-    d = fmaxf(d, sm[1][k]);
-  }
+// Rebuild decision after a mapping: rebuild when a centre moved more than skin/2 since the
+// last build (it could have changed class or found a new partner) or when the widest
+// molecule makes max(rc_cg, rc_at + 2 ext) + 2 disp exceed the list cutoff.  The mapping
+// just written becomes current; the maxima are reset for the next mapping.
+__global__ void k_decide(Sys s, Bufs b, DecideArgs da) {
   Ctrl* c = b.ctrl;
-  const float ext = fmaxf(e, sm[0][0]);
-  const float md = sqrtf(fmaxf(d, sm[1][0]));
-  const double cut = fmax(s.rc_cg, s.rc_at + 2.0 * (double)ext);
-  int rb = force || (md > 0.5 * s.skin) || (cut + 2.0 * md > s.r_list);
-  if (cut > s.r_list) set_error(c, ADRESS_ERR_EXTENT, (int)(ext * 1000));
+  const float e = sqrtf(__uint_as_float(c->maxext2));
+  const float md = sqrtf(__uint_as_float(c->maxdisp2));
+  c->maxext2 = 0u;
+  c->maxdisp2 = 0u;
+  const double cut = fmax(s.rc_cg, s.rc_at + 2.0 * (double)e);
+  const int rb = da.force || (md > 0.5 * s.skin) || (cut + 2.0 * md > s.r_list);
+  if (cut > s.r_list) set_error(c, ADRESS_ERR_EXTENT, (int)(e * 1000));
   c->rebuild = rb;
-  c->ext_now = ext;
+  c->ext_now = e;
   if (rb) c->rebuilds += 1;
-  if (advance) c->step += 1;
-  c->parity ^= 1;  // the mapping just written becomes current
-  if (use_h) cudaGraphSetConditional(h, (unsigned int)rb);
+  if (da.advance) c->step += 1;
+  c->parity ^= 1;
+  if (da.use_h) cudaGraphSetConditional(da.h, (unsigned int)rb);
+}
+
+cudaError_t launch_decide(const Sys& s, const Bufs& b, DecideArgs da, cudaStream_t st) {
+  k_decide<<<1, 1, 0, st>>>(s, b, da);
+  return cudaGetLastError();
 }
 
 // ---- deterministic FP64 reductions: per-block partials, then one fixed-order block ----
@@ -126,21 +110,27 @@ __device__ double com_x64(const Sys& s, const double* x, int a) {
 // The FP32 path takes |dxc| from its float mapping and recomputes it in double for the
 // few molecules within 1e-4 of a bin edge, so the bin is the one the double value gives.
 template <int NA>
-__global__ void k_density(Sys s, Bufs b) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a == 0) atomicAdd((unsigned long long*)b.nsamples, 1ull);
-  if (a >= s.M) return;
+__global__ void __launch_bounds__(1024) k_density(Sys s, Bufs b) {
+  extern __shared__ unsigned hs[];
+  for (int k = threadIdx.x; k < s.tf_n; k += blockDim.x) hs[k] = 0u;
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)b.nsamples, 1ull);
   const int cur = b.ctrl->parity;
-  double d;
-  if (s.fp64) {
-    d = fabs(b.dxc64[cur][a]);
-  } else {
-    d = (double)fabsf(b.molf[cur][a].x);
-    const double u = d / s.tf_dx, fr = u - floor(u);
-    if (fr < 1e-4 || fr > 1.0 - 1e-4) d = fabs(minimg_cmp(com_x64<NA>(s, b.x, a) - s.xc, s.L[0], s.halfL[0]));
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < s.M; a += gridDim.x * blockDim.x) {
+    int k;
+    if (s.fp64) {
+      k = (int)floor(fabs(b.dxc64[cur][a]) / s.tf_dx);
+    } else {
+      const float u = fabsf(b.molf[cur][a].x) * s.f.tf_inv_dx, fr = u - floorf(u);
+      k = (int)floorf(u);
+      if (fr < 1e-4f || fr > 1.f - 1e-4f)
+        k = (int)floor(fabs(minimg_cmp(com_x64<NA>(s, b.x, a) - s.xc, s.L[0], s.halfL[0])) / s.tf_dx);
+    }
+    if (k < s.tf_n) atomicAdd(&hs[k], 1u);
   }
-  const int k = (int)floor(d / s.tf_dx);
-  if (k < s.tf_n) atomicAdd(&b.hist[k], 1ull);
+  __syncthreads();
+  for (int k = threadIdx.x; k < s.tf_n; k += blockDim.x)
+    if (hs[k]) atomicAdd(&b.hist[k], (unsigned long long)hs[k]);
 }
 
 // Thermodynamic-force iteration on the accumulated profile (one block, tf_n nodes):
@@ -200,11 +190,6 @@ __global__ void k_export_com(Sys s, Bufs b, double* com, double* w) {
 
 // ---- launchers -----------------------------------------------------------------------
 
-cudaError_t launch_decide(const Sys& s, const Bufs& b, int force, int advance,
-                          cudaGraphConditionalHandle h, int use_h, cudaStream_t st) {
-  k_decide<<<1, 1024, 0, st>>>(s, b, force, advance, h, use_h);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_energy_reduce(const Sys& s, const Bufs& b, int nparts, int nvals, cudaStream_t st) {
   k_reduce_parts<<<1, 1024, 0, st>>>(b.part, nparts, nvals, b.result);
@@ -225,12 +210,13 @@ cudaError_t launch_kinetic(const Sys& s, const Bufs& b, cudaStream_t st) {
 }
 
 cudaError_t launch_density(const Sys& s, const Bufs& b, int, cudaStream_t st) {
-  const int blocks = ceil_div(s.M, 256);
+  const int blocks = std::min(ceil_div(s.M, 1024), 2 * 152);
+  const size_t smem = sizeof(unsigned) * std::max(1, s.tf_n);
   switch (s.NA) {
-    case 1: k_density<1><<<blocks, 256, 0, st>>>(s, b); break;
-    case 2: k_density<2><<<blocks, 256, 0, st>>>(s, b); break;
-    case 3: k_density<3><<<blocks, 256, 0, st>>>(s, b); break;
-    default: k_density<4><<<blocks, 256, 0, st>>>(s, b); break;
+    case 1: k_density<1><<<blocks, 1024, smem, st>>>(s, b); break;
+    case 2: k_density<2><<<blocks, 1024, smem, st>>>(s, b); break;
+    case 3: k_density<3><<<blocks, 1024, smem, st>>>(s, b); break;
+    default: k_density<4><<<blocks, 1024, smem, st>>>(s, b); break;
   }
   return cudaGetLastError();
 }

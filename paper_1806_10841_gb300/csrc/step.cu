@@ -299,8 +299,9 @@ __device__ __forceinline__ void map_group64(const Sys& s, const Bufs& b, int nxt
   }
 }
 
-// Block maximum of the molecule extent and the displacement since the last list build,
-// stored as one record per block (no same-address atomics); the decide kernel reduces them.
+// Block maximum of the molecule extent and of the displacement since the last list
+// build, merged into the control block with one fire-and-forget atomic per block (no
+// fence, no returned value, so blocks retire at once); the decide kernel reads them.
 __device__ __forceinline__ void publish_extent(const Bufs& b, float ext2, float disp2) {
   __shared__ unsigned red[2][kForceBlock / 32];
   const unsigned e = __reduce_max_sync(0xffffffffu, __float_as_uint(ext2));
@@ -318,8 +319,8 @@ __device__ __forceinline__ void publish_extent(const Bufs& b, float ext2, float 
       me = max(me, red[0][k]);
       md = max(md, red[1][k]);
     }
-    b.blk_ext[blockIdx.x] = make_float2(sqrtf(__uint_as_float(me)), __uint_as_float(md));
-    if (blockIdx.x == 0) *b.blk_n = gridDim.x;
+    atomicMax(&b.ctrl->maxext2, me);
+    atomicMax(&b.ctrl->maxdisp2, md);
   }
 }
 
@@ -369,7 +370,6 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
   const bool live = t < s.M;
   const bool own = live && g < NA;
-  const int M = s.M;
   const int cur = b.ctrl->parity;
 
   const real eps = par<real>(s.eps, s.f.eps), sig2 = par<real>(s.sig2, s.f.sig2);
@@ -396,14 +396,14 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
     int m_n = 0;
     auto C_n = Ca;
     if (nnb > 0) {
-      m_n = b.nbr[t];
+      m_n = b.nbr[(size_t)t * s.cap];
       C_n = Q::com(b, cur, m_n);
     }
     for (int q = 0; q < nnb; ++q) {
       const int m = m_n;
       const auto Cb = C_n;
       if (q + 1 < nnb) {
-        m_n = b.nbr[(size_t)(q + 1) * M + t];
+        m_n = b.nbr[(size_t)t * s.cap + q + 1];
         C_n = Q::com(b, cur, m_n);
       }
       const auto R = Q::dR(s, Ca, Cb);
@@ -453,10 +453,10 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
     if (live && g == 0 && wa != (real)0) set_error(b.ctrl, ADRESS_ERR_STATE, a);
     real Fx = 0, Fy = 0, Fz = 0;
     auto C_n = Ca;
-    if (g < nnb) C_n = Q::com(b, cur, b.nbr[(size_t)g * M + t]);
+    if (g < nnb) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + g]);
     for (int q = g; q < nnb; q += kGroup) {
       const auto Cb = C_n;
-      if (q + kGroup < nnb) C_n = Q::com(b, cur, b.nbr[(size_t)(q + kGroup) * M + t]);
+      if (q + kGroup < nnb) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + q + kGroup]);
       const auto R = Q::dR(s, Ca, Cb);
       const real r2 = R.x * R.x + R.y * R.y + R.z * R.z;
       if (r2 < rc_cg2) {
@@ -670,30 +670,31 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
 // ---------------- launchers ----------------------------------------------------------
 
 template <class P, int NA>
-static void launch_prologue_na(const Sys& s, const Bufs& b, int integrate, cudaStream_t st) {
+static void launch_prologue_na(const Sys& s, const Bufs& b, int integrate, cudaStream_t st, DecideArgs da) {
   const int blocks = ceil_div((long long)s.M * kGroup, kForceBlock);
   if (integrate) k_prologue<P, NA, true><<<blocks, kForceBlock, 0, st>>>(s, b);
   else k_prologue<P, NA, false><<<blocks, kForceBlock, 0, st>>>(s, b);
 }
 
 template <class P>
-static void launch_prologue_p(const Sys& s, const Bufs& b, int integrate, cudaStream_t st) {
+static void launch_prologue_p(const Sys& s, const Bufs& b, int integrate, cudaStream_t st, DecideArgs da) {
   switch (s.NA) {
-    case 1: launch_prologue_na<P, 1>(s, b, integrate, st); break;
-    case 2: launch_prologue_na<P, 2>(s, b, integrate, st); break;
-    case 3: launch_prologue_na<P, 3>(s, b, integrate, st); break;
-    default: launch_prologue_na<P, 4>(s, b, integrate, st); break;
+    case 1: launch_prologue_na<P, 1>(s, b, integrate, st, da); break;
+    case 2: launch_prologue_na<P, 2>(s, b, integrate, st, da); break;
+    case 3: launch_prologue_na<P, 3>(s, b, integrate, st, da); break;
+    default: launch_prologue_na<P, 4>(s, b, integrate, st, da); break;
   }
 }
 
-cudaError_t launch_com(const Sys& s, const Bufs& b, int precision, int integrate, cudaStream_t st) {
-  if (precision == ADRESS_FP64) launch_prologue_p<P64>(s, b, integrate, st);
-  else launch_prologue_p<P32>(s, b, integrate, st);
-  return cudaGetLastError();
+cudaError_t launch_com(const Sys& s, const Bufs& b, int precision, int integrate, cudaStream_t st, DecideArgs da) {
+  if (precision == ADRESS_FP64) launch_prologue_p<P64>(s, b, integrate, st, da);
+  else launch_prologue_p<P32>(s, b, integrate, st, da);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? launch_decide(s, b, da, st) : e;
 }
 
 template <class P, int NA>
-static void launch_step_na(const Sys& s, const Bufs& b, int mode, int energy, cudaStream_t st) {
+static void launch_step_na(const Sys& s, const Bufs& b, int mode, int energy, cudaStream_t st, DecideArgs da) {
   const int blocks = ceil_div((long long)s.M * kGroup, kForceBlock);
   switch (mode) {
     case MODE_FORCES:
@@ -706,19 +707,21 @@ static void launch_step_na(const Sys& s, const Bufs& b, int mode, int energy, cu
 }
 
 template <class P>
-static void launch_step_p(const Sys& s, const Bufs& b, int mode, int energy, cudaStream_t st) {
+static void launch_step_p(const Sys& s, const Bufs& b, int mode, int energy, cudaStream_t st, DecideArgs da) {
   switch (s.NA) {
-    case 1: launch_step_na<P, 1>(s, b, mode, energy, st); break;
-    case 2: launch_step_na<P, 2>(s, b, mode, energy, st); break;
-    case 3: launch_step_na<P, 3>(s, b, mode, energy, st); break;
-    default: launch_step_na<P, 4>(s, b, mode, energy, st); break;
+    case 1: launch_step_na<P, 1>(s, b, mode, energy, st, da); break;
+    case 2: launch_step_na<P, 2>(s, b, mode, energy, st, da); break;
+    case 3: launch_step_na<P, 3>(s, b, mode, energy, st, da); break;
+    default: launch_step_na<P, 4>(s, b, mode, energy, st, da); break;
   }
 }
 
-cudaError_t launch_step(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st) {
-  if (precision == ADRESS_FP64) launch_step_p<P64>(s, b, mode, energy, st);
-  else launch_step_p<P32>(s, b, mode, energy, st);
-  return cudaGetLastError();
+cudaError_t launch_step(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st,
+                        DecideArgs da) {
+  if (precision == ADRESS_FP64) launch_step_p<P64>(s, b, mode, energy, st, da);
+  else launch_step_p<P32>(s, b, mode, energy, st, da);
+  cudaError_t e = cudaGetLastError();
+  return (e == cudaSuccess && mode == MODE_FUSED) ? launch_decide(s, b, da, st) : e;
 }
 
 }  // namespace adress

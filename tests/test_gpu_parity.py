@@ -291,3 +291,54 @@ def test_invalid_configs_are_rejected():
     s = inputs.tetra_system(1, (20.0, 20.0, 20.0), 1.0, 1.0)
     with pytest.raises(adress.AdressError):
         gpu(s, "fp64")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_run_block_matches_oracle_sequence(precision):
+    """adress_run: 20 steps with a density sample every 5 and one thermodynamic-force update,
+    against the oracle doing the same sequence."""
+    s, x, v, f0, _ = case("scaled_20k")
+    o = oracle.Oracle(s)
+    sim = gpu(s, precision)
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    sim.run(20, sample_every=5, tf_update=True, alpha=2.0)
+    sim.check()
+    xg, vg, _ = sim.get_state()
+    xo, vo, fo = x, v, f0
+    counts = np.zeros(len(s.tf), dtype=np.int64)
+    for k in range(4):
+        xo, vo, fo = o.run(xo, vo, fo, 5 * k, 5)
+        cd, _ = o.density(xo, len(s.tf), 4)
+        counts += cd
+    tf_ref = o.tf_update(np.zeros(len(s.tf)), counts, nsamples=4, alpha=2.0)
+    L = np.array(s.box)
+    dx = xg - xo
+    dx -= L * np.rint(dx / L)
+    assert np.abs(dx).max() < (1e-10 if precision == "fp64" else 1e-4)
+    tf_gpu = sim.get_tf()
+    assert np.allclose(tf_gpu, tf_ref, rtol=1e-9, atol=1e-12)
+    assert sim.get_step() == 20
+    counts_g, ns = sim.density_get()
+    assert ns == 0 and not counts_g.any()  # reset by the update
+
+
+def test_neighbour_lists_are_complete_and_exact():
+    """Every molecule pair within the list cutoff is listed (both directions), no pair beyond it."""
+    s, x, v, f, e = case("hybrid_216")
+    sim = gpu(s, "fp64")
+    sim.set_state(x)
+    sim.build_lists()
+    st = sim.list_stats()
+    com, _ = sim.com_lambda()
+    L = np.array(s.box)
+    d = com[:, None, :] - com[None, :, :]
+    d -= L * np.rint(d / L)
+    r = np.sqrt((d ** 2).sum(-1))
+    r_list = max(s.rc_cg, s.rc_at + 2 * s.r_ext) + s.skin
+    expect = {(a, b_) for a in range(s.M) for b_ in range(s.M) if a != b_ and r[a, b_] < r_list - 1e-6}
+    maybe = {(a, b_) for a in range(s.M) for b_ in range(s.M) if a != b_ and abs(r[a, b_] - r_list) <= 1e-6}
+    assert st["max_nn"] <= st["capacity"]
+    assert expect  # non-trivial
+    got = sim.neighbour_pairs()
+    assert expect <= got and got <= expect | maybe
