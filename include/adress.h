@@ -192,6 +192,26 @@ adress_status adress_list_stats(adress_handle h, int64_t* out);
  * mapping), list rebuild (average), fused step (average), last step}.  Synchronises. */
 adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out);
 
+/* Kinetic energy and momentum of a velocity array without allocating anything: out
+ * device double [4] = {KE, Px, Py, Pz} with KE = sum 1/2 m v^2, P = sum m v.
+ * The paper has no counterpart; this is a convenience for callers that cannot allocate
+ * device memory when they need the observable (a fixed-budget memory pool, an allocator
+ * owned by another framework, a monitoring hook that must not change the simulation's
+ * allocation pattern): it needs no handle and calls no cudaMalloc, cudaFree or
+ * allocating library routine.  Inputs: v device double [3][n_atoms] (the layout of
+ * adress_bind_state), atoms_per_mol 1..4 with per-site masses mass (host [atoms_per_mol]),
+ * stream (a cudaStream_t, NULL = legacy default stream).  The partial sums live in a
+ * file-scope device array of 1024 x 4 doubles (32 KiB) that every GPU loading the library
+ * holds until the process exits, which limits n_atoms to 16,777,216 (1024 blocks x 256
+ * threads x 64 atoms per thread); larger sizes return ADRESS_ERR_ARG with a message in
+ * adress_last_error(NULL).  The first call on a device looks up the array's device
+ * address with that device current (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the one array and it keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other host threads) race.
+ * Asynchronous on `stream`; errors are returned as adress_status. */
+adress_status adress_kinetic_noalloc(const double* v, int64_t n_atoms, int32_t atoms_per_mol,
+                                     const double* mass, void* stream, double* out);
+
 /* Synchronise the stream and return (then clear) the first device-side error. */
 adress_status adress_check(adress_handle h);
 

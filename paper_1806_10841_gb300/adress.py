@@ -25,7 +25,7 @@ EXPORTS = ["adress_init", "adress_bind_state", "adress_build_lists", "adress_com
            "adress_density_accumulate", "adress_density_get", "adress_density_reset",
            "adress_tf_update", "adress_set_tf", "adress_get_tf", "adress_list_stats", "adress_list_export",
            "adress_time_kernels",
-           "adress_check",
+           "adress_kinetic_noalloc", "adress_check",
            "adress_last_error", "adress_status_string", "adress_destroy"]
 
 
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
         "adress_list_stats": ([H, i64p], C.c_int),
         "adress_list_export": ([H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
         "adress_time_kernels": ([H, C.c_int32, C.POINTER(C.c_float)], C.c_int),
+        "adress_kinetic_noalloc": ([vp, C.c_int64, C.c_int32, d, vp, vp], C.c_int),
         "adress_check": ([H], C.c_int),
         "adress_last_error": ([H], C.c_char_p),
         "adress_status_string": ([C.c_int], C.c_char_p),

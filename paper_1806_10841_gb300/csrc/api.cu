@@ -35,6 +35,11 @@ struct adress_ctx {
 static thread_local std::string g_init_error;
 static constexpr int kMaxGraphSteps = 100;  // longest captured step graph
 
+adress_status adress::set_global_error(adress_status s, const std::string& msg) {
+  g_init_error = msg;
+  return s;
+}
+
 static adress_status fail(adress_ctx* h, adress_status s, const std::string& msg) {
   if (h) h->err = msg;
   else g_init_error = msg;

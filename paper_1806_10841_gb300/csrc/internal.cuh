@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/adress.h"
 
 namespace adress {
@@ -168,6 +170,9 @@ cudaError_t launch_tf_update(const Sys& s, const Bufs& b, double alpha, cudaStre
 cudaError_t launch_export_com(const Sys& s, const Bufs& b, int precision, double* com, double* w, cudaStream_t st);
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Record the message returned by adress_last_error(NULL) and return the status.
+adress_status set_global_error(adress_status s, const std::string& msg);
 
 constexpr int kForceBlock = 128;
 
