@@ -43,6 +43,13 @@ class orc_sys(C.Structure):
     ]
 
 
+class orc_mlp(C.Structure):
+    _fields_ = [("nh", C.c_int), ("W1", C.POINTER(C.c_double)), ("b1", C.POINTER(C.c_double)),
+                ("W2", C.POINTER(C.c_double)), ("b2", C.POINTER(C.c_double)), ("w3", C.POINTER(C.c_double)),
+                ("b3", C.c_double), ("in_mean", C.POINTER(C.c_double)), ("in_std", C.POINTER(C.c_double)),
+                ("out_scale", C.c_double), ("bf16", C.c_int)]
+
+
 def build(force: bool = False, extra_flags: tuple = ()) -> str:
     """Compile the oracle with gcc (plain C, -O2, no fast-math).  Returns the .so path."""
     out = _LIB if not extra_flags else os.path.join(
@@ -86,6 +93,16 @@ def _load(path: str | None = None):
     lib.orc_kinetic.argtypes = [S, d, d]
     lib.orc_density.argtypes = [S, d, C.c_int, i64, C.c_int, i64]
     lib.orc_tf_update.argtypes = [S, d, C.c_int, i64, C.c_int, C.c_double, C.c_double]
+    lib.orc_bf16.argtypes = [C.c_double]
+    lib.orc_bf16.restype = C.c_double
+    lib.orc_pair_features.argtypes = [S, d, C.c_int, C.c_int, d, d]
+    lib.orc_collect_pairs.argtypes = [S, d, C.c_double, C.c_long, d, d, C.POINTER(C.c_int)]
+    lib.orc_collect_pairs.restype = C.c_long
+    M = C.POINTER(orc_mlp)
+    lib.orc_mlp_forward.argtypes = [M, C.c_long, d, d]
+    lib.orc_mlp_pair_force.argtypes = [M, C.c_long, d, d]
+    lib.orc_mlp_loss_grad.argtypes = [M, C.c_long, d, d, d, d, d, d, d, d]
+    lib.orc_mlp_loss_grad.restype = C.c_double
     if path is None:
         _lib = lib
     return lib
@@ -182,12 +199,73 @@ class Oracle:
         self.lib.orc_density(C.byref(self.sys), _ptr(x), nd, _ptr(cd, C.c_int64), nx, _ptr(cx, C.c_int64))
         return cd, cx
 
+    def pair_features(self, x, a: int, b: int):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        feat = np.zeros(9)
+        t = np.zeros(1)
+        self.lib.orc_pair_features(C.byref(self.sys), _ptr(x), int(a), int(b), _ptr(feat), _ptr(t))
+        return feat, float(t[0])
+
+    def collect_pairs(self, x, rc: float, cap: int = 10_000_000):
+        """Features [n, 9], targets [n], ids [n, 2] of every pair a < b with COM distance < rc."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        n = self.lib.orc_collect_pairs(C.byref(self.sys), _ptr(x), float(rc), 0, None, None, None)
+        feat = np.zeros((n, 9))
+        t = np.zeros(n)
+        ids = np.zeros((n, 2), dtype=np.int32)
+        self.lib.orc_collect_pairs(C.byref(self.sys), _ptr(x), float(rc), n, _ptr(feat), _ptr(t),
+                                   ids.ctypes.data_as(C.POINTER(C.c_int)))
+        return feat, t, ids
+
     def tf_update(self, tf, counts_d, nsamples: float, alpha: float):
         tf = np.array(tf, dtype=np.float64, order="C")
         cd = np.ascontiguousarray(counts_d, dtype=np.int64)
         self.lib.orc_tf_update(C.byref(self.sys), _ptr(tf), len(tf), _ptr(cd, C.c_int64), len(cd),
                                float(nsamples), float(alpha))
         return tf
+
+
+class OracleMLP:
+    """FP64 network of the learned CG pair force (see adress_oracle.c).  params: dict with
+    W1 [nh, 9], b1 [nh], W2 [nh, nh], b2 [nh], w3 [nh], b3, in_mean [9], in_std [9],
+    out_scale."""
+
+    def __init__(self, params, bf16: bool = False):
+        self.lib = _load()
+        self.nh = int(np.asarray(params["b1"]).size)
+        k = {n: np.ascontiguousarray(np.asarray(params[n], dtype=np.float64).reshape(-1))
+             for n in ("W1", "b1", "W2", "b2", "w3", "in_mean", "in_std")}
+        self._keep = k
+        self.m = orc_mlp(nh=self.nh, W1=_ptr(k["W1"]), b1=_ptr(k["b1"]), W2=_ptr(k["W2"]), b2=_ptr(k["b2"]),
+                         w3=_ptr(k["w3"]), b3=float(params["b3"]), in_mean=_ptr(k["in_mean"]),
+                         in_std=_ptr(k["in_std"]), out_scale=float(params["out_scale"]), bf16=int(bf16))
+
+    def forward(self, feat):
+        feat = np.ascontiguousarray(feat, dtype=np.float64)
+        y = np.zeros(len(feat))
+        self.lib.orc_mlp_forward(C.byref(self.m), len(feat), _ptr(feat), _ptr(y))
+        return y
+
+    def pair_force(self, feat):
+        feat = np.ascontiguousarray(feat, dtype=np.float64)
+        f = np.zeros(len(feat))
+        self.lib.orc_mlp_pair_force(C.byref(self.m), len(feat), _ptr(feat), _ptr(f))
+        return f
+
+    def loss_grad(self, feat, target):
+        feat = np.ascontiguousarray(feat, dtype=np.float64)
+        target = np.ascontiguousarray(target, dtype=np.float64)
+        nh = self.nh
+        g = dict(W1=np.zeros((nh, 9)), b1=np.zeros(nh), W2=np.zeros((nh, nh)), b2=np.zeros(nh), w3=np.zeros(nh))
+        gb3 = np.zeros(1)
+        loss = self.lib.orc_mlp_loss_grad(C.byref(self.m), len(feat), _ptr(feat), _ptr(target), _ptr(g["W1"]),
+                                          _ptr(g["b1"]), _ptr(g["W2"]), _ptr(g["b2"]), _ptr(g["w3"]), _ptr(gb3))
+        g["b3"] = float(gb3[0])
+        return loss, g
+
+
+def bf16(v: float) -> float:
+    return _load().orc_bf16(float(v))
 
 
 def philox4x32(ctr, key):

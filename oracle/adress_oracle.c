@@ -421,3 +421,230 @@ void orc_tf_update(const orc_sys* s, double* tf, int n, const int64_t* counts_d,
   }
   free(rho); free(g);
 }
+
+/* =================================================================================
+ * Learned coarse-grained pair force (force matching).  The paper's CG force is "a CG
+ * force between the molecules, typically evaluated between their centers of mass"
+ * (Sec. "Force interpolation"); the learned variant replaces the tabulated F^CG by a
+ * small network of the COM distance and orientation invariants, trained so that its
+ * output matches the atomistic force between the two molecules projected on the COM axis.
+ *
+ * Features of a molecule pair (a, b):  e = minimg(R_b - R_a)/d, d = |minimg(R_b - R_a)|;
+ *   s_a = the na projections (x_i - R_a).e of a's atoms, sorted ascending;
+ *   s_b = the na projections (x_j - R_b).(-e) of b's atoms, sorted ascending;
+ *   feature vector (d, s_a[0..3], s_b[0..3]) (padded with 0 when na < 4).
+ * Target: t = (sum_{i in a, j in b} f^WCA_ij) . (-e), the atomistic force on a from b along
+ * the COM axis (positive = repulsive).
+ * Network: x = (feat - mean)/std; z1 = W1 x + b1; h1 = silu(z1); z2 = W2 h1 + b2;
+ *   h2 = silu(z2); y = w3.h2 + b3; force = out_scale * y.  With bf16 != 0 the inputs, W1,
+ *   W2 and h1 are rounded to bfloat16 (round to nearest even) before their products, as the
+ *   tensor-core path stores them.  Pair force used in dynamics: the mean of the network on
+ *   (d, s_a, s_b) and on (d, s_b, s_a), so both molecules of a pair see the same value.
+ * ================================================================================= */
+
+static double silu(double z) { return z / (1.0 + exp(-z)); }
+static double dsilu(double z) {
+  double sg = 1.0 / (1.0 + exp(-z));
+  return sg * (1.0 + z * (1.0 - sg));
+}
+
+double orc_bf16(double v) {
+  float f = (float)v;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return v; /* inf / nan unchanged */
+  uint32_t r = u + 0x7fffu + ((u >> 16) & 1u);     /* round to nearest even */
+  r &= 0xffff0000u;
+  memcpy(&f, &r, 4);
+  return (double)f;
+}
+
+static void sort4(double* v, int n) {
+  for (int i = 1; i < n; ++i) {
+    double key = v[i];
+    int j = i - 1;
+    while (j >= 0 && v[j] > key) {
+      v[j + 1] = v[j];
+      --j;
+    }
+    v[j + 1] = key;
+  }
+}
+
+/* Features and target of the pair (a, b) at positions x. */
+void orc_pair_features(const orc_sys* s, const double* x, int a, int b, double* feat, double* target) {
+  double R[2][3];
+  const int mol[2] = {a, b};
+  const double Mt = mol_mass(s);
+  for (int q = 0; q < 2; ++q) {
+    const double* x0 = x + 3 * (size_t)mol[q] * s->na;
+    for (int d = 0; d < 3; ++d) {
+      double acc = 0;
+      for (int k = 0; k < s->na; ++k) acc += s->mass[k] * (x0[d] + minimg(x0[3 * k + d] - x0[d], s->L[d]));
+      R[q][d] = acc / Mt;
+    }
+  }
+  double e[3], dd = 0;
+  for (int d = 0; d < 3; ++d) {
+    e[d] = minimg(R[1][d] - R[0][d], s->L[d]);
+    dd += e[d] * e[d];
+  }
+  dd = sqrt(dd);
+  for (int d = 0; d < 3; ++d) e[d] /= dd;
+  double sa[4] = {0, 0, 0, 0}, sb[4] = {0, 0, 0, 0};
+  for (int k = 0; k < s->na; ++k) {
+    double pa = 0, pb = 0;
+    for (int d = 0; d < 3; ++d) {
+      pa += minimg(x[3 * ((size_t)a * s->na + k) + d] - R[0][d], s->L[d]) * e[d];
+      pb -= minimg(x[3 * ((size_t)b * s->na + k) + d] - R[1][d], s->L[d]) * e[d];
+    }
+    sa[k] = pa;
+    sb[k] = pb;
+  }
+  sort4(sa, s->na);
+  sort4(sb, s->na);
+  feat[0] = dd;
+  for (int k = 0; k < 4; ++k) {
+    feat[1 + k] = sa[k];
+    feat[5 + k] = sb[k];
+  }
+  if (target) {
+    double F[3] = {0, 0, 0};
+    const double rc2 = s->rc_at * s->rc_at;
+    for (int i = a * s->na; i < (a + 1) * s->na; ++i)
+      for (int j = b * s->na; j < (b + 1) * s->na; ++j) {
+        double r[3], r2 = 0;
+        for (int d = 0; d < 3; ++d) {
+          r[d] = minimg(x[3 * i + d] - x[3 * j + d], s->L[d]);
+          r2 += r[d] * r[d];
+        }
+        if (r2 >= rc2) continue;
+        double V, fr = wca_fr(s, r2, &V);
+        for (int d = 0; d < 3; ++d) F[d] += fr * r[d];
+      }
+    *target = -(F[0] * e[0] + F[1] * e[1] + F[2] * e[2]);
+  }
+}
+
+/* All pairs a < b whose COM distance is below rc: features [n][9], targets [n], ids [n][2].
+ * Returns the number of pairs written (at most cap; the count of all pairs if larger). */
+long orc_collect_pairs(const orc_sys* s, const double* x, double rc, long cap, double* feat, double* target,
+                       int* ids) {
+  double* R = (double*)malloc(sizeof(double) * 3 * s->M);
+  orc_com_lambda(s, x, R, NULL, NULL);
+  long n = 0;
+  for (int a = 0; a < s->M; ++a)
+    for (int b = a + 1; b < s->M; ++b) {
+      double r2 = 0;
+      for (int d = 0; d < 3; ++d) {
+        double t = minimg(R[3 * b + d] - R[3 * a + d], s->L[d]);
+        r2 += t * t;
+      }
+      if (r2 >= rc * rc) continue;
+      if (n < cap) {
+        orc_pair_features(s, x, a, b, feat + 9 * n, target + n);
+        ids[2 * n] = a;
+        ids[2 * n + 1] = b;
+      }
+      ++n;
+    }
+  free(R);
+  return n;
+}
+
+
+/* Network output y (before out_scale) for one feature vector; keeps z1, h1, z2, h2 when
+ * cache != NULL (cache = [4][nh]). */
+static double mlp_forward1(const orc_mlp* m, const double* feat, double* cache) {
+  const int nh = m->nh;
+  double x[9], z1[256], h1[256], z2[256], h2[256];
+  for (int k = 0; k < 9; ++k) {
+    x[k] = (feat[k] - m->in_mean[k]) / m->in_std[k];
+    if (m->bf16) x[k] = orc_bf16(x[k]);
+  }
+  for (int o = 0; o < nh; ++o) {
+    double acc = m->b1[o];
+    for (int k = 0; k < 9; ++k) acc += (m->bf16 ? orc_bf16(m->W1[o * 9 + k]) : m->W1[o * 9 + k]) * x[k];
+    z1[o] = acc;
+    h1[o] = silu(acc);
+    if (m->bf16) h1[o] = orc_bf16(h1[o]);
+  }
+  for (int o = 0; o < nh; ++o) {
+    double acc = m->b2[o];
+    for (int k = 0; k < nh; ++k) acc += (m->bf16 ? orc_bf16(m->W2[o * nh + k]) : m->W2[o * nh + k]) * h1[k];
+    z2[o] = acc;
+    h2[o] = silu(acc);
+  }
+  double y = m->b3;
+  for (int k = 0; k < nh; ++k) y += m->w3[k] * h2[k];
+  if (cache) {
+    memcpy(cache, z1, sizeof(double) * nh);
+    memcpy(cache + nh, h1, sizeof(double) * nh);
+    memcpy(cache + 2 * nh, z2, sizeof(double) * nh);
+    memcpy(cache + 3 * nh, h2, sizeof(double) * nh);
+  }
+  return y;
+}
+
+/* Forward over n feature vectors: y [n] (network output, before out_scale). */
+void orc_mlp_forward(const orc_mlp* m, long n, const double* feat, double* y) {
+  for (long s = 0; s < n; ++s) y[s] = mlp_forward1(m, feat + 9 * s, NULL);
+}
+
+/* Symmetrised pair force (after out_scale) for n feature vectors. */
+void orc_mlp_pair_force(const orc_mlp* m, long n, const double* feat, double* f) {
+  for (long s = 0; s < n; ++s) {
+    double sw[9];
+    sw[0] = feat[9 * s];
+    for (int k = 0; k < 4; ++k) {
+      sw[1 + k] = feat[9 * s + 5 + k];
+      sw[5 + k] = feat[9 * s + 1 + k];
+    }
+    f[s] = 0.5 * m->out_scale * (mlp_forward1(m, feat + 9 * s, NULL) + mlp_forward1(m, sw, NULL));
+  }
+}
+
+/* Loss L = (1/n) sum_s (y_s - t_s/out_scale)^2 and its gradient with respect to every
+ * parameter (gW1 [nh][9], gb1, gW2 [nh][nh], gb2, gw3, gb3), by the chain rule through the
+ * layers above (rounding to bfloat16 treated as the identity). Returns L. */
+double orc_mlp_loss_grad(const orc_mlp* m, long n, const double* feat, const double* target, double* gW1,
+                         double* gb1, double* gW2, double* gb2, double* gw3, double* gb3) {
+  const int nh = m->nh;
+  memset(gW1, 0, sizeof(double) * nh * 9);
+  memset(gb1, 0, sizeof(double) * nh);
+  memset(gW2, 0, sizeof(double) * nh * nh);
+  memset(gb2, 0, sizeof(double) * nh);
+  memset(gw3, 0, sizeof(double) * nh);
+  *gb3 = 0;
+  double loss = 0;
+  double cache[4 * 256], x[9], d2[256], d1[256];
+  for (long s = 0; s < n; ++s) {
+    const double* f = feat + 9 * s;
+    double y = mlp_forward1(m, f, cache);
+    double r = y - target[s] / m->out_scale;
+    loss += r * r;
+    double dy = 2.0 * r / n;
+    const double *z1 = cache, *h1 = cache + nh, *z2 = cache + 2 * nh, *h2 = cache + 3 * nh;
+    for (int k = 0; k < 9; ++k) {
+      x[k] = (f[k] - m->in_mean[k]) / m->in_std[k];
+      if (m->bf16) x[k] = orc_bf16(x[k]);
+    }
+    *gb3 += dy;
+    for (int k = 0; k < nh; ++k) {
+      gw3[k] += dy * h2[k];
+      d2[k] = dy * m->w3[k] * dsilu(z2[k]);
+      gb2[k] += d2[k];
+    }
+    for (int o = 0; o < nh; ++o)
+      for (int k = 0; k < nh; ++k) gW2[o * nh + k] += d2[o] * h1[k];
+    for (int k = 0; k < nh; ++k) {
+      double acc = 0;
+      for (int o = 0; o < nh; ++o) acc += d2[o] * (m->bf16 ? orc_bf16(m->W2[o * nh + k]) : m->W2[o * nh + k]);
+      d1[k] = acc * dsilu(z1[k]);
+      gb1[k] += d1[k];
+    }
+    for (int o = 0; o < nh; ++o)
+      for (int k = 0; k < 9; ++k) gW1[o * 9 + k] += d1[o] * x[k];
+  }
+  return loss / n;
+}

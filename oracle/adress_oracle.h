@@ -43,4 +43,22 @@ void orc_density(const orc_sys* s, const double* x, int nd, int64_t* counts_d, i
                  int64_t* counts_x);
 void orc_tf_update(const orc_sys* s, double* tf, int n, const int64_t* counts_d, int nd,
                    double nsamples, double alpha);
+
+/* learned CG pair force (force matching) */
+typedef struct {
+  int nh;
+  const double *W1, *b1, *W2, *b2, *w3;
+  double b3;
+  const double *in_mean, *in_std;
+  double out_scale;
+  int bf16;
+} orc_mlp;
+double orc_bf16(double v);
+void orc_pair_features(const orc_sys* s, const double* x, int a, int b, double* feat, double* target);
+long orc_collect_pairs(const orc_sys* s, const double* x, double rc, long cap, double* feat, double* target,
+                       int* ids);
+void orc_mlp_forward(const orc_mlp* m, long n, const double* feat, double* y);
+void orc_mlp_pair_force(const orc_mlp* m, long n, const double* feat, double* f);
+double orc_mlp_loss_grad(const orc_mlp* m, long n, const double* feat, const double* target, double* gW1,
+                         double* gb1, double* gW2, double* gb2, double* gw3, double* gb3);
 #endif
