@@ -145,6 +145,40 @@ adress_status adress_step(adress_handle h, int32_t nsteps);
 adress_status adress_run(adress_handle h, int32_t nsteps, int32_t sample_every, int32_t tf_update,
                          double alpha);
 
+/* ---- learned coarse-grained force (force matching) ------------------------------------
+ * The CG force of Eq. 1 acts between centres of mass (Sec. "Force interpolation"); the
+ * learned variant is a 9 -> 64 -> 64 -> 1 SiLU network of the COM distance d and eight
+ * orientation invariants (the projections of each molecule's atoms on the COM axis, each
+ * set sorted), trained to reproduce the atomistic force between the two molecules projected
+ * on the axis.  It runs on BF16 tensor cores with FP32 accumulation from FP32 master
+ * weights; the pair force is the mean over the two orderings of the molecules.
+ * params: host float [4865] = W1 [64][9] | b1 [64] | W2 [64][64] | b2 [64] | w3 [64] | b3
+ * norm:   host float [19]   = input means [9] | input standard deviations [9] | out_scale
+ * force = out_scale * (w3 . silu(W2 silu(W1 (feat - mean)/std + b1) + b2) + b3). */
+adress_status adress_mlp_set(adress_handle h, const float* params, const float* norm);
+adress_status adress_mlp_get(adress_handle h, float* params, float* norm); /* synchronises */
+/* 0: tabulated CG force (default); 1: learned network for every pair with COM distance
+ * < rc_cg and l_a l_b < 1 (no CG energy is accumulated in mode 1). */
+adress_status adress_set_cg_mode(adress_handle h, int32_t mode);
+/* Append training samples from the bound positions (lists rebuilt first): every molecule
+ * pair a < b with COM distance < rc_cg gives features (d, s_a[4], s_b[4]), the atomistic
+ * force on a from b along the axis as target, and the ids (a, b); at most cap samples are
+ * kept.  *n_total = samples now held.  Synchronises. */
+adress_status adress_mlp_collect(adress_handle h, int64_t cap, int64_t* n_total);
+/* Copy the first n held samples to the host (any pointer may be NULL). Synchronises. */
+adress_status adress_mlp_samples(adress_handle h, float* feat, float* target, int32_t* ids, int64_t n);
+/* Replace the held samples by n host samples (features [n][9], targets [n]). Synchronises. */
+adress_status adress_mlp_load_samples(adress_handle h, const float* feat, const float* target, int64_t n);
+/* Network outputs before out_scale: feat device float [n][9] -> y device float [n]. Async. */
+adress_status adress_mlp_forward(adress_handle h, const float* feat, int64_t n, float* y);
+/* Mean-squared force-matching loss L = (1/n) sum (y - t/out_scale)^2 of device samples and
+ * its gradient: grad host float [4866] = dL/dparams [4865] | n L.  Synchronises. */
+adress_status adress_mlp_loss_grad(adress_handle h, const float* feat, const float* target, int64_t n, float* grad);
+/* Adam (lr, betas 0.9/0.999, eps 1e-8) over the held samples in mini-batches of `batch`,
+ * visiting them in a fixed permutation; loss host float [epochs] = mean loss per epoch.
+ * Synchronises. */
+adress_status adress_mlp_train(adress_handle h, int32_t epochs, int32_t batch, float lr, float* loss);
+
 /* Time level of the bound state (keys the thermostat noise). */
 adress_status adress_set_step(adress_handle h, int64_t step);
 adress_status adress_get_step(adress_handle h, int64_t* step); /* synchronises */

@@ -25,6 +25,13 @@ _LIB = os.path.join(_BUILD, "libadress_oracle.so")
 ORC_OK, ORC_ERR_BOND = 0, 1
 
 
+class orc_mlp(C.Structure):
+    _fields_ = [("nh", C.c_int), ("W1", C.POINTER(C.c_double)), ("b1", C.POINTER(C.c_double)),
+                ("W2", C.POINTER(C.c_double)), ("b2", C.POINTER(C.c_double)), ("w3", C.POINTER(C.c_double)),
+                ("b3", C.c_double), ("in_mean", C.POINTER(C.c_double)), ("in_std", C.POINTER(C.c_double)),
+                ("out_scale", C.c_double), ("bf16", C.c_int)]
+
+
 class orc_sys(C.Structure):
     _fields_ = [
         ("M", C.c_int), ("na", C.c_int),
@@ -40,14 +47,8 @@ class orc_sys(C.Structure):
         ("tf", C.POINTER(C.c_double)), ("tf_n", C.c_int), ("tf_dx", C.c_double),
         ("kT", C.c_double), ("gamma", C.c_double), ("dt", C.c_double),
         ("seed", C.c_uint64), ("replica", C.c_int64),
+        ("mlp", C.POINTER(orc_mlp)),
     ]
-
-
-class orc_mlp(C.Structure):
-    _fields_ = [("nh", C.c_int), ("W1", C.POINTER(C.c_double)), ("b1", C.POINTER(C.c_double)),
-                ("W2", C.POINTER(C.c_double)), ("b2", C.POINTER(C.c_double)), ("w3", C.POINTER(C.c_double)),
-                ("b3", C.c_double), ("in_mean", C.POINTER(C.c_double)), ("in_std", C.POINTER(C.c_double)),
-                ("out_scale", C.c_double), ("bf16", C.c_int)]
 
 
 def build(force: bool = False, extra_flags: tuple = ()) -> str:
@@ -141,6 +142,12 @@ class Oracle:
             cgF=_ptr(k["cgF"]), cgV=_ptr(k["cgV"]), cg_n=len(k["cgF"]) - 1, cg_dr=s.cg_dr,
             rc_cg=s.rc_cg, tf=_ptr(k["tf"]), tf_n=len(k["tf"]), tf_dx=s.tf_dx,
             kT=s.kT, gamma=s.gamma, dt=s.dt, seed=int(s.seed), replica=int(replica))
+
+    def set_mlp(self, net):
+        """Use the learned CG pair force of `net` (an OracleMLP) in place of the table, or
+        the table again with net=None."""
+        self._mlp = net
+        self.sys.mlp = C.pointer(net.m) if net is not None else C.POINTER(orc_mlp)()
 
     def set_tf(self, tf):
         self._keep["tf"] = np.ascontiguousarray(tf, dtype=np.float64)

@@ -182,7 +182,14 @@ static void pair_ab(const orc_sys* s, const double* x, const double* R, const do
       r2 += Rab[d] * Rab[d];
     }
     if (r2 < s->rc_cg * s->rc_cg) {
-      double r = sqrt(r2), V, F = cg_table(s, r, &V);
+      double r = sqrt(r2), V = 0.0, F;
+      if (s->mlp) {
+        double feat[9];
+        orc_pair_features(s, x, a, b, feat, NULL);
+        orc_mlp_pair_force(s->mlp, 1, feat, &F);
+      } else {
+        F = cg_table(s, r, &V);
+      }
       double c = (1.0 - wab) * F / r;
       const double Mt = mol_mass(s);
       /* the COM force reaches each atom in proportion m_i / M (dR/dx_i = m_i/M) */

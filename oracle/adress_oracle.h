@@ -9,6 +9,16 @@
 
 enum { ORC_OK = 0, ORC_ERR_BOND = 1 };
 
+/* learned CG pair force (force matching) */
+typedef struct {
+  int nh;
+  const double *W1, *b1, *W2, *b2, *w3;
+  double b3;
+  const double *in_mean, *in_std;
+  double out_scale;
+  int bf16;
+} orc_mlp;
+
 typedef struct {
   int M, na;
   const double* mass; /* na per-site masses */
@@ -28,6 +38,7 @@ typedef struct {
   double kT, gamma, dt;
   uint64_t seed;
   int64_t replica;
+  const orc_mlp* mlp; /* when non-NULL the CG force of Eq. 1 is the learned pair force */
 } orc_sys;
 
 void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -44,15 +55,6 @@ void orc_density(const orc_sys* s, const double* x, int nd, int64_t* counts_d, i
 void orc_tf_update(const orc_sys* s, double* tf, int n, const int64_t* counts_d, int nd,
                    double nsamples, double alpha);
 
-/* learned CG pair force (force matching) */
-typedef struct {
-  int nh;
-  const double *W1, *b1, *W2, *b2, *w3;
-  double b3;
-  const double *in_mean, *in_std;
-  double out_scale;
-  int bf16;
-} orc_mlp;
 double orc_bf16(double v);
 void orc_pair_features(const orc_sys* s, const double* x, int a, int b, double* feat, double* target);
 long orc_collect_pairs(const orc_sys* s, const double* x, double rc, long cap, double* feat, double* target,

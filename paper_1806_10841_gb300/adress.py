@@ -25,7 +25,9 @@ EXPORTS = ["adress_init", "adress_bind_state", "adress_build_lists", "adress_com
            "adress_density_accumulate", "adress_density_get", "adress_density_reset",
            "adress_tf_update", "adress_set_tf", "adress_get_tf", "adress_list_stats", "adress_list_export",
            "adress_time_kernels",
-           "adress_kinetic_noalloc", "adress_check",
+           "adress_kinetic_noalloc", "adress_check", "adress_mlp_set", "adress_mlp_get", "adress_set_cg_mode",
+           "adress_mlp_collect", "adress_mlp_samples", "adress_mlp_load_samples", "adress_mlp_forward",
+           "adress_mlp_loss_grad", "adress_mlp_train",
            "adress_last_error", "adress_status_string", "adress_destroy"]
 
 
@@ -91,6 +93,16 @@ def load_library(path: str = LIB_PATH):
         "adress_time_kernels": ([H, C.c_int32, C.POINTER(C.c_float)], C.c_int),
         "adress_kinetic_noalloc": ([vp, C.c_int64, C.c_int32, d, vp, vp], C.c_int),
         "adress_check": ([H], C.c_int),
+        "adress_mlp_set": ([H, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
+        "adress_mlp_get": ([H, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
+        "adress_set_cg_mode": ([H, C.c_int32], C.c_int),
+        "adress_mlp_collect": ([H, C.c_int64, i64p], C.c_int),
+        "adress_mlp_samples": ([H, C.POINTER(C.c_float), C.POINTER(C.c_float), C.POINTER(C.c_int32), C.c_int64],
+                               C.c_int),
+        "adress_mlp_load_samples": ([H, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int64], C.c_int),
+        "adress_mlp_forward": ([H, vp, C.c_int64, vp], C.c_int),
+        "adress_mlp_loss_grad": ([H, vp, vp, C.c_int64, C.POINTER(C.c_float)], C.c_int),
+        "adress_mlp_train": ([H, C.c_int32, C.c_int32, C.c_float, C.POINTER(C.c_float)], C.c_int),
         "adress_last_error": ([H], C.c_char_p),
         "adress_status_string": ([C.c_int], C.c_char_p),
         "adress_destroy": ([H], None),
@@ -288,6 +300,89 @@ class AdResS:
         out = (C.c_float * 4)()
         self._call("adress_time_kernels", C.c_int32(int(reps)), out)
         return dict(prologue=out[0], rebuild=out[1], step=out[2], last=out[3])
+
+    # -- learned CG force ---------------------------------------------------------------
+    MLP_NPAR, MLP_NNORM = 4865, 19
+
+    @staticmethod
+    def mlp_flatten(p):
+        """dict (W1 [64,9], b1, W2 [64,64], b2, w3, b3) -> flat float32 [4865]."""
+        return np.concatenate([np.asarray(p[k], dtype=np.float32).reshape(-1)
+                               for k in ("W1", "b1", "W2", "b2", "w3")] + [np.float32([p["b3"]])])
+
+    @staticmethod
+    def mlp_unflatten(v):
+        v = np.asarray(v, dtype=np.float64)
+        o = 0
+        out = {}
+        for k, shape in (("W1", (64, 9)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("w3", (64,))):
+            n = int(np.prod(shape))
+            out[k] = v[o:o + n].reshape(shape)
+            o += n
+        out["b3"] = float(v[o])
+        return out
+
+    def mlp_set(self, params, in_mean, in_std, out_scale):
+        flat = np.ascontiguousarray(self.mlp_flatten(params))
+        norm = np.ascontiguousarray(np.concatenate([in_mean, in_std, [out_scale]]).astype(np.float32))
+        f32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+        self._call("adress_mlp_set", f32(flat), f32(norm))
+
+    def mlp_get(self):
+        flat = np.zeros(self.MLP_NPAR, dtype=np.float32)
+        norm = np.zeros(self.MLP_NNORM, dtype=np.float32)
+        f32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+        self._call("adress_mlp_get", f32(flat), f32(norm))
+        p = self.mlp_unflatten(flat)
+        p.update(in_mean=norm[:9].astype(np.float64), in_std=norm[9:18].astype(np.float64),
+                 out_scale=float(norm[18]))
+        return p
+
+    def set_cg_mode(self, mode: int):
+        self._call("adress_set_cg_mode", C.c_int32(int(mode)))
+
+    def mlp_collect(self, cap: int) -> int:
+        n = C.c_int64()
+        self._call("adress_mlp_collect", C.c_int64(int(cap)), C.byref(n))
+        return n.value
+
+    def mlp_samples(self, n: int):
+        feat = np.zeros((n, 9), dtype=np.float32)
+        t = np.zeros(n, dtype=np.float32)
+        ids = np.zeros((n, 2), dtype=np.int32)
+        self._call("adress_mlp_samples", feat.ctypes.data_as(C.POINTER(C.c_float)),
+                   t.ctypes.data_as(C.POINTER(C.c_float)), ids.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int64(n))
+        return feat, t, ids
+
+    def mlp_load_samples(self, feat, target):
+        feat = np.ascontiguousarray(feat, dtype=np.float32)
+        target = np.ascontiguousarray(target, dtype=np.float32)
+        self._call("adress_mlp_load_samples", feat.ctypes.data_as(C.POINTER(C.c_float)),
+                   target.ctypes.data_as(C.POINTER(C.c_float)), C.c_int64(len(target)))
+
+    def mlp_forward(self, feat):
+        t = self.torch
+        fd = t.from_numpy(np.ascontiguousarray(feat, dtype=np.float32)).to(self.device)
+        y = t.zeros(len(fd), dtype=t.float32, device=self.device)
+        self._call("adress_mlp_forward", C.c_void_p(fd.data_ptr()), C.c_int64(len(fd)), C.c_void_p(y.data_ptr()))
+        self.stream.synchronize()
+        return y.cpu().numpy().astype(np.float64)
+
+    def mlp_loss_grad(self, feat, target):
+        t = self.torch
+        fd = t.from_numpy(np.ascontiguousarray(feat, dtype=np.float32)).to(self.device)
+        td = t.from_numpy(np.ascontiguousarray(target, dtype=np.float32)).to(self.device)
+        g = np.zeros(self.MLP_NPAR + 1, dtype=np.float32)
+        self._call("adress_mlp_loss_grad", C.c_void_p(fd.data_ptr()), C.c_void_p(td.data_ptr()),
+                   C.c_int64(len(td)), g.ctypes.data_as(C.POINTER(C.c_float)))
+        grads = self.mlp_unflatten(g[:-1])
+        return float(g[-1]) / len(td), grads
+
+    def mlp_train(self, epochs: int, batch: int = 1024, lr: float = 1e-3):
+        loss = np.zeros(epochs, dtype=np.float32)
+        self._call("adress_mlp_train", C.c_int32(int(epochs)), C.c_int32(int(batch)), C.c_float(lr),
+                   loss.ctypes.data_as(C.POINTER(C.c_float)))
+        return loss
 
     def check(self):
         self._call("adress_check")

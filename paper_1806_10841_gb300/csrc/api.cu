@@ -30,6 +30,23 @@ struct adress_ctx {
   // captured step graphs keyed by (steps, sample interval, TF update, alpha bits)
   std::map<std::tuple<int, int, int, uint64_t>, std::pair<cudaGraph_t, cudaGraphExec_t>> graphs;
   bool eager = false;  // ADRESS_EAGER=1: launch kernel by kernel (for per-kernel profilers)
+  // learned CG force
+  float* mlp_P = nullptr;
+  unsigned *mlp_W1p = nullptr, *mlp_W2p = nullptr, *mlp_W2Tp = nullptr;
+  float *mlp_norm = nullptr, *mlp_mom = nullptr, *mlp_vel = nullptr, *mlp_grad = nullptr, *mlp_loss = nullptr;
+  float* mlp_part = nullptr;
+  long long mlp_part_blocks = 0;
+  int mlp_step = 0;
+  bool mlp_ready = false;
+  float* smp_feat = nullptr;
+  float* smp_target = nullptr;
+  int* smp_ids = nullptr;
+  long long smp_n = 0, smp_cap = 0;
+  float *bat_feat = nullptr, *bat_target = nullptr;
+  long long bat_cap = 0;
+  int* mlp_counts = nullptr;  // [M + 1]
+  int* mlp_offs = nullptr;    // [M + 1]
+  MlpDevArgs mlp_args() const { return MlpDevArgs{mlp_P, mlp_W1p, mlp_W2p, mlp_W2Tp, mlp_norm}; }
 };
 
 static thread_local std::string g_init_error;
@@ -61,6 +78,18 @@ static cudaError_t dalloc(adress_ctx* h, T** p, size_t n) {
   h->allocs.push_back(q);
   *p = (T*)q;
   return cudaSuccess;
+}
+
+// Replace an owned device buffer by a new allocation of n elements (contents not kept).
+template <class T>
+static cudaError_t realloc_owned(adress_ctx* h, T** p, size_t n) {
+  if (*p) {
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), (void*)*p);
+    if (it != h->allocs.end()) h->allocs.erase(it);
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  return dalloc(h, p, n);
 }
 
 static void free_graphs(adress_ctx* h) {
@@ -411,6 +440,7 @@ static adress_status build_lists_sync(adress_handle h) {
       cudaFree(old);
       h->buf.nbr = nbr;
       h->sys.cap = cap;
+      if (h->buf.fpair) CUDA_OR_FAIL(h, realloc_owned(h, &h->buf.fpair, (size_t)cap * h->sys.M));
       free_graphs(h);
       int zero = 0;
       CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->buf.ctrl->err, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -435,6 +465,7 @@ adress_status adress_compute_forces(adress_handle h, double* energies) {
   if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
   adress_status st = build_lists_sync(h);
   if (st != ADRESS_OK) return st;
+  if (h->sys.cg_mode) CUDA_OR_FAIL(h, mlp_pairs(h->sys, h->buf, h->mlp_args(), h->buf.fpair, h->stream));
   CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 0, energies != nullptr, h->stream));
   if (energies) {
     CUDA_OR_FAIL(h, launch_energy_reduce(h->sys, h->buf, force_warps(h->sys), 4, h->stream));
@@ -474,8 +505,11 @@ static adress_status capture_steps(adress_handle h, int nsteps, int sample_every
                                       cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
     const DecideArgs da{0, 1, 1, cond};  // the mapping kernel's last block sets the conditional
-    cudaError_t le = k == 0 ? launch_com(h->sys, h->buf, h->precision, 1, cs, da)
-                            : launch_step(h->sys, h->buf, h->precision, 2, 0, cs, da);
+    cudaError_t le = cudaSuccess;
+    if (k > 0 && h->sys.cg_mode) le = mlp_pairs(h->sys, h->buf, h->mlp_args(), h->buf.fpair, cs);
+    if (le == cudaSuccess)
+      le = k == 0 ? launch_com(h->sys, h->buf, h->precision, 1, cs, da)
+                  : launch_step(h->sys, h->buf, h->precision, 2, 0, cs, da);
     std::vector<cudaGraphNode_t> tail;
     cudaError_t ge = grab(tail);
     cudaGraph_t gg = g;
@@ -515,7 +549,9 @@ static adress_status capture_steps(adress_handle h, int nsteps, int sample_every
   if (e == cudaSuccess) {
     e = cudaStreamBeginCaptureToGraph(cs, g, deps.data(), nullptr, deps.size(), cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      cudaError_t le = launch_step(h->sys, h->buf, h->precision, 1, 0, cs);
+      cudaError_t le = cudaSuccess;
+      if (h->sys.cg_mode) le = mlp_pairs(h->sys, h->buf, h->mlp_args(), h->buf.fpair, cs);
+      if (le == cudaSuccess) le = launch_step(h->sys, h->buf, h->precision, 1, 0, cs);
       if (le == cudaSuccess && tf_update) le = launch_tf_update(h->sys, h->buf, alpha, cs);
       cudaGraph_t gg = g;
       e = cudaStreamEndCapture(cs, &gg);
@@ -560,6 +596,7 @@ adress_status adress_run(adress_handle h, int32_t nsteps, int32_t sample_every, 
   if (h->eager) {
     for (int k = 0; k < nsteps; ++k) {
       const DecideArgs da{0, 1, 0, 0};
+      if (k > 0 && h->sys.cg_mode) CUDA_OR_FAIL(h, mlp_pairs(h->sys, h->buf, h->mlp_args(), h->buf.fpair, h->stream));
       if (k == 0) CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 1, h->stream, da));
       else CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 2, 0, h->stream, da));
       Ctrl c;
@@ -569,6 +606,7 @@ adress_status adress_run(adress_handle h, int32_t nsteps, int32_t sample_every, 
       if (sample_every > 0 && (k + 1) % sample_every == 0)
         CUDA_OR_FAIL(h, launch_density(h->sys, h->buf, h->precision, h->stream));
     }
+    if (h->sys.cg_mode) CUDA_OR_FAIL(h, mlp_pairs(h->sys, h->buf, h->mlp_args(), h->buf.fpair, h->stream));
     CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 1, 0, h->stream));
     if (tf_update) CUDA_OR_FAIL(h, launch_tf_update(h->sys, h->buf, alpha, h->stream));
     return ADRESS_OK;
@@ -584,6 +622,7 @@ adress_status adress_step(adress_handle h, int32_t nsteps) {
   if (h->eager) {
     for (int k = 0; k < nsteps; ++k) {
       const DecideArgs da{0, 1, 0, 0};
+      if (k > 0 && h->sys.cg_mode) CUDA_OR_FAIL(h, mlp_pairs(h->sys, h->buf, h->mlp_args(), h->buf.fpair, h->stream));
       if (k == 0) CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 1, h->stream, da));
       else CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 2, 0, h->stream, da));
       Ctrl c;
@@ -591,6 +630,7 @@ adress_status adress_step(adress_handle h, int32_t nsteps) {
       if (st != ADRESS_OK) return st;
       if (c.rebuild) CUDA_OR_FAIL(h, launch_rebuild(h->sys, h->buf, h->stream));
     }
+    if (h->sys.cg_mode) CUDA_OR_FAIL(h, mlp_pairs(h->sys, h->buf, h->mlp_args(), h->buf.fpair, h->stream));
     CUDA_OR_FAIL(h, launch_step(h->sys, h->buf, h->precision, 1, 0, h->stream));
     return ADRESS_OK;
   }
@@ -725,9 +765,11 @@ adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out) 
   timed(0, [&] { return launch_com(h->sys, h->buf, h->precision, 1, st, DecideArgs{1, 1, 0, 0}); });
   timed(1, [&] { return launch_rebuild(h->sys, h->buf, st); });
   for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    if (h->sys.cg_mode && e == cudaSuccess) e = mlp_pairs(h->sys, h->buf, h->mlp_args(), h->buf.fpair, st);
     timed(2, [&] { return launch_step(h->sys, h->buf, h->precision, 2, 0, st, DecideArgs{1, 1, 0, 0}); });
     timed(1, [&] { return launch_rebuild(h->sys, h->buf, st); });
   }
+  if (h->sys.cg_mode && e == cudaSuccess) e = mlp_pairs(h->sys, h->buf, h->mlp_args(), h->buf.fpair, st);
   timed(3, [&] { return launch_step(h->sys, h->buf, h->precision, 1, 0, st); });
   for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
   if (e != cudaSuccess) return fail(h, ADRESS_ERR_CUDA, std::string("kernel timing: ") + cudaGetErrorString(e));
@@ -746,6 +788,205 @@ adress_status adress_list_export(adress_handle h, int32_t* items, int32_t* nn, i
   CUDA_OR_FAIL(h, cudaMemcpyAsync(nn, h->buf.nn, sizeof(int) * M, cudaMemcpyDeviceToHost, h->stream));
   CUDA_OR_FAIL(h, cudaMemcpyAsync(nbr, h->buf.nbr, sizeof(int) * M * h->sys.cap, cudaMemcpyDeviceToHost, h->stream));
   CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
+// ---------------- learned CG force ------------------------------------------------------
+
+static adress_status mlp_alloc(adress_handle h) {
+  if (h->mlp_P) return ADRESS_OK;
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_P, kMlpNPar));
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_W1p, 64 * 8));
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_W2p, 64 * 32));
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_W2Tp, 64 * 32));
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_norm, kMlpNNorm));
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_mom, kMlpNPar));
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_vel, kMlpNPar));
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_grad, kMlpNPar + 1));
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_loss, 1024));
+  return ADRESS_OK;
+}
+
+static adress_status mlp_part_for(adress_handle h, long long n) {
+  const long long blocks = (n + 63) / 64;
+  if (blocks <= h->mlp_part_blocks) return ADRESS_OK;
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  CUDA_OR_FAIL(h, realloc_owned(h, &h->mlp_part, (size_t)blocks * kMlpGradStride));
+  h->mlp_part_blocks = blocks;
+  return ADRESS_OK;
+}
+
+adress_status adress_mlp_set(adress_handle h, const float* params, const float* norm) {
+  if (!h || !params || !norm) return ADRESS_ERR_ARG;
+  for (int k = 0; k < 9; ++k)
+    if (!(norm[9 + k] > 0)) return fail(h, ADRESS_ERR_ARG, "input standard deviations must be > 0");
+  adress_status st = mlp_alloc(h);
+  if (st != ADRESS_OK) return st;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->mlp_P, params, sizeof(float) * kMlpNPar, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->mlp_norm, norm, sizeof(float) * kMlpNNorm, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaMemsetAsync(h->mlp_mom, 0, sizeof(float) * kMlpNPar, h->stream));
+  CUDA_OR_FAIL(h, cudaMemsetAsync(h->mlp_vel, 0, sizeof(float) * kMlpNPar, h->stream));
+  CUDA_OR_FAIL(h, mlp_pack(h->mlp_args(), h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  h->mlp_step = 0;
+  h->mlp_ready = true;
+  return ADRESS_OK;
+}
+
+adress_status adress_mlp_get(adress_handle h, float* params, float* norm) {
+  if (!h || !params || !norm) return ADRESS_ERR_ARG;
+  if (!h->mlp_ready) return fail(h, ADRESS_ERR_STATE, "no network parameters set");
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(params, h->mlp_P, sizeof(float) * kMlpNPar, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(norm, h->mlp_norm, sizeof(float) * kMlpNNorm, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_set_cg_mode(adress_handle h, int32_t mode) {
+  if (!h || mode < 0 || mode > 1) return ADRESS_ERR_ARG;
+  if (mode == 1) {
+    if (!h->mlp_ready) return fail(h, ADRESS_ERR_STATE, "set the network parameters first");
+    if (h->sys.NA != 4 && h->sys.NA != 3 && h->sys.NA != 2 && h->sys.NA != 1) return ADRESS_ERR_ARG;
+    if (!h->buf.fpair) CUDA_OR_FAIL(h, dalloc(h, &h->buf.fpair, (size_t)h->sys.cap * h->sys.M));
+  }
+  if (h->sys.cg_mode != mode) free_graphs(h);
+  h->sys.cg_mode = mode;
+  return ADRESS_OK;
+}
+
+adress_status adress_mlp_collect(adress_handle h, int64_t cap, int64_t* n_total) {
+  if (!h || cap < 1 || !n_total) return ADRESS_ERR_ARG;
+  if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
+  adress_status st = build_lists_sync(h);
+  if (st != ADRESS_OK) return st;
+  const int M = h->sys.M;
+  if (!h->mlp_counts) {
+    CUDA_OR_FAIL(h, dalloc(h, &h->mlp_counts, M + 1));
+    CUDA_OR_FAIL(h, dalloc(h, &h->mlp_offs, M + 1));
+  }
+  CUDA_OR_FAIL(h, mlp_collect(h->sys, h->buf, 0, nullptr, 0, 0, nullptr, nullptr, nullptr, h->mlp_counts, h->stream));
+  CUDA_OR_FAIL(h, device_exclusive_scan(h->mlp_counts, h->mlp_offs, M, h->buf.scan_tmp, h->mlp_offs + M, h->stream));
+  int found = 0;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(&found, h->mlp_offs + M, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  if (h->smp_cap < cap) {
+    // grow, keeping the samples collected so far
+    float *nf = nullptr, *nt = nullptr;
+    int* ni = nullptr;
+    CUDA_OR_FAIL(h, dalloc(h, &nf, (size_t)cap * 9));
+    CUDA_OR_FAIL(h, dalloc(h, &nt, (size_t)cap));
+    CUDA_OR_FAIL(h, dalloc(h, &ni, (size_t)cap * 2));
+    if (h->smp_n > 0) {
+      CUDA_OR_FAIL(h, cudaMemcpyAsync(nf, h->smp_feat, sizeof(float) * 9 * h->smp_n, cudaMemcpyDeviceToDevice, h->stream));
+      CUDA_OR_FAIL(h, cudaMemcpyAsync(nt, h->smp_target, sizeof(float) * h->smp_n, cudaMemcpyDeviceToDevice, h->stream));
+      CUDA_OR_FAIL(h, cudaMemcpyAsync(ni, h->smp_ids, sizeof(int) * 2 * h->smp_n, cudaMemcpyDeviceToDevice, h->stream));
+      CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    }
+    for (void* old : {(void*)h->smp_feat, (void*)h->smp_target, (void*)h->smp_ids})
+      if (old) {
+        h->allocs.erase(std::find(h->allocs.begin(), h->allocs.end(), old));
+        cudaFree(old);
+      }
+    h->smp_feat = nf;
+    h->smp_target = nt;
+    h->smp_ids = ni;
+    h->smp_cap = cap;
+  }
+  CUDA_OR_FAIL(h, mlp_collect(h->sys, h->buf, 1, h->mlp_offs, h->smp_cap, h->smp_n, h->smp_feat, h->smp_target,
+                              h->smp_ids, nullptr, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  h->smp_n = std::min<long long>(h->smp_cap, h->smp_n + found);
+  *n_total = h->smp_n;
+  return ADRESS_OK;
+}
+
+adress_status adress_mlp_samples(adress_handle h, float* feat, float* target, int32_t* ids, int64_t n) {
+  if (!h || n < 0 || n > h->smp_n) return ADRESS_ERR_ARG;
+  if (n == 0) return ADRESS_OK;
+  if (feat) CUDA_OR_FAIL(h, cudaMemcpyAsync(feat, h->smp_feat, sizeof(float) * 9 * n, cudaMemcpyDeviceToHost, h->stream));
+  if (target) CUDA_OR_FAIL(h, cudaMemcpyAsync(target, h->smp_target, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+  if (ids) CUDA_OR_FAIL(h, cudaMemcpyAsync(ids, h->smp_ids, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_mlp_load_samples(adress_handle h, const float* feat, const float* target, int64_t n) {
+  if (!h || !feat || !target || n < 1) return ADRESS_ERR_ARG;
+  if (h->smp_cap < n) {
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    CUDA_OR_FAIL(h, realloc_owned(h, &h->smp_feat, (size_t)n * 9));
+    CUDA_OR_FAIL(h, realloc_owned(h, &h->smp_target, (size_t)n));
+    CUDA_OR_FAIL(h, realloc_owned(h, &h->smp_ids, (size_t)n * 2));
+    h->smp_cap = n;
+  }
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->smp_feat, feat, sizeof(float) * 9 * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->smp_target, target, sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaMemsetAsync(h->smp_ids, 0xff, sizeof(int) * 2 * n, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  h->smp_n = n;
+  return ADRESS_OK;
+}
+
+adress_status adress_mlp_forward(adress_handle h, const float* feat, int64_t n, float* y) {
+  if (!h || !feat || !y || n < 1) return ADRESS_ERR_ARG;
+  if (!h->mlp_ready) return fail(h, ADRESS_ERR_STATE, "no network parameters set");
+  CUDA_OR_FAIL(h, mlp_forward(h->mlp_args(), feat, n, y, h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_mlp_loss_grad(adress_handle h, const float* feat, const float* target, int64_t n, float* grad) {
+  if (!h || !feat || !target || !grad || n < 1) return ADRESS_ERR_ARG;
+  if (!h->mlp_ready) return fail(h, ADRESS_ERR_STATE, "no network parameters set");
+  adress_status st = mlp_part_for(h, n);
+  if (st != ADRESS_OK) return st;
+  CUDA_OR_FAIL(h, mlp_grad(h->mlp_args(), feat, target, n, n, h->mlp_part, h->mlp_grad, nullptr, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(grad, h->mlp_grad, sizeof(float) * (kMlpNPar + 1), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
+static long long coprime_stride(long long n) {
+  long long p = 1000003;  // prime; advance to the next value coprime with n
+  auto gcd = [](long long a, long long b) {
+    while (b) {
+      long long t = a % b;
+      a = b;
+      b = t;
+    }
+    return a;
+  };
+  while (gcd(p, n) != 1) p += 2;
+  return p % n == 0 ? 1 : p;
+}
+
+adress_status adress_mlp_train(adress_handle h, int32_t epochs, int32_t batch, float lr, float* loss) {
+  if (!h || epochs < 1 || epochs > 1024 || batch < 16 || !(lr > 0)) return ADRESS_ERR_ARG;
+  if (!h->mlp_ready) return fail(h, ADRESS_ERR_STATE, "no network parameters set");
+  if (h->smp_n < batch) return fail(h, ADRESS_ERR_STATE, "fewer samples than one batch");
+  adress_status st = mlp_part_for(h, batch);
+  if (st != ADRESS_OK) return st;
+  if (h->bat_cap < batch) {
+    CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+    CUDA_OR_FAIL(h, realloc_owned(h, &h->bat_feat, (size_t)batch * 9));
+    CUDA_OR_FAIL(h, realloc_owned(h, &h->bat_target, (size_t)batch));
+    h->bat_cap = batch;
+  }
+  const long long n = h->smp_n, nb = n / batch, stride = coprime_stride(n);
+  CUDA_OR_FAIL(h, cudaMemsetAsync(h->mlp_loss, 0, sizeof(float) * epochs, h->stream));
+  for (int e = 0; e < epochs; ++e)
+    for (long long bi = 0; bi < nb; ++bi) {
+      CUDA_OR_FAIL(h, mlp_gather(h->smp_feat, h->smp_target, n, (e * nb + bi) * batch, batch, stride, h->bat_feat,
+                                 h->bat_target, h->stream));
+      CUDA_OR_FAIL(h, mlp_grad(h->mlp_args(), h->bat_feat, h->bat_target, batch, batch, h->mlp_part, h->mlp_grad,
+                               h->mlp_loss + e, h->stream));
+      CUDA_OR_FAIL(h, mlp_adam(h->mlp_args(), h->mlp_mom, h->mlp_vel, h->mlp_grad, lr, ++h->mlp_step, h->stream));
+      CUDA_OR_FAIL(h, mlp_pack(h->mlp_args(), h->stream));
+    }
+  std::vector<float> acc(epochs);
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(acc.data(), h->mlp_loss, sizeof(float) * epochs, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  if (loss)
+    for (int e = 0; e < epochs; ++e) loss[e] = acc[e] / (float)(nb * batch);
   return ADRESS_OK;
 }
 

@@ -72,6 +72,7 @@ struct Sys {
   int nc[3];
   int ncell;
   int cap;  // neighbour-list capacity per molecule
+  int cg_mode;  // 0: tabulated F^CG, 1: learned network (pair forces in Bufs::fpair)
   double dt_m[kMaxNA];  // dt / m (both half kicks of a fused step)
   // float copies of the parameters the FP32 path uses (no run-time double->float work)
   struct {
@@ -123,7 +124,20 @@ struct Bufs {
   unsigned long long* hist;  // density histogram [tf_n]
   long long* nsamples;
   Ctrl* ctrl;
+  float* fpair;  // [M*cap] network CG pair force per list slot (CG mode 1)
 };
+
+// Learned CG force: device parameter arrays (see mlp.cu).
+struct MlpDevArgs {
+  const float* P;
+  const unsigned* W1p;
+  const unsigned* W2p;
+  const unsigned* W2Tp;
+  const float* norm;
+};
+constexpr int kMlpNPar = 4865;   // 64*9 + 64 + 64*64 + 64 + 64 + 1
+constexpr int kMlpNNorm = 19;    // in_mean[9], in_std[9], out_scale
+constexpr int kMlpGradStride = 4868;
 
 __device__ __forceinline__ void set_error(Ctrl* c, int code, int info = 0) {
   if (atomicCAS(&c->err, 0, code) == 0) c->err_info = info;
@@ -158,6 +172,8 @@ cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st);
 // molecule arrays and, in a graph, sets the conditional of the rebuild node.
 cudaError_t launch_decide(const Sys& s, const Bufs& b, DecideArgs da, cudaStream_t st);
 cudaError_t launch_max_nn(const Sys& s, const Bufs& b, cudaStream_t st);
+// out[i] = sum_{j<i} in[j] for i < n, *total = sum of all (n <= 8M)
+cudaError_t device_exclusive_scan(const int* in, int* out, int n, int* tmp, int* total, cudaStream_t st);
 // mode: 0 conservative forces, 1 last step of a run (thermostat + second half kick),
 // 2 fused step (thermostat + both half kicks + drift + next mapping)
 cudaError_t launch_step(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st,
@@ -170,6 +186,18 @@ cudaError_t launch_tf_update(const Sys& s, const Bufs& b, double alpha, cudaStre
 cudaError_t launch_export_com(const Sys& s, const Bufs& b, int precision, double* com, double* w, cudaStream_t st);
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+cudaError_t mlp_forward(const MlpDevArgs& a, const float* feat, long long n, float* y, cudaStream_t st);
+cudaError_t mlp_grad(const MlpDevArgs& a, const float* feat, const float* target, long long n, long long n_total,
+                     float* part, float* grad, float* loss_acc, cudaStream_t st);
+cudaError_t mlp_adam(const MlpDevArgs& a, float* mom, float* vel, const float* grad, float lr, int step,
+                     cudaStream_t st);
+cudaError_t mlp_pack(const MlpDevArgs& a, cudaStream_t st);
+cudaError_t mlp_collect(const Sys& s, const Bufs& b, int pass, const int* offs, long long cap, long long base,
+                        float* feat, float* target, int* ids, int* counts, cudaStream_t st);
+cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* fpair, cudaStream_t st);
+cudaError_t mlp_gather(const float* feat, const float* target, long long n, long long start, long long cnt,
+                       long long stride, float* feat_out, float* target_out, cudaStream_t st);
 
 // Record the message returned by adress_last_error(NULL) and return the status.
 adress_status set_global_error(adress_status s, const std::string& msg);

@@ -325,6 +325,10 @@ cudaError_t launch_max_nn(const Sys& s, const Bufs& b, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+cudaError_t device_exclusive_scan(const int* in, int* out, int n, int* tmp, int* total, cudaStream_t st) {
+  return exclusive_scan(in, out, n, tmp, total, st);
+}
+
 cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st) {
   cudaError_t e;
   k_rb_zero<<<ceil_div(s.ncell, 256) < 1024 ? ceil_div(s.ncell, 256) : 1024, 256, 0, st>>>(s, b);

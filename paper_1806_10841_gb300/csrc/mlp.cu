@@ -1,0 +1,733 @@
+// Learned coarse-grained pair force: a 9 -> 64 -> 64 -> 1 SiLU network of the COM
+// distance and eight orientation invariants, trained by force matching on atomistic pair
+// forces, replacing the tabulated F^CG of Eq. 1 (Sec. "Force interpolation": the CG force
+// acts between the molecules' centres of mass).
+//
+// Features of a pair (a, b): e = (R_b - R_a)/d, d = |R_b - R_a|; the four projections of
+// a's atoms on e and of b's atoms on -e, each sorted ascending.  Target: the atomistic
+// force on a from b projected on -e (positive = repulsive).  Network: x = (feat - mean)/std,
+// h1 = silu(W1 x + b1), h2 = silu(W2 h1 + b2), y = w3.h2 + b3, force = out_scale * y; the
+// pair force is the mean over the two orderings of (s_a, s_b), so it is the same for both
+// molecules and Newton's third law holds exactly.
+//
+// Tensor cores: warp-level BF16 mma (m16n8k16) with FP32 accumulation.  The layer-1
+// accumulators of a 16-sample tile are, element for element, the A fragments of layer 2,
+// so activations never leave registers in the forward pass.  Weights are BF16 copies of
+// FP32 master weights; the backward pass propagates deltas with the same tensor-core
+// product and forms the weight gradients as BF16 tensor-core products over the samples of
+// a block, with FP32 accumulation, per-block partials and a fixed-order reduction.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace adress {
+
+// ---------------- parameters ----------------------------------------------------------
+// Flat FP32 master vector: [W1 (64 x 9) | b1 (64) | W2 (64 x 64) | b2 (64) | w3 (64) | b3]
+constexpr int kH = 64;
+constexpr int kIn = 9;
+constexpr int oW1 = 0, ob1 = oW1 + kH * kIn, oW2 = ob1 + kH, ob2 = oW2 + kH * kH, ow3 = ob2 + kH, ob3 = ow3 + kH;
+constexpr int kNPar = ob3 + 1;  // 4865
+constexpr int kGradStride = kMlpGradStride;  // per-block partial record (params + loss, padded)
+static_assert(kNPar == kMlpNPar, "parameter layout");
+
+struct MlpDev {
+  const float* P;       // master parameters (FP32)
+  const unsigned* W1p;  // W1 as bf16 pairs, K padded to 16: [64][8]
+  const unsigned* W2p;  // W2 as bf16 pairs: [64 out][32 in-pairs]
+  const unsigned* W2Tp; // W2 transposed as bf16 pairs: [64 in][32 out-pairs]
+  const float* norm;    // in_mean[9], in_std[9], out_scale
+};
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<unsigned*>(&v);
+}
+__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float dsilu_f(float z) {
+  const float sg = 1.0f / (1.0f + __expf(-z));
+  return sg * (1.0f + z * (1.0f - sg));
+}
+
+// D = A (16x16 bf16, row) * B (16x8 bf16, col) + C, FP32 accumulate.
+__device__ __forceinline__ void mma16816(float d[4], const unsigned a[4], unsigned b0, unsigned b1, const float c[4]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%11,%12,%13};\n"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(c[0]), "f"(c[1]), "f"(c[2]),
+        "f"(c[3]));
+}
+
+// Forward of one 16-sample tile held by a warp.  Lane = 4 g + tg; the lane's A fragment of
+// the normalised inputs covers rows g, g+8 and columns 2tg, 2tg+1, 2tg+8, 2tg+9.
+// Outputs: z1, z2 (pre-activations, D layout: n-tile j holds columns 8j + 2tg, +1 of rows g
+// (elements 0, 1) and g+8 (elements 2, 3)), y for rows g and g+8 (all four lanes of a group).
+struct Tile {
+  float z1[8][4], z2[8][4];
+};
+
+__device__ __forceinline__ void tile_forward(const MlpDev& m, const unsigned ax[4], Tile& T, float& y_g, float& y_g8) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+  const float* b1 = m.P + ob1;
+  const float* b2 = m.P + ob2;
+  const float* w3 = m.P + ow3;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int o = 8 * j + 2 * tg;
+    const float c[4] = {b1[o], b1[o + 1], b1[o], b1[o + 1]};
+    mma16816(T.z1[j], ax, m.W1p[(8 * j + g) * 8 + tg], m.W1p[(8 * j + g) * 8 + tg + 4], c);
+  }
+  unsigned a2[4][4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    a2[kk][0] = pack_bf16(silu_f(T.z1[2 * kk][0]), silu_f(T.z1[2 * kk][1]));
+    a2[kk][1] = pack_bf16(silu_f(T.z1[2 * kk][2]), silu_f(T.z1[2 * kk][3]));
+    a2[kk][2] = pack_bf16(silu_f(T.z1[2 * kk + 1][0]), silu_f(T.z1[2 * kk + 1][1]));
+    a2[kk][3] = pack_bf16(silu_f(T.z1[2 * kk + 1][2]), silu_f(T.z1[2 * kk + 1][3]));
+  }
+  float pg = 0.f, pg8 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int o = 8 * j + 2 * tg;
+    float c[4] = {b2[o], b2[o + 1], b2[o], b2[o + 1]};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+      mma16816(c, a2[kk], m.W2p[(8 * j + g) * 32 + 8 * kk + tg], m.W2p[(8 * j + g) * 32 + 8 * kk + tg + 4], c);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) T.z2[j][e] = c[e];
+    pg += w3[o] * silu_f(c[0]) + w3[o + 1] * silu_f(c[1]);
+    pg8 += w3[o] * silu_f(c[2]) + w3[o + 1] * silu_f(c[3]);
+  }
+  pg += __shfl_xor_sync(0xffffffffu, pg, 1);
+  pg += __shfl_xor_sync(0xffffffffu, pg, 2);
+  pg8 += __shfl_xor_sync(0xffffffffu, pg8, 1);
+  pg8 += __shfl_xor_sync(0xffffffffu, pg8, 2);
+  y_g = pg + m.P[ob3];
+  y_g8 = pg8 + m.P[ob3];
+}
+
+// A fragment of normalised inputs from a [16][9] feature tile (row stride 9 floats).
+__device__ __forceinline__ void input_fragment(const MlpDev& m, const float* f16x9, unsigned ax[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+  float v[2][4];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int k = (c < 2 ? 2 * tg + c : 2 * tg + 8 + (c - 2));
+      const int row = g + 8 * r;
+      v[r][c] = k < kIn ? (f16x9[row * kIn + k] - m.norm[k]) / m.norm[kIn + k] : 0.f;
+    }
+  ax[0] = pack_bf16(v[0][0], v[0][1]);
+  ax[1] = pack_bf16(v[1][0], v[1][1]);
+  ax[2] = pack_bf16(v[0][2], v[0][3]);
+  ax[3] = pack_bf16(v[1][2], v[1][3]);
+}
+
+// ---------------- forward over a feature array ------------------------------------------
+// y[n] = network output (before out_scale); rows past n are padding.
+__global__ void __launch_bounds__(128) k_mlp_forward(MlpDev m, const float* __restrict__ feat, long long n,
+                                                     float* __restrict__ y) {
+  __shared__ float tile[4][16 * kIn];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long base = ((long long)blockIdx.x * 4 + w) * 16;
+  for (int e = lane; e < 16 * kIn; e += 32) {
+    const long long s = base + e / kIn;
+    tile[w][e] = s < n ? feat[s * kIn + e % kIn] : 0.f;
+  }
+  __syncwarp();
+  unsigned ax[4];
+  input_fragment(m, tile[w], ax);
+  Tile T;
+  float yg, yg8;
+  tile_forward(m, ax, T, yg, yg8);
+  const int g = lane >> 2, tg = lane & 3;
+  if (tg == 0) {
+    if (base + g < n) y[base + g] = yg;
+    if (base + g + 8 < n) y[base + g + 8] = yg8;
+  }
+}
+
+// ---------------- loss and gradient of one block of 64 samples ---------------------------
+// Writes the block's partial gradient (sum over its samples of dL/dparam with
+// L = (1/n_total) sum (y - t/out_scale)^2) and loss partial to part[blockIdx.x].
+__global__ void __launch_bounds__(128) k_mlp_grad(MlpDev m, const float* __restrict__ feat,
+                                                  const float* __restrict__ target, long long n, long long n_total,
+                                                  float* __restrict__ part) {
+  __shared__ float ftile[4][16 * kIn];
+  __shared__ __nv_bfloat16 sd2[64][kH + 8];  // delta of layer 2 [sample][out]
+  __shared__ __nv_bfloat16 sh1[64][kH + 8];  // h1 [sample][in]
+  __shared__ __nv_bfloat16 sd1[64][kH + 8];  // delta of layer 1 [sample][out]
+  __shared__ __nv_bfloat16 sx[64][16 + 8];   // normalised inputs [sample][k]
+  __shared__ float sb[4][3][kH];             // per-warp partials of gb1, gb2, gw3
+  __shared__ float sl[4][2];                 // per-warp gb3 and loss
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+  const long long base = ((long long)blockIdx.x * 4 + w) * 16;
+  const float inv_scale = 1.0f / m.norm[2 * kIn];
+  for (int e = lane; e < 16 * kIn; e += 32) {
+    const long long s = base + e / kIn;
+    ftile[w][e] = s < n ? feat[s * kIn + e % kIn] : 0.f;
+  }
+  __syncwarp();
+  unsigned ax[4];
+  input_fragment(m, ftile[w], ax);
+  Tile T;
+  float yg, yg8;
+  tile_forward(m, ax, T, yg, yg8);
+  const bool vg = base + g < n, vg8 = base + g + 8 < n;
+  const float rg = vg ? yg - target[base + g] * inv_scale : 0.f;
+  const float rg8 = vg8 ? yg8 - target[base + g + 8] * inv_scale : 0.f;
+  const float dyg = 2.f * rg / (float)n_total, dyg8 = 2.f * rg8 / (float)n_total;
+  // layer 2 deltas, bias / w3 partials, and stores for the weight-gradient products
+  const float* w3 = m.P + ow3;
+  float pb2[8][2], pw3[8][2];
+  unsigned ad2[4][4];
+  float d2v[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int o = 8 * j + 2 * tg;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float dy = e < 2 ? dyg : dyg8;
+      d2v[j][e] = dy * w3[o + (e & 1)] * dsilu_f(T.z2[j][e]);
+    }
+    pb2[j][0] = d2v[j][0] + d2v[j][2];
+    pb2[j][1] = d2v[j][1] + d2v[j][3];
+    pw3[j][0] = dyg * silu_f(T.z2[j][0]) + dyg8 * silu_f(T.z2[j][2]);
+    pw3[j][1] = dyg * silu_f(T.z2[j][1]) + dyg8 * silu_f(T.z2[j][3]);
+    const int r0 = 16 * w + g;
+    sd2[r0][o] = __float2bfloat16_rn(d2v[j][0]);
+    sd2[r0][o + 1] = __float2bfloat16_rn(d2v[j][1]);
+    sd2[r0 + 8][o] = __float2bfloat16_rn(d2v[j][2]);
+    sd2[r0 + 8][o + 1] = __float2bfloat16_rn(d2v[j][3]);
+    sh1[r0][o] = __float2bfloat16_rn(silu_f(T.z1[j][0]));
+    sh1[r0][o + 1] = __float2bfloat16_rn(silu_f(T.z1[j][1]));
+    sh1[r0 + 8][o] = __float2bfloat16_rn(silu_f(T.z1[j][2]));
+    sh1[r0 + 8][o + 1] = __float2bfloat16_rn(silu_f(T.z1[j][3]));
+  }
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    ad2[kk][0] = pack_bf16(d2v[2 * kk][0], d2v[2 * kk][1]);
+    ad2[kk][1] = pack_bf16(d2v[2 * kk][2], d2v[2 * kk][3]);
+    ad2[kk][2] = pack_bf16(d2v[2 * kk + 1][0], d2v[2 * kk + 1][1]);
+    ad2[kk][3] = pack_bf16(d2v[2 * kk + 1][2], d2v[2 * kk + 1][3]);
+  }
+  // delta of layer 1 = (delta2 W2) * silu'(z1): a 16 x 64 x 64 tensor-core product
+  float pb1[8][2];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+      mma16816(c, ad2[kk], m.W2Tp[(8 * j + g) * 32 + 8 * kk + tg], m.W2Tp[(8 * j + g) * 32 + 8 * kk + tg + 4], c);
+    const int o = 8 * j + 2 * tg;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) c[e] *= dsilu_f(T.z1[j][e]);
+    pb1[j][0] = c[0] + c[2];
+    pb1[j][1] = c[1] + c[3];
+    const int r0 = 16 * w + g;
+    sd1[r0][o] = __float2bfloat16_rn(c[0]);
+    sd1[r0][o + 1] = __float2bfloat16_rn(c[1]);
+    sd1[r0 + 8][o] = __float2bfloat16_rn(c[2]);
+    sd1[r0 + 8][o + 1] = __float2bfloat16_rn(c[3]);
+  }
+  // normalised inputs (bf16) for the W1 gradient
+  {
+    const int r0 = 16 * w + g;
+    const __nv_bfloat162* a0 = reinterpret_cast<const __nv_bfloat162*>(&ax[0]);
+    const __nv_bfloat162* a1 = reinterpret_cast<const __nv_bfloat162*>(&ax[1]);
+    const __nv_bfloat162* a2 = reinterpret_cast<const __nv_bfloat162*>(&ax[2]);
+    const __nv_bfloat162* a3 = reinterpret_cast<const __nv_bfloat162*>(&ax[3]);
+    sx[r0][2 * tg] = a0->x;
+    sx[r0][2 * tg + 1] = a0->y;
+    sx[r0 + 8][2 * tg] = a1->x;
+    sx[r0 + 8][2 * tg + 1] = a1->y;
+    sx[r0][2 * tg + 8] = a2->x;
+    sx[r0][2 * tg + 9] = a2->y;
+    sx[r0 + 8][2 * tg + 8] = a3->x;
+    sx[r0 + 8][2 * tg + 9] = a3->y;
+  }
+  // warp reductions of the bias / w3 partials over the 16 samples (across groups g)
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+      for (int off = 4; off < 32; off <<= 1) {
+        pb1[j][e] += __shfl_xor_sync(0xffffffffu, pb1[j][e], off);
+        pb2[j][e] += __shfl_xor_sync(0xffffffffu, pb2[j][e], off);
+        pw3[j][e] += __shfl_xor_sync(0xffffffffu, pw3[j][e], off);
+      }
+  if (g == 0)
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        sb[w][0][8 * j + 2 * tg + e] = pb1[j][e];
+        sb[w][1][8 * j + 2 * tg + e] = pb2[j][e];
+        sb[w][2][8 * j + 2 * tg + e] = pw3[j][e];
+      }
+  float pgb3 = (tg == 0) ? dyg + dyg8 : 0.f, pl = (tg == 0) ? rg * rg + rg8 * rg8 : 0.f;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    pgb3 += __shfl_xor_sync(0xffffffffu, pgb3, off);
+    pl += __shfl_xor_sync(0xffffffffu, pl, off);
+  }
+  if (lane == 0) {
+    sl[w][0] = pgb3;
+    sl[w][1] = pl;
+  }
+  __syncthreads();
+
+  float* out = part + (size_t)blockIdx.x * kGradStride;
+  // W2 gradient rows o in [16w, 16w + 16): sum over the block's 64 samples of d2[s][o] h1[s][k]
+  {
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[j][e] = 0.f;
+    const int o0 = 16 * w;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int s0 = 16 * ks;
+      unsigned a[4];
+      a[0] = pack_bf16(__bfloat162float(sd2[s0 + 2 * tg][o0 + g]), __bfloat162float(sd2[s0 + 2 * tg + 1][o0 + g]));
+      a[1] = pack_bf16(__bfloat162float(sd2[s0 + 2 * tg][o0 + g + 8]), __bfloat162float(sd2[s0 + 2 * tg + 1][o0 + g + 8]));
+      a[2] = pack_bf16(__bfloat162float(sd2[s0 + 2 * tg + 8][o0 + g]), __bfloat162float(sd2[s0 + 2 * tg + 9][o0 + g]));
+      a[3] = pack_bf16(__bfloat162float(sd2[s0 + 2 * tg + 8][o0 + g + 8]),
+                       __bfloat162float(sd2[s0 + 2 * tg + 9][o0 + g + 8]));
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const unsigned b0 = pack_bf16(__bfloat162float(sh1[s0 + 2 * tg][8 * j + g]),
+                                      __bfloat162float(sh1[s0 + 2 * tg + 1][8 * j + g]));
+        const unsigned b1 = pack_bf16(__bfloat162float(sh1[s0 + 2 * tg + 8][8 * j + g]),
+                                      __bfloat162float(sh1[s0 + 2 * tg + 9][8 * j + g]));
+        mma16816(acc[j], a, b0, b1, acc[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k = 8 * j + 2 * tg;
+      out[oW2 + (o0 + g) * kH + k] = acc[j][0];
+      out[oW2 + (o0 + g) * kH + k + 1] = acc[j][1];
+      out[oW2 + (o0 + g + 8) * kH + k] = acc[j][2];
+      out[oW2 + (o0 + g + 8) * kH + k + 1] = acc[j][3];
+    }
+  }
+  // W1 gradient rows o in [16w, 16w + 16): sum over samples of d1[s][o] x[s][k], k < 9
+  {
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    const int o0 = 16 * w;
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int s0 = 16 * ks;
+      unsigned a[4];
+      a[0] = pack_bf16(__bfloat162float(sd1[s0 + 2 * tg][o0 + g]), __bfloat162float(sd1[s0 + 2 * tg + 1][o0 + g]));
+      a[1] = pack_bf16(__bfloat162float(sd1[s0 + 2 * tg][o0 + g + 8]), __bfloat162float(sd1[s0 + 2 * tg + 1][o0 + g + 8]));
+      a[2] = pack_bf16(__bfloat162float(sd1[s0 + 2 * tg + 8][o0 + g]), __bfloat162float(sd1[s0 + 2 * tg + 9][o0 + g]));
+      a[3] = pack_bf16(__bfloat162float(sd1[s0 + 2 * tg + 8][o0 + g + 8]),
+                       __bfloat162float(sd1[s0 + 2 * tg + 9][o0 + g + 8]));
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const unsigned b0 = pack_bf16(__bfloat162float(sx[s0 + 2 * tg][8 * j + g]),
+                                      __bfloat162float(sx[s0 + 2 * tg + 1][8 * j + g]));
+        const unsigned b1 = pack_bf16(__bfloat162float(sx[s0 + 2 * tg + 8][8 * j + g]),
+                                      __bfloat162float(sx[s0 + 2 * tg + 9][8 * j + g]));
+        mma16816(acc[j], a, b0, b1, acc[j]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int k = 8 * j + 2 * tg + (e & 1), o = o0 + g + (e >= 2 ? 8 : 0);
+        if (k < kIn) out[oW1 + o * kIn + k] = acc[j][e];
+      }
+  }
+  for (int o = threadIdx.x; o < kH; o += blockDim.x) {
+    out[ob1 + o] = sb[0][0][o] + sb[1][0][o] + sb[2][0][o] + sb[3][0][o];
+    out[ob2 + o] = sb[0][1][o] + sb[1][1][o] + sb[2][1][o] + sb[3][1][o];
+    out[ow3 + o] = sb[0][2][o] + sb[1][2][o] + sb[2][2][o] + sb[3][2][o];
+  }
+  if (threadIdx.x == 0) {
+    out[ob3] = sl[0][0] + sl[1][0] + sl[2][0] + sl[3][0];
+    out[kNPar] = sl[0][1] + sl[1][1] + sl[2][1] + sl[3][1];
+  }
+}
+
+// Fixed-order sum of the block partials: grad [kNPar + 1] (last entry: sum of squared
+// residuals, also added to *loss_acc when given).
+__global__ void k_mlp_grad_reduce(const float* part, int nblk, float* grad, float* loss_acc) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > kNPar) return;
+  float acc = 0.f;
+  for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * kGradStride + p];
+  grad[p] = acc;
+  if (p == kNPar && loss_acc) *loss_acc += acc;
+}
+
+// Adam on the FP32 master parameters.
+__global__ void k_mlp_adam(float* P, float* mom, float* vel, const float* grad, float lr, float b1c, float b2c) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= kNPar) return;
+  const float gr = grad[p];
+  const float mo = 0.9f * mom[p] + 0.1f * gr;
+  const float ve = 0.999f * vel[p] + 0.001f * gr * gr;
+  mom[p] = mo;
+  vel[p] = ve;
+  P[p] -= lr * (mo / b1c) / (sqrtf(ve / b2c) + 1e-8f);
+}
+
+// BF16 operand copies of W1 (K padded to 16), W2 and W2 transposed, from the master.
+__global__ void k_mlp_pack(const float* P, unsigned* W1p, unsigned* W2p, unsigned* W2Tp) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < kH * 8) {
+    const int o = t / 8, kp = t % 8;
+    const float lo = 2 * kp < kIn ? P[oW1 + o * kIn + 2 * kp] : 0.f;
+    const float hi = 2 * kp + 1 < kIn ? P[oW1 + o * kIn + 2 * kp + 1] : 0.f;
+    W1p[t] = pack_bf16(lo, hi);
+  }
+  if (t < kH * 32) {
+    const int r = t / 32, kp = t % 32;
+    W2p[t] = pack_bf16(P[oW2 + r * kH + 2 * kp], P[oW2 + r * kH + 2 * kp + 1]);
+    W2Tp[t] = pack_bf16(P[oW2 + (2 * kp) * kH + r], P[oW2 + (2 * kp + 1) * kH + r]);
+  }
+}
+
+// ---------------- features of a pair from the current mapping --------------------------
+
+__device__ __forceinline__ void sort4f(float v[4]) {
+  float a = fminf(v[0], v[1]), b = fmaxf(v[0], v[1]), c = fminf(v[2], v[3]), d = fmaxf(v[2], v[3]);
+  const float lo = fminf(a, c), hi = fmaxf(b, d), m1 = fmaxf(a, c), m2 = fminf(b, d);
+  v[0] = lo;
+  v[1] = fminf(m1, m2);
+  v[2] = fmaxf(m1, m2);
+  v[3] = hi;
+}
+
+// COM-relative offset of atom i in the current mapping, as float (either path's layout).
+template <bool F64>
+__device__ __forceinline__ float4 offset_f(const Bufs& b, int cur, int i) {
+  if (F64) {
+    const double4_32a o = b.off64[cur][i];
+    return make_float4((float)o.x, (float)o.y, (float)o.z, 0.f);
+  }
+  return b.off32[cur][i];
+}
+
+// Features of (a, b) with e from a to b; feat[9].  Atoms beyond na project to 0 (padding).
+template <int NA, bool F64>
+__device__ __forceinline__ void pair_features32(const Sys& s, const Bufs& b, int cur, int a, int bb, float feat[9]) {
+  const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][bb];
+  const float ex = (float)(int)((unsigned)B.x - (unsigned)A.x) * s.fx_scale[0];
+  const float ey = (float)(int)((unsigned)B.y - (unsigned)A.y) * s.fx_scale[1];
+  const float ez = (float)(int)((unsigned)B.z - (unsigned)A.z) * s.fx_scale[2];
+  const float d = sqrtf(ex * ex + ey * ey + ez * ez), id = 1.f / d;
+  float sa[4] = {0.f, 0.f, 0.f, 0.f}, sb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < NA; ++k) {
+    const float4 oa = offset_f<F64>(b, cur, a * NA + k), ob = offset_f<F64>(b, cur, bb * NA + k);
+    sa[k] = (oa.x * ex + oa.y * ey + oa.z * ez) * id;
+    sb[k] = -(ob.x * ex + ob.y * ey + ob.z * ez) * id;
+  }
+  if (NA == 4) {
+    sort4f(sa);
+    sort4f(sb);
+  } else {
+    for (int i = 1; i < NA; ++i)
+      for (int j = i; j > 0 && sa[j - 1] > sa[j]; --j) {
+        const float t = sa[j]; sa[j] = sa[j - 1]; sa[j - 1] = t;
+      }
+    for (int i = 1; i < NA; ++i)
+      for (int j = i; j > 0 && sb[j - 1] > sb[j]; --j) {
+        const float t = sb[j]; sb[j] = sb[j - 1]; sb[j - 1] = t;
+      }
+  }
+  feat[0] = d;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    feat[1 + k] = sa[k];
+    feat[5 + k] = sb[k];
+  }
+}
+
+// Atomistic force on a from b projected on -e (the force-matching target), FP32.
+template <int NA, bool F64>
+__device__ __forceinline__ float pair_target32(const Sys& s, const Bufs& b, int cur, int a, int bb) {
+  const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][bb];
+  const float Rx = (float)(int)((unsigned)A.x - (unsigned)B.x) * s.fx_scale[0];
+  const float Ry = (float)(int)((unsigned)A.y - (unsigned)B.y) * s.fx_scale[1];
+  const float Rz = (float)(int)((unsigned)A.z - (unsigned)B.z) * s.fx_scale[2];
+  float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+#pragma unroll
+  for (int i = 0; i < NA; ++i) {
+    const float4 oi = offset_f<F64>(b, cur, a * NA + i);
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+      const float4 oj = offset_f<F64>(b, cur, bb * NA + j);
+      const float dx = Rx + oi.x - oj.x, dy = Ry + oi.y - oj.y, dz = Rz + oi.z - oj.z;
+      const float d2 = dx * dx + dy * dy + dz * dz;
+      if (d2 < s.f.rc_at2) {
+        const float ir2 = 1.f / d2, sr2 = s.f.sig2 * ir2, sr6 = sr2 * sr2 * sr2;
+        const float fr = 24.f * s.f.eps * (2.f * sr6 * sr6 - sr6) * ir2;
+        Fx += fr * dx;
+        Fy += fr * dy;
+        Fz += fr * dz;
+      }
+    }
+  }
+  const float r = sqrtf(Rx * Rx + Ry * Ry + Rz * Rz);
+  return (Fx * Rx + Fy * Ry + Fz * Rz) / r;
+}
+
+// Count (pass 0) or write (pass 1) the samples of every work item: pairs with a < b, COM
+// distance below rc_cg.  Writing uses per-item offsets from an exclusive scan, so the
+// sample order is deterministic (item order, then list order).
+template <int NA, bool F64>
+__global__ void k_mlp_collect(Sys s, Bufs b, int pass, const int* offs, long long cap, long long base, float* feat,
+                              float* target, int* ids, int* counts) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s.M) return;
+  const int cur = b.ctrl->parity;
+  const int a = b.items[t];
+  const int n = b.nn[t];
+  int c = 0;
+  long long o = pass ? base + offs[t] : 0;
+  for (int q = 0; q < n; ++q) {
+    const int m = b.nbr[(size_t)t * s.cap + q];
+    if (m <= a) continue;
+    const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][m];
+    const float dx = (float)(int)((unsigned)B.x - (unsigned)A.x) * s.fx_scale[0];
+    const float dy = (float)(int)((unsigned)B.y - (unsigned)A.y) * s.fx_scale[1];
+    const float dz = (float)(int)((unsigned)B.z - (unsigned)A.z) * s.fx_scale[2];
+    if (dx * dx + dy * dy + dz * dz >= s.f.rc_cg2) continue;
+    if (pass && o < cap) {
+      float f[9];
+      pair_features32<NA, F64>(s, b, cur, a, m, f);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) feat[o * 9 + k] = f[k];
+      target[o] = pair_target32<NA, F64>(s, b, cur, a, m);
+      ids[2 * o] = a;
+      ids[2 * o + 1] = m;
+    }
+    ++c;
+    ++o;
+  }
+  if (!pass) counts[t] = c;
+}
+
+// ---------------- pair forces for the dynamics -------------------------------------------
+// Every list slot (t, q) whose pair needs a CG force (COM distance < rc_cg and w_ab < 1)
+// gets the symmetrised network force in fpair[t cap + q]; the pair is evaluated once, by
+// the molecule with the smaller id, and the value is written to both molecules' slots.
+// A warp gathers 16 pairs at a time (ballot compaction), evaluates the two orderings as
+// two 16-row tensor-core tiles and scatters the results.
+template <int NA, bool F64>
+__global__ void __launch_bounds__(128) k_mlp_pairs(Sys s, Bufs b, MlpDev m, float* fpair) {
+  __shared__ float ft[4][2][16 * kIn];
+  __shared__ int slot_a[4][16], slot_b[4][16];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+  const int cur = b.ctrl->parity;
+  const int items_per_warp = 32;
+  const int t0 = (blockIdx.x * 4 + w) * items_per_warp;
+  const float scale = m.norm[2 * kIn];
+  int nq = 0;  // pairs gathered in the tile
+  // lane l walks the list of item t0 + l; the warp loops until every lane is done
+  const int t = t0 + lane;
+  const bool live = t < s.M;
+  const int a = live ? b.items[t] : 0;
+  const int n = live ? b.nn[t] : 0;
+  const float wa = live ? __int_as_float(b.com_fx[cur][a].w) : 0.f;
+  int q = 0;
+  while (true) {
+    // next qualifying slot of this lane
+    int found = -1, mb = 0;
+    while (q < n && found < 0) {
+      const int mm = b.nbr[(size_t)t * s.cap + q];
+      if (mm > a) {
+        const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][mm];
+        const float dx = (float)(int)((unsigned)B.x - (unsigned)A.x) * s.fx_scale[0];
+        const float dy = (float)(int)((unsigned)B.y - (unsigned)A.y) * s.fx_scale[1];
+        const float dz = (float)(int)((unsigned)B.z - (unsigned)A.z) * s.fx_scale[2];
+        if (dx * dx + dy * dy + dz * dz < s.f.rc_cg2 && wa * __int_as_float(B.w) < 1.f) {
+          found = q;
+          mb = mm;
+        }
+      }
+      ++q;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, found >= 0);
+    if (bal == 0u) break;
+    // append this round's pairs; evaluate whenever 16 are gathered
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    const int nb = __popc(bal);
+    int done = 0;
+    while (done < nb) {
+      const int take = min(16 - nq, nb - done);
+      if (found >= 0 && rank >= done && rank < done + take) {
+        const int r = nq + rank - done;
+        float f[9];
+        pair_features32<NA, F64>(s, b, cur, a, mb, f);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ft[w][0][r * kIn + k] = f[k];
+        ft[w][1][r * kIn] = f[0];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          ft[w][1][r * kIn + 1 + k] = f[5 + k];
+          ft[w][1][r * kIn + 5 + k] = f[1 + k];
+        }
+        slot_a[w][r] = t * s.cap + found;
+        slot_b[w][r] = mb;  // resolved to the mirror slot after the evaluation
+      }
+      nq += take;
+      done += take;
+      __syncwarp();
+      if (nq == 16) {
+        unsigned ax[4];
+        Tile T;
+        float y0g, y0g8, y1g, y1g8;
+        input_fragment(m, ft[w][0], ax);
+        tile_forward(m, ax, T, y0g, y0g8);
+        input_fragment(m, ft[w][1], ax);
+        tile_forward(m, ax, T, y1g, y1g8);
+        if (tg == 0) {
+          ft[w][0][g * kIn] = 0.5f * scale * (y0g + y1g);
+          ft[w][0][(g + 8) * kIn] = 0.5f * scale * (y0g8 + y1g8);
+        }
+        __syncwarp();
+        if (lane < 16) {
+          const float fv = ft[w][0][lane * kIn];
+          const int sa = slot_a[w][lane], mm = slot_b[w][lane];
+          fpair[sa] = fv;
+          const int tb = b.item_of[mm], nbb = b.nn[tb];
+          const int aa = b.items[sa / s.cap];
+          for (int qq = 0; qq < nbb; ++qq)
+            if (b.nbr[(size_t)tb * s.cap + qq] == aa) {
+              fpair[(size_t)tb * s.cap + qq] = fv;
+              break;
+            }
+        }
+        nq = 0;
+        __syncwarp();
+      }
+    }
+  }
+  // remainder (fewer than 16 pairs): pad the tile with copies of row 0
+  if (nq > 0) {
+    for (int e = lane; e < (16 - nq) * kIn; e += 32) {
+      ft[w][0][nq * kIn + e] = ft[w][0][e % kIn];
+      ft[w][1][nq * kIn + e] = ft[w][1][e % kIn];
+    }
+    __syncwarp();
+    unsigned ax[4];
+    Tile T;
+    float y0g, y0g8, y1g, y1g8;
+    input_fragment(m, ft[w][0], ax);
+    tile_forward(m, ax, T, y0g, y0g8);
+    input_fragment(m, ft[w][1], ax);
+    tile_forward(m, ax, T, y1g, y1g8);
+    __syncwarp();
+    if (tg == 0) {
+      ft[w][0][g * kIn] = 0.5f * scale * (y0g + y1g);
+      ft[w][0][(g + 8) * kIn] = 0.5f * scale * (y0g8 + y1g8);
+    }
+    __syncwarp();
+    if (lane < nq) {
+      const float fv = ft[w][0][lane * kIn];
+      const int sa = slot_a[w][lane], mm = slot_b[w][lane];
+      fpair[sa] = fv;
+      const int tb = b.item_of[mm], nbb = b.nn[tb];
+      const int aa = b.items[sa / s.cap];
+      for (int qq = 0; qq < nbb; ++qq)
+        if (b.nbr[(size_t)tb * s.cap + qq] == aa) {
+          fpair[(size_t)tb * s.cap + qq] = fv;
+          break;
+        }
+    }
+  }
+}
+
+// Training batch `cnt` samples starting at `start` of a fixed permutation of the n
+// samples: sample (start + i) * stride mod n (stride coprime with n).
+__global__ void k_mlp_gather(const float* feat, const float* target, long long n, long long start, long long cnt,
+                             long long stride, float* fo, float* to) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  const long long src = (long long)(((unsigned long long)(start + i) * (unsigned long long)stride) % (unsigned long long)n);
+#pragma unroll
+  for (int k = 0; k < kIn; ++k) fo[i * kIn + k] = feat[src * kIn + k];
+  to[i] = target[src];
+}
+
+// ---------------- launchers ------------------------------------------------------------
+
+cudaError_t mlp_gather(const float* feat, const float* target, long long n, long long start, long long cnt,
+                       long long stride, float* fo, float* to, cudaStream_t st) {
+  k_mlp_gather<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(feat, target, n, start, cnt, stride, fo, to);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_forward(const MlpDevArgs& a, const float* feat, long long n, float* y, cudaStream_t st) {
+  const MlpDev m{a.P, a.W1p, a.W2p, a.W2Tp, a.norm};
+  const long long tiles = (n + 15) / 16;
+  k_mlp_forward<<<(unsigned)((tiles + 3) / 4), 128, 0, st>>>(m, feat, n, y);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_grad(const MlpDevArgs& a, const float* feat, const float* target, long long n, long long n_total,
+                     float* part, float* grad, float* loss_acc, cudaStream_t st) {
+  const MlpDev m{a.P, a.W1p, a.W2p, a.W2Tp, a.norm};
+  const int nblk = (int)((n + 63) / 64);
+  k_mlp_grad<<<nblk, 128, 0, st>>>(m, feat, target, n, n_total, part);
+  k_mlp_grad_reduce<<<(kNPar + 1 + 255) / 256, 256, 0, st>>>(part, nblk, grad, loss_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(const MlpDevArgs& a, float* mom, float* vel, const float* grad, float lr, int step,
+                     cudaStream_t st) {
+  const float b1c = 1.f - powf(0.9f, (float)step), b2c = 1.f - powf(0.999f, (float)step);
+  k_mlp_adam<<<(kNPar + 255) / 256, 256, 0, st>>>((float*)a.P, mom, vel, grad, lr, b1c, b2c);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_pack(const MlpDevArgs& a, cudaStream_t st) {
+  k_mlp_pack<<<(kH * 32 + 255) / 256, 256, 0, st>>>(a.P, (unsigned*)a.W1p, (unsigned*)a.W2p, (unsigned*)a.W2Tp);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_collect(const Sys& s, const Bufs& b, int pass, const int* offs, long long cap, long long base,
+                        float* feat, float* target, int* ids, int* counts, cudaStream_t st) {
+  const int blocks = ceil_div(s.M, 128);
+#define COLLECT(NA_)                                                                                       \
+  (s.fp64 ? k_mlp_collect<NA_, true><<<blocks, 128, 0, st>>>(s, b, pass, offs, cap, base, feat, target, ids, counts) \
+          : k_mlp_collect<NA_, false><<<blocks, 128, 0, st>>>(s, b, pass, offs, cap, base, feat, target, ids, counts))
+  switch (s.NA) {
+    case 1: COLLECT(1); break;
+    case 2: COLLECT(2); break;
+    case 3: COLLECT(3); break;
+    default: COLLECT(4); break;
+  }
+#undef COLLECT
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* fpair, cudaStream_t st) {
+  const MlpDev m{a.P, a.W1p, a.W2p, a.W2Tp, a.norm};
+  const int blocks = ceil_div(s.M, 4 * 32);
+#define PAIRS(NA_)                                                               \
+  (s.fp64 ? k_mlp_pairs<NA_, true><<<blocks, 128, 0, st>>>(s, b, m, fpair) \
+          : k_mlp_pairs<NA_, false><<<blocks, 128, 0, st>>>(s, b, m, fpair))
+  switch (s.NA) {
+    case 1: PAIRS(1); break;
+    case 2: PAIRS(2); break;
+    case 3: PAIRS(3); break;
+    default: PAIRS(4); break;
+  }
+#undef PAIRS
+  return cudaGetLastError();
+}
+
+}  // namespace adress

@@ -435,8 +435,8 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
       }
       if (own && wab < (real)1 && r2 < rc_cg2) {
         const real r = Q::sqrt_(r2);
-        real V;
-        const real F = Q::cg(b, s.cg_n, r, inv_dr, &V);
+        real V = 0;
+        const real F = s.cg_mode ? (real)b.fpair[(size_t)t * s.cap + q] : Q::cg(b, s.cg_n, r, inv_dr, &V);
         const real c = Q::div_(((real)1 - wab) * F, r);
         fx += frac_g * c * R.x;
         fy += frac_g * c * R.y;
@@ -461,8 +461,8 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
       const real r2 = R.x * R.x + R.y * R.y + R.z * R.z;
       if (r2 < rc_cg2) {
         const real r = Q::sqrt_(r2);
-        real V;
-        const real F = Q::cg(b, s.cg_n, r, inv_dr, &V);
+        real V = 0;
+        const real F = s.cg_mode ? (real)b.fpair[(size_t)t * s.cap + q] : Q::cg(b, s.cg_n, r, inv_dr, &V);
         const real c = Q::div_(F, r);
         Fx += c * R.x;
         Fy += c * R.y;

@@ -1,0 +1,196 @@
+"""Learned CG pair force on the GPU against the oracle.
+
+Forward and gradient parity of the BF16 tensor-core kernels (FP32 accumulation) with the
+FP64 oracle network evaluated at the same bfloat16 rounding points; training-sample
+collection; a 1-D fit of the tabulated CG force; MD forces in network mode; and the
+force-matching gain of the trained network over the tabulated potential.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_10841_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def rand_params(seed, scale=0.25):
+    rng = np.random.default_rng(seed)
+    return dict(W1=rng.normal(0, scale, (64, 9)), b1=rng.normal(0, 0.1, 64), W2=rng.normal(0, scale, (64, 64)),
+                b2=rng.normal(0, 0.1, 64), w3=rng.normal(0, scale, 64), b3=0.1)
+
+
+def sim_with_net(s, params, mean, std, scale, precision="fp32"):
+    from paper_1806_10841_gb300 import adress
+
+    sim = adress.AdResS(s, precision=precision)
+    sim.mlp_set(params, mean, std, scale)
+    return sim
+
+
+def oracle_net(params, mean, std, scale, bf16=True):
+    p = {k: np.asarray(v, dtype=np.float32).astype(np.float64) for k, v in params.items() if k != "b3"}
+    p["b3"] = float(np.float32(params["b3"]))
+    p.update(in_mean=np.asarray(mean, np.float32).astype(np.float64),
+             in_std=np.asarray(std, np.float32).astype(np.float64), out_scale=float(np.float32(scale)))
+    return oracle.OracleMLP(p, bf16=bf16)
+
+
+def system_samples(M=2000, seed=21):
+    s = inputs.scaled_c2(M, seed=seed)
+    s.d_at = 1e3  # all atomistic: the force-matching reference
+    x, v = inputs.tetra_state(s)
+    return s, x, v
+
+
+def test_mlp_forward_matches_oracle_bf16():
+    s, x, _ = system_samples()
+    feat, _, _ = oracle.Oracle(s).collect_pairs(x, s.rc_cg)
+    mean, std = feat.mean(0), feat.std(0) + 1e-3
+    params = rand_params(1)
+    sim = sim_with_net(s, params, mean, std, 5.0)
+    y = sim.mlp_forward(feat)
+    ref = oracle_net(params, mean, std, 5.0).forward(feat.astype(np.float32).astype(np.float64))
+    err = np.abs(y - ref) / (np.abs(ref) + 0.1 * ref.std())
+    assert np.median(err) < 1e-4
+    assert np.percentile(err, 99) < 1e-2
+    sim.close()
+
+
+def test_mlp_gradient_matches_oracle():
+    s, x, _ = system_samples()
+    feat, _, _ = oracle.Oracle(s).collect_pairs(x, s.rc_cg)
+    feat = feat[:512].astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(3)
+    target = rng.normal(0, 4.0, len(feat)).astype(np.float32)
+    mean, std = feat.mean(0), feat.std(0) + 1e-3
+    params = rand_params(2)
+    sim = sim_with_net(s, params, mean, std, 4.0)
+    loss, g = sim.mlp_loss_grad(feat, target)
+    loss_ref, g_ref = oracle_net(params, mean, std, 4.0).loss_grad(feat, target.astype(np.float64))
+    assert loss == pytest.approx(loss_ref, rel=2e-3)
+    for k in ("W1", "b1", "W2", "b2", "w3"):
+        a, r = np.asarray(g[k]).ravel(), np.asarray(g_ref[k]).ravel()
+        assert np.linalg.norm(a - r) <= 3e-2 * np.linalg.norm(r), k
+    assert g["b3"] == pytest.approx(g_ref["b3"], rel=1e-2, abs=1e-4)
+    sim.close()
+
+
+def test_mlp_sample_collection_matches_oracle():
+    s, x, v = system_samples(M=2000, seed=22)
+    feat_o, t_o, ids_o = oracle.Oracle(s).collect_pairs(x, s.rc_cg)
+    params = rand_params(3)
+    sim = sim_with_net(s, params, np.zeros(9), np.ones(9), 1.0)
+    sim.set_state(x, v)
+    n = sim.mlp_collect(cap=100_000)
+    feat, t, ids = sim.mlp_samples(n)
+    key_o = {tuple(map(int, p)): k for k, p in enumerate(ids_o)}
+    assert {tuple(map(int, p)) for p in ids} == set(key_o)
+    order = np.array([key_o[tuple(map(int, p))] for p in ids])
+    assert np.abs(feat - feat_o[order]).max() < 2e-5
+    scale = np.abs(t_o).max()
+    assert scale > 0
+    assert np.abs(t - t_o[order]).max() <= 1e-4 * scale + 1e-5
+    # appending: a second collection adds the same number of samples
+    assert sim.mlp_collect(cap=100_000) == 2 * n
+    sim.close()
+
+
+def test_mlp_training_reproduces_the_tabulated_force_1d():
+    """A network trained on the tabulated CG force as a function of d alone reproduces it
+    to 1e-2 (relative RMS)."""
+    s = inputs.scaled_c2(2000)
+    rng = np.random.default_rng(5)
+    n = 16384
+    d = rng.uniform(1.8, 2.3, n)
+    F = np.interp(d, np.arange(len(s.cg_F)) * s.cg_dr, s.cg_F)
+    feat = np.zeros((n, 9))
+    feat[:, 0] = d
+    feat[:, 1:] = rng.uniform(-0.5, 0.5, (n, 8))
+    mean, std = feat.mean(0), feat.std(0)
+    scale = float(F.std())
+    rng2 = np.random.default_rng(6)
+    params = dict(W1=rng2.normal(0, 1 / 3, (64, 9)), b1=np.zeros(64), W2=rng2.normal(0, 1 / 8, (64, 64)),
+                  b2=np.zeros(64), w3=rng2.normal(0, 1 / 8, 64), b3=float(F.mean() / scale))
+    sim = sim_with_net(s, params, mean, std, scale)
+    sim.mlp_load_samples(feat, F)
+    loss = sim.mlp_train(epochs=300, batch=512, lr=2e-3)
+    assert loss[-1] < 0.1 * loss[0]
+    test_d = np.linspace(1.8, 2.3, 400)
+    tf = np.zeros((400, 9))
+    tf[:, 0] = test_d
+    y = sim.mlp_forward(tf) * scale
+    ref = np.interp(test_d, np.arange(len(s.cg_F)) * s.cg_dr, s.cg_F)
+    rel = math.sqrt(np.mean((y - ref) ** 2) / np.mean(ref ** 2))
+    print("1-D fit relative RMS", rel, "loss", loss[0], loss[-1])
+    assert rel < 1e-2
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_md_forces_with_learned_cg_force_match_oracle(precision):
+    s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, seed=5)
+    x, _ = inputs.tetra_state(s)
+    o = oracle.Oracle(s)
+    feat, _, _ = o.collect_pairs(x, s.rc_cg)
+    mean, std = feat.mean(0), feat.std(0) + 1e-3
+    params = rand_params(7, scale=0.2)
+    net = oracle_net(params, mean, std, 3.0)
+    o.set_mlp(net)
+    f_ref, _ = o.forces(x)
+    sim = sim_with_net(s, params, mean, std, 3.0, precision=precision)
+    sim.set_cg_mode(1)
+    sim.set_state(x)
+    f, e = sim.forces()
+    sim.check()
+    rel = math.sqrt(((f - f_ref) ** 2).sum() / (f_ref ** 2).sum())
+    assert rel < 2e-3, rel
+    assert np.abs(f.sum(0)).max() <= 1e-5 * np.abs(f).sum()
+    # the table is back with mode 0
+    sim.set_cg_mode(0)
+    o.set_mlp(None)
+    f_tab, _ = sim.forces()
+    f_tab_ref, _ = o.forces(x)
+    assert math.sqrt(((f_tab - f_tab_ref) ** 2).sum() / (f_tab_ref ** 2).sum()) < (2e-5 if precision == "fp32" else 1e-10)
+    sim.close()
+
+
+def test_trained_network_beats_the_table_on_held_out_atomistic_forces():
+    """Force matching on atomistic pair forces: the trained network's error on held-out
+    pairs is well below that of the tabulated CG potential (the method without it)."""
+    from paper_1806_10841_gb300 import adress
+
+    s, x, v = system_samples(M=4000, seed=23)
+    sim = adress.AdResS(s, precision="fp32")
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    # equilibrate the all-atomistic fluid a little and collect pairs from a few snapshots
+    total = 0
+    for _ in range(4):
+        sim.step(200)
+        total = sim.mlp_collect(cap=400_000)
+    feat, t, _ = sim.mlp_samples(total)
+    rng = np.random.default_rng(9)
+    idx = rng.permutation(total)
+    ntr = int(0.8 * total)
+    tr, te = idx[:ntr], idx[ntr:]
+    mean, std = feat[tr].mean(0), feat[tr].std(0) + 1e-3
+    scale = float(t[tr].std())
+    rng2 = np.random.default_rng(10)
+    params = dict(W1=rng2.normal(0, 1 / 3, (64, 9)), b1=np.zeros(64), W2=rng2.normal(0, 1 / 8, (64, 64)),
+                  b2=np.zeros(64), w3=rng2.normal(0, 1 / 8, 64), b3=float(t[tr].mean() / scale))
+    sim.mlp_set(params, mean, std, scale)
+    sim.mlp_load_samples(feat[tr], t[tr])
+    sim.mlp_train(epochs=30, batch=1024, lr=2e-3)
+    sw = feat[te].copy()
+    sw[:, 1:5], sw[:, 5:9] = feat[te][:, 5:9], feat[te][:, 1:5]
+    pred = 0.5 * scale * (sim.mlp_forward(feat[te]) + sim.mlp_forward(sw))
+    table = np.interp(feat[te][:, 0], np.arange(len(s.cg_F)) * s.cg_dr, s.cg_F)
+    rms = lambda a: math.sqrt(np.mean(a ** 2))
+    err_net, err_tab, ref = rms(pred - t[te]), rms(table - t[te]), rms(t[te])
+    print(f"held-out force RMS: target {ref:.3f}, network {err_net:.3f}, table {err_tab:.3f}")
+    assert err_net < 0.5 * err_tab
+    assert err_net < ref
+    sim.close()

@@ -154,3 +154,31 @@ def test_collect_pairs_matches_pairwise_definition():
     for k in range(0, len(ids), 17):
         f1, t1 = o.pair_features(x, *ids[k])
         assert np.array_equal(f1, feat[k]) and t1 == t[k]
+
+
+def test_forces_with_learned_cg_force_all_cg_reduce_to_pair_sums_and_conserve_momentum():
+    """lambda = 0 everywhere: the total force on each molecule is the sum over partners of
+    the symmetrised network force along the COM axis (bonded terms cancel in the sum)."""
+    s = inputs.tetra_system(64, (17.2, 6.45, 6.45), 0.0, 0.0, seed=14)
+    x, _ = inputs.tetra_state(s)
+    o = oracle.Oracle(s)
+    net = oracle.OracleMLP(random_params(seed=15, scale=0.2))
+    o.set_mlp(net)
+    f, e = o.forces(x)
+    assert e["E_cg"] == 0.0
+    assert np.abs(f.sum(0)).max() <= 1e-12 * np.abs(f).sum()
+    feat, _, ids = o.collect_pairs(x, s.rc_cg)
+    fp = net.pair_force(feat)
+    R, _, _ = o.com_lambda(x)
+    L = np.array(s.box)
+    Fm = np.zeros((s.M, 3))
+    for (a, b), fab in zip(ids, fp):
+        d = R[a] - R[b]
+        d -= L * np.rint(d / L)
+        u = d / np.linalg.norm(d)
+        Fm[a] += fab * u
+        Fm[b] -= fab * u
+    assert np.allclose(f.reshape(s.M, 4, 3).sum(1), Fm, rtol=1e-9, atol=1e-9 * np.abs(Fm).max())
+    o.set_mlp(None)
+    f_tab, e_tab = o.forces(x)
+    assert e_tab["E_cg"] != 0.0 and not np.allclose(f_tab, f)
