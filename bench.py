@@ -204,6 +204,109 @@ def run_block(sim, nsteps=MD_PER_BLOCK):
     sim.run(nsteps, sample_every=SAMPLE_EVERY, tf_update=True, alpha=TF_ALPHA)
 
 
+def learned_arm(s, x0, v0, make, timed, steps):
+    """FP32 path with the learned CG force: samples from an all-atomistic FP64 run of the
+    same fluid, GPU training, then the same timed blocks in network mode."""
+    import copy
+
+    from paper_1806_10841_gb300 import adress
+
+    t0 = time.perf_counter()
+    s_at = copy.copy(s)
+    s_at.d_at = 1e4  # every molecule atomistic
+    at = adress.AdResS(s_at, precision="fp64")
+    at.set_state(x0, v0)
+    at.compute_forces(energies=False)
+    n = 0
+    for _ in range(3):
+        at.step(100)
+        n = at.mlp_collect(cap=1_000_000)
+    feat, t, _ = at.mlp_samples(n)
+    at.close()
+    rng = np.random.default_rng(20180628)
+    idx = rng.permutation(n)
+    ntr = int(0.9 * n)
+    tr, te = idx[:ntr], idx[ntr:]
+    mean, std = feat[tr].mean(0), feat[tr].std(0) + 1e-3
+    scale = float(t[tr].std())
+    params = dict(W1=rng.normal(0, 1 / 3, (64, 9)), b1=np.zeros(64), W2=rng.normal(0, 1 / 8, (64, 64)),
+                  b2=np.zeros(64), w3=rng.normal(0, 1 / 8, 64), b3=float(t[tr].mean() / scale))
+    sim = make("fp32")
+    sim.mlp_set(params, mean, std, scale)
+    sim.mlp_load_samples(feat[tr], t[tr])
+    t1 = time.perf_counter()
+    losses = sim.mlp_train(epochs=5, batch=4096, lr=2e-3)
+    t_train = time.perf_counter() - t1
+    sw = feat[te].copy()
+    sw[:, 1:5], sw[:, 5:9] = feat[te][:, 5:9], feat[te][:, 1:5]
+    pred = 0.5 * scale * (sim.mlp_forward(feat[te]) + sim.mlp_forward(sw))
+    table = np.interp(feat[te][:, 0], np.arange(len(s.cg_F)) * s.cg_dr, s.cg_F)
+    rms = lambda a: float(math.sqrt(np.mean(np.square(a))))
+    prep_s = time.perf_counter() - t0
+    sim.set_cg_mode(1)
+    sim.set_state(x0, v0)
+    sim.compute_forces(energies=False)
+    tot, _, _ = timed(sim, steps, 2)
+    value = s.N * MD_PER_BLOCK * steps / tot
+    sim.close()
+    return {"value": value, "unit": "atom-steps/s", "training_samples": int(ntr), "held_out": int(n - ntr),
+            "epoch_loss": [float(v) for v in losses], "train_s": t_train, "prep_s": prep_s,
+            "held_out_force_rms": {"target": rms(t[te]), "network_error": rms(pred - t[te]),
+                                   "table_error": rms(table - t[te])},
+            "source": "pairs with COM distance < rc_cg from 3 snapshots of an all-atomistic FP64 run"}
+
+
+def replicas_arm(timed, steps, local):
+    """64 independent replicas (log-uniform 500..20000 molecules, AT width U(3, 15), hybrid
+    U(1, 5)) in one handle: every MD step is one launch over all replicas' molecules, the
+    bench step one captured graph.  Timed with the default launch configuration, then after
+    the autotuner, and against the same replicas stepped one handle after another."""
+    import torch
+
+    from paper_1806_10841_gb300 import adress, inputs
+
+    systems = inputs.replica_batch(64)
+    x, v = inputs.replica_states(systems)
+    sim = adress.AdResS(systems, precision="fp32", device=f"cuda:{local}")
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    sim.check()
+    n_atoms = sim.N
+    t_def, _, _ = timed(sim, steps, 2)
+    rows = sim.autotune(nsteps=50)
+    tuning = sim.get_tuning()
+    t_tuned, ms, clocks = timed(sim, steps, 2)
+    sim.close()
+    # the same replicas one handle at a time (one graph launch per replica per bench step)
+    sims = []
+    a0 = np.concatenate([[0], np.cumsum([q.N for q in systems])])
+    for r, s in enumerate(systems):
+        one = adress.AdResS(s, precision="fp32", device=f"cuda:{local}", replica=r)
+        one.set_state(x[a0[r]:a0[r + 1]], v[a0[r]:a0[r + 1]])
+        one.compute_forces(energies=False)
+        run_block(one)
+        sims.append(one)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = sims[0].stream
+    e0.record(stream)
+    for _ in range(steps):
+        for one in sims:
+            run_block(one)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    for one in sims:
+        one.check()
+        one.close()
+    per = lambda t: n_atoms * MD_PER_BLOCK * steps / t
+    return {"value": per(t_tuned), "unit": "atom-steps/s", "replicas": len(systems), "atoms": n_atoms,
+            "molecules": [int(s.M) for s in systems], "value_default_tuning": per(t_def),
+            "value_one_handle_per_replica": per(t_seq), "tuning": {"force_block": tuning[0], "skin": tuning[1]},
+            "autotune_rows_block_skin_ms_per_md_step": rows, "ms_per_bench_step": t_tuned / steps * 1e3,
+            "clocks": clocks}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,6 +316,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 GPU comparison arm")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-CG-force arm")
+    ap.add_argument("--no-replicas", action="store_true", help="skip the 64-replica batch arm")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up, run this many MD steps, exit (no timing output)")
     ap.add_argument("--molecules", type=int, default=200_000,
@@ -359,6 +464,14 @@ def main():
     else:
         sim.close()
 
+    learned = None
+    if not args.no_learned and rank == 0:
+        learned = learned_arm(s, x0, v0, make, timed, max(2, args.steps // 2))
+
+    replicas = None
+    if not args.no_replicas and rank == 0:
+        replicas = replicas_arm(timed, max(2, args.steps // 2), local)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -418,6 +531,8 @@ def main():
         "clocks": clocks,
         "pair_stats": stats,
         "compare": compare,
+        "learned_cg": learned,
+        "replicas_64": replicas,
         "per_step_ms": ms,
     }
     if not args.no_cpu_baseline:

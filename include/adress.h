@@ -89,7 +89,9 @@ typedef struct {
   int32_t tf_n;
   double tf_dx;
   /* Langevin thermostat in velocity Verlet: F_L = -gamma m v + sqrt(24 gamma kT m/dt)(u-1/2),
-   * u from Philox4x64-10 with key (seed, time level) and counter (atom, replica, 0, 0) */
+   * u from Philox4x32-10 with key (low, high 32 bits of seed) and counter (atom index within
+   * the replica, low and high 32 bits of the time level, 2 replica + block); the FP64 path
+   * draws blocks 0 and 1 and forms 53-bit uniforms, the FP32 path takes 24 bits of block 0 */
   double kT, gamma, dt;
   uint64_t seed;
   int64_t replica;
@@ -103,6 +105,20 @@ typedef struct {
  * device and bind `stream` (a cudaStream_t; NULL = legacy default stream).
  * On failure *out is NULL and the status says why. */
 adress_status adress_init(const adress_config* cfg, void* stream, adress_handle* out);
+
+/* Batched replicas: n_replicas independent systems in one handle, stepped together by the
+ * same kernels (one launch per step over all replicas' molecules, captured in one graph).
+ * cfgs[r] describes replica r; the replicas may differ in n_mols, box, x_center,
+ * d_at_half, d_hy, replica and the values of tf, and must agree in everything else
+ * (ADRESS_ERR_ARG names the first difference).  Replica r's molecules follow those of
+ * replicas 0..r-1 in the state arrays (so its atoms are a contiguous range of every
+ * component), its lists only hold its own molecules, and each replica's result equals
+ * that of a single-system handle with the same config.  The thermodynamic-force table and
+ * the density histogram hold tf_n entries per replica, replica after replica; energies and
+ * the kinetic observables are sums over all replicas; the rebuild decision is shared (all
+ * replicas rebuild when one needs it).  1 <= n_replicas <= 65536, total molecules < 2^23. */
+adress_status adress_init_batch(const adress_config* cfgs, int32_t n_replicas, void* stream,
+                                adress_handle* out);
 
 /* Borrow the caller's device state: x, v double [3][N]; f [3][N] of double
  * (ADRESS_FP64) or float (ADRESS_FP32_MIXED).  Pointers must stay valid until the next
@@ -225,6 +241,24 @@ adress_status adress_list_stats(adress_handle h, int64_t* out);
  * then the last step).  ms_out host [4] = milliseconds of {prologue (half kick + drift +
  * mapping), list rebuild (average), fused step (average), last step}.  Synchronises. */
 adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out);
+
+/* Launch configuration: threads per block of the mapping and force kernels (32, 64 or
+ * 128; 4 threads per molecule) and the list skin (cells have edge >= max(rc_cg, rc_at +
+ * 2 r_ext) + skin, so the skin sets the cell size and how often lists are rebuilt).  The
+ * results do not depend on either beyond the order of floating-point sums.  Setting them
+ * discards captured graphs and the lists (build them again before stepping). */
+adress_status adress_set_tuning(adress_handle h, int32_t force_block, double skin);
+adress_status adress_get_tuning(adress_handle h, int32_t* force_block, double* skin);
+
+/* Autotuner: for every force_block in {32, 64, 128} and skin in {0.5, 1, 1.5, 2} x the
+ * configured skin (those the boxes admit), run nsteps (1..100) steps of the bound state once to
+ * capture the graph and once timed with CUDA events, and keep the fastest pair.  The bound
+ * state (x, v, f, time level) is copied aside first and restored after every trial, and
+ * the lists are rebuilt for the chosen pair, so the call leaves the state as it found
+ * it.  results (host, may be NULL): up to max_results rows of {force_block, skin,
+ * ms per step}; *n_results (may be NULL) = rows written.  Synchronises. */
+adress_status adress_autotune(adress_handle h, int32_t nsteps, double* results, int32_t max_results,
+                              int32_t* n_results);
 
 /* Kinetic energy and momentum of a velocity array without allocating anything: out
  * device double [4] = {KE, Px, Py, Pz} with KE = sum 1/2 m v^2, P = sum m v.

@@ -20,7 +20,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "neighbour list ov
           7: "invalid state", 8: "molecule wider than the list cutoff allows"}
 
 # Every symbol include/adress.h declares (checked by the CPU test suite).
-EXPORTS = ["adress_init", "adress_bind_state", "adress_build_lists", "adress_compute_forces",
+EXPORTS = ["adress_init", "adress_init_batch", "adress_set_tuning", "adress_get_tuning", "adress_autotune",
+           "adress_bind_state", "adress_build_lists", "adress_compute_forces",
            "adress_step", "adress_run", "adress_set_step", "adress_get_step", "adress_com_lambda", "adress_kinetic",
            "adress_density_accumulate", "adress_density_get", "adress_density_reset",
            "adress_tf_update", "adress_set_tf", "adress_get_tf", "adress_list_stats", "adress_list_export",
@@ -73,6 +74,10 @@ def load_library(path: str = LIB_PATH):
     i64p = C.POINTER(C.c_int64)
     sig = {
         "adress_init": ([C.POINTER(adress_config), vp, C.POINTER(H)], C.c_int),
+        "adress_init_batch": ([C.POINTER(adress_config), C.c_int32, vp, C.POINTER(H)], C.c_int),
+        "adress_set_tuning": ([H, C.c_int32, C.c_double], C.c_int),
+        "adress_get_tuning": ([H, C.POINTER(C.c_int32), d], C.c_int),
+        "adress_autotune": ([H, C.c_int32, d, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
         "adress_bind_state": ([H, vp, vp, vp], C.c_int),
         "adress_build_lists": ([H], C.c_int),
         "adress_compute_forces": ([H, d], C.c_int),
@@ -119,16 +124,43 @@ def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _config(s, keep, replica, max_neighbors, precision):
+    """adress_config of one system; the host arrays it points to are appended to keep."""
+    arrs = dict(
+        mass=np.ascontiguousarray(s.mass, dtype=np.float64),
+        bonds=np.ascontiguousarray(np.asarray(s.bonds, dtype=np.int32).reshape(-1)),
+        cgF=np.ascontiguousarray(s.cg_F, dtype=np.float64),
+        cgV=np.ascontiguousarray(s.cg_V, dtype=np.float64),
+        tf=np.ascontiguousarray(s.tf if s.tf is not None else np.zeros(0), dtype=np.float64),
+    )
+    keep.append(arrs)
+    tf_n = len(arrs["tf"])
+    return adress_config(
+        n_mols=int(s.M), atoms_per_mol=int(s.na), mass=_dptr(arrs["mass"]), box=(C.c_double * 3)(*s.box),
+        x_center=s.xc, d_at_half=s.d_at, d_hy=s.d_hy, wca_eps=s.eps, wca_sigma=s.sigma,
+        rc_at=s.rc_at, n_bonds=len(arrs["bonds"]) // 2,
+        bonds=arrs["bonds"].ctypes.data_as(C.POINTER(C.c_int32)), fene_k=s.fene_k,
+        fene_r0=s.fene_r0, intra_wca=int(s.intra_wca), cg_F=_dptr(arrs["cgF"]), cg_V=_dptr(arrs["cgV"]),
+        cg_n=len(arrs["cgF"]) - 1, cg_dr=s.cg_dr, rc_cg=s.rc_cg,
+        tf=_dptr(arrs["tf"]) if tf_n else None, tf_n=tf_n, tf_dx=s.tf_dx,
+        kT=s.kT, gamma=s.gamma, dt=s.dt, seed=int(s.seed), replica=int(replica), skin=s.skin,
+        r_ext=s.r_ext, max_neighbors=int(max_neighbors),
+        precision=ADRESS_FP64 if precision == "fp64" else ADRESS_FP32_MIXED)
+
+
 class AdResS:
-    """One AdResS system on one GPU.
+    """One AdResS system, or a batch of independent replicas, on one GPU.
 
     State tensors live on the device in structure-of-arrays layout ``[3, N]``:
     ``x``, ``v`` float64 and ``f`` float64 (``precision='fp64'``) or float32
-    (``precision='fp32'``, the mixed path).
+    (``precision='fp32'``, the mixed path).  With a list of systems (``adress_init_batch``)
+    replica r's molecules follow those of replicas 0..r-1; ``replica`` is then a list of
+    replica ids (default 0, 1, ...), and ``mol0`` / ``atom0`` give each replica's first
+    molecule / atom.
     """
 
     def __init__(self, system, *, precision: str = "fp32", device: str = "cuda:0", stream=None,
-                 max_neighbors: int = 0, replica: int = 0):
+                 max_neighbors: int = 0, replica=0):
         import torch
 
         self.torch = torch
@@ -136,33 +168,29 @@ class AdResS:
         self.system = system
         self.precision = precision
         self.device = torch.device(device)
-        s = system
-        self.M, self.na = int(s.M), int(s.na)
+        batch = isinstance(system, (list, tuple))
+        systems = list(system) if batch else [system]
+        if batch and isinstance(replica, int):
+            replica = list(range(replica, replica + len(systems)))
+        reps = list(replica) if batch else [replica]
+        self._keep = []
+        cfgs = (adress_config * len(systems))(*[_config(s, self._keep, r, max_neighbors, precision)
+                                                  for s, r in zip(systems, reps)])
+        self.n_replicas = len(systems)
+        self.na = int(systems[0].na)
+        self.mol0 = np.concatenate([[0], np.cumsum([int(s.M) for s in systems])]).astype(np.int64)
+        self.M = int(self.mol0[-1])
+        self.atom0 = self.mol0 * self.na
         self.N = self.M * self.na
-        self._keep = dict(
-            mass=np.ascontiguousarray(s.mass, dtype=np.float64),
-            bonds=np.ascontiguousarray(np.asarray(s.bonds, dtype=np.int32).reshape(-1)),
-            cgF=np.ascontiguousarray(s.cg_F, dtype=np.float64),
-            cgV=np.ascontiguousarray(s.cg_V, dtype=np.float64),
-            tf=np.ascontiguousarray(s.tf if s.tf is not None else np.zeros(0), dtype=np.float64),
-        )
-        k = self._keep
-        self.tf_n = len(k["tf"])
-        cfg = adress_config(
-            n_mols=self.M, atoms_per_mol=self.na, mass=_dptr(k["mass"]), box=(C.c_double * 3)(*s.box),
-            x_center=s.xc, d_at_half=s.d_at, d_hy=s.d_hy, wca_eps=s.eps, wca_sigma=s.sigma,
-            rc_at=s.rc_at, n_bonds=len(k["bonds"]) // 2,
-            bonds=k["bonds"].ctypes.data_as(C.POINTER(C.c_int32)), fene_k=s.fene_k,
-            fene_r0=s.fene_r0, intra_wca=int(s.intra_wca), cg_F=_dptr(k["cgF"]), cg_V=_dptr(k["cgV"]),
-            cg_n=len(k["cgF"]) - 1, cg_dr=s.cg_dr, rc_cg=s.rc_cg,
-            tf=_dptr(k["tf"]) if self.tf_n else None, tf_n=self.tf_n, tf_dx=s.tf_dx,
-            kT=s.kT, gamma=s.gamma, dt=s.dt, seed=int(s.seed), replica=int(replica), skin=s.skin,
-            r_ext=s.r_ext, max_neighbors=int(max_neighbors),
-            precision=ADRESS_FP64 if precision == "fp64" else ADRESS_FP32_MIXED)
+        self.tf_n = len(self._keep[0]["tf"]) * len(systems)
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.h = C.c_void_p()
-            st = self.lib.adress_init(C.byref(cfg), C.c_void_p(self.stream.cuda_stream), C.byref(self.h))
+            sp = C.c_void_p(self.stream.cuda_stream)
+            if batch:
+                st = self.lib.adress_init_batch(cfgs, len(systems), sp, C.byref(self.h))
+            else:
+                st = self.lib.adress_init(C.byref(cfgs[0]), sp, C.byref(self.h))
             if st != 0:
                 raise AdressError(st, self.lib.adress_last_error(None).decode())
             fdt = torch.float64 if precision == "fp64" else torch.float32
@@ -274,6 +302,22 @@ class AdResS:
         tf = np.zeros(self.tf_n)
         self._call("adress_get_tf", _dptr(tf), self.tf_n)
         return tf
+
+    def set_tuning(self, force_block: int, skin: float):
+        self._call("adress_set_tuning", C.c_int32(int(force_block)), C.c_double(float(skin)))
+
+    def get_tuning(self):
+        b, sk = C.c_int32(), C.c_double()
+        self._call("adress_get_tuning", C.byref(b), C.byref(sk))
+        return b.value, sk.value
+
+    def autotune(self, nsteps: int = 20):
+        """Pick threads per block and list skin by timing nsteps-step runs (the state is
+        restored); returns the trial table as rows (force_block, skin, ms per step)."""
+        rows = np.zeros((16, 3))
+        n = C.c_int32()
+        self._call("adress_autotune", C.c_int32(int(nsteps)), _dptr(rows), 16, C.byref(n))
+        return [(int(r[0]), float(r[1]), float(r[2])) for r in rows[:n.value]]
 
     def list_stats(self):
         out = np.zeros(8, dtype=np.int64)

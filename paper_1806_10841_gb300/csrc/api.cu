@@ -46,6 +46,15 @@ struct adress_ctx {
   long long bat_cap = 0;
   int* mlp_counts = nullptr;  // [M + 1]
   int* mlp_offs = nullptr;    // [M + 1]
+  // boxes (one per replica) and the cell arrays sized for ncell_cap cells
+  std::vector<Box> boxes;
+  Box* d_boxes = nullptr;
+  int* mol_box = nullptr;
+  int* cell_box = nullptr;
+  int* cell_rank = nullptr;
+  int* rank_cell = nullptr;
+  int ncell_cap = 0;
+  double skin0 = 0.0;  // skin of the configuration (the autotuner scales it)
   MlpDevArgs mlp_args() const { return MlpDevArgs{mlp_P, mlp_W1p, mlp_W2p, mlp_W2Tp, mlp_norm}; }
 };
 
@@ -121,65 +130,199 @@ static uint64_t morton3(uint64_t x, uint64_t y, uint64_t z) {
   return c;
 }
 
-static int auto_capacity(const Sys& s) {
-  const double vol = s.L[0] * s.L[1] * s.L[2];
-  const double expect = 4.0 / 3.0 * M_PI * s.r_list * s.r_list * s.r_list * s.M / vol;
+// Expected neighbours of the densest box, doubled, as the initial list capacity.
+static int auto_capacity(const Sys& s, const std::vector<Box>& boxes, const std::vector<int>& nmol) {
+  double expect = 0.0;
+  for (size_t k = 0; k < boxes.size(); ++k) {
+    const Box& B = boxes[k];
+    const double vol = B.L[0] * B.L[1] * B.L[2];
+    expect = std::max(expect, 4.0 / 3.0 * M_PI * s.r_list * s.r_list * s.r_list * nmol[k] / vol);
+  }
   int cap = (int)ceil(2.0 * expect + 16.0);
   cap = (cap + 3) & ~3;
   return std::min(cap, std::max(4, s.M - 1));
 }
 
-extern "C" {
-
-const char* adress_status_string(adress_status s) {
-  switch (s) {
-    case ADRESS_OK: return "ok";
-    case ADRESS_ERR_ARG: return "invalid argument";
-    case ADRESS_ERR_CUDA: return "CUDA error";
-    case ADRESS_ERR_LIST_OVERFLOW: return "neighbour list overflow";
-    case ADRESS_ERR_NONFINITE: return "non-finite force";
-    case ADRESS_ERR_BOND_BROKEN: return "FENE bond broken";
-    case ADRESS_ERR_TIMEOUT: return "device wait timed out";
-    case ADRESS_ERR_STATE: return "invalid state";
-    case ADRESS_ERR_EXTENT: return "molecule wider than the list cutoff allows";
-  }
-  return "unknown status";
+// Validation of one configuration; empty when valid.
+static std::string config_error(const adress_config* c) {
+  if (c->n_mols < 2) return "n_mols must be >= 2";
+  if (c->atoms_per_mol < 1 || c->atoms_per_mol > kMaxNA) return "atoms_per_mol must be in 1..4";
+  if ((long long)c->n_mols * c->atoms_per_mol > (1ll << 30)) return "too many atoms";
+  if (!c->mass) return "mass is NULL";
+  for (int k = 0; k < c->atoms_per_mol; ++k)
+    if (!(c->mass[k] > 0)) return "masses must be > 0";
+  for (int d = 0; d < 3; ++d)
+    if (!(c->box[d] > 0)) return "box edges must be > 0";
+  if (c->n_bonds < 0 || c->n_bonds > kMaxBonds || (c->n_bonds > 0 && !c->bonds))
+    return "n_bonds must be 0..6 with a bond array";
+  for (int q = 0; q < 2 * c->n_bonds; ++q)
+    if (c->bonds[q] < 0 || c->bonds[q] >= c->atoms_per_mol) return "bond index out of range";
+  if (c->n_bonds > 0 && !(c->fene_r0 > 0)) return "fene_r0 must be > 0";
+  if (!c->cg_F || !c->cg_V || c->cg_n < 1 || !(c->cg_dr > 0)) return "CG table missing";
+  if (c->rc_cg > c->cg_n * c->cg_dr * (1 + 1e-12)) return "rc_cg beyond the CG table";
+  if (c->tf_n < 0 || (c->tf_n > 0 && (!c->tf || !(c->tf_dx > 0)))) return "thermodynamic-force table invalid";
+  if (c->tf_n > 4096) return "tf_n must be <= 4096";
+  if (!(c->d_at_half >= 0) || !(c->d_hy >= 0)) return "slab widths must be >= 0";
+  if (!(c->dt > 0) || c->gamma < 0 || c->kT < 0) return "dt, gamma, kT invalid";
+  if (c->precision != ADRESS_FP64 && c->precision != ADRESS_FP32_MIXED) return "unknown precision";
+  if (!(c->skin >= 0) || !(c->r_ext >= 0) || !(c->rc_at > 0) || !(c->rc_cg > 0)) return "cutoffs invalid";
+  return "";
 }
 
-const char* adress_last_error(adress_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+// Replicas of a batch share the molecule model, the interaction, the tables' grids, the
+// thermostat and the list parameters; they differ in size, box, slab and replica id.
+static std::string shared_mismatch(const adress_config* a, const adress_config* c) {
+  if (c->atoms_per_mol != a->atoms_per_mol) return "atoms_per_mol";
+  for (int k = 0; k < a->atoms_per_mol; ++k)
+    if (c->mass[k] != a->mass[k]) return "mass";
+  if (c->wca_eps != a->wca_eps || c->wca_sigma != a->wca_sigma || c->rc_at != a->rc_at) return "WCA parameters";
+  if (c->n_bonds != a->n_bonds || c->fene_k != a->fene_k || c->fene_r0 != a->fene_r0 ||
+      c->intra_wca != a->intra_wca)
+    return "bonded model";
+  for (int q = 0; q < 2 * a->n_bonds; ++q)
+    if (c->bonds[q] != a->bonds[q]) return "bond list";
+  if (c->cg_n != a->cg_n || c->cg_dr != a->cg_dr || c->rc_cg != a->rc_cg) return "CG table grid";
+  for (int k = 0; k <= a->cg_n; ++k)
+    if (c->cg_F[k] != a->cg_F[k] || c->cg_V[k] != a->cg_V[k]) return "CG table";
+  if (c->tf_n != a->tf_n || (a->tf_n > 0 && c->tf_dx != a->tf_dx)) return "thermodynamic-force grid";
+  if (c->kT != a->kT || c->gamma != a->gamma || c->dt != a->dt || c->seed != a->seed) return "thermostat";
+  if (c->skin != a->skin || c->r_ext != a->r_ext || c->max_neighbors != a->max_neighbors) return "list parameters";
+  if (c->precision != a->precision) return "precision";
+  return "";
+}
 
-adress_status adress_init(const adress_config* c, void* stream, adress_handle* out) {
+// Geometry of one box: edges, fixed-point maps and slab (cells are set by setup_cells).
+static Box make_box(const adress_config* c, double skin) {
+  Box B{};
+  for (int d = 0; d < 3; ++d) {
+    B.L[d] = c->box[d];
+    B.halfL[d] = 0.5 * c->box[d];
+    memcpy(&B.Lbits[d], &c->box[d], sizeof(double));
+    B.fx_inv[d] = 4294967296.0 / c->box[d];
+    B.fx_scale[d] = (float)(c->box[d] / 4294967296.0);
+    int q = 63;
+    while (ldexp(1.0, q) / c->box[d] < 9223372036854775808.0) ++q;  // 2^q / L >= 2^63
+    while (ldexp(1.0, q) / c->box[d] >= 18446744073709551616.0) --q;
+    B.fxq[d] = q;
+    B.fxK[d] = (unsigned long long)(ldexp(1.0, q) / c->box[d]);
+  }
+  B.xc32 = fixed32_host(c->x_center - c->box[0] * floor(c->x_center / c->box[0]), B.fxK[0], B.fxq[0]);
+  B.xc = c->x_center;
+  B.d_at = c->d_at_half;
+  B.d_hy = c->d_hy;
+  B.d_hr = c->d_at_half + c->d_hy + 0.5 * skin;
+  B.pi_half_over_dhy = c->d_hy > 0 ? 0.5 * M_PI / c->d_hy : 0.0;
+  B.d_at_f = (float)B.d_at;
+  B.d_hyend_f = (float)(B.d_at + B.d_hy);
+  B.pi_half_over_dhy_f = (float)B.pi_half_over_dhy;
+  B.near_at = 1e-4f * (1.f + B.d_at_f);
+  B.near_hyend = 1e-4f * (1.f + B.d_hyend_f);
+  B.replica = c->replica;
+  return B;
+}
+
+// List cutoff r_list = max(rc_cg, rc_at + 2 r_ext) + skin and everything that follows from
+// it: cells of edge >= r_list in every box (ranked in Morton order inside each box, boxes
+// one after another), the high-resolution candidate bound, and the device copies.
+static adress_status setup_cells(adress_ctx* h, double skin) {
+  Sys& s = h->sys;
+  Bufs& b = h->buf;
+  const double r_list = std::max(s.rc_cg, s.rc_at + 2.0 * s.r_ext) + skin;
+  for (const Box& B : h->boxes)
+    for (int d = 0; d < 3; ++d)
+      if (B.L[d] < 2.0 * r_list) return fail(h, ADRESS_ERR_ARG, "box edge shorter than twice the list cutoff");
+  long long total = 0;
+  for (Box& B : h->boxes) {
+    for (int d = 0; d < 3; ++d) B.nc[d] = std::max(1, (int)floor(B.L[d] / r_list));
+    B.ncell = B.nc[0] * B.nc[1] * B.nc[2];
+    B.cell0 = (int)std::min<long long>(total, 1ll << 30);
+    total += (long long)B.nc[0] * B.nc[1] * B.nc[2];
+  }
+  if (total > 4096ll * 2048ll) return fail(h, ADRESS_ERR_ARG, "too many cells for the device scans (max 8388608)");
+  s.skin = skin;
+  s.r_list = r_list;
+  s.r_list2 = r_list * r_list;
+  s.ncell = (int)total;
+  for (Box& B : h->boxes) B.d_hr = B.d_at + B.d_hy + 0.5 * skin;
+  s.bx = h->boxes[0];
+
+  cudaError_t e = cudaSuccess;
+  if (s.ncell > h->ncell_cap) {
+    int *cc = b.cell_count, *cf = b.cell_fill, *cs = b.cell_start;
+    if (e == cudaSuccess) e = realloc_owned(h, &cc, s.ncell);
+    if (e == cudaSuccess) e = realloc_owned(h, &cf, s.ncell);
+    if (e == cudaSuccess) e = realloc_owned(h, &cs, s.ncell + 1);
+    if (e == cudaSuccess) e = realloc_owned(h, &h->cell_rank, s.ncell);
+    if (e == cudaSuccess) e = realloc_owned(h, &h->rank_cell, s.ncell);
+    if (e == cudaSuccess && s.nbox > 1) e = realloc_owned(h, &h->cell_box, s.ncell);
+    b.cell_count = cc;
+    b.cell_fill = cf;
+    b.cell_start = cs;
+    if (e != cudaSuccess) return fail(h, ADRESS_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    h->ncell_cap = s.ncell;
+  }
+  b.cell_rank = h->cell_rank;
+  b.rank_cell = h->rank_cell;
+  b.cell_box = h->cell_box;
+
+  std::vector<int> rank(s.ncell), rcell(s.ncell), cbox(s.nbox > 1 ? s.ncell : 0);
+  for (int k = 0; k < s.nbox; ++k) {
+    const Box& B = h->boxes[k];
+    std::vector<std::pair<uint64_t, int>> codes(B.ncell);
+    for (int x = 0; x < B.nc[0]; ++x)
+      for (int y = 0; y < B.nc[1]; ++y)
+        for (int z = 0; z < B.nc[2]; ++z) {
+          const int lin = (x * B.nc[1] + y) * B.nc[2] + z;
+          codes[lin] = {morton3(x, y, z), lin};
+        }
+    std::sort(codes.begin(), codes.end());
+    for (int r = 0; r < B.ncell; ++r) {
+      rank[B.cell0 + codes[r].second] = B.cell0 + r;
+      rcell[B.cell0 + r] = B.cell0 + codes[r].second;
+      if (s.nbox > 1) cbox[B.cell0 + r] = k;
+    }
+  }
+  cudaStream_t st = h->stream;
+  e = cudaMemcpyAsync(h->cell_rank, rank.data(), sizeof(int) * s.ncell, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->rank_cell, rcell.data(), sizeof(int) * s.ncell, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && s.nbox > 1)
+    e = cudaMemcpyAsync(h->cell_box, cbox.data(), sizeof(int) * s.ncell, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && s.nbox > 1)
+    e = cudaMemcpyAsync(h->d_boxes, h->boxes.data(), sizeof(Box) * s.nbox, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
+  if (e != cudaSuccess) return fail(h, ADRESS_ERR_CUDA, std::string("cell upload: ") + cudaGetErrorString(e));
+  free_graphs(h);
+  h->lists_built = false;
+  return ADRESS_OK;
+}
+
+static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream, adress_handle* out) {
   if (!out) return fail(nullptr, ADRESS_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (!c) return fail(nullptr, ADRESS_ERR_ARG, "config is NULL");
-  if (c->n_mols < 2) return fail(nullptr, ADRESS_ERR_ARG, "n_mols must be >= 2");
-  if (c->atoms_per_mol < 1 || c->atoms_per_mol > kMaxNA)
-    return fail(nullptr, ADRESS_ERR_ARG, "atoms_per_mol must be in 1..4");
-  if ((long long)c->n_mols * c->atoms_per_mol > (1ll << 30))
-    return fail(nullptr, ADRESS_ERR_ARG, "too many atoms");
-  if (!c->mass) return fail(nullptr, ADRESS_ERR_ARG, "mass is NULL");
-  for (int k = 0; k < c->atoms_per_mol; ++k)
-    if (!(c->mass[k] > 0)) return fail(nullptr, ADRESS_ERR_ARG, "masses must be > 0");
-  for (int d = 0; d < 3; ++d)
-    if (!(c->box[d] > 0)) return fail(nullptr, ADRESS_ERR_ARG, "box edges must be > 0");
-  if (c->n_bonds < 0 || c->n_bonds > kMaxBonds || (c->n_bonds > 0 && !c->bonds))
-    return fail(nullptr, ADRESS_ERR_ARG, "n_bonds must be 0..6 with a bond array");
-  for (int q = 0; q < 2 * c->n_bonds; ++q)
-    if (c->bonds[q] < 0 || c->bonds[q] >= c->atoms_per_mol)
-      return fail(nullptr, ADRESS_ERR_ARG, "bond index out of range");
-  if (c->n_bonds > 0 && !(c->fene_r0 > 0)) return fail(nullptr, ADRESS_ERR_ARG, "fene_r0 must be > 0");
-  if (!c->cg_F || !c->cg_V || c->cg_n < 1 || !(c->cg_dr > 0))
-    return fail(nullptr, ADRESS_ERR_ARG, "CG table missing");
-  if (c->rc_cg > c->cg_n * c->cg_dr * (1 + 1e-12))
-    return fail(nullptr, ADRESS_ERR_ARG, "rc_cg beyond the CG table");
-  if (c->tf_n < 0 || (c->tf_n > 0 && (!c->tf || !(c->tf_dx > 0))))
-    return fail(nullptr, ADRESS_ERR_ARG, "thermodynamic-force table invalid");
-  if (!(c->d_at_half >= 0) || !(c->d_hy >= 0)) return fail(nullptr, ADRESS_ERR_ARG, "slab widths must be >= 0");
-  if (!(c->dt > 0) || c->gamma < 0 || c->kT < 0) return fail(nullptr, ADRESS_ERR_ARG, "dt, gamma, kT invalid");
-  if (c->precision != ADRESS_FP64 && c->precision != ADRESS_FP32_MIXED)
-    return fail(nullptr, ADRESS_ERR_ARG, "unknown precision");
-  if (!(c->skin >= 0) || !(c->r_ext >= 0) || !(c->rc_at > 0) || !(c->rc_cg > 0))
-    return fail(nullptr, ADRESS_ERR_ARG, "cutoffs invalid");
+  if (!cfgs) return fail(nullptr, ADRESS_ERR_ARG, "config is NULL");
+  if (nbox < 1 || nbox > 65536) return fail(nullptr, ADRESS_ERR_ARG, "n_replicas must be in 1..65536");
+  long long mtot = 0;
+  for (int k = 0; k < nbox; ++k) {
+    const std::string why = config_error(&cfgs[k]);
+    if (!why.empty())
+      return fail(nullptr, ADRESS_ERR_ARG, nbox > 1 ? "replica " + std::to_string(k) + ": " + why : why);
+    if (k > 0) {
+      const std::string what = shared_mismatch(&cfgs[0], &cfgs[k]);
+      if (!what.empty())
+        return fail(nullptr, ADRESS_ERR_ARG, "replica " + std::to_string(k) + " differs from replica 0 in " + what);
+    }
+    const double r_list = std::max(cfgs[k].rc_cg, cfgs[k].rc_at + 2.0 * cfgs[k].r_ext) + cfgs[k].skin;
+    for (int d = 0; d < 3; ++d)
+      if (cfgs[k].box[d] < 2.0 * r_list)
+        return fail(nullptr, ADRESS_ERR_ARG,
+                    (nbox > 1 ? "replica " + std::to_string(k) + ": " : std::string()) +
+                        "box edge shorter than twice the list cutoff");
+    mtot += cfgs[k].n_mols;
+  }
+  if (mtot > 4096 * 2048 - 1)
+    return fail(nullptr, ADRESS_ERR_ARG, "too many molecules for the device scans (max 8388607)");
+  const adress_config* c = &cfgs[0];
 
   adress_ctx* h = new adress_ctx();
   h->precision = c->precision;
@@ -190,9 +333,11 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   }
   cudaGetDevice(&h->device);
   Sys& s = h->sys;
-  s.M = c->n_mols;
+  s.nbox = nbox;
+  s.M = (int)mtot;
   s.NA = c->atoms_per_mol;
   s.N = s.M * s.NA;
+  s.force_block = 128;
   double Mtot = 0;
   for (int k = 0; k < s.NA; ++k) Mtot += c->mass[k];
   s.Mtot = Mtot;
@@ -208,25 +353,6 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
     s.gmf[k] = (float)s.gm[k];
   }
   s.fp64 = c->precision == ADRESS_FP64;
-  for (int d = 0; d < 3; ++d) {
-    s.L[d] = c->box[d];
-    s.halfL[d] = 0.5 * c->box[d];
-    memcpy(&s.Lbits[d], &c->box[d], sizeof(double));
-    s.fx_inv[d] = 4294967296.0 / c->box[d];
-    s.fx_scale[d] = (float)(c->box[d] / 4294967296.0);
-    s.Lf[d] = (float)c->box[d];
-    int q = 63;
-    while (ldexp(1.0, q) / c->box[d] < 9223372036854775808.0) ++q;  // 2^q / L >= 2^63
-    while (ldexp(1.0, q) / c->box[d] >= 18446744073709551616.0) --q;
-    s.fxq[d] = q;
-    s.fxK[d] = (unsigned long long)(ldexp(1.0, q) / c->box[d]);
-  }
-  s.xc32 = fixed32_host(c->x_center - c->box[0] * floor(c->x_center / c->box[0]), s.fxK[0], s.fxq[0]);
-  s.xc = c->x_center;
-  s.d_at = c->d_at_half;
-  s.d_hy = c->d_hy;
-  s.d_hr = c->d_at_half + c->d_hy + 0.5 * c->skin;
-  s.pi_half_over_dhy = c->d_hy > 0 ? 0.5 * M_PI / c->d_hy : 0.0;
   s.eps = c->wca_eps;
   s.sig2 = c->wca_sigma * c->wca_sigma;
   s.rc_at = c->rc_at;
@@ -249,28 +375,8 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   s.seed = c->seed;
   s.seed_lo = (unsigned)(c->seed & 0xffffffffull);
   s.seed_hi = (unsigned)(c->seed >> 32);
-  s.replica = c->replica;
-  s.skin = c->skin;
   s.r_ext = c->r_ext;
-  s.r_list = std::max(c->rc_cg, c->rc_at + 2.0 * c->r_ext) + c->skin;
-  s.r_list2 = s.r_list * s.r_list;
   s.reach_at2 = (c->rc_at + 2.0 * c->r_ext) * (c->rc_at + 2.0 * c->r_ext);
-  for (int d = 0; d < 3; ++d) {
-    if (c->box[d] < 2.0 * s.r_list) {
-      delete h;
-      return fail(nullptr, ADRESS_ERR_ARG, "box edge shorter than twice the list cutoff");
-    }
-    s.nc[d] = std::max(1, (int)floor(c->box[d] / s.r_list));
-  }
-  if ((long long)s.nc[0] * s.nc[1] * s.nc[2] > 4096ll * 2048ll || s.M > 4096 * 2048 - 1) {
-    delete h;
-    return fail(nullptr, ADRESS_ERR_ARG, "too many cells or molecules for the device scans (max 8388607)");
-  }
-  if (c->tf_n > 4096) {
-    delete h;
-    return fail(nullptr, ADRESS_ERR_ARG, "tf_n must be <= 4096");
-  }
-  s.ncell = s.nc[0] * s.nc[1] * s.nc[2];
   for (int k = 0; k < kMaxNA; ++k) {
     s.dt_m[k] = c->dt / s.mass[k];
     s.f.frac[k] = (float)s.frac[k];
@@ -283,18 +389,34 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   s.f.cg_inv_dr = (float)s.cg_inv_dr;
   s.f.fene_k = (float)s.fene_k;
   s.f.fene_r02 = (float)s.fene_r02;
-  s.f.d_at = (float)s.d_at;
-  s.f.d_hyend = (float)(s.d_at + s.d_hy);
-  s.f.pi_half_over_dhy = (float)s.pi_half_over_dhy;
   s.f.tf_inv_dx = (float)s.tf_inv_dx;
-  s.f.near_at = 1e-4f * (1.f + s.f.d_at);
-  s.f.near_hyend = 1e-4f * (1.f + s.f.d_hyend);
-  s.cap = c->max_neighbors > 0 ? std::min(c->max_neighbors, s.M - 1) : auto_capacity(s);
+
+  std::vector<int> nmol(nbox);
+  h->boxes.resize(nbox);
+  int mol0 = 0;
+  for (int k = 0; k < nbox; ++k) {
+    Box& B = h->boxes[k];
+    B = make_box(&cfgs[k], c->skin);
+    B.mol0 = mol0;
+    B.index = k;
+    B.tf0 = k * s.tf_n;
+    nmol[k] = cfgs[k].n_mols;
+    mol0 += cfgs[k].n_mols;
+  }
+  h->skin0 = c->skin;
+  s.r_list = std::max(c->rc_cg, c->rc_at + 2.0 * c->r_ext) + c->skin;
+  s.cap = c->max_neighbors > 0 ? std::min(c->max_neighbors, s.M - 1) : auto_capacity(s, h->boxes, nmol);
 
   // ---- device buffers ----
   Bufs& b = h->buf;
   const int M = s.M, N = s.N;
-  h->nparts = std::max(force_warps(s), ceil_div(N, 256));
+  {
+    int warps = 0;
+    for (int blk = 32; blk <= kMaxForceBlock; blk *= 2)
+      warps = std::max(warps, ceil_div((long long)M * kGroup, blk) * (blk / 32));
+    h->nparts = std::max(warps, ceil_div(N, 256));
+  }
+  const int ntf = std::max(1, nbox * s.tf_n);
   cudaError_t e = cudaSuccess;
 #define A(ptr, n)                                  \
   do {                                             \
@@ -313,9 +435,6 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
     }
   }
   A(b.mcell, M);
-  A(b.cell_count, s.ncell);
-  A(b.cell_fill, s.ncell);
-  A(b.cell_start, s.ncell + 1);
   A(b.sorted, M);
   A(b.flag, M);
   A(b.pos, M + 1);
@@ -324,12 +443,6 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   A(b.nn, M);
   A(b.nbr, (size_t)s.cap * M);
   A(b.scan_tmp, 4096);
-  int* cell_rank = nullptr;
-  int* rank_cell = nullptr;
-  A(cell_rank, s.ncell);
-  A(rank_cell, s.ncell);
-  b.cell_rank = cell_rank;
-  b.rank_cell = rank_cell;
   double* cgF = nullptr;
   double* cgV = nullptr;
   float2* cgFV = nullptr;
@@ -339,56 +452,59 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   b.cgF64 = cgF;
   b.cgV64 = cgV;
   b.cgFV32 = cgFV;
-  A(b.tf64, std::max(1, s.tf_n));
-  A(b.tf32, std::max(1, s.tf_n));
+  A(b.tf64, ntf);
+  A(b.tf32, ntf);
   A(b.part, (size_t)h->nparts * 4);
   A(b.result, 8);
-  A(b.hist, std::max(1, s.tf_n));
+  A(b.hist, ntf);
   A(b.nsamples, 1);
   A(b.ctrl, 1);
+  if (nbox > 1) {
+    A(h->d_boxes, nbox);
+    A(h->mol_box, M);
+  }
 #undef A
+  b.boxes = h->d_boxes;
+  b.mol_box = h->mol_box;
   if (e != cudaSuccess) {
     adress_destroy(h);
     return fail(nullptr, ADRESS_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   }
-
-  // ---- Morton ranks of cells ----
-  std::vector<std::pair<uint64_t, int>> codes(s.ncell);
-  for (int x = 0; x < s.nc[0]; ++x)
-    for (int y = 0; y < s.nc[1]; ++y)
-      for (int z = 0; z < s.nc[2]; ++z) {
-        int lin = (x * s.nc[1] + y) * s.nc[2] + z;
-        codes[lin] = {morton3(x, y, z), lin};
-      }
-  std::sort(codes.begin(), codes.end());
-  std::vector<int> rank(s.ncell), rcell(s.ncell);
-  for (int r = 0; r < s.ncell; ++r) {
-    rank[codes[r].second] = r;
-    rcell[r] = codes[r].second;
+  {
+    adress_status st = setup_cells(h, c->skin);
+    if (st != ADRESS_OK) {
+      const std::string msg = h->err;
+      adress_destroy(h);
+      return fail(nullptr, st, msg);
+    }
   }
+
   std::vector<float2> fv(s.cg_n + 1);
   for (int k = 0; k <= s.cg_n; ++k) fv[k] = make_float2((float)c->cg_F[k], (float)c->cg_V[k]);
-  std::vector<double> tf(std::max(1, s.tf_n), 0.0);
-  std::vector<float> tff(std::max(1, s.tf_n), 0.f);
-  for (int k = 0; k < s.tf_n; ++k) {
-    tf[k] = c->tf[k];
-    tff[k] = (float)c->tf[k];
-  }
+  std::vector<double> tf(ntf, 0.0);
+  std::vector<float> tff(ntf, 0.f);
+  for (int r = 0; r < nbox; ++r)
+    for (int k = 0; k < s.tf_n; ++k) {
+      tf[r * s.tf_n + k] = cfgs[r].tf[k];
+      tff[r * s.tf_n + k] = (float)cfgs[r].tf[k];
+    }
+  std::vector<int> mb(nbox > 1 ? M : 0);
+  for (int r = 0; r < nbox && nbox > 1; ++r)
+    std::fill(mb.begin() + h->boxes[r].mol0, mb.begin() + h->boxes[r].mol0 + cfgs[r].n_mols, r);
   cudaStream_t st = h->stream;
 #define H2D(dst, src, bytes)                                                                  \
   do {                                                                                        \
     if (e == cudaSuccess) e = cudaMemcpyAsync((void*)(dst), (src), (bytes), cudaMemcpyHostToDevice, st); \
   } while (0)
-  H2D(cell_rank, rank.data(), sizeof(int) * s.ncell);
-  H2D(rank_cell, rcell.data(), sizeof(int) * s.ncell);
   H2D(cgF, c->cg_F, sizeof(double) * (s.cg_n + 1));
   H2D(cgV, c->cg_V, sizeof(double) * (s.cg_n + 1));
   H2D(cgFV, fv.data(), sizeof(float2) * (s.cg_n + 1));
   H2D(b.tf64, tf.data(), sizeof(double) * tf.size());
   H2D(b.tf32, tff.data(), sizeof(float) * tff.size());
+  if (nbox > 1) H2D(h->mol_box, mb.data(), sizeof(int) * M);
 #undef H2D
   if (e == cudaSuccess) e = cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(b.hist, 0, sizeof(unsigned long long) * std::max(1, s.tf_n), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.hist, 0, sizeof(unsigned long long) * ntf, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.nsamples, 0, sizeof(long long), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.com_ref, 0, sizeof(int4) * M, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors go out of scope
@@ -400,6 +516,33 @@ adress_status adress_init(const adress_config* c, void* stream, adress_handle* o
   }
   *out = h;
   return ADRESS_OK;
+}
+
+extern "C" {
+
+const char* adress_status_string(adress_status s) {
+  switch (s) {
+    case ADRESS_OK: return "ok";
+    case ADRESS_ERR_ARG: return "invalid argument";
+    case ADRESS_ERR_CUDA: return "CUDA error";
+    case ADRESS_ERR_LIST_OVERFLOW: return "neighbour list overflow";
+    case ADRESS_ERR_NONFINITE: return "non-finite force";
+    case ADRESS_ERR_BOND_BROKEN: return "FENE bond broken";
+    case ADRESS_ERR_TIMEOUT: return "device wait timed out";
+    case ADRESS_ERR_STATE: return "invalid state";
+    case ADRESS_ERR_EXTENT: return "molecule wider than the list cutoff allows";
+  }
+  return "unknown status";
+}
+
+const char* adress_last_error(adress_handle h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+adress_status adress_init(const adress_config* c, void* stream, adress_handle* out) {
+  return init_impl(c, 1, stream, out);
+}
+
+adress_status adress_init_batch(const adress_config* cfgs, int32_t n_replicas, void* stream, adress_handle* out) {
+  return init_impl(cfgs, n_replicas, stream, out);
 }
 
 adress_status adress_bind_state(adress_handle h, double* x, double* v, void* f) {
@@ -686,7 +829,7 @@ adress_status adress_density_accumulate(adress_handle h) {
 }
 
 adress_status adress_density_get(adress_handle h, int64_t* counts, int32_t n, int64_t* nsamples) {
-  if (!h || (!counts && n > 0) || n < 0 || n > h->sys.tf_n) return ADRESS_ERR_ARG;
+  if (!h || (!counts && n > 0) || n < 0 || n > h->sys.nbox * h->sys.tf_n) return ADRESS_ERR_ARG;
   if (n > 0)
     CUDA_OR_FAIL(h, cudaMemcpyAsync(counts, h->buf.hist, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, h->stream));
   long long ns = 0;
@@ -698,7 +841,8 @@ adress_status adress_density_get(adress_handle h, int64_t* counts, int32_t n, in
 
 adress_status adress_density_reset(adress_handle h) {
   if (!h) return ADRESS_ERR_ARG;
-  CUDA_OR_FAIL(h, cudaMemsetAsync(h->buf.hist, 0, sizeof(unsigned long long) * std::max(1, h->sys.tf_n), h->stream));
+  CUDA_OR_FAIL(h, cudaMemsetAsync(h->buf.hist, 0, sizeof(unsigned long long) * std::max(1, h->sys.nbox * h->sys.tf_n),
+                                  h->stream));
   CUDA_OR_FAIL(h, cudaMemsetAsync(h->buf.nsamples, 0, sizeof(long long), h->stream));
   return ADRESS_OK;
 }
@@ -710,7 +854,7 @@ adress_status adress_tf_update(adress_handle h, double alpha) {
 }
 
 adress_status adress_set_tf(adress_handle h, const double* tf, int32_t n) {
-  if (!h || n != h->sys.tf_n || (n > 0 && !tf)) return ADRESS_ERR_ARG;
+  if (!h || n != h->sys.nbox * h->sys.tf_n || (n > 0 && !tf)) return ADRESS_ERR_ARG;
   if (n == 0) return ADRESS_OK;
   std::vector<float> f(n);
   for (int k = 0; k < n; ++k) f[k] = (float)tf[k];
@@ -721,7 +865,7 @@ adress_status adress_set_tf(adress_handle h, const double* tf, int32_t n) {
 }
 
 adress_status adress_get_tf(adress_handle h, double* tf, int32_t n) {
-  if (!h || n != h->sys.tf_n || (n > 0 && !tf)) return ADRESS_ERR_ARG;
+  if (!h || n != h->sys.nbox * h->sys.tf_n || (n > 0 && !tf)) return ADRESS_ERR_ARG;
   if (n == 0) return ADRESS_OK;
   CUDA_OR_FAIL(h, cudaMemcpyAsync(tf, h->buf.tf64, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
   CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
@@ -778,6 +922,132 @@ adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out) 
   ms_out[2] = (float)(acc[2] / reps);
   ms_out[3] = (float)acc[3];
   return ADRESS_OK;
+}
+
+adress_status adress_set_tuning(adress_handle h, int32_t force_block, double skin) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (force_block != 32 && force_block != 64 && force_block != 128)
+    return fail(h, ADRESS_ERR_ARG, "force_block must be 32, 64 or 128");
+  if (!(skin >= 0)) return fail(h, ADRESS_ERR_ARG, "skin must be >= 0");
+  const double old_skin = h->sys.skin;
+  adress_status st = setup_cells(h, skin);
+  if (st != ADRESS_OK) {
+    setup_cells(h, old_skin);
+    return fail(h, st, "set_tuning: " + h->err);
+  }
+  h->sys.force_block = force_block;
+  free_graphs(h);
+  h->lists_built = false;
+  return ADRESS_OK;
+}
+
+adress_status adress_get_tuning(adress_handle h, int32_t* force_block, double* skin) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (force_block) *force_block = h->sys.force_block;
+  if (skin) *skin = h->sys.skin;
+  return ADRESS_OK;
+}
+
+adress_status adress_autotune(adress_handle h, int32_t nsteps, double* results, int32_t max_results,
+                              int32_t* n_results) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (nsteps < 1 || nsteps > kMaxGraphSteps) return fail(h, ADRESS_ERR_ARG, "nsteps must be in 1..100");
+  if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
+  if (n_results) *n_results = 0;
+  Sys& s = h->sys;
+  const size_t n3 = (size_t)3 * s.N;
+  const size_t fbytes = n3 * (h->precision == ADRESS_FP64 ? sizeof(double) : sizeof(float));
+  double *x0 = nullptr, *v0 = nullptr;
+  void* f0 = nullptr;
+  Ctrl c0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaMalloc(&x0, n3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&v0, n3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&f0, fbytes);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  auto cleanup = [&]() {
+    cudaFree(x0);
+    cudaFree(v0);
+    cudaFree(f0);
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(h, ADRESS_ERR_CUDA, std::string("autotune scratch: ") + cudaGetErrorString(e));
+  }
+  cudaStream_t st = h->stream;
+  e = cudaMemcpyAsync(x0, h->buf.x, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v0, h->buf.v, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f0, h->buf.f, fbytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&c0, h->buf.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(h, ADRESS_ERR_CUDA, std::string("autotune save: ") + cudaGetErrorString(e));
+  }
+  c0.err = 0;
+  auto restore = [&]() -> cudaError_t {
+    cudaError_t r = cudaMemcpyAsync(h->buf.x, x0, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(h->buf.v, v0, n3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(h->buf.f, f0, fbytes, cudaMemcpyDeviceToDevice, st);
+    if (r == cudaSuccess) r = cudaMemcpyAsync(h->buf.ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st);
+    if (r == cudaSuccess) r = cudaStreamSynchronize(st);
+    return r;
+  };
+  const double skin0 = h->skin0;
+  const int block0 = s.force_block;
+  const double cur_skin = s.skin;
+  std::vector<double> skins;
+  for (double m : {0.5, 1.0, 1.5, 2.0}) {
+    const double sk = m * skin0;
+    if (std::find(skins.begin(), skins.end(), sk) == skins.end()) skins.push_back(sk);
+  }
+  int best_block = block0, rows = 0;
+  double best_skin = cur_skin, best_ms = 1e300;
+  adress_status status = ADRESS_OK;
+  for (double sk : skins) {
+    for (int blk : {32, 64, 128}) {
+      if (adress_set_tuning(h, blk, sk) != ADRESS_OK) continue;  // a box too small for this skin
+      cudaError_t r = restore();
+      if (r != cudaSuccess) {
+        status = fail(h, ADRESS_ERR_CUDA, std::string("autotune restore: ") + cudaGetErrorString(r));
+        break;
+      }
+      status = build_lists_sync(h);
+      if (status == ADRESS_OK) status = launch_graph(h, nsteps, 0, 0, 0.0);  // capture + warm-up
+      if (status == ADRESS_OK && cudaEventRecord(ev[0], st) != cudaSuccess) status = ADRESS_ERR_CUDA;
+      if (status == ADRESS_OK) status = launch_graph(h, nsteps, 0, 0, 0.0);
+      if (status == ADRESS_OK && cudaEventRecord(ev[1], st) != cudaSuccess) status = ADRESS_ERR_CUDA;
+      if (status == ADRESS_OK) status = adress_check(h);
+      if (status != ADRESS_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      const double per = ms / nsteps;
+      if (results && rows < max_results) {
+        results[3 * rows + 0] = blk;
+        results[3 * rows + 1] = sk;
+        results[3 * rows + 2] = per;
+      }
+      ++rows;
+      if (per < best_ms) {
+        best_ms = per;
+        best_block = blk;
+        best_skin = sk;
+      }
+    }
+    if (status != ADRESS_OK) break;
+  }
+  if (n_results) *n_results = std::min(rows, std::max(0, max_results));
+  adress_status st2 = adress_set_tuning(h, status == ADRESS_OK ? best_block : block0,
+                                        status == ADRESS_OK ? best_skin : cur_skin);
+  cudaError_t r = restore();
+  cleanup();
+  if (status != ADRESS_OK) return status;
+  if (st2 != ADRESS_OK) return st2;
+  if (r != cudaSuccess) return fail(h, ADRESS_ERR_CUDA, std::string("autotune restore: ") + cudaGetErrorString(r));
+  return build_lists_sync(h);
 }
 
 adress_status adress_list_export(adress_handle h, int32_t* items, int32_t* nn, int32_t* nbr) {

@@ -36,10 +36,8 @@ struct DecideArgs {
   cudaGraphConditionalHandle h;
 };
 
-// Per-system constants, passed by value to every kernel.
-struct Sys {
-  int M, NA, N;
-  int fp64;  // 1: FP64 path, 0: FP32 mixed path
+// Geometry of one periodic box (one replica): edges, fixed-point maps, slab and cells.
+struct Box {
   double L[3], halfL[3];
   long long Lbits[3];           // bit patterns of L (wrap tests on the integer pipe)
   double fx_inv[3];             // 2^32 / L  (fixed-point COM)
@@ -47,9 +45,24 @@ struct Sys {
   unsigned long long fxK[3];    // floor(2^fxq / L), in [2^63, 2^64)
   int fxq[3];
   unsigned xc32;                // slab centre in 32-bit fixed point
-  float Lf[3];
   double xc, d_at, d_hy, d_hr;  // d_hr: high-resolution candidate bound at list build
   double pi_half_over_dhy;
+  float d_at_f, d_hyend_f, pi_half_over_dhy_f, near_at, near_hyend;
+  int nc[3];
+  int ncell;   // cells of this box
+  int cell0;   // first global cell index (and Morton rank) of this box
+  int mol0;    // first molecule of this box
+  int index;   // position of this box in the batch
+  int tf0;     // first entry of this box's thermodynamic-force table and density histogram
+  long long replica;  // replica id (thermostat noise counter)
+};
+
+// Per-system constants, passed by value to every kernel.
+struct Sys {
+  int M, NA, N;
+  int fp64;  // 1: FP64 path, 0: FP32 mixed path
+  int nbox;  // 1: a single box (bx); > 1: batched replicas (Bufs::boxes, Bufs::mol_box)
+  Box bx;
   double mass[kMaxNA], inv_mass[kMaxNA], frac[kMaxNA], Mtot;
   double hdt_m[kMaxNA];          // dt / (2 m)
   double amp[kMaxNA], gm[kMaxNA];  // Langevin: sqrt(24 gamma kT m / dt), gamma m
@@ -66,18 +79,17 @@ struct Sys {
   double kT, gamma, dt;
   unsigned long long seed;
   unsigned seed_lo, seed_hi;
-  long long replica;
   double skin, r_ext, r_list, r_list2, reach_at2;  // reach_at: rc_at + 2 r_ext
   double rc_at, rc_cg;
-  int nc[3];
-  int ncell;
+  int ncell;  // cells of all boxes
   int cap;  // neighbour-list capacity per molecule
+  int force_block;  // threads per block of the mapping and force kernels
   int cg_mode;  // 0: tabulated F^CG, 1: learned network (pair forces in Bufs::fpair)
   double dt_m[kMaxNA];  // dt / m (both half kicks of a fused step)
   // float copies of the parameters the FP32 path uses (no run-time double->float work)
   struct {
     float eps, sig2, rc_at, rc_at2, rc_cg2, cg_inv_dr, fene_k, fene_r02;
-    float d_at, d_hyend, pi_half_over_dhy, tf_inv_dx, near_at, near_hyend;
+    float tf_inv_dx;
     float frac[kMaxNA];
   } f;
 };
@@ -125,7 +137,20 @@ struct Bufs {
   long long* nsamples;
   Ctrl* ctrl;
   float* fpair;  // [M*cap] network CG pair force per list slot (CG mode 1)
+  // batched replicas (nbox > 1)
+  const Box* boxes;    // [nbox]
+  const int* mol_box;  // [M] box of each molecule
+  const int* cell_box; // [ncell] box of each global cell rank
 };
+
+// Box of molecule a (the single box unless the system holds batched replicas).
+__device__ __forceinline__ const Box& box_of(const Sys& s, const Bufs& b, int a) {
+  return s.nbox > 1 ? b.boxes[b.mol_box[a]] : s.bx;
+}
+template <bool MULTI>
+__device__ __forceinline__ const Box& box_t(const Sys& s, const Bufs& b, int a) {
+  return MULTI ? b.boxes[b.mol_box[a]] : s.bx;
+}
 
 // Learned CG force: device parameter arrays (see mlp.cu).
 struct MlpDevArgs {
@@ -202,9 +227,14 @@ cudaError_t mlp_gather(const float* feat, const float* target, long long n, long
 // Record the message returned by adress_last_error(NULL) and return the status.
 adress_status set_global_error(adress_status s, const std::string& msg);
 
-constexpr int kForceBlock = 128;
+// Threads per block of the mapping and force kernels: 32, 64 or 128 (Sys::force_block).
+// 128 is also the launch bound the kernels are compiled for (a bound of 256 costs them
+// registers and ~4% time at 128 threads).
+constexpr int kMaxForceBlock = 128;
 
 // Warps launched by the force kernel (one energy partial each).
-inline int force_warps(const Sys& s) { return ceil_div((long long)s.M * kGroup, kForceBlock) * (kForceBlock / 32); }
+inline int force_warps(const Sys& s) {
+  return ceil_div((long long)s.M * kGroup, s.force_block) * (s.force_block / 32);
+}
 
 }  // namespace adress

@@ -18,20 +18,21 @@ __device__ __forceinline__ int cell_of(unsigned int X, int nc) {
   return (int)(((unsigned long long)X * (unsigned long long)nc) >> 32);
 }
 
-__global__ void k_rb_zero(Sys s, Bufs b) {
+__global__ void k_rb_zero(const __grid_constant__ Sys s, Bufs b) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.ncell; c += gridDim.x * blockDim.x) {
     b.cell_count[c] = 0;
     b.cell_fill[c] = 0;
   }
 }
 
-__global__ void k_rb_count(Sys s, Bufs b) {
+__global__ void k_rb_count(const __grid_constant__ Sys s, Bufs b) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= s.M) return;
+  const Box& B = box_of(s, b, a);
   const int4 C = b.com_fx[b.ctrl->parity][a];
-  const int cx = cell_of((unsigned)C.x, s.nc[0]), cy = cell_of((unsigned)C.y, s.nc[1]),
-            cz = cell_of((unsigned)C.z, s.nc[2]);
-  const int r = b.cell_rank[(cx * s.nc[1] + cy) * s.nc[2] + cz];
+  const int cx = cell_of((unsigned)C.x, B.nc[0]), cy = cell_of((unsigned)C.y, B.nc[1]),
+            cz = cell_of((unsigned)C.z, B.nc[2]);
+  const int r = b.cell_rank[B.cell0 + (cx * B.nc[1] + cy) * B.nc[2] + cz];
   b.mcell[a] = r;
   atomicAdd(&b.cell_count[r], 1);
 }
@@ -137,7 +138,7 @@ static cudaError_t exclusive_scan(const int* in, int* out, int n, int* tmp, int*
   return cudaGetLastError();
 }
 
-__global__ void k_rb_fill(Sys s, Bufs b) {
+__global__ void k_rb_fill(const __grid_constant__ Sys s, Bufs b) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= s.M) return;
   const int r = b.mcell[a];
@@ -145,15 +146,15 @@ __global__ void k_rb_fill(Sys s, Bufs b) {
   b.sorted[p] = a;
 }
 
-__global__ void k_rb_flag(Sys s, Bufs b) {
+__global__ void k_rb_flag(const __grid_constant__ Sys s, Bufs b) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= s.M) return;
   const int a = b.sorted[k], cur = b.ctrl->parity;
   const double d = s.fp64 ? fabs(b.dxc64[cur][a]) : (double)fabsf(b.molf[cur][a].x);
-  b.flag[k] = d < s.d_hr + (s.fp64 ? 0.0 : 1e-3) ? 1 : 0;
+  b.flag[k] = d < box_of(s, b, a).d_hr + (s.fp64 ? 0.0 : 1e-3) ? 1 : 0;
 }
 
-__global__ void k_rb_items(Sys s, Bufs b) {
+__global__ void k_rb_items(const __grid_constant__ Sys s, Bufs b) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int n_hr = b.pos[s.M];
   if (k == 0) {
@@ -173,19 +174,20 @@ __global__ void k_rb_items(Sys s, Bufs b) {
 // a dimension has < 3 cells) in fixed order, each cell's members in id order.
 __device__ void scan_neighbours(const Sys& s, const Bufs& b, const int4* com, int a, int t) {
   const int4 C = com[a];
-  const int c0 = cell_of((unsigned)C.x, s.nc[0]), c1 = cell_of((unsigned)C.y, s.nc[1]),
-            c2 = cell_of((unsigned)C.z, s.nc[2]);
+  const Box& B = box_of(s, b, a);
+  const int c0 = cell_of((unsigned)C.x, B.nc[0]), c1 = cell_of((unsigned)C.y, B.nc[1]),
+            c2 = cell_of((unsigned)C.z, B.nc[2]);
   const float rl2 = (float)s.r_list2;
   int cnt = 0;
-  const int lo0 = s.nc[0] >= 3 ? -1 : 0, lo1 = s.nc[1] >= 3 ? -1 : 0, lo2 = s.nc[2] >= 3 ? -1 : 0;
-  const int hi0 = s.nc[0] >= 2 ? 1 : 0, hi1 = s.nc[1] >= 2 ? 1 : 0, hi2 = s.nc[2] >= 2 ? 1 : 0;
+  const int lo0 = B.nc[0] >= 3 ? -1 : 0, lo1 = B.nc[1] >= 3 ? -1 : 0, lo2 = B.nc[2] >= 3 ? -1 : 0;
+  const int hi0 = B.nc[0] >= 2 ? 1 : 0, hi1 = B.nc[1] >= 2 ? 1 : 0, hi2 = B.nc[2] >= 2 ? 1 : 0;
   for (int o0 = lo0; o0 <= hi0; ++o0) {
-    const int x = (c0 + o0 + s.nc[0]) % s.nc[0];
+    const int x = (c0 + o0 + B.nc[0]) % B.nc[0];
     for (int o1 = lo1; o1 <= hi1; ++o1) {
-      const int y = (c1 + o1 + s.nc[1]) % s.nc[1];
+      const int y = (c1 + o1 + B.nc[1]) % B.nc[1];
       for (int o2 = lo2; o2 <= hi2; ++o2) {
-        const int z = (c2 + o2 + s.nc[2]) % s.nc[2];
-        const int r = b.cell_rank[(x * s.nc[1] + y) * s.nc[2] + z];
+        const int z = (c2 + o2 + B.nc[2]) % B.nc[2];
+        const int r = b.cell_rank[B.cell0 + (x * B.nc[1] + y) * B.nc[2] + z];
         const int ps = b.cell_start[r], pe = b.cell_start[r + 1];
         // members in increasing id (cells are filled in no fixed order)
         int last = -1;
@@ -198,9 +200,9 @@ __device__ void scan_neighbours(const Sys& s, const Bufs& b, const int4* com, in
           last = m;
           if (m == a) continue;
           const int4 D = com[m];
-          const float d0 = (float)(int)((unsigned)C.x - (unsigned)D.x) * s.fx_scale[0];
-          const float d1 = (float)(int)((unsigned)C.y - (unsigned)D.y) * s.fx_scale[1];
-          const float d2 = (float)(int)((unsigned)C.z - (unsigned)D.z) * s.fx_scale[2];
+          const float d0 = (float)(int)((unsigned)C.x - (unsigned)D.x) * B.fx_scale[0];
+          const float d1 = (float)(int)((unsigned)C.y - (unsigned)D.y) * B.fx_scale[1];
+          const float d2 = (float)(int)((unsigned)C.z - (unsigned)D.z) * B.fx_scale[2];
           if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
             if (cnt < s.cap) b.nbr[(size_t)t * s.cap + cnt] = m;
             ++cnt;
@@ -221,24 +223,25 @@ __device__ void scan_neighbours(const Sys& s, const Bufs& b, const int4* com, in
 // candidate order with ballot/popc compaction — the same lists scan_neighbours builds.
 constexpr int kNbrWarps = 4;
 constexpr int kMaxCand = 256;  // typical neighbourhoods hold ~70 (denser ones use the scan)
-__global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(Sys s, Bufs b) {
+__global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant__ Sys s, Bufs b) {
   __shared__ int4 stage[kNbrWarps][kMaxCand];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * kNbrWarps + w;
   if (r >= s.ncell) return;  // warp-uniform
   const int4* com = b.com_fx[b.ctrl->parity];
-  const int lin = b.rank_cell[r];
-  const int cz = lin % s.nc[2], cy = (lin / s.nc[2]) % s.nc[1], cx = lin / (s.nc[1] * s.nc[2]);
+  const Box& B = s.nbox > 1 ? b.boxes[b.cell_box[r]] : s.bx;
+  const int lin = b.rank_cell[r] - B.cell0;
+  const int cz = lin % B.nc[2], cy = (lin / B.nc[2]) % B.nc[1], cx = lin / (B.nc[1] * B.nc[2]);
   int cnt = 0, start = 0;
   if (lane < 27) {
     const int o0 = lane / 9 - 1, o1 = (lane / 3) % 3 - 1, o2 = lane % 3 - 1;
-    const bool ok = (o0 >= (s.nc[0] >= 3 ? -1 : 0)) && (o0 <= (s.nc[0] >= 2 ? 1 : 0)) &&
-                    (o1 >= (s.nc[1] >= 3 ? -1 : 0)) && (o1 <= (s.nc[1] >= 2 ? 1 : 0)) &&
-                    (o2 >= (s.nc[2] >= 3 ? -1 : 0)) && (o2 <= (s.nc[2] >= 2 ? 1 : 0));
+    const bool ok = (o0 >= (B.nc[0] >= 3 ? -1 : 0)) && (o0 <= (B.nc[0] >= 2 ? 1 : 0)) &&
+                    (o1 >= (B.nc[1] >= 3 ? -1 : 0)) && (o1 <= (B.nc[1] >= 2 ? 1 : 0)) &&
+                    (o2 >= (B.nc[2] >= 3 ? -1 : 0)) && (o2 <= (B.nc[2] >= 2 ? 1 : 0));
     if (ok) {
-      const int x = (cx + o0 + s.nc[0]) % s.nc[0], y = (cy + o1 + s.nc[1]) % s.nc[1],
-                z = (cz + o2 + s.nc[2]) % s.nc[2];
-      const int rr = b.cell_rank[(x * s.nc[1] + y) * s.nc[2] + z];
+      const int x = (cx + o0 + B.nc[0]) % B.nc[0], y = (cy + o1 + B.nc[1]) % B.nc[1],
+                z = (cz + o2 + B.nc[2]) % B.nc[2];
+      const int rr = b.cell_rank[B.cell0 + (x * B.nc[1] + y) * B.nc[2] + z];
       start = b.cell_start[rr];
       cnt = b.cell_start[rr + 1] - start;
     }
@@ -291,9 +294,9 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(Sys s, Bufs b) {
       if (k < total) {
         const int4 D = stage[w][k];
         m = D.w;
-        const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * s.fx_scale[0];
-        const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * s.fx_scale[1];
-        const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * s.fx_scale[2];
+        const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * B.fx_scale[0];
+        const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * B.fx_scale[1];
+        const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * B.fx_scale[2];
         hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < rl2;
       }
       const unsigned bal = __ballot_sync(0xffffffffu, hit);
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(Sys s, Bufs b) {
 }
 
 // Largest neighbour count of the last build (host-side capacity check only).
-__global__ void k_max_nn(const Sys s, const Bufs b) {
+__global__ void k_max_nn(const __grid_constant__ Sys s, const Bufs b) {
   int m = 0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s.M; t += gridDim.x * blockDim.x) m = max(m, b.nn[t]);
   m = __reduce_max_sync(0xffffffffu, m);

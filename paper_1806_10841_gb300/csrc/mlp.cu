@@ -422,9 +422,10 @@ __device__ __forceinline__ float4 offset_f(const Bufs& b, int cur, int i) {
 template <int NA, bool F64>
 __device__ __forceinline__ void pair_features32(const Sys& s, const Bufs& b, int cur, int a, int bb, float feat[9]) {
   const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][bb];
-  const float ex = (float)(int)((unsigned)B.x - (unsigned)A.x) * s.fx_scale[0];
-  const float ey = (float)(int)((unsigned)B.y - (unsigned)A.y) * s.fx_scale[1];
-  const float ez = (float)(int)((unsigned)B.z - (unsigned)A.z) * s.fx_scale[2];
+  const Box& X = box_of(s, b, a);
+  const float ex = (float)(int)((unsigned)B.x - (unsigned)A.x) * X.fx_scale[0];
+  const float ey = (float)(int)((unsigned)B.y - (unsigned)A.y) * X.fx_scale[1];
+  const float ez = (float)(int)((unsigned)B.z - (unsigned)A.z) * X.fx_scale[2];
   const float d = sqrtf(ex * ex + ey * ey + ez * ez), id = 1.f / d;
   float sa[4] = {0.f, 0.f, 0.f, 0.f}, sb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -458,9 +459,10 @@ __device__ __forceinline__ void pair_features32(const Sys& s, const Bufs& b, int
 template <int NA, bool F64>
 __device__ __forceinline__ float pair_target32(const Sys& s, const Bufs& b, int cur, int a, int bb) {
   const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][bb];
-  const float Rx = (float)(int)((unsigned)A.x - (unsigned)B.x) * s.fx_scale[0];
-  const float Ry = (float)(int)((unsigned)A.y - (unsigned)B.y) * s.fx_scale[1];
-  const float Rz = (float)(int)((unsigned)A.z - (unsigned)B.z) * s.fx_scale[2];
+  const Box& X = box_of(s, b, a);
+  const float Rx = (float)(int)((unsigned)A.x - (unsigned)B.x) * X.fx_scale[0];
+  const float Ry = (float)(int)((unsigned)A.y - (unsigned)B.y) * X.fx_scale[1];
+  const float Rz = (float)(int)((unsigned)A.z - (unsigned)B.z) * X.fx_scale[2];
   float Fx = 0.f, Fy = 0.f, Fz = 0.f;
 #pragma unroll
   for (int i = 0; i < NA; ++i) {
@@ -487,7 +489,7 @@ __device__ __forceinline__ float pair_target32(const Sys& s, const Bufs& b, int 
 // distance below rc_cg.  Writing uses per-item offsets from an exclusive scan, so the
 // sample order is deterministic (item order, then list order).
 template <int NA, bool F64>
-__global__ void k_mlp_collect(Sys s, Bufs b, int pass, const int* offs, long long cap, long long base, float* feat,
+__global__ void k_mlp_collect(const __grid_constant__ Sys s, Bufs b, int pass, const int* offs, long long cap, long long base, float* feat,
                               float* target, int* ids, int* counts) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= s.M) return;
@@ -500,9 +502,10 @@ __global__ void k_mlp_collect(Sys s, Bufs b, int pass, const int* offs, long lon
     const int m = b.nbr[(size_t)t * s.cap + q];
     if (m <= a) continue;
     const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][m];
-    const float dx = (float)(int)((unsigned)B.x - (unsigned)A.x) * s.fx_scale[0];
-    const float dy = (float)(int)((unsigned)B.y - (unsigned)A.y) * s.fx_scale[1];
-    const float dz = (float)(int)((unsigned)B.z - (unsigned)A.z) * s.fx_scale[2];
+    const Box& X = box_of(s, b, a);
+    const float dx = (float)(int)((unsigned)B.x - (unsigned)A.x) * X.fx_scale[0];
+    const float dy = (float)(int)((unsigned)B.y - (unsigned)A.y) * X.fx_scale[1];
+    const float dz = (float)(int)((unsigned)B.z - (unsigned)A.z) * X.fx_scale[2];
     if (dx * dx + dy * dy + dz * dz >= s.f.rc_cg2) continue;
     if (pass && o < cap) {
       float f[9];
@@ -526,7 +529,7 @@ __global__ void k_mlp_collect(Sys s, Bufs b, int pass, const int* offs, long lon
 // A warp gathers 16 pairs at a time (ballot compaction), evaluates the two orderings as
 // two 16-row tensor-core tiles and scatters the results.
 template <int NA, bool F64>
-__global__ void __launch_bounds__(128) k_mlp_pairs(Sys s, Bufs b, MlpDev m, float* fpair) {
+__global__ void __launch_bounds__(128) k_mlp_pairs(const __grid_constant__ Sys s, Bufs b, MlpDev m, float* fpair) {
   __shared__ float ft[4][2][16 * kIn];
   __shared__ int slot_a[4][16], slot_b[4][16];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
@@ -549,9 +552,10 @@ __global__ void __launch_bounds__(128) k_mlp_pairs(Sys s, Bufs b, MlpDev m, floa
       const int mm = b.nbr[(size_t)t * s.cap + q];
       if (mm > a) {
         const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][mm];
-        const float dx = (float)(int)((unsigned)B.x - (unsigned)A.x) * s.fx_scale[0];
-        const float dy = (float)(int)((unsigned)B.y - (unsigned)A.y) * s.fx_scale[1];
-        const float dz = (float)(int)((unsigned)B.z - (unsigned)A.z) * s.fx_scale[2];
+        const Box& X = box_of(s, b, a);
+        const float dx = (float)(int)((unsigned)B.x - (unsigned)A.x) * X.fx_scale[0];
+        const float dy = (float)(int)((unsigned)B.y - (unsigned)A.y) * X.fx_scale[1];
+        const float dz = (float)(int)((unsigned)B.z - (unsigned)A.z) * X.fx_scale[2];
         if (dx * dx + dy * dy + dz * dz < s.f.rc_cg2 && wa * __int_as_float(B.w) < 1.f) {
           found = q;
           mb = mm;

@@ -13,7 +13,7 @@ namespace adress {
 // last build (it could have changed class or found a new partner) or when the widest
 // molecule makes max(rc_cg, rc_at + 2 ext) + 2 disp exceed the list cutoff.  The mapping
 // just written becomes current; the maxima are reset for the next mapping.
-__global__ void k_decide(Sys s, Bufs b, DecideArgs da) {
+__global__ void k_decide(const __grid_constant__ Sys s, Bufs b, DecideArgs da) {
   Ctrl* c = b.ctrl;
   const float e = sqrtf(__uint_as_float(c->maxext2));
   const float md = sqrtf(__uint_as_float(c->maxdisp2));
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(1024) k_reduce_parts(const double* part, int n
 }
 
 template <int NA>
-__global__ void __launch_bounds__(256) k_kinetic(Sys s, Bufs b) {
+__global__ void __launch_bounds__(256) k_kinetic(const __grid_constant__ Sys s, Bufs b) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (i < s.N) {
@@ -96,27 +96,32 @@ __global__ void __launch_bounds__(256) k_kinetic(Sys s, Bufs b) {
 
 // Centre-of-mass x in double exactly as R = sum_k m_k (x_0 + minimg(x_k - x_0)) / M, wrapped.
 template <int NA>
-__device__ double com_x64(const Sys& s, const double* x, int a) {
+__device__ double com_x64(const Sys& s, const Box& B, const double* x, int a) {
   const double x0 = x[a * NA];
   double acc = 0.0;
-  for (int k = 0; k < NA; ++k) acc += s.mass[k] * (x0 + minimg_cmp(x[a * NA + k] - x0, s.L[0], s.halfL[0]));
+  for (int k = 0; k < NA; ++k) acc += s.mass[k] * (x0 + minimg_cmp(x[a * NA + k] - x0, B.L[0], B.halfL[0]));
   double r = acc / s.Mtot;
-  r -= s.L[0] * floor(r / s.L[0]);
-  if (r >= s.L[0]) r -= s.L[0];
+  r -= B.L[0] * floor(r / B.L[0]);
+  if (r >= B.L[0]) r -= B.L[0];
   return r;
 }
 
-// COM histogram folded about the slab centre: bin floor(|dxc| / tf_dx), integer atomics.
-// The FP32 path takes |dxc| from its float mapping and recomputes it in double for the
-// few molecules within 1e-4 of a bin edge, so the bin is the one the double value gives.
+// COM histogram folded about the slab centre: bin floor(|dxc| / tf_dx), integer atomics
+// (one histogram of tf_n bins per box).  The FP32 path takes |dxc| from its float mapping
+// and recomputes it in double for the few molecules within 1e-4 of a bin edge, so the bin
+// is the one the double value gives.  A single box counts into shared memory first.
 template <int NA>
-__global__ void __launch_bounds__(1024) k_density(Sys s, Bufs b) {
+__global__ void __launch_bounds__(1024) k_density(const __grid_constant__ Sys s, Bufs b) {
   extern __shared__ unsigned hs[];
-  for (int k = threadIdx.x; k < s.tf_n; k += blockDim.x) hs[k] = 0u;
-  __syncthreads();
+  const bool multi = s.nbox > 1;
+  if (!multi) {
+    for (int k = threadIdx.x; k < s.tf_n; k += blockDim.x) hs[k] = 0u;
+    __syncthreads();
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd((unsigned long long*)b.nsamples, 1ull);
   const int cur = b.ctrl->parity;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < s.M; a += gridDim.x * blockDim.x) {
+    const Box& B = box_of(s, b, a);
     int k;
     if (s.fp64) {
       k = (int)floor(fabs(b.dxc64[cur][a]) / s.tf_dx);
@@ -124,26 +129,33 @@ __global__ void __launch_bounds__(1024) k_density(Sys s, Bufs b) {
       const float u = fabsf(b.molf[cur][a].x) * s.f.tf_inv_dx, fr = u - floorf(u);
       k = (int)floorf(u);
       if (fr < 1e-4f || fr > 1.f - 1e-4f)
-        k = (int)floor(fabs(minimg_cmp(com_x64<NA>(s, b.x, a) - s.xc, s.L[0], s.halfL[0])) / s.tf_dx);
+        k = (int)floor(fabs(minimg_cmp(com_x64<NA>(s, B, b.x, a) - B.xc, B.L[0], B.halfL[0])) / s.tf_dx);
     }
-    if (k < s.tf_n) atomicAdd(&hs[k], 1u);
+    if (k < s.tf_n) {
+      if (multi) atomicAdd(&b.hist[B.tf0 + k], 1ull);
+      else atomicAdd(&hs[k], 1u);
+    }
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < s.tf_n; k += blockDim.x)
-    if (hs[k]) atomicAdd(&b.hist[k], (unsigned long long)hs[k]);
+  if (!multi) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < s.tf_n; k += blockDim.x)
+      if (hs[k]) atomicAdd(&b.hist[k], (unsigned long long)hs[k]);
+  }
 }
 
-// Thermodynamic-force iteration on the accumulated profile (one block, tf_n nodes):
+// Thermodynamic-force iteration on the accumulated profile, one block per box (tf_n nodes):
 // rho_k = counts_k / (nsamples 2 dx Ly Lz), g_k = (rho_k - rho_{k-1})/dx, g_0 = 0,
-// three-point moving average, tf_k -= alpha g_k on hybrid-layer nodes, then reset.
-__global__ void k_tf_update(Sys s, Bufs b, double alpha) {
+// three-point moving average, tf_k -= alpha g_k on hybrid-layer nodes, then the box's
+// histogram is cleared (the sample count is cleared by the launcher afterwards).
+__global__ void k_tf_update(const __grid_constant__ Sys s, Bufs b, double alpha) {
   extern __shared__ double g[];
-  const int n = s.tf_n;
+  const Box& B = s.nbox > 1 ? b.boxes[blockIdx.x] : s.bx;
+  const int n = s.tf_n, o = B.tf0;
   const double ns = (double)(*b.nsamples);
-  const double vol = ns * 2.0 * s.tf_dx * s.L[1] * s.L[2];
+  const double vol = ns * 2.0 * s.tf_dx * B.L[1] * B.L[2];
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     double gk = 0.0;
-    if (k > 0 && ns > 0) gk = ((double)b.hist[k] / vol - (double)b.hist[k - 1] / vol) / s.tf_dx;
+    if (k > 0 && ns > 0) gk = ((double)b.hist[o + k] / vol - (double)b.hist[o + k - 1] / vol) / s.tf_dx;
     g[k] = gk;
   }
   __syncthreads();
@@ -156,32 +168,34 @@ __global__ void k_tf_update(Sys s, Bufs b, double alpha) {
         ++cnt;
       }
     const double dk = k * s.tf_dx;
-    if (ns > 0 && dk >= s.d_at && dk <= s.d_at + s.d_hy) {
-      double t = b.tf64[k] - alpha * sum / cnt;
-      b.tf64[k] = t;
-      b.tf32[k] = (float)t;
+    if (ns > 0 && dk >= B.d_at && dk <= B.d_at + B.d_hy) {
+      double t = b.tf64[o + k] - alpha * sum / cnt;
+      b.tf64[o + k] = t;
+      b.tf32[o + k] = (float)t;
     }
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) b.hist[k] = 0ull;
-  if (threadIdx.x == 0) *b.nsamples = 0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) b.hist[o + k] = 0ull;
 }
 
 // FP64 centres of mass of the current positions (computed from x as the definition
 // states) and the resolution values the force kernels use.
+__global__ void k_clear_samples(long long* n) { *n = 0; }
+
 template <int NA>
-__global__ void k_export_com(Sys s, Bufs b, double* com, double* w) {
+__global__ void k_export_com(const __grid_constant__ Sys s, Bufs b, double* com, double* w) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= s.M) return;
+  const Box& B = box_of(s, b, a);
   const size_t N = (size_t)s.N;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int d = 0; d < 3; ++d) {
     const double x0 = b.x[d * N + a * NA];
     for (int k = 0; k < NA; ++k)
-      acc[d] += s.mass[k] * (x0 + minimg_cmp(b.x[d * N + a * NA + k] - x0, s.L[d], s.halfL[d]));
+      acc[d] += s.mass[k] * (x0 + minimg_cmp(b.x[d * N + a * NA + k] - x0, B.L[d], B.halfL[d]));
     double r = acc[d] / s.Mtot;
-    r -= s.L[d] * floor(r / s.L[d]);
-    if (r >= s.L[d]) r -= s.L[d];
+    r -= B.L[d] * floor(r / B.L[d]);
+    if (r >= B.L[d]) r -= B.L[d];
     com[(size_t)d * s.M + a] = r;
   }
   const int cur = b.ctrl->parity;
@@ -211,7 +225,7 @@ cudaError_t launch_kinetic(const Sys& s, const Bufs& b, cudaStream_t st) {
 
 cudaError_t launch_density(const Sys& s, const Bufs& b, int, cudaStream_t st) {
   const int blocks = std::min(ceil_div(s.M, 1024), 2 * 152);
-  const size_t smem = sizeof(unsigned) * std::max(1, s.tf_n);
+  const size_t smem = s.nbox > 1 ? 0 : sizeof(unsigned) * std::max(1, s.tf_n);
   switch (s.NA) {
     case 1: k_density<1><<<blocks, 1024, smem, st>>>(s, b); break;
     case 2: k_density<2><<<blocks, 1024, smem, st>>>(s, b); break;
@@ -223,7 +237,10 @@ cudaError_t launch_density(const Sys& s, const Bufs& b, int, cudaStream_t st) {
 
 cudaError_t launch_tf_update(const Sys& s, const Bufs& b, double alpha, cudaStream_t st) {
   if (s.tf_n <= 0) return cudaSuccess;
-  k_tf_update<<<1, 256, sizeof(double) * s.tf_n, st>>>(s, b, alpha);
+  k_tf_update<<<s.nbox, 256, sizeof(double) * s.tf_n, st>>>(s, b, alpha);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_clear_samples<<<1, 1, 0, st>>>(b.nsamples);
   return cudaGetLastError();
 }
 

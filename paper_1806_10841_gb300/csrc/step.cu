@@ -117,9 +117,9 @@ struct Prec<P64> {
   };
   static __device__ __forceinline__ double4_32a com(const Bufs& b, int cur, int a) { return b.com64[cur][a]; }
   static __device__ __forceinline__ double w(const double4_32a& c) { return c.w; }
-  static __device__ __forceinline__ V3 dR(const Sys& s, const double4_32a& A, const double4_32a& B) {
-    return {minimg_cmp(A.x - B.x, s.L[0], s.halfL[0]), minimg_cmp(A.y - B.y, s.L[1], s.halfL[1]),
-            minimg_cmp(A.z - B.z, s.L[2], s.halfL[2])};
+  static __device__ __forceinline__ V3 dR(const Box& X, const double4_32a& A, const double4_32a& B) {
+    return {minimg_cmp(A.x - B.x, X.L[0], X.halfL[0]), minimg_cmp(A.y - B.y, X.L[1], X.halfL[1]),
+            minimg_cmp(A.z - B.z, X.L[2], X.halfL[2])};
   }
   static __device__ __forceinline__ double4_32a off(const Bufs& b, int cur, int i) { return b.off64[cur][i]; }
   static __device__ __forceinline__ double cg(const Bufs& b, int cg_n, double r, double inv_dr, double* V) {
@@ -145,10 +145,10 @@ struct Prec<P32> {
   static __device__ __forceinline__ int4 com(const Bufs& b, int cur, int a) { return b.com_fx[cur][a]; }
   static __device__ __forceinline__ float w(const int4& c) { return __int_as_float(c.w); }
   // exact integer difference of fixed-point centres (periodic wrap for free), then float
-  static __device__ __forceinline__ V3 dR(const Sys& s, const int4& A, const int4& B) {
-    return {(float)(int)((unsigned)A.x - (unsigned)B.x) * s.fx_scale[0],
-            (float)(int)((unsigned)A.y - (unsigned)B.y) * s.fx_scale[1],
-            (float)(int)((unsigned)A.z - (unsigned)B.z) * s.fx_scale[2]};
+  static __device__ __forceinline__ V3 dR(const Box& X, const int4& A, const int4& B) {
+    return {(float)(int)((unsigned)A.x - (unsigned)B.x) * X.fx_scale[0],
+            (float)(int)((unsigned)A.y - (unsigned)B.y) * X.fx_scale[1],
+            (float)(int)((unsigned)A.z - (unsigned)B.z) * X.fx_scale[2]};
   }
   static __device__ __forceinline__ float4 off(const Bufs& b, int cur, int i) { return b.off32[cur][i]; }
   static __device__ __forceinline__ float cg(const Bufs& b, int cg_n, float r, float inv_dr, float* V) {
@@ -180,24 +180,24 @@ __device__ __forceinline__ double shfl_xor_d(unsigned mask, double v, int o) {
 // wrapped; all lanes of the group get the x component.  Used where a decision must be
 // taken in FP64 (region boundaries).
 template <int NA>
-__device__ __forceinline__ double com_x_fp64(const Sys& s, unsigned gmask, int base, int g, double xk) {
+__device__ __forceinline__ double com_x_fp64(const Sys& s, const Box& B, unsigned gmask, int base, int g, double xk) {
   const double x0 = shfl_d(gmask, xk, base);
   double acc = 0.0;
 #pragma unroll
   for (int k = 0; k < NA; ++k) {
     const double xkk = shfl_d(gmask, xk, base + k);
-    acc += s.mass[k] * (x0 + minimg_cmp(xkk - x0, s.L[0], s.halfL[0]));
+    acc += s.mass[k] * (x0 + minimg_cmp(xkk - x0, B.L[0], B.halfL[0]));
   }
   double r = acc / s.Mtot;
-  r -= s.L[0] * floor(r / s.L[0]);
-  if (r >= s.L[0]) r -= s.L[0];
+  r -= B.L[0] * floor(r / B.L[0]);
+  if (r >= B.L[0]) r -= B.L[0];
   return r;
 }
 
 // Map one molecule: fixed-point centre, resolution value, offsets, region flag.
 // P32: integer fixed-point arithmetic (exact, periodic) on the bits of the doubles.
 template <int NA>
-__device__ __forceinline__ void map_group32(const Sys& s, const Bufs& b, int nxt, int a, int g, unsigned gmask,
+__device__ __forceinline__ void map_group32(const Sys& s, const Box& B, const Bufs& b, int nxt, int a, int g, unsigned gmask,
                                             int base, bool live, const double x[3], float& ext2, float& disp2) {
   const bool own = live && g < NA;
   unsigned Pk[3], P0[3], R[3];
@@ -205,7 +205,7 @@ __device__ __forceinline__ void map_group32(const Sys& s, const Bufs& b, int nxt
   float cs[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    Pk[d] = fixed32(x[d], s.fxK[d], s.fxq[d]);
+    Pk[d] = fixed32(x[d], B.fxK[d], B.fxq[d]);
     P0[d] = __shfl_sync(gmask, Pk[d], base);
     const int dl = own ? (int)(Pk[d] - P0[d]) : 0;
     o32[d] = dl;
@@ -217,57 +217,57 @@ __device__ __forceinline__ void map_group32(const Sys& s, const Bufs& b, int nxt
     o32[d] -= c32;
     R[d] = P0[d] + (unsigned)c32;
   }
-  float4 o = make_float4((float)o32[0] * s.fx_scale[0], (float)o32[1] * s.fx_scale[1],
-                         (float)o32[2] * s.fx_scale[2], 0.f);
+  float4 o = make_float4((float)o32[0] * B.fx_scale[0], (float)o32[1] * B.fx_scale[1],
+                         (float)o32[2] * B.fx_scale[2], 0.f);
   if (own) {
     b.off32[nxt][a * NA + g] = o;
     ext2 = fmaxf(ext2, o.x * o.x + o.y * o.y + o.z * o.z);
   }
   // signed x distance to the slab centre; region decided in FP64 near a boundary
-  const float dxc = (float)(int)(R[0] - s.xc32) * s.fx_scale[0];
+  const float dxc = (float)(int)(R[0] - B.xc32) * B.fx_scale[0];
   float dd = fabsf(dxc);
-  const bool near = fabsf(dd - s.f.d_at) < s.f.near_at || fabsf(dd - s.f.d_hyend) < s.f.near_hyend;
+  const bool near = fabsf(dd - B.d_at_f) < B.near_at || fabsf(dd - B.d_hyend_f) < B.near_hyend;
   int region;  // 0 AT, 1 hybrid, 2 CG
   if (__any_sync(gmask, live && near)) {
-    const double rx = com_x_fp64<NA>(s, gmask, base, g, x[0]);
-    const double dxd = fabs(minimg_cmp(rx - s.xc, s.L[0], s.halfL[0]));
-    region = dxd < s.d_at ? 0 : (dxd >= s.d_at + s.d_hy ? 2 : 1);
+    const double rx = com_x_fp64<NA>(s, B, gmask, base, g, x[0]);
+    const double dxd = fabs(minimg_cmp(rx - B.xc, B.L[0], B.halfL[0]));
+    region = dxd < B.d_at ? 0 : (dxd >= B.d_at + B.d_hy ? 2 : 1);
   } else {
-    region = dd < s.f.d_at ? 0 : (dd >= s.f.d_hyend ? 2 : 1);
+    region = dd < B.d_at_f ? 0 : (dd >= B.d_hyend_f ? 2 : 1);
   }
   if (live && g == 0) {
     float w = region == 0 ? 1.f : 0.f;
     if (region == 1) {
-      const float c = cosf((dd - s.f.d_at) * s.f.pi_half_over_dhy);
+      const float c = cosf((dd - B.d_at_f) * B.pi_half_over_dhy_f);
       w = c * c;
     }
     b.com_fx[nxt][a] = make_int4((int)R[0], (int)R[1], (int)R[2], __float_as_int(w));
     b.molf[nxt][a] = make_float2(dxc, region == 1 ? 1.f : 0.f);
     const int4 ref = b.com_ref[a];
-    const float d0 = (float)(int)(R[0] - (unsigned)ref.x) * s.fx_scale[0];
-    const float d1 = (float)(int)(R[1] - (unsigned)ref.y) * s.fx_scale[1];
-    const float d2 = (float)(int)(R[2] - (unsigned)ref.z) * s.fx_scale[2];
+    const float d0 = (float)(int)(R[0] - (unsigned)ref.x) * B.fx_scale[0];
+    const float d1 = (float)(int)(R[1] - (unsigned)ref.y) * B.fx_scale[1];
+    const float d2 = (float)(int)(R[2] - (unsigned)ref.z) * B.fx_scale[2];
     disp2 = d0 * d0 + d1 * d1 + d2 * d2;
   }
 }
 
 // P64: the plain double-precision mapping (the FP64 reference path).
 template <int NA>
-__device__ __forceinline__ void map_group64(const Sys& s, const Bufs& b, int nxt, int a, int g, unsigned gmask,
+__device__ __forceinline__ void map_group64(const Sys& s, const Box& B, const Bufs& b, int nxt, int a, int g, unsigned gmask,
                                             int base, bool live, const double x[3], float& ext2, float& disp2) {
   const bool own = live && g < NA;
   double dl[3], c[3], R[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const double x0 = shfl_d(gmask, x[d], base);
-    dl[d] = own ? minimg_cmp(x[d] - x0, s.L[d], s.halfL[d]) : 0.0;
+    dl[d] = own ? minimg_cmp(x[d] - x0, B.L[d], B.halfL[d]) : 0.0;
     double cs = own ? s.frac[g] * dl[d] : 0.0;
     cs += shfl_xor_d(gmask, cs, 1);
     cs += shfl_xor_d(gmask, cs, 2);
     c[d] = cs;
     double r = x0 + cs;
-    if (r < 0.0) r += s.L[d];
-    if (r >= s.L[d]) r -= s.L[d];
+    if (r < 0.0) r += B.L[d];
+    if (r >= B.L[d]) r -= B.L[d];
     R[d] = r;
   }
   if (own) {
@@ -276,25 +276,25 @@ __device__ __forceinline__ void map_group64(const Sys& s, const Bufs& b, int nxt
     ext2 = fmaxf(ext2, (float)(o0 * o0 + o1 * o1 + o2 * o2));
   }
   if (live && g == 0) {
-    const double dxc = minimg_cmp(R[0] - s.xc, s.L[0], s.halfL[0]);
+    const double dxc = minimg_cmp(R[0] - B.xc, B.L[0], B.halfL[0]);
     const double dd = fabs(dxc);
     double w;
-    if (dd < s.d_at) w = 1.0;
-    else if (dd >= s.d_at + s.d_hy) w = 0.0;
+    if (dd < B.d_at) w = 1.0;
+    else if (dd >= B.d_at + B.d_hy) w = 0.0;
     else {
-      const double cs = cos((dd - s.d_at) * s.pi_half_over_dhy);
+      const double cs = cos((dd - B.d_at) * B.pi_half_over_dhy);
       w = cs * cs;
     }
     b.com64[nxt][a] = make_double4_32a(R[0], R[1], R[2], w);
     b.dxc64[nxt][a] = dxc;
     unsigned X[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) X[d] = (unsigned)(unsigned long long)llrint(R[d] * s.fx_inv[d]);
+    for (int d = 0; d < 3; ++d) X[d] = (unsigned)(unsigned long long)llrint(R[d] * B.fx_inv[d]);
     b.com_fx[nxt][a] = make_int4((int)X[0], (int)X[1], (int)X[2], __float_as_int((float)w));
     const int4 ref = b.com_ref[a];
-    const float d0 = (float)(int)(X[0] - (unsigned)ref.x) * s.fx_scale[0];
-    const float d1 = (float)(int)(X[1] - (unsigned)ref.y) * s.fx_scale[1];
-    const float d2 = (float)(int)(X[2] - (unsigned)ref.z) * s.fx_scale[2];
+    const float d0 = (float)(int)(X[0] - (unsigned)ref.x) * B.fx_scale[0];
+    const float d1 = (float)(int)(X[1] - (unsigned)ref.y) * B.fx_scale[1];
+    const float d2 = (float)(int)(X[2] - (unsigned)ref.z) * B.fx_scale[2];
     disp2 = d0 * d0 + d1 * d1 + d2 * d2;
   }
 }
@@ -303,7 +303,7 @@ __device__ __forceinline__ void map_group64(const Sys& s, const Bufs& b, int nxt
 // build, merged into the control block with one fire-and-forget atomic per block (no
 // fence, no returned value, so blocks retire at once); the decide kernel reads them.
 __device__ __forceinline__ void publish_extent(const Bufs& b, float ext2, float disp2) {
-  __shared__ unsigned red[2][kForceBlock / 32];
+  __shared__ unsigned red[2][kMaxForceBlock / 32];
   const unsigned e = __reduce_max_sync(0xffffffffu, __float_as_uint(ext2));
   const unsigned dm = __reduce_max_sync(0xffffffffu, __float_as_uint(disp2));
   const int w = threadIdx.x >> 5;
@@ -315,7 +315,7 @@ __device__ __forceinline__ void publish_extent(const Bufs& b, float ext2, float 
   if (threadIdx.x == 0) {
     unsigned me = red[0][0], md = red[1][0];
 #pragma unroll
-    for (int k = 1; k < kForceBlock / 32; ++k) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
       me = max(me, red[0][k]);
       md = max(md, red[1][k]);
     }
@@ -326,14 +326,15 @@ __device__ __forceinline__ void publish_extent(const Bufs& b, float ext2, float 
 
 // ---------------- k_map / k_prologue ---------------------------------------------------
 
-template <class P, int NA, bool INTEGRATE>
-__global__ void __launch_bounds__(kForceBlock) k_prologue(Sys s, Bufs b) {
+template <class P, int NA, bool INTEGRATE, bool MULTI>
+__global__ void __launch_bounds__(kMaxForceBlock) k_prologue(const __grid_constant__ Sys s, Bufs b) {
   const int lane = threadIdx.x & 31, g = threadIdx.x & 3, base = lane & ~3;
   const unsigned gmask = 0xFu << base;
   const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
   const bool live = a < s.M;
   const int i = (live ? a : 0) * NA + (g < NA ? g : 0);
   const int nxt = b.ctrl->parity ^ 1;
+  const Box& B = box_t<MULTI>(s, b, live ? a : 0);
   const size_t N = (size_t)s.N;
   double x[3];
 #pragma unroll
@@ -344,25 +345,25 @@ __global__ void __launch_bounds__(kForceBlock) k_prologue(Sys s, Bufs b) {
       const double v = fma(s.hdt_m[g], fv, b.v[d * N + i]);
       x[d] = P::fp64 ? [&] {
         double y = fma(s.dt, v, x[d]);
-        if (y < 0.0) y += s.L[d];
-        if (y >= s.L[d]) y -= s.L[d];
+        if (y < 0.0) y += B.L[d];
+        if (y >= B.L[d]) y -= B.L[d];
         return y;
       }()
-                     : wrap_bits(fma(s.dt, v, x[d]), s.L[d], s.Lbits[d]);
+                     : wrap_bits(fma(s.dt, v, x[d]), B.L[d], B.Lbits[d]);
       b.v[d * N + i] = v;
       b.x[d * N + i] = x[d];
     }
   }
   float ext2 = 0.f, disp2 = 0.f;
-  if (P::fp64) map_group64<NA>(s, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
-  else map_group32<NA>(s, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
+  if (P::fp64) map_group64<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
+  else map_group32<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
   publish_extent(b, ext2, disp2);
 }
 
 // ---------------- k_step ----------------------------------------------------------------
 
-template <class P, int NA, int MODE, bool ENERGY>
-__global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
+template <class P, int NA, int MODE, bool ENERGY, bool MULTI>
+__global__ void __launch_bounds__(kMaxForceBlock) k_step(const __grid_constant__ Sys s, Bufs b) {
   using Q = Prec<P>;
   using real = typename Q::real;
   const int lane = threadIdx.x & 31, g = threadIdx.x & 3, base = lane & ~3;
@@ -384,6 +385,7 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
   double e_at = 0.0, e_cg = 0.0, e_b = 0.0, vir = 0.0;
 
   const int a = live ? b.items[t] : 0;
+  const Box& B = box_t<MULTI>(s, b, a);
   const int i = a * NA + (g < NA ? g : 0);
   const auto Ca = Q::com(b, cur, a);
   const real wa = Q::w(Ca);
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
         m_n = b.nbr[(size_t)t * s.cap + q + 1];
         C_n = Q::com(b, cur, m_n);
       }
-      const auto R = Q::dR(s, Ca, Cb);
+      const auto R = Q::dR(B, Ca, Cb);
       const real r2 = R.x * R.x + R.y * R.y + R.z * R.z;
       const real wab = wa * Q::w(Cb);
       if (own && wab > (real)0 && r2 < reach_at2) {
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
     for (int q = g; q < nnb; q += kGroup) {
       const auto Cb = C_n;
       if (q + kGroup < nnb) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + q + kGroup]);
-      const auto R = Q::dR(s, Ca, Cb);
+      const auto R = Q::dR(B, Ca, Cb);
       const real r2 = R.x * R.x + R.y * R.y + R.z * R.z;
       if (r2 < rc_cg2) {
         const real r = Q::sqrt_(r2);
@@ -537,7 +539,7 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
       if (P::fp64) {
         const double dd = b.dxc64[cur][a], ad = fabs(dd);
         dxc = (real)dd;
-        hy = ad >= s.d_at && ad < s.d_at + s.d_hy;
+        hy = ad >= B.d_at && ad < B.d_at + B.d_hy;
       } else {
         const float2 mf = b.molf[cur][a];
         dxc = (real)mf.x;
@@ -550,9 +552,9 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
         real F = 0;
         if (k + 1 < s.tf_n) {
           const real tt = u - (real)k;
-          F = Q::tf(b, k) * ((real)1 - tt) + Q::tf(b, k + 1) * tt;
+          F = Q::tf(b, B.tf0 + k) * ((real)1 - tt) + Q::tf(b, B.tf0 + k + 1) * tt;
         } else if (k + 1 == s.tf_n && u == (real)k) {
-          F = Q::tf(b, k);
+          F = Q::tf(b, B.tf0 + k);
         }
         fx += frac_g * (dxc < (real)0 ? -F : F);
       }
@@ -571,13 +573,13 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
     if (own) {
       // Langevin force with the half-step velocity, noise keyed by (seed, time level n)
       const long long step = b.ctrl->step;
-      unsigned c[4] = {(unsigned)i, (unsigned)step, (unsigned)((unsigned long long)step >> 32),
-                       (unsigned)(2 * s.replica)};
+      const unsigned ia = (unsigned)(i - B.mol0 * NA);  // atom index within its replica
+      unsigned c[4] = {ia, (unsigned)step, (unsigned)((unsigned long long)step >> 32), (unsigned)(2 * B.replica)};
       philox4x32_10(c, s.seed_lo, s.seed_hi);
       const double vx = vo[0], vy = vo[1], vz = vo[2];
       if (P::fp64) {
-        unsigned lo[4] = {(unsigned)i, (unsigned)step, (unsigned)((unsigned long long)step >> 32),
-                          (unsigned)(2 * s.replica + 1)};
+        unsigned lo[4] = {ia, (unsigned)step, (unsigned)((unsigned long long)step >> 32),
+                          (unsigned)(2 * B.replica + 1)};
         philox4x32_10(lo, s.seed_lo, s.seed_hi);
         const double k53 = 1.0 / 9007199254740992.0, amp = s.amp[g], gm = s.gm[g];
         const double u0 = (double)(((unsigned long long)c[0] << 21) | (lo[0] >> 11)) * k53;
@@ -612,16 +614,16 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
         const double nvx = fma(h2, fdx, vx), nvy = fma(h2, fdy, vy), nvz = fma(h2, fdz, vz);
         double y0 = fma(s.dt, nvx, xo[0]), y1 = fma(s.dt, nvy, xo[1]), y2 = fma(s.dt, nvz, xo[2]);
         if (P::fp64) {
-          if (y0 < 0.0) y0 += s.L[0];
-          if (y0 >= s.L[0]) y0 -= s.L[0];
-          if (y1 < 0.0) y1 += s.L[1];
-          if (y1 >= s.L[1]) y1 -= s.L[1];
-          if (y2 < 0.0) y2 += s.L[2];
-          if (y2 >= s.L[2]) y2 -= s.L[2];
+          if (y0 < 0.0) y0 += B.L[0];
+          if (y0 >= B.L[0]) y0 -= B.L[0];
+          if (y1 < 0.0) y1 += B.L[1];
+          if (y1 >= B.L[1]) y1 -= B.L[1];
+          if (y2 < 0.0) y2 += B.L[2];
+          if (y2 >= B.L[2]) y2 -= B.L[2];
         } else {
-          y0 = wrap_bits(y0, s.L[0], s.Lbits[0]);
-          y1 = wrap_bits(y1, s.L[1], s.Lbits[1]);
-          y2 = wrap_bits(y2, s.L[2], s.Lbits[2]);
+          y0 = wrap_bits(y0, B.L[0], B.Lbits[0]);
+          y1 = wrap_bits(y1, B.L[1], B.Lbits[1]);
+          y2 = wrap_bits(y2, B.L[2], B.Lbits[2]);
         }
         b.v[i] = nvx;
         b.v[N + i] = nvy;
@@ -643,8 +645,8 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
       }
       float ext2 = 0.f, disp2 = 0.f;
       const int nxt = cur ^ 1;
-      if (P::fp64) map_group64<NA>(s, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
-      else map_group32<NA>(s, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
+      if (P::fp64) map_group64<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
+      else map_group32<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
       publish_extent(b, ext2, disp2);
     }
   }
@@ -671,9 +673,14 @@ __global__ void __launch_bounds__(kForceBlock) k_step(Sys s, Bufs b) {
 
 template <class P, int NA>
 static void launch_prologue_na(const Sys& s, const Bufs& b, int integrate, cudaStream_t st, DecideArgs da) {
-  const int blocks = ceil_div((long long)s.M * kGroup, kForceBlock);
-  if (integrate) k_prologue<P, NA, true><<<blocks, kForceBlock, 0, st>>>(s, b);
-  else k_prologue<P, NA, false><<<blocks, kForceBlock, 0, st>>>(s, b);
+  const int blocks = ceil_div((long long)s.M * kGroup, s.force_block);
+  if (s.nbox > 1) {
+    if (integrate) k_prologue<P, NA, true, true><<<blocks, s.force_block, 0, st>>>(s, b);
+    else k_prologue<P, NA, false, true><<<blocks, s.force_block, 0, st>>>(s, b);
+  } else {
+    if (integrate) k_prologue<P, NA, true, false><<<blocks, s.force_block, 0, st>>>(s, b);
+    else k_prologue<P, NA, false, false><<<blocks, s.force_block, 0, st>>>(s, b);
+  }
 }
 
 template <class P>
@@ -695,14 +702,26 @@ cudaError_t launch_com(const Sys& s, const Bufs& b, int precision, int integrate
 
 template <class P, int NA>
 static void launch_step_na(const Sys& s, const Bufs& b, int mode, int energy, cudaStream_t st, DecideArgs da) {
-  const int blocks = ceil_div((long long)s.M * kGroup, kForceBlock);
+  const int blocks = ceil_div((long long)s.M * kGroup, s.force_block);
+  const bool multi = s.nbox > 1;
   switch (mode) {
     case MODE_FORCES:
-      if (energy) k_step<P, NA, MODE_FORCES, true><<<blocks, kForceBlock, 0, st>>>(s, b);
-      else k_step<P, NA, MODE_FORCES, false><<<blocks, kForceBlock, 0, st>>>(s, b);
+      if (multi) {
+        if (energy) k_step<P, NA, MODE_FORCES, true, true><<<blocks, s.force_block, 0, st>>>(s, b);
+        else k_step<P, NA, MODE_FORCES, false, true><<<blocks, s.force_block, 0, st>>>(s, b);
+      } else {
+        if (energy) k_step<P, NA, MODE_FORCES, true, false><<<blocks, s.force_block, 0, st>>>(s, b);
+        else k_step<P, NA, MODE_FORCES, false, false><<<blocks, s.force_block, 0, st>>>(s, b);
+      }
       break;
-    case MODE_LAST: k_step<P, NA, MODE_LAST, false><<<blocks, kForceBlock, 0, st>>>(s, b); break;
-    default: k_step<P, NA, MODE_FUSED, false><<<blocks, kForceBlock, 0, st>>>(s, b); break;
+    case MODE_LAST:
+      if (multi) k_step<P, NA, MODE_LAST, false, true><<<blocks, s.force_block, 0, st>>>(s, b);
+      else k_step<P, NA, MODE_LAST, false, false><<<blocks, s.force_block, 0, st>>>(s, b);
+      break;
+    default:
+      if (multi) k_step<P, NA, MODE_FUSED, false, true><<<blocks, s.force_block, 0, st>>>(s, b);
+      else k_step<P, NA, MODE_FUSED, false, false><<<blocks, s.force_block, 0, st>>>(s, b);
+      break;
   }
 }
 

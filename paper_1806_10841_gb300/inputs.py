@@ -250,3 +250,32 @@ def scaled_c2(M: int, **kw) -> System:
     Ly = (M / 0.1 / 2.0) ** (1.0 / 3.0)
     Lx = 2 * Ly
     return tetra_system(M, (Lx, Ly, Ly), 0.2 * Lx, 0.05 * Lx, **kw)
+
+
+def replica_batch(n: int = 64, *, m_lo: int = 500, m_hi: int = 20000, seed: int = 20180628, **kw):
+    """Independent replicas of the tetrahedral fluid: M_r = exp(U(ln m_lo, ln m_hi)) molecules
+    in a (2a, a, a) box with a = (M_r / 0.2)^(1/3) (density 0.1), full AT width U(3, 15) and
+    hybrid width U(1, 5).  The replicas share every model parameter (including the
+    thermostat seed and a common thermodynamic-force grid); initial states come from
+    replica_states with seed + r."""
+    rng = np.random.default_rng(seed)
+    ms = np.exp(rng.uniform(math.log(m_lo), math.log(m_hi), n)).astype(int)
+    at = rng.uniform(3.0, 15.0, n)
+    hy = rng.uniform(1.0, 5.0, n)
+    tf_dx = kw.get("tf_dx", 0.5)
+    bins = int(math.ceil(max(0.5 * a + h for a, h in zip(at, hy)) / tf_dx)) + 2
+    out = []
+    for M, w_at, w_hy in zip(ms, at, hy):
+        a = (M / 0.2) ** (1.0 / 3.0)
+        out.append(tetra_system(int(M), (2 * a, a, a), float(w_at), float(w_hy), tf_bins=bins, seed=seed, **kw))
+    return out
+
+
+def replica_states(systems, seed: int = 20180628):
+    """Initial (x, v) of each replica (tetra_state with seed + r), concatenated in order."""
+    xs, vs = [], []
+    for r, s in enumerate(systems):
+        x, v = tetra_state(s, seed=seed + r)
+        xs.append(x)
+        vs.append(v)
+    return np.concatenate(xs), np.concatenate(vs)

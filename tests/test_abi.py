@@ -57,6 +57,33 @@ def test_init_rejects_bad_config_without_touching_the_gpu(lib):
     assert not h.value
 
 
+def test_batch_init_rejects_replicas_that_differ_in_shared_parameters(lib):
+    """Replicas of a batch may differ in size, box, slab and replica id only; validation
+    happens on the host before any device call."""
+    from paper_1806_10841_gb300 import adress, inputs
+
+    L = adress.load_library()
+    keep = []
+    a = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, tf_bins=20)
+    b = inputs.tetra_system(300, (30.0, 15.0, 15.0), 3.0, 1.0, tf_bins=20)
+    bad = inputs.tetra_system(300, (30.0, 15.0, 15.0), 3.0, 1.0, tf_bins=20, gamma=1.0)
+    h = ctypes.c_void_p()
+    cfgs = (adress.adress_config * 2)(adress._config(a, keep, 0, 0, "fp32"), adress._config(bad, keep, 1, 0, "fp32"))
+    assert L.adress_init_batch(cfgs, 2, None, ctypes.byref(h)) == 1
+    assert b"replica 1" in L.adress_last_error(None) and b"thermostat" in L.adress_last_error(None)
+    assert not h.value
+    c = inputs.tetra_system(300, (30.0, 15.0, 15.0), 3.0, 1.0, tf_bins=21)
+    cfgs = (adress.adress_config * 2)(adress._config(a, keep, 0, 0, "fp32"), adress._config(c, keep, 1, 0, "fp32"))
+    assert L.adress_init_batch(cfgs, 2, None, ctypes.byref(h)) == 1
+    assert b"thermodynamic-force grid" in L.adress_last_error(None)
+    cfgs = (adress.adress_config * 2)(adress._config(a, keep, 0, 0, "fp32"), adress._config(b, keep, 1, 0, "fp32"))
+    assert L.adress_init_batch(cfgs, 0, None, ctypes.byref(h)) == 1
+    small = inputs.tetra_system(8, (4.0, 4.0, 4.0), 1.0, 1.0, tf_bins=20)
+    cfgs = (adress.adress_config * 2)(adress._config(a, keep, 0, 0, "fp32"), adress._config(small, keep, 1, 0, "fp32"))
+    assert L.adress_init_batch(cfgs, 2, None, ctypes.byref(h)) == 1 and not h.value
+    assert b"replica 1: box edge shorter" in L.adress_last_error(None)
+
+
 def test_oracle_and_cuda_path_share_no_code():
     """Neither side imports or includes the other (only the input generator is shared)."""
     pkg = os.path.join(ROOT, "paper_1806_10841_gb300")
