@@ -32,6 +32,7 @@ MD_PER_BLOCK = 100
 SAMPLE_EVERY = 10
 TF_ALPHA = 0.5
 METRIC = "AdResS atom-steps/s"
+RDF_BINS, RDF_DR, RDF_EQ, RDF_SNAPS, RDF_EVERY = 250, 0.02, 500, 5, 100
 CONFIG_NAME = "tetrahedral AdResS fluid, 200k molecules / 800k atoms, 200x100x100 sigma, AT 40 + 2x10 hybrid"
 
 
@@ -222,6 +223,18 @@ def learned_arm(s, x0, v0, make, timed, steps):
         at.step(100)
         n = at.mlp_collect(cap=1_000_000)
     feat, t, _ = at.mlp_samples(n)
+    nb, dr = RDF_BINS, RDF_DR
+
+    def rdf_of(sim, eq):
+        sim.step(eq)
+        c = np.zeros(nb, dtype=np.int64)
+        for _ in range(RDF_SNAPS):
+            sim.step(RDF_EVERY)
+            c += sim.rdf_counts(nb, dr)[0]
+        sim.check()
+        return adress.AdResS.rdf_normalise(c, s.M, float(np.prod(s.box)), dr, RDF_SNAPS)
+
+    g_at = rdf_of(at, RDF_EQ - 300)
     at.close()
     rng = np.random.default_rng(20180628)
     idx = rng.permutation(n)
@@ -248,12 +261,26 @@ def learned_arm(s, x0, v0, make, timed, steps):
     sim.compute_forces(energies=False)
     tot, _, _ = timed(sim, steps, 2)
     value = s.N * MD_PER_BLOCK * steps / tot
+    # structure: COM g(r) of the learned run, the tabulated run and the all-atomistic run,
+    # each from the initial state after RDF_EQ steps, over RDF_SNAPS snapshots
+    sim.set_state(x0, v0)
+    sim.compute_forces(energies=False)
+    g_net = rdf_of(sim, RDF_EQ)
     sim.close()
+    tab = make("fp32")
+    g_tab = rdf_of(tab, RDF_EQ)
+    tab.close()
+    l2 = lambda a, b: float(math.sqrt(((a - b) ** 2).sum() * dr))
     return {"value": value, "unit": "atom-steps/s", "training_samples": int(ntr), "held_out": int(n - ntr),
             "epoch_loss": [float(v) for v in losses], "train_s": t_train, "prep_s": prep_s,
             "held_out_force_rms": {"target": rms(t[te]), "network_error": rms(pred - t[te]),
                                    "table_error": rms(table - t[te])},
-            "source": "pairs with COM distance < rc_cg from 3 snapshots of an all-atomistic FP64 run"}
+            "source": "pairs with COM distance < rc_cg from 3 snapshots of an all-atomistic FP64 run",
+            "rdf_l2": {"network_vs_table": l2(g_net, g_tab), "network_vs_all_atomistic": l2(g_net, g_at),
+                       "table_vs_all_atomistic": l2(g_tab, g_at),
+                       "recipe": f"COM g(r) 0..{nb * dr:g} sigma, dr {dr}, {RDF_SNAPS} snapshots every "
+                                 f"{RDF_EVERY} steps after {RDF_EQ} steps from the initial state; "
+                                 "L2 = sqrt(sum (g1 - g2)^2 dr)"}}
 
 
 def replicas_arm(timed, steps, local):

@@ -161,6 +161,15 @@ adress_status adress_step(adress_handle h, int32_t nsteps);
 adress_status adress_run(adress_handle h, int32_t nsteps, int32_t sample_every, int32_t tf_update,
                          double alpha);
 
+/* Radial distribution function numerator of the bound positions: counts (host int64
+ * [n_replicas][nbins]) = number of molecule pairs a < b (of the same replica) whose
+ * minimum-image centre-of-mass distance r (centres in FP64 as adress_com_lambda computes
+ * them) has floor(r / dr) = k < nbins.  All pairs, decided in FP64.  g(r) of bin k is
+ * counts_k / (n_samples (M(M-1)/2) (4/3 pi ((k+1)^3 - k^3) dr^3) / V).  The CG model is
+ * judged by g(r) (structure) next to forces.  Requires nbins dr <= half of every box edge,
+ * nbins <= 4096.  Synchronises. */
+adress_status adress_rdf(adress_handle h, int32_t nbins, double dr, int64_t* counts);
+
 /* ---- learned coarse-grained force (force matching) ------------------------------------
  * The CG force of Eq. 1 acts between centres of mass (Sec. "Force interpolation"); the
  * learned variant is a 9 -> 64 -> 64 -> 1 SiLU network of the COM distance d and eight

@@ -94,6 +94,7 @@ def _load(path: str | None = None):
     lib.orc_kinetic.argtypes = [S, d, d]
     lib.orc_density.argtypes = [S, d, C.c_int, i64, C.c_int, i64]
     lib.orc_tf_update.argtypes = [S, d, C.c_int, i64, C.c_int, C.c_double, C.c_double]
+    lib.orc_rdf.argtypes = [S, d, C.c_int, C.c_double, i64]
     lib.orc_bf16.argtypes = [C.c_double]
     lib.orc_bf16.restype = C.c_double
     lib.orc_pair_features.argtypes = [S, d, C.c_int, C.c_int, d, d]
@@ -205,6 +206,13 @@ class Oracle:
         cx = np.zeros(nx, dtype=np.int64)
         self.lib.orc_density(C.byref(self.sys), _ptr(x), nd, _ptr(cd, C.c_int64), nx, _ptr(cx, C.c_int64))
         return cd, cx
+
+    def rdf_counts(self, x, nbins: int, dr: float):
+        """Pair counts of COM distances in bins [k dr, (k+1) dr), all pairs a < b."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        c = np.zeros(nbins, dtype=np.int64)
+        self.lib.orc_rdf(C.byref(self.sys), _ptr(x), int(nbins), float(dr), _ptr(c, C.c_int64))
+        return c
 
     def pair_features(self, x, a: int, b: int):
         x = np.ascontiguousarray(x, dtype=np.float64)

@@ -406,6 +406,26 @@ void orc_density(const orc_sys* s, const double* x, int nd, int64_t* counts_d, i
   free(R); free(dxc);
 }
 
+/* COM pair-distance histogram (the numerator of the radial distribution function g(r),
+ * the structural observable that judges a coarse-grained model): counts[k] += number of
+ * molecule pairs a < b whose minimum-image COM distance r has floor(r / dr) = k < nbins.
+ * All pairs, no lists. */
+void orc_rdf(const orc_sys* s, const double* x, int nbins, double dr, int64_t* counts) {
+  double* R = (double*)malloc(sizeof(double) * 3 * s->M);
+  orc_com_lambda(s, x, R, NULL, NULL);
+  for (int a = 0; a < s->M; ++a)
+    for (int b = a + 1; b < s->M; ++b) {
+      double r2 = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        double t = minimg(R[3 * a + d] - R[3 * b + d], s->L[d]);
+        r2 += t * t;
+      }
+      int k = (int)floor(sqrt(r2) / dr);
+      if (k < nbins) counts[k] += 1;
+    }
+  free(R);
+}
+
 /* Thermodynamic-force iteration: tf_k <- tf_k - alpha * g_k for hybrid-layer nodes,
  * where rho_k = counts_d[k] / (nsamples * 2 tf_dx Ly Lz) is the folded COM density in
  * bin [k dx, (k+1) dx), g_k = (rho_k - rho_{k-1}) / dx is its gradient at node d_k

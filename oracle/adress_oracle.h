@@ -54,6 +54,7 @@ void orc_density(const orc_sys* s, const double* x, int nd, int64_t* counts_d, i
                  int64_t* counts_x);
 void orc_tf_update(const orc_sys* s, double* tf, int n, const int64_t* counts_d, int nd,
                    double nsamples, double alpha);
+void orc_rdf(const orc_sys* s, const double* x, int nbins, double dr, int64_t* counts);
 
 double orc_bf16(double v);
 void orc_pair_features(const orc_sys* s, const double* x, int a, int b, double* feat, double* target);

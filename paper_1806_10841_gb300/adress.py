@@ -20,7 +20,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "neighbour list ov
           7: "invalid state", 8: "molecule wider than the list cutoff allows"}
 
 # Every symbol include/adress.h declares (checked by the CPU test suite).
-EXPORTS = ["adress_init", "adress_init_batch", "adress_set_tuning", "adress_get_tuning", "adress_autotune",
+EXPORTS = ["adress_init", "adress_init_batch", "adress_rdf", "adress_set_tuning", "adress_get_tuning", "adress_autotune",
            "adress_bind_state", "adress_build_lists", "adress_compute_forces",
            "adress_step", "adress_run", "adress_set_step", "adress_get_step", "adress_com_lambda", "adress_kinetic",
            "adress_density_accumulate", "adress_density_get", "adress_density_reset",
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "adress_init": ([C.POINTER(adress_config), vp, C.POINTER(H)], C.c_int),
         "adress_init_batch": ([C.POINTER(adress_config), C.c_int32, vp, C.POINTER(H)], C.c_int),
         "adress_set_tuning": ([H, C.c_int32, C.c_double], C.c_int),
+        "adress_rdf": ([H, C.c_int32, C.c_double, i64p], C.c_int),
         "adress_get_tuning": ([H, C.POINTER(C.c_int32), d], C.c_int),
         "adress_autotune": ([H, C.c_int32, d, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
         "adress_bind_state": ([H, vp, vp, vp], C.c_int),
@@ -278,6 +279,21 @@ class AdResS:
         out = np.zeros(4)
         self._call("adress_kinetic", _dptr(out))
         return out[0], out[1:].copy()
+
+    def rdf_counts(self, nbins: int = 250, dr: float = 0.02):
+        """COM pair-distance histogram [n_replicas, nbins] of the current positions."""
+        c = np.zeros(self.n_replicas * int(nbins), dtype=np.int64)
+        self._call("adress_rdf", C.c_int32(int(nbins)), C.c_double(float(dr)), c.ctypes.data_as(C.POINTER(C.c_int64)))
+        return c.reshape(self.n_replicas, int(nbins))
+
+    @staticmethod
+    def rdf_normalise(counts, n_mols: int, volume: float, dr: float, n_samples: int = 1):
+        """g(r) per bin from pair counts summed over n_samples snapshots: counts divided by
+        the ideal-gas pair count of the bin's shell."""
+        k = np.arange(len(counts), dtype=np.float64)
+        shell = 4.0 / 3.0 * np.pi * ((k + 1) ** 3 - k ** 3) * dr ** 3
+        ideal = n_samples * 0.5 * n_mols * (n_mols - 1) * shell / volume
+        return np.asarray(counts, dtype=np.float64) / ideal
 
     def density_accumulate(self):
         self._call("adress_density_accumulate")

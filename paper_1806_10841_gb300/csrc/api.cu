@@ -55,6 +55,10 @@ struct adress_ctx {
   int* rank_cell = nullptr;
   int ncell_cap = 0;
   double skin0 = 0.0;  // skin of the configuration (the autotuner scales it)
+  // radial distribution function scratch
+  double* rdf_com = nullptr;
+  unsigned long long* rdf_counts = nullptr;
+  size_t rdf_cap = 0;
   MlpDevArgs mlp_args() const { return MlpDevArgs{mlp_P, mlp_W1p, mlp_W2p, mlp_W2Tp, mlp_norm}; }
 };
 
@@ -398,6 +402,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
     Box& B = h->boxes[k];
     B = make_box(&cfgs[k], c->skin);
     B.mol0 = mol0;
+    B.nmol = cfgs[k].n_mols;
     B.index = k;
     B.tf0 = k * s.tf_n;
     nmol[k] = cfgs[k].n_mols;
@@ -808,6 +813,28 @@ adress_status adress_com_lambda(adress_handle h, double* com, double* w) {
   if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
   CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream, DecideArgs{0, 0, 0, 0}));
   CUDA_OR_FAIL(h, launch_export_com(h->sys, h->buf, h->precision, com, w, h->stream));
+  return ADRESS_OK;
+}
+
+adress_status adress_rdf(adress_handle h, int32_t nbins, double dr, int64_t* counts) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
+  if (!counts || nbins < 1 || nbins > 4096 || !(dr > 0)) return fail(h, ADRESS_ERR_ARG, "need counts, 1 <= nbins <= 4096, dr > 0");
+  for (const Box& B : h->boxes)
+    for (int d = 0; d < 3; ++d)
+      if (nbins * dr > B.halfL[d]) return fail(h, ADRESS_ERR_ARG, "nbins * dr exceeds half a box edge");
+  const Sys& s = h->sys;
+  if (!h->rdf_com) CUDA_OR_FAIL(h, dalloc(h, &h->rdf_com, (size_t)3 * s.M));
+  const size_t n = (size_t)s.nbox * nbins;
+  if (h->rdf_cap < n) {
+    CUDA_OR_FAIL(h, realloc_owned(h, &h->rdf_counts, n));
+    h->rdf_cap = n;
+  }
+  CUDA_OR_FAIL(h, cudaMemsetAsync(h->rdf_counts, 0, sizeof(unsigned long long) * n, h->stream));
+  CUDA_OR_FAIL(h, launch_export_com(s, h->buf, h->precision, h->rdf_com, nullptr, h->stream));
+  CUDA_OR_FAIL(h, launch_rdf(s, h->buf, h->rdf_com, nbins, dr, h->rdf_counts, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(counts, h->rdf_counts, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
   return ADRESS_OK;
 }
 

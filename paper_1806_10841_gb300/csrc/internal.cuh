@@ -52,6 +52,7 @@ struct Box {
   int ncell;   // cells of this box
   int cell0;   // first global cell index (and Morton rank) of this box
   int mol0;    // first molecule of this box
+  int nmol;    // molecules of this box
   int index;   // position of this box in the batch
   int tf0;     // first entry of this box's thermodynamic-force table and density histogram
   long long replica;  // replica id (thermostat noise counter)
@@ -209,6 +210,9 @@ cudaError_t launch_kinetic(const Sys& s, const Bufs& b, cudaStream_t st);
 cudaError_t launch_density(const Sys& s, const Bufs& b, int precision, cudaStream_t st);
 cudaError_t launch_tf_update(const Sys& s, const Bufs& b, double alpha, cudaStream_t st);
 cudaError_t launch_export_com(const Sys& s, const Bufs& b, int precision, double* com, double* w, cudaStream_t st);
+// COM pair-distance histogram of the centres com [3][M] into counts [nbox][nbins] (added).
+cudaError_t launch_rdf(const Sys& s, const Bufs& b, const double* com, int nbins, double dr,
+                       unsigned long long* counts, cudaStream_t st);
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 

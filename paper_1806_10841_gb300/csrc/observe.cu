@@ -198,8 +198,84 @@ __global__ void k_export_com(const __grid_constant__ Sys s, Bufs b, double* com,
     if (r >= B.L[d]) r -= B.L[d];
     com[(size_t)d * s.M + a] = r;
   }
-  const int cur = b.ctrl->parity;
-  w[a] = s.fp64 ? b.com64[cur][a].w : (double)__int_as_float(b.com_fx[cur][a].w);
+  if (w) {
+    const int cur = b.ctrl->parity;
+    w[a] = s.fp64 ? b.com64[cur][a].w : (double)__int_as_float(b.com_fx[cur][a].w);
+  }
+}
+
+// COM pair-distance histogram (numerator of the radial distribution function): every pair
+// a < b of the same box with minimum-image distance r < nbins dr adds one to bin
+// floor(r / dr) of its box.  All pairs, tiled: a block owns 256 molecules a and streams the
+// molecules b >= its first one (up to the end of the last box it touches) through shared
+// memory.  A float test with a margin discards the distant pairs; the rest are decided in
+// double with explicitly rounded products and sums (no contraction), the operations the
+// oracle performs, so bins are the oracle's.  One box counts into shared memory first.
+constexpr int kRdfTile = 256;
+__global__ void __launch_bounds__(kRdfTile) k_rdf(const __grid_constant__ Sys s, Bufs b, const double* __restrict__ com,
+                                                  int nbins, double dr, float lim2, unsigned long long* counts) {
+  extern __shared__ unsigned rh[];
+  __shared__ double sx[kRdfTile], sy[kRdfTile], sz[kRdfTile];
+  __shared__ float fx[kRdfTile], fy[kRdfTile], fz[kRdfTile];
+  __shared__ int sbox[kRdfTile];
+  const bool multi = s.nbox > 1;
+  const int M = s.M;
+  if (!multi)
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) rh[k] = 0u;
+  const int i0 = blockIdx.x * kRdfTile;
+  const int a = i0 + threadIdx.x;
+  const bool live = a < M;
+  const int ac = live ? a : M - 1;
+  const Box& B = box_of(s, b, ac);
+  const int mybox = multi ? b.mol_box[ac] : 0;
+  int jend = M;
+  if (multi) {
+    const Box& BL = b.boxes[b.mol_box[min(i0 + kRdfTile, M) - 1]];
+    jend = BL.mol0 + BL.nmol;
+  }
+  const double xa = com[ac], ya = com[(size_t)M + ac], za = com[2 * (size_t)M + ac];
+  const float xaf = (float)xa, yaf = (float)ya, zaf = (float)za;
+  const float Lx = (float)B.L[0], Ly = (float)B.L[1], Lz = (float)B.L[2];
+  const float hx = 0.5f * Lx, hy = 0.5f * Ly, hz = 0.5f * Lz;
+  for (int j0 = i0; j0 < jend; j0 += kRdfTile) {
+    __syncthreads();
+    const int j = j0 + threadIdx.x;
+    if (j < jend) {
+      const double X = com[j], Y = com[(size_t)M + j], Z = com[2 * (size_t)M + j];
+      sx[threadIdx.x] = X;
+      sy[threadIdx.x] = Y;
+      sz[threadIdx.x] = Z;
+      fx[threadIdx.x] = (float)X;
+      fy[threadIdx.x] = (float)Y;
+      fz[threadIdx.x] = (float)Z;
+      sbox[threadIdx.x] = multi ? b.mol_box[j] : 0;
+    }
+    __syncthreads();
+    if (!live) continue;
+    const int n = min(kRdfTile, jend - j0);
+    for (int q = max(0, a + 1 - j0); q < n; ++q) {
+      float dx = xaf - fx[q], dy = yaf - fy[q], dz = zaf - fz[q];
+      dx = dx > hx ? dx - Lx : (dx < -hx ? dx + Lx : dx);
+      dy = dy > hy ? dy - Ly : (dy < -hy ? dy + Ly : dy);
+      dz = dz > hz ? dz - Lz : (dz < -hz ? dz + Lz : dz);
+      if (dx * dx + dy * dy + dz * dz >= lim2) continue;
+      if (multi && sbox[q] != mybox) continue;
+      const double ex = minimg_cmp(xa - sx[q], B.L[0], B.halfL[0]);
+      const double ey = minimg_cmp(ya - sy[q], B.L[1], B.halfL[1]);
+      const double ez = minimg_cmp(za - sz[q], B.L[2], B.halfL[2]);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+      const int k = (int)floor(sqrt(r2) / dr);
+      if (k < nbins) {
+        if (multi) atomicAdd(&counts[(size_t)mybox * nbins + k], 1ull);
+        else atomicAdd(&rh[k], 1u);
+      }
+    }
+  }
+  if (!multi) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+      if (rh[k]) atomicAdd(&counts[k], (unsigned long long)rh[k]);
+  }
 }
 
 // ---- launchers -----------------------------------------------------------------------
@@ -241,6 +317,15 @@ cudaError_t launch_tf_update(const Sys& s, const Bufs& b, double alpha, cudaStre
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_clear_samples<<<1, 1, 0, st>>>(b.nsamples);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rdf(const Sys& s, const Bufs& b, const double* com, int nbins, double dr,
+                       unsigned long long* counts, cudaStream_t st) {
+  const double rmax = nbins * dr;
+  const float lim2 = (float)((rmax + 1e-3 * (1.0 + rmax)) * (rmax + 1e-3 * (1.0 + rmax)));
+  const size_t smem = s.nbox > 1 ? 0 : sizeof(unsigned) * nbins;
+  k_rdf<<<ceil_div(s.M, kRdfTile), kRdfTile, smem, st>>>(s, b, com, nbins, dr, lim2, counts);
   return cudaGetLastError();
 }
 

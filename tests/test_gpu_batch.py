@@ -140,6 +140,17 @@ def test_batch_density_histograms_and_tf_update_per_replica(precision):
     sim.close()
 
 
+def test_batch_rdf_counts_per_replica_bit_exact():
+    systems, x, v = batch_case()
+    sim = sim_of(systems, "fp32")
+    sim.set_state(x)
+    c = sim.rdf_counts(150, 0.02)
+    xs = split(x, sim)
+    for r, s in enumerate(systems):
+        assert np.array_equal(c[r], oracle.Oracle(s, replica=r).rdf_counts(xs[r], 150, 0.02)), r
+    sim.close()
+
+
 def test_batch_run_block_with_tf_iteration_matches_single_handles():
     """adress_run over the batch (density samples + one TF update) gives each replica the
     thermodynamic-force table its own single-system handle gets."""

@@ -194,3 +194,59 @@ def test_trained_network_beats_the_table_on_held_out_atomistic_forces():
     assert err_net < 0.5 * err_tab
     assert err_net < ref
     sim.close()
+
+
+def test_learned_cg_run_reproduces_the_atomistic_rdf_better_than_the_table():
+    """Structure (COM g(r), 0..5 sigma): an all-CG run with the trained network is closer to
+    the all-atomistic run than an all-CG run with the tabulated potential (L2 of g over r,
+    reading of the RDF criterion: sqrt(sum (g1 - g2)^2 dr))."""
+    import copy
+
+    from paper_1806_10841_gb300 import adress
+
+    s, x, v = system_samples(M=4000, seed=31)  # all atomistic
+    nb, dr = 250, 0.02
+    vol = float(np.prod(s.box))
+
+    def rdf_run(sim, n_eq=300, snaps=6, every=100):
+        sim.set_state(x, v)
+        sim.compute_forces(energies=False)
+        sim.step(n_eq)
+        c = np.zeros(nb, dtype=np.int64)
+        for _ in range(snaps):
+            sim.step(every)
+            c += sim.rdf_counts(nb, dr)[0]
+        sim.check()
+        return adress.AdResS.rdf_normalise(c, s.M, vol, dr, snaps)
+
+    at = adress.AdResS(s, precision="fp32")
+    g_at = rdf_run(at)
+    at.set_state(x, v)
+    at.compute_forces(energies=False)
+    total = 0
+    for _ in range(4):
+        at.step(200)
+        total = at.mlp_collect(cap=400_000)
+    feat, t, _ = at.mlp_samples(total)
+    at.close()
+    s_cg = copy.copy(s)
+    s_cg.d_at, s_cg.d_hy = 0.0, 0.0  # every molecule coarse-grained
+    table = adress.AdResS(s_cg, precision="fp32")
+    g_tab = rdf_run(table)
+    table.close()
+    net = adress.AdResS(s_cg, precision="fp32")
+    mean, std = feat.mean(0), feat.std(0) + 1e-3
+    scale = float(t.std())
+    rng = np.random.default_rng(12)
+    params = dict(W1=rng.normal(0, 1 / 3, (64, 9)), b1=np.zeros(64), W2=rng.normal(0, 1 / 8, (64, 64)),
+                  b2=np.zeros(64), w3=rng.normal(0, 1 / 8, 64), b3=float(t.mean() / scale))
+    net.mlp_set(params, mean, std, scale)
+    net.mlp_load_samples(feat, t)
+    net.mlp_train(epochs=30, batch=1024, lr=2e-3)
+    net.set_cg_mode(1)
+    g_net = rdf_run(net)
+    net.close()
+    l2 = lambda a, b: math.sqrt(((a - b) ** 2).sum() * dr)
+    e_net, e_tab = l2(g_net, g_at), l2(g_tab, g_at)
+    print(f"RDF L2 vs all-atomistic: network {e_net:.4f}, table {e_tab:.4f}")
+    assert e_net < e_tab

@@ -253,6 +253,26 @@ def test_density_histogram_bit_exact_and_tf_update(precision):
     assert ns == 0 and not counts.any()
 
 
+# ---- radial distribution function -------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_rdf_counts_bit_exact(precision):
+    """COM pair-distance histogram (0..5 sigma, 0.02 bins) equals the oracle's all-pairs
+    count on 80k atoms; bins are decided in FP64 on both sides."""
+    s, x, v, f, e = case("scaled_20k")
+    sim = gpu(s, precision)
+    sim.set_state(x)
+    c = sim.rdf_counts(250, 0.02)[0]
+    ref = oracle.Oracle(s).rdf_counts(x, 250, 0.02)
+    assert np.array_equal(c, ref)
+    assert ref.sum() > 100_000
+    from paper_1806_10841_gb300 import adress
+
+    with pytest.raises(adress.AdressError):
+        sim.rdf_counts(5000, 0.02)  # beyond half the box
+    sim.close()
+
+
 # ---- host-visible error paths (no GPU fault: device flags read back by the host) ----------
 
 def test_list_capacity_grows_automatically():
