@@ -347,6 +347,8 @@ def main():
     ap.add_argument("--no-replicas", action="store_true", help="skip the 64-replica batch arm")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up, run this many MD steps, exit (no timing output)")
+    ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1],
+                    help="for --profile: 1 = learned CG force (untrained network of the production shape)")
     ap.add_argument("--molecules", type=int, default=200_000,
                     help="system size for --profile (same density, shape and slab proportions)")
     args = ap.parse_args()
@@ -374,6 +376,14 @@ def main():
         x0, v0 = inputs.tetra_state(s)
         sim = adress.AdResS(s, precision=args.precision, device=f"cuda:{local}")
         sim.set_state(x0, v0)
+        if args.cg_mode:
+            # an untrained network of the production shape: the kernels' cost does not
+            # depend on the weights
+            rng = np.random.default_rng(1)
+            params = dict(W1=rng.normal(0, 1 / 3, (64, 9)), b1=np.zeros(64), W2=rng.normal(0, 1 / 8, (64, 64)),
+                          b2=np.zeros(64), w3=rng.normal(0, 1 / 8, 64), b3=0.0)
+            sim.mlp_set(params, np.r_[1.9, np.zeros(8)], np.full(9, 0.3), 5.0)
+            sim.set_cg_mode(1)
         sim.compute_forces(energies=False)
         sim.run(args.profile, sample_every=SAMPLE_EVERY, tf_update=True, alpha=TF_ALPHA)
         sim.check()

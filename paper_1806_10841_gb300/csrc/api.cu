@@ -105,6 +105,19 @@ static cudaError_t realloc_owned(adress_ctx* h, T** p, size_t n) {
   return dalloc(h, p, n);
 }
 
+// Pair buffers of the network CG force: every unordered listed pair at most once
+// (sum of list lengths / 2 <= M cap / 2).
+static cudaError_t alloc_pair_buffers(adress_ctx* h) {
+  Bufs& b = h->buf;
+  const long long pcap = (long long)h->sys.M * h->sys.cap / 2 + 32;
+  cudaError_t e = realloc_owned(h, &b.pfeat, (size_t)pcap * 9);
+  if (e == cudaSuccess) e = realloc_owned(h, &b.pslot, (size_t)pcap);
+  if (e == cudaSuccess) e = realloc_owned(h, &b.mirror, (size_t)h->sys.M * h->sys.cap);
+  if (e == cudaSuccess && !b.npair) e = dalloc(h, &b.npair, 1);
+  if (e == cudaSuccess) b.pcap = pcap;
+  return e;
+}
+
 static void free_graphs(adress_ctx* h) {
   for (auto& kv : h->graphs) {
     if (kv.second.second) cudaGraphExecDestroy(kv.second.second);
@@ -588,7 +601,10 @@ static adress_status build_lists_sync(adress_handle h) {
       cudaFree(old);
       h->buf.nbr = nbr;
       h->sys.cap = cap;
-      if (h->buf.fpair) CUDA_OR_FAIL(h, realloc_owned(h, &h->buf.fpair, (size_t)cap * h->sys.M));
+      if (h->buf.fpair) {
+        CUDA_OR_FAIL(h, realloc_owned(h, &h->buf.fpair, (size_t)cap * h->sys.M));
+        CUDA_OR_FAIL(h, alloc_pair_buffers(h));
+      }
       free_graphs(h);
       int zero = 0;
       CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->buf.ctrl->err, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -1096,7 +1112,7 @@ static adress_status mlp_alloc(adress_handle h) {
   CUDA_OR_FAIL(h, dalloc(h, &h->mlp_W1p, 64 * 8));
   CUDA_OR_FAIL(h, dalloc(h, &h->mlp_W2p, 64 * 32));
   CUDA_OR_FAIL(h, dalloc(h, &h->mlp_W2Tp, 64 * 32));
-  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_norm, kMlpNNorm));
+  CUDA_OR_FAIL(h, dalloc(h, &h->mlp_norm, kMlpNNorm + 9));  // + 1/in_std
   CUDA_OR_FAIL(h, dalloc(h, &h->mlp_mom, kMlpNPar));
   CUDA_OR_FAIL(h, dalloc(h, &h->mlp_vel, kMlpNPar));
   CUDA_OR_FAIL(h, dalloc(h, &h->mlp_grad, kMlpNPar + 1));
@@ -1120,7 +1136,10 @@ adress_status adress_mlp_set(adress_handle h, const float* params, const float* 
   adress_status st = mlp_alloc(h);
   if (st != ADRESS_OK) return st;
   CUDA_OR_FAIL(h, cudaMemcpyAsync(h->mlp_P, params, sizeof(float) * kMlpNPar, cudaMemcpyHostToDevice, h->stream));
-  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->mlp_norm, norm, sizeof(float) * kMlpNNorm, cudaMemcpyHostToDevice, h->stream));
+  float ext[kMlpNNorm + 9];
+  memcpy(ext, norm, sizeof(float) * kMlpNNorm);
+  for (int k = 0; k < 9; ++k) ext[kMlpNNorm + k] = (float)(1.0 / (double)norm[9 + k]);
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->mlp_norm, ext, sizeof(ext), cudaMemcpyHostToDevice, h->stream));
   CUDA_OR_FAIL(h, cudaMemsetAsync(h->mlp_mom, 0, sizeof(float) * kMlpNPar, h->stream));
   CUDA_OR_FAIL(h, cudaMemsetAsync(h->mlp_vel, 0, sizeof(float) * kMlpNPar, h->stream));
   CUDA_OR_FAIL(h, mlp_pack(h->mlp_args(), h->stream));
@@ -1144,10 +1163,15 @@ adress_status adress_set_cg_mode(adress_handle h, int32_t mode) {
   if (mode == 1) {
     if (!h->mlp_ready) return fail(h, ADRESS_ERR_STATE, "set the network parameters first");
     if (h->sys.NA != 4 && h->sys.NA != 3 && h->sys.NA != 2 && h->sys.NA != 1) return ADRESS_ERR_ARG;
-    if (!h->buf.fpair) CUDA_OR_FAIL(h, dalloc(h, &h->buf.fpair, (size_t)h->sys.cap * h->sys.M));
+    if (!h->buf.fpair) {
+      CUDA_OR_FAIL(h, dalloc(h, &h->buf.fpair, (size_t)h->sys.cap * h->sys.M));
+      CUDA_OR_FAIL(h, alloc_pair_buffers(h));
+    }
   }
   if (h->sys.cg_mode != mode) free_graphs(h);
   h->sys.cg_mode = mode;
+  // mirror slots of the lists already built (later builds add them themselves)
+  if (mode == 1 && h->lists_built) CUDA_OR_FAIL(h, launch_mirror(h->sys, h->buf, h->stream));
   return ADRESS_OK;
 }
 

@@ -138,6 +138,11 @@ struct Bufs {
   long long* nsamples;
   Ctrl* ctrl;
   float* fpair;  // [M*cap] network CG pair force per list slot (CG mode 1)
+  float* pfeat;  // [pcap][9] features of the pairs the network evaluates this step
+  int2* pslot;   // [pcap] the pair's two list slots
+  int* mirror;   // [M*cap] (CG mode 1) slot of the same pair in the partner's list, from the last build
+  unsigned* npair;  // pairs written this step
+  long long pcap;
   // batched replicas (nbox > 1)
   const Box* boxes;    // [nbox]
   const int* mol_box;  // [M] box of each molecule
@@ -162,11 +167,21 @@ struct MlpDevArgs {
   const float* norm;
 };
 constexpr int kMlpNPar = 4865;   // 64*9 + 64 + 64*64 + 64 + 64 + 1
-constexpr int kMlpNNorm = 19;    // in_mean[9], in_std[9], out_scale
+constexpr int kMlpNNorm = 19;    // in_mean[9], in_std[9], out_scale (the device copy adds 1/in_std[9])
 constexpr int kMlpGradStride = 4868;
 
 __device__ __forceinline__ void set_error(Ctrl* c, int code, int info = 0) {
   if (atomicCAS(&c->err, 0, code) == 0) c->err_info = info;
+}
+
+// Squared length of a COM separation with explicit roundings: every kernel that tests a
+// pair against a cutoff forms it this way, so the force kernel and the network pair kernel
+// decide alike for pairs on the cutoff.
+__device__ __forceinline__ float pair_r2(float x, float y, float z) {
+  return __fmaf_rn(z, z, __fmaf_rn(y, y, __fmul_rn(x, x)));
+}
+__device__ __forceinline__ double pair_r2(double x, double y, double z) {
+  return __fma_rn(z, z, __fma_rn(y, y, __dmul_rn(x, x)));
 }
 
 // Minimum image for |d| < 1.5 L by comparison (no division).
@@ -198,6 +213,8 @@ cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st);
 // molecule arrays and, in a graph, sets the conditional of the rebuild node.
 cudaError_t launch_decide(const Sys& s, const Bufs& b, DecideArgs da, cudaStream_t st);
 cudaError_t launch_max_nn(const Sys& s, const Bufs& b, cudaStream_t st);
+// Mirror slots of the current lists (Bufs::mirror); launch_rebuild runs it in CG mode 1.
+cudaError_t launch_mirror(const Sys& s, const Bufs& b, cudaStream_t st);
 // out[i] = sum_{j<i} in[j] for i < n, *total = sum of all (n <= 8M)
 cudaError_t device_exclusive_scan(const int* in, int* out, int n, int* tmp, int* total, cudaStream_t st);
 // mode: 0 conservative forces, 1 last step of a run (thermostat + second half kick),

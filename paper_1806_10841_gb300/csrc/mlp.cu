@@ -37,16 +37,65 @@ struct MlpDev {
   const unsigned* W1p;  // W1 as bf16 pairs, K padded to 16: [64][8]
   const unsigned* W2p;  // W2 as bf16 pairs: [64 out][32 in-pairs]
   const unsigned* W2Tp; // W2 transposed as bf16 pairs: [64 in][32 out-pairs]
-  const float* norm;    // in_mean[9], in_std[9], out_scale
+  const float* norm;    // in_mean[9], in_std[9], out_scale, 1/in_std[9]
 };
+
+// What the forward pass reads: operand copies, biases, output weights and the input
+// normalisation, in global memory or staged in shared memory.
+struct MlpView {
+  const unsigned* W1p;
+  const unsigned* W2p;
+  const float *b1, *b2, *w3;
+  float b3;
+  const float* mean;
+  const float* inv_std;
+};
+// Loads of the view's arrays.  From shared memory they go through volatile ld.shared so
+// that the compiler reloads them per tile instead of hoisting all 80 words per lane out of
+// the pair loop into registers (which would cut the kernel's occupancy to a quarter).
+struct LdGlobal {
+  static __device__ __forceinline__ unsigned u(const unsigned* p) { return *p; }
+  static __device__ __forceinline__ float f(const float* p) { return *p; }
+};
+struct LdShared {
+  static __device__ __forceinline__ unsigned u(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+  }
+  static __device__ __forceinline__ float f(const float* p) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"((unsigned)__cvta_generic_to_shared(p)));
+    return v;
+  }
+};
+
+__device__ __forceinline__ MlpView view_of(const MlpDev& m) {
+  return MlpView{m.W1p, m.W2p, m.P + ob1, m.P + ob2, m.P + ow3, m.P[ob3], m.norm, m.norm + 2 * kIn + 1};
+}
 
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<unsigned*>(&v);
 }
-__device__ __forceinline__ float silu_f(float z) { return z / (1.0f + __expf(-z)); }
+// SiLU z sigma(z) and its derivative, sigma(z) = 1 / (1 + e^-z) from the hardware base-2
+// exponential and reciprocal approximations (a few ulp, far below the bfloat16 resolution of
+// the activations; e^-z = inf gives sigma = 0).  An IEEE division here was most of the
+// instructions of the network evaluation.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// e^-z = 2^(-z log2 e)
+__device__ __forceinline__ float exp_neg(float z) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(z * -1.4426950408889634f));
+  return r;
+}
+__device__ __forceinline__ float silu_f(float z) { return z * rcp_approx(1.0f + exp_neg(z)); }
 __device__ __forceinline__ float dsilu_f(float z) {
-  const float sg = 1.0f / (1.0f + __expf(-z));
+  const float sg = rcp_approx(1.0f + exp_neg(z));
   return sg * (1.0f + z * (1.0f - sg));
 }
 
@@ -68,16 +117,18 @@ struct Tile {
   float z1[8][4], z2[8][4];
 };
 
-__device__ __forceinline__ void tile_forward(const MlpDev& m, const unsigned ax[4], Tile& T, float& y_g, float& y_g8) {
+template <class LD = LdGlobal>
+__device__ __forceinline__ void tile_forward(const MlpView& m, const unsigned ax[4], Tile& T, float& y_g, float& y_g8) {
   const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
-  const float* b1 = m.P + ob1;
-  const float* b2 = m.P + ob2;
-  const float* w3 = m.P + ow3;
+  const float* b1 = m.b1;
+  const float* b2 = m.b2;
+  const float* w3 = m.w3;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int o = 8 * j + 2 * tg;
-    const float c[4] = {b1[o], b1[o + 1], b1[o], b1[o + 1]};
-    mma16816(T.z1[j], ax, m.W1p[(8 * j + g) * 8 + tg], m.W1p[(8 * j + g) * 8 + tg + 4], c);
+    const float c0 = LD::f(b1 + o), c1 = LD::f(b1 + o + 1);
+    const float c[4] = {c0, c1, c0, c1};
+    mma16816(T.z1[j], ax, LD::u(m.W1p + (8 * j + g) * 8 + tg), LD::u(m.W1p + (8 * j + g) * 8 + tg + 4), c);
   }
   unsigned a2[4][4];
 #pragma unroll
@@ -91,25 +142,141 @@ __device__ __forceinline__ void tile_forward(const MlpDev& m, const unsigned ax[
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int o = 8 * j + 2 * tg;
-    float c[4] = {b2[o], b2[o + 1], b2[o], b2[o + 1]};
+    const float c0 = LD::f(b2 + o), c1 = LD::f(b2 + o + 1);
+    float c[4] = {c0, c1, c0, c1};
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk)
-      mma16816(c, a2[kk], m.W2p[(8 * j + g) * 32 + 8 * kk + tg], m.W2p[(8 * j + g) * 32 + 8 * kk + tg + 4], c);
+      mma16816(c, a2[kk], LD::u(m.W2p + (8 * j + g) * 32 + 8 * kk + tg), LD::u(m.W2p + (8 * j + g) * 32 + 8 * kk + tg + 4), c);
 #pragma unroll
     for (int e = 0; e < 4; ++e) T.z2[j][e] = c[e];
-    pg += w3[o] * silu_f(c[0]) + w3[o + 1] * silu_f(c[1]);
-    pg8 += w3[o] * silu_f(c[2]) + w3[o + 1] * silu_f(c[3]);
+    const float w0 = LD::f(w3 + o), w1 = LD::f(w3 + o + 1);
+    pg += w0 * silu_f(c[0]) + w1 * silu_f(c[1]);
+    pg8 += w0 * silu_f(c[2]) + w1 * silu_f(c[3]);
   }
   pg += __shfl_xor_sync(0xffffffffu, pg, 1);
   pg += __shfl_xor_sync(0xffffffffu, pg, 2);
   pg8 += __shfl_xor_sync(0xffffffffu, pg8, 1);
   pg8 += __shfl_xor_sync(0xffffffffu, pg8, 2);
-  y_g = pg + m.P[ob3];
-  y_g8 = pg8 + m.P[ob3];
+  y_g = pg + m.b3;
+  y_g8 = pg8 + m.b3;
+}
+
+// Forward of one 16-sample tile returning only the outputs (no pre-activations kept), with
+// the layer-2 column tiles evaluated two at a time to bound the registers in flight.
+template <class LD>
+__device__ __forceinline__ void tile_forward_y(const MlpView& m, const unsigned ax[4], float& y_g, float& y_g8) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+  unsigned a2[4][4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    float z[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = 2 * kk + h;
+      const int o = 8 * j + 2 * tg;
+      const float c0 = LD::f(m.b1 + o), c1 = LD::f(m.b1 + o + 1);
+      const float c[4] = {c0, c1, c0, c1};
+      mma16816(z[h], ax, LD::u(m.W1p + (8 * j + g) * 8 + tg), LD::u(m.W1p + (8 * j + g) * 8 + tg + 4), c);
+    }
+    a2[kk][0] = pack_bf16(silu_f(z[0][0]), silu_f(z[0][1]));
+    a2[kk][1] = pack_bf16(silu_f(z[0][2]), silu_f(z[0][3]));
+    a2[kk][2] = pack_bf16(silu_f(z[1][0]), silu_f(z[1][1]));
+    a2[kk][3] = pack_bf16(silu_f(z[1][2]), silu_f(z[1][3]));
+  }
+  float pg = 0.f, pg8 = 0.f;
+#pragma unroll 2
+  for (int j = 0; j < 8; ++j) {
+    const int o = 8 * j + 2 * tg;
+    const float c0 = LD::f(m.b2 + o), c1 = LD::f(m.b2 + o + 1);
+    float c[4] = {c0, c1, c0, c1};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+      mma16816(c, a2[kk], LD::u(m.W2p + (8 * j + g) * 32 + 8 * kk + tg),
+               LD::u(m.W2p + (8 * j + g) * 32 + 8 * kk + tg + 4), c);
+    const float w0 = LD::f(m.w3 + o), w1 = LD::f(m.w3 + o + 1);
+    pg += w0 * silu_f(c[0]) + w1 * silu_f(c[1]);
+    pg8 += w0 * silu_f(c[2]) + w1 * silu_f(c[3]);
+  }
+  pg += __shfl_xor_sync(0xffffffffu, pg, 1);
+  pg += __shfl_xor_sync(0xffffffffu, pg, 2);
+  pg8 += __shfl_xor_sync(0xffffffffu, pg8, 1);
+  pg8 += __shfl_xor_sync(0xffffffffu, pg8, 2);
+  y_g = pg + m.b3;
+  y_g8 = pg8 + m.b3;
+}
+
+// Forward of two 16-sample tiles at once (the two orderings of 16 pairs): every weight
+// fragment is loaded once (as one 64-bit word from the staged W1q / W2q layouts) and feeds
+// both tiles' products.  Outputs y for rows g and g + 8 of each tile.
+struct MlpViewQ {
+  const uint2* W1q;  // [(8 j + g) * 4 + tg] = W1p words tg, tg + 4 of row 8 j + g
+  const uint2* W2q;  // [(8 j + g) * 16 + 4 kk + tg] = W2p words 8 kk + tg, 8 kk + tg + 4
+  const float *b1, *b2, *w3;
+  float b3;
+};
+__device__ __forceinline__ uint2 lds_u2(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return v;
+}
+__device__ __forceinline__ void tile_forward_y2(const MlpViewQ& m, const unsigned ax0[4], const unsigned ax1[4],
+                                                float y[2][2]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+  unsigned a2[2][4][4];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    float z[2][2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = 2 * kk + h;
+      const int o = 8 * j + 2 * tg;
+      const float c0 = LdShared::f(m.b1 + o), c1 = LdShared::f(m.b1 + o + 1);
+      const float c[4] = {c0, c1, c0, c1};
+      const uint2 wq = lds_u2(m.W1q + (8 * j + g) * 4 + tg);
+      mma16816(z[0][h], ax0, wq.x, wq.y, c);
+      mma16816(z[1][h], ax1, wq.x, wq.y, c);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      a2[u][kk][0] = pack_bf16(silu_f(z[u][0][0]), silu_f(z[u][0][1]));
+      a2[u][kk][1] = pack_bf16(silu_f(z[u][0][2]), silu_f(z[u][0][3]));
+      a2[u][kk][2] = pack_bf16(silu_f(z[u][1][0]), silu_f(z[u][1][1]));
+      a2[u][kk][3] = pack_bf16(silu_f(z[u][1][2]), silu_f(z[u][1][3]));
+    }
+  }
+  float p[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 2
+  for (int j = 0; j < 8; ++j) {
+    const int o = 8 * j + 2 * tg;
+    const float c0 = LdShared::f(m.b2 + o), c1 = LdShared::f(m.b2 + o + 1);
+    float c[2][4] = {{c0, c1, c0, c1}, {c0, c1, c0, c1}};
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      const uint2 wq = lds_u2(m.W2q + (8 * j + g) * 16 + 4 * kk + tg);
+      mma16816(c[0], a2[0][kk], wq.x, wq.y, c[0]);
+      mma16816(c[1], a2[1][kk], wq.x, wq.y, c[1]);
+    }
+    const float w0 = LdShared::f(m.w3 + o), w1 = LdShared::f(m.w3 + o + 1);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      p[u][0] += w0 * silu_f(c[u][0]) + w1 * silu_f(c[u][1]);
+      p[u][1] += w0 * silu_f(c[u][2]) + w1 * silu_f(c[u][3]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      float v = p[u][r];
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      v += __shfl_xor_sync(0xffffffffu, v, 2);
+      y[u][r] = v + m.b3;
+    }
 }
 
 // A fragment of normalised inputs from a [16][9] feature tile (row stride 9 floats).
-__device__ __forceinline__ void input_fragment(const MlpDev& m, const float* f16x9, unsigned ax[4]) {
+template <class LD = LdGlobal>
+__device__ __forceinline__ void input_fragment(const MlpView& m, const float* f16x9, unsigned ax[4]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
   float v[2][4];
 #pragma unroll
@@ -118,7 +285,7 @@ __device__ __forceinline__ void input_fragment(const MlpDev& m, const float* f16
     for (int c = 0; c < 4; ++c) {
       const int k = (c < 2 ? 2 * tg + c : 2 * tg + 8 + (c - 2));
       const int row = g + 8 * r;
-      v[r][c] = k < kIn ? (f16x9[row * kIn + k] - m.norm[k]) / m.norm[kIn + k] : 0.f;
+      v[r][c] = k < kIn ? (f16x9[row * kIn + k] - LD::f(m.mean + k)) * LD::f(m.inv_std + k) : 0.f;
     }
   ax[0] = pack_bf16(v[0][0], v[0][1]);
   ax[1] = pack_bf16(v[1][0], v[1][1]);
@@ -138,11 +305,11 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpDev m, const float* __re
     tile[w][e] = s < n ? feat[s * kIn + e % kIn] : 0.f;
   }
   __syncwarp();
+  const MlpView mv = view_of(m);
   unsigned ax[4];
-  input_fragment(m, tile[w], ax);
-  Tile T;
+  input_fragment(mv, tile[w], ax);
   float yg, yg8;
-  tile_forward(m, ax, T, yg, yg8);
+  tile_forward_y<LdGlobal>(mv, ax, yg, yg8);
   const int g = lane >> 2, tg = lane & 3;
   if (tg == 0) {
     if (base + g < n) y[base + g] = yg;
@@ -171,11 +338,12 @@ __global__ void __launch_bounds__(128) k_mlp_grad(MlpDev m, const float* __restr
     ftile[w][e] = s < n ? feat[s * kIn + e % kIn] : 0.f;
   }
   __syncwarp();
+  const MlpView mv = view_of(m);
   unsigned ax[4];
-  input_fragment(m, ftile[w], ax);
+  input_fragment(mv, ftile[w], ax);
   Tile T;
   float yg, yg8;
-  tile_forward(m, ax, T, yg, yg8);
+  tile_forward(mv, ax, T, yg, yg8);
   const bool vg = base + g < n, vg8 = base + g + 8 < n;
   const float rg = vg ? yg - target[base + g] * inv_scale : 0.f;
   const float rg8 = vg8 ? yg8 - target[base + g + 8] * inv_scale : 0.f;
@@ -523,134 +691,134 @@ __global__ void k_mlp_collect(const __grid_constant__ Sys s, Bufs b, int pass, c
 }
 
 // ---------------- pair forces for the dynamics -------------------------------------------
-// Every list slot (t, q) whose pair needs a CG force (COM distance < rc_cg and w_ab < 1)
-// gets the symmetrised network force in fpair[t cap + q]; the pair is evaluated once, by
-// the molecule with the smaller id, and the value is written to both molecules' slots.
-// A warp gathers 16 pairs at a time (ballot compaction), evaluates the two orderings as
-// two 16-row tensor-core tiles and scatters the results.
+// Every list slot (t, q) whose pair needs a CG force (COM distance < rc_cg and w_ab < 1, the
+// force kernel's test in its own precision and arithmetic) gets the symmetrised network
+// force in fpair[t cap + q].  Two kernels: k_mlp_feat walks the lists (a thread per work
+// item), takes every such pair once (from the molecule with the smaller id), computes its
+// features, finds the mirror slot in the partner's list and appends both to a pair buffer
+// (one atomic per warp; the buffer order varies between runs, the values do not);
+// k_mlp_eval then evaluates the buffer 16 pairs per warp tile (both orderings as two
+// tensor-core tiles, weights staged in shared memory) and writes the force to both slots.
+
+template <bool F64>
+__device__ __forceinline__ bool needs_network(const Sys& s, const Box& X, const Bufs& b, int cur, int a, int m) {
+  if (F64) {
+    const double4_32a A = b.com64[cur][a], B = b.com64[cur][m];
+    const double r2 = pair_r2(minimg_cmp(A.x - B.x, X.L[0], X.halfL[0]), minimg_cmp(A.y - B.y, X.L[1], X.halfL[1]),
+                              minimg_cmp(A.z - B.z, X.L[2], X.halfL[2]));
+    return A.w * B.w < 1.0 && r2 < s.rc_cg2;
+  }
+  const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][m];
+  const float r2 = pair_r2((float)(int)((unsigned)A.x - (unsigned)B.x) * X.fx_scale[0],
+                           (float)(int)((unsigned)A.y - (unsigned)B.y) * X.fx_scale[1],
+                           (float)(int)((unsigned)A.z - (unsigned)B.z) * X.fx_scale[2]);
+  return __int_as_float(A.w) * __int_as_float(B.w) < 1.f && r2 < s.f.rc_cg2;
+}
+
 template <int NA, bool F64>
-__global__ void __launch_bounds__(128) k_mlp_pairs(const __grid_constant__ Sys s, Bufs b, MlpDev m, float* fpair) {
-  __shared__ float ft[4][2][16 * kIn];
-  __shared__ int slot_a[4][16], slot_b[4][16];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
-  const int cur = b.ctrl->parity;
-  const int items_per_warp = 32;
-  const int t0 = (blockIdx.x * 4 + w) * items_per_warp;
-  const float scale = m.norm[2 * kIn];
-  int nq = 0;  // pairs gathered in the tile
-  // lane l walks the list of item t0 + l; the warp loops until every lane is done
-  const int t = t0 + lane;
+__global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s, Bufs b) {
+  // four lanes per work item, lane g taking list slots g, g + 4, ...
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2, g = threadIdx.x & 3;
+  const int lane = threadIdx.x & 31;
   const bool live = t < s.M;
+  const int cur = b.ctrl->parity;
   const int a = live ? b.items[t] : 0;
   const int n = live ? b.nn[t] : 0;
-  const float wa = live ? __int_as_float(b.com_fx[cur][a].w) : 0.f;
-  int q = 0;
-  while (true) {
-    // next qualifying slot of this lane
-    int found = -1, mb = 0;
-    while (q < n && found < 0) {
-      const int mm = b.nbr[(size_t)t * s.cap + q];
-      if (mm > a) {
-        const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][mm];
-        const Box& X = box_of(s, b, a);
-        const float dx = (float)(int)((unsigned)B.x - (unsigned)A.x) * X.fx_scale[0];
-        const float dy = (float)(int)((unsigned)B.y - (unsigned)A.y) * X.fx_scale[1];
-        const float dz = (float)(int)((unsigned)B.z - (unsigned)A.z) * X.fx_scale[2];
-        if (dx * dx + dy * dy + dz * dz < s.f.rc_cg2 && wa * __int_as_float(B.w) < 1.f) {
-          found = q;
-          mb = mm;
-        }
-      }
-      ++q;
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, found >= 0);
-    if (bal == 0u) break;
-    // append this round's pairs; evaluate whenever 16 are gathered
-    const int rank = __popc(bal & ((1u << lane) - 1u));
-    const int nb = __popc(bal);
-    int done = 0;
-    while (done < nb) {
-      const int take = min(16 - nq, nb - done);
-      if (found >= 0 && rank >= done && rank < done + take) {
-        const int r = nq + rank - done;
-        float f[9];
-        pair_features32<NA, F64>(s, b, cur, a, mb, f);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) ft[w][0][r * kIn + k] = f[k];
-        ft[w][1][r * kIn] = f[0];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          ft[w][1][r * kIn + 1 + k] = f[5 + k];
-          ft[w][1][r * kIn + 5 + k] = f[1 + k];
-        }
-        slot_a[w][r] = t * s.cap + found;
-        slot_b[w][r] = mb;  // resolved to the mirror slot after the evaluation
-      }
-      nq += take;
-      done += take;
-      __syncwarp();
-      if (nq == 16) {
-        unsigned ax[4];
-        Tile T;
-        float y0g, y0g8, y1g, y1g8;
-        input_fragment(m, ft[w][0], ax);
-        tile_forward(m, ax, T, y0g, y0g8);
-        input_fragment(m, ft[w][1], ax);
-        tile_forward(m, ax, T, y1g, y1g8);
-        if (tg == 0) {
-          ft[w][0][g * kIn] = 0.5f * scale * (y0g + y1g);
-          ft[w][0][(g + 8) * kIn] = 0.5f * scale * (y0g8 + y1g8);
-        }
-        __syncwarp();
-        if (lane < 16) {
-          const float fv = ft[w][0][lane * kIn];
-          const int sa = slot_a[w][lane], mm = slot_b[w][lane];
-          fpair[sa] = fv;
-          const int tb = b.item_of[mm], nbb = b.nn[tb];
-          const int aa = b.items[sa / s.cap];
-          for (int qq = 0; qq < nbb; ++qq)
-            if (b.nbr[(size_t)tb * s.cap + qq] == aa) {
-              fpair[(size_t)tb * s.cap + qq] = fv;
-              break;
-            }
-        }
-        nq = 0;
-        __syncwarp();
-      }
-    }
+  const Box& X = box_of(s, b, a);
+  const int* row = b.nbr + (size_t)t * s.cap;
+  int cnt = 0;
+  for (int q = g; q < n; q += 4) {
+    const int m = row[q];
+    if (m > a && needs_network<F64>(s, X, b, cur, a, m)) ++cnt;
   }
-  // remainder (fewer than 16 pairs): pad the tile with copies of row 0
-  if (nq > 0) {
-    for (int e = lane; e < (16 - nq) * kIn; e += 32) {
-      ft[w][0][nq * kIn + e] = ft[w][0][e % kIn];
-      ft[w][1][nq * kIn + e] = ft[w][1][e % kIn];
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  unsigned base = 0;
+  if (lane == 31 && incl > 0) base = atomicAdd(b.npair, (unsigned)incl);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  long long p = (long long)base + (incl - cnt);
+  if (cnt == 0) return;
+  for (int q = g; q < n; q += 4) {
+    const int m = row[q];
+    if (!(m > a && needs_network<F64>(s, X, b, cur, a, m))) continue;
+    if (p >= b.pcap) {
+      set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, (int)p);
+      return;
+    }
+    float f[9];
+    pair_features32<NA, F64>(s, b, cur, a, m, f);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) b.pfeat[p * 9 + k] = f[k];
+    b.pslot[p] = make_int2(t * s.cap + q, b.mirror[(size_t)t * s.cap + q]);
+    ++p;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_mlp_eval(MlpDev m, const float* __restrict__ pfeat,
+                                                  const int2* __restrict__ pslot, const unsigned* npair,
+                                                  float* __restrict__ fpair) {
+  __shared__ float ft[4][2][16 * kIn];
+  __shared__ float yo[4][2][16];
+  __shared__ uint2 sW1[kH * 4], sW2[kH * 16];
+  __shared__ float sB[3 * kH], sNorm[2 * kIn];
+  for (int i = threadIdx.x; i < kH * 16; i += blockDim.x) {
+    const int r = i >> 4, kk = (i >> 2) & 3, tg = i & 3;
+    sW2[i] = make_uint2(m.W2p[r * 32 + 8 * kk + tg], m.W2p[r * 32 + 8 * kk + tg + 4]);
+  }
+  for (int i = threadIdx.x; i < kH * 4; i += blockDim.x) {
+    const int r = i >> 2, tg = i & 3;
+    sW1[i] = make_uint2(m.W1p[r * 8 + tg], m.W1p[r * 8 + tg + 4]);
+  }
+  for (int i = threadIdx.x; i < kH; i += blockDim.x) {
+    sB[i] = m.P[ob1 + i];
+    sB[kH + i] = m.P[ob2 + i];
+    sB[2 * kH + i] = m.P[ow3 + i];
+  }
+  for (int i = threadIdx.x; i < kIn; i += blockDim.x) {
+    sNorm[i] = m.norm[i];
+    sNorm[kIn + i] = m.norm[2 * kIn + 1 + i];
+  }
+  __syncthreads();
+  const MlpView mv{nullptr, nullptr, sB, sB + kH, sB + 2 * kH, m.P[ob3], sNorm, sNorm + kIn};
+  const MlpViewQ mq{sW1, sW2, sB, sB + kH, sB + 2 * kH, m.P[ob3]};
+  const float scale = m.norm[2 * kIn];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
+  const long long np = *npair;
+  const long long ntiles = (np + 15) / 16;
+  for (long long tile = (long long)blockIdx.x * 4 + w; tile < ntiles; tile += (long long)gridDim.x * 4) {
+    const long long p0 = tile * 16;
+    for (int e = lane; e < 16 * kIn; e += 32)
+      ft[w][0][e] = p0 + e / kIn < np ? pfeat[p0 * kIn + e] : 0.f;
+    __syncwarp();
+    // the other ordering: (d, s_b, s_a)
+    for (int e = lane; e < 16 * kIn; e += 32) {
+      const int r = e / kIn, k = e % kIn;
+      ft[w][1][e] = ft[w][0][r * kIn + (k == 0 ? 0 : (k < 5 ? k + 4 : k - 4))];
     }
     __syncwarp();
-    unsigned ax[4];
-    Tile T;
-    float y0g, y0g8, y1g, y1g8;
-    input_fragment(m, ft[w][0], ax);
-    tile_forward(m, ax, T, y0g, y0g8);
-    input_fragment(m, ft[w][1], ax);
-    tile_forward(m, ax, T, y1g, y1g8);
-    __syncwarp();
+    unsigned ax0[4], ax1[4];
+    float y[2][2];
+    input_fragment<LdShared>(mv, ft[w][0], ax0);
+    input_fragment<LdShared>(mv, ft[w][1], ax1);
+    tile_forward_y2(mq, ax0, ax1, y);
     if (tg == 0) {
-      ft[w][0][g * kIn] = 0.5f * scale * (y0g + y1g);
-      ft[w][0][(g + 8) * kIn] = 0.5f * scale * (y0g8 + y1g8);
+      yo[w][0][g] = y[0][0];
+      yo[w][0][g + 8] = y[0][1];
+      yo[w][1][g] = y[1][0];
+      yo[w][1][g + 8] = y[1][1];
     }
     __syncwarp();
-    if (lane < nq) {
-      const float fv = ft[w][0][lane * kIn];
-      const int sa = slot_a[w][lane], mm = slot_b[w][lane];
-      fpair[sa] = fv;
-      const int tb = b.item_of[mm], nbb = b.nn[tb];
-      const int aa = b.items[sa / s.cap];
-      for (int qq = 0; qq < nbb; ++qq)
-        if (b.nbr[(size_t)tb * s.cap + qq] == aa) {
-          fpair[(size_t)tb * s.cap + qq] = fv;
-          break;
-        }
+    if (lane < 16 && p0 + lane < np) {
+      const float fv = 0.5f * scale * (yo[w][0][lane] + yo[w][1][lane]);
+      const int2 sl = pslot[p0 + lane];
+      fpair[sl.x] = fv;
+      if (sl.y >= 0) fpair[sl.y] = fv;
     }
+    __syncwarp();
   }
 }
 
@@ -720,17 +888,32 @@ cudaError_t mlp_collect(const Sys& s, const Bufs& b, int pass, const int* offs, 
 
 cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* fpair, cudaStream_t st) {
   const MlpDev m{a.P, a.W1p, a.W2p, a.W2Tp, a.norm};
-  const int blocks = ceil_div(s.M, 4 * 32);
-#define PAIRS(NA_)                                                               \
-  (s.fp64 ? k_mlp_pairs<NA_, true><<<blocks, 128, 0, st>>>(s, b, m, fpair) \
-          : k_mlp_pairs<NA_, false><<<blocks, 128, 0, st>>>(s, b, m, fpair))
+  cudaError_t e = cudaMemsetAsync(b.npair, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const int blocks = ceil_div((long long)s.M * 4, 128);
+#define FEAT(NA_)                                                       \
+  (s.fp64 ? k_mlp_feat<NA_, true><<<blocks, 128, 0, st>>>(s, b)        \
+          : k_mlp_feat<NA_, false><<<blocks, 128, 0, st>>>(s, b))
   switch (s.NA) {
-    case 1: PAIRS(1); break;
-    case 2: PAIRS(2); break;
-    case 3: PAIRS(3); break;
-    default: PAIRS(4); break;
+    case 1: FEAT(1); break;
+    case 2: FEAT(2); break;
+    case 3: FEAT(3); break;
+    default: FEAT(4); break;
   }
-#undef PAIRS
+#undef FEAT
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // persistent grid: as many blocks as fit on the device at once
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_eval, 128, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 4;
+    grid = per_sm * sms;
+  }
+  k_mlp_eval<<<grid, 128, 0, st>>>(m, b.pfeat, b.pslot, b.npair, fpair);
   return cudaGetLastError();
 }
 

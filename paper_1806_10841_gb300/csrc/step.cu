@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kMaxForceBlock) k_step(const __grid_constant__
         C_n = Q::com(b, cur, m_n);
       }
       const auto R = Q::dR(B, Ca, Cb);
-      const real r2 = R.x * R.x + R.y * R.y + R.z * R.z;
+      const real r2 = pair_r2(R.x, R.y, R.z);
       const real wab = wa * Q::w(Cb);
       if (own && wab > (real)0 && r2 < reach_at2) {
         const real px = R.x + (real)oi.x, py = R.y + (real)oi.y, pz = R.z + (real)oi.z;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kMaxForceBlock) k_step(const __grid_constant__
       const auto Cb = C_n;
       if (q + kGroup < nnb) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + q + kGroup]);
       const auto R = Q::dR(B, Ca, Cb);
-      const real r2 = R.x * R.x + R.y * R.y + R.z * R.z;
+      const real r2 = pair_r2(R.x, R.y, R.z);
       if (r2 < rc_cg2) {
         const real r = Q::sqrt_(r2);
         real V = 0;
