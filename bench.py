@@ -205,17 +205,16 @@ def run_block(sim, nsteps=MD_PER_BLOCK):
     sim.run(nsteps, sample_every=SAMPLE_EVERY, tf_update=True, alpha=TF_ALPHA)
 
 
-def learned_arm(s, x0, v0, make, timed, steps):
-    """FP32 path with the learned CG force: samples from an all-atomistic FP64 run of the
-    same fluid, GPU training, then the same timed blocks in network mode."""
+def atomistic_samples(s, x0, v0, device="cuda:0"):
+    """Force-matching samples from an all-atomistic FP64 run of the same fluid: every pair
+    with COM distance < rc_cg in 3 snapshots 100 steps apart.  Returns (feat, target, sim)."""
     import copy
 
     from paper_1806_10841_gb300 import adress
 
-    t0 = time.perf_counter()
     s_at = copy.copy(s)
     s_at.d_at = 1e4  # every molecule atomistic
-    at = adress.AdResS(s_at, precision="fp64")
+    at = adress.AdResS(s_at, precision="fp64", device=device)
     at.set_state(x0, v0)
     at.compute_forces(energies=False)
     n = 0
@@ -223,6 +222,36 @@ def learned_arm(s, x0, v0, make, timed, steps):
         at.step(100)
         n = at.mlp_collect(cap=1_000_000)
     feat, t, _ = at.mlp_samples(n)
+    return feat, t, at
+
+
+def train_network(sim, feat, t, epochs=5, seed=20180628):
+    """Standardise, initialise and train the 9-64-64-1 network on 90% of the samples (on
+    the GPU, in `sim`).  Returns the split, normalisation and per-epoch losses."""
+    n = len(t)
+    rng = np.random.default_rng(seed)
+    idx = rng.permutation(n)
+    ntr = int(0.9 * n)
+    tr, te = idx[:ntr], idx[ntr:]
+    mean, std = feat[tr].mean(0), feat[tr].std(0) + 1e-3
+    scale = float(t[tr].std())
+    params = dict(W1=rng.normal(0, 1 / 3, (64, 9)), b1=np.zeros(64), W2=rng.normal(0, 1 / 8, (64, 64)),
+                  b2=np.zeros(64), w3=rng.normal(0, 1 / 8, 64), b3=float(t[tr].mean() / scale))
+    sim.mlp_set(params, mean, std, scale)
+    sim.mlp_load_samples(feat[tr], t[tr])
+    t1 = time.perf_counter()
+    losses = sim.mlp_train(epochs=epochs, batch=4096, lr=2e-3)
+    return {"tr": tr, "te": te, "scale": scale, "losses": losses, "train_s": time.perf_counter() - t1}
+
+
+def learned_arm(s, x0, v0, make, timed, steps, device):
+    """FP32 path with the learned CG force: samples from an all-atomistic FP64 run of the
+    same fluid, GPU training, then the same timed blocks in network mode."""
+    from paper_1806_10841_gb300 import adress
+
+    t0 = time.perf_counter()
+    feat, t, at = atomistic_samples(s, x0, v0, device=device)
+    n = len(t)
     nb, dr = RDF_BINS, RDF_DR
 
     def rdf_of(sim, eq):
@@ -236,20 +265,10 @@ def learned_arm(s, x0, v0, make, timed, steps):
 
     g_at = rdf_of(at, RDF_EQ - 300)
     at.close()
-    rng = np.random.default_rng(20180628)
-    idx = rng.permutation(n)
-    ntr = int(0.9 * n)
-    tr, te = idx[:ntr], idx[ntr:]
-    mean, std = feat[tr].mean(0), feat[tr].std(0) + 1e-3
-    scale = float(t[tr].std())
-    params = dict(W1=rng.normal(0, 1 / 3, (64, 9)), b1=np.zeros(64), W2=rng.normal(0, 1 / 8, (64, 64)),
-                  b2=np.zeros(64), w3=rng.normal(0, 1 / 8, 64), b3=float(t[tr].mean() / scale))
     sim = make("fp32")
-    sim.mlp_set(params, mean, std, scale)
-    sim.mlp_load_samples(feat[tr], t[tr])
-    t1 = time.perf_counter()
-    losses = sim.mlp_train(epochs=5, batch=4096, lr=2e-3)
-    t_train = time.perf_counter() - t1
+    tn = train_network(sim, feat, t)
+    tr, te, scale, losses, t_train = tn["tr"], tn["te"], tn["scale"], tn["losses"], tn["train_s"]
+    ntr = len(tr)
     sw = feat[te].copy()
     sw[:, 1:5], sw[:, 5:9] = feat[te][:, 5:9], feat[te][:, 1:5]
     pred = 0.5 * scale * (sim.mlp_forward(feat[te]) + sim.mlp_forward(sw))
@@ -377,12 +396,10 @@ def main():
         sim = adress.AdResS(s, precision=args.precision, device=f"cuda:{local}")
         sim.set_state(x0, v0)
         if args.cg_mode:
-            # an untrained network of the production shape: the kernels' cost does not
-            # depend on the weights
-            rng = np.random.default_rng(1)
-            params = dict(W1=rng.normal(0, 1 / 3, (64, 9)), b1=np.zeros(64), W2=rng.normal(0, 1 / 8, (64, 64)),
-                          b2=np.zeros(64), w3=rng.normal(0, 1 / 8, 64), b3=0.0)
-            sim.mlp_set(params, np.r_[1.9, np.zeros(8)], np.full(9, 0.3), 5.0)
+            # the production network: trained on samples of an all-atomistic run
+            feat, t, at = atomistic_samples(s, x0, v0, device=f"cuda:{local}")
+            at.close()
+            train_network(sim, feat, t)
             sim.set_cg_mode(1)
         sim.compute_forces(energies=False)
         sim.run(args.profile, sample_every=SAMPLE_EVERY, tf_update=True, alpha=TF_ALPHA)
@@ -503,7 +520,7 @@ def main():
 
     learned = None
     if not args.no_learned and rank == 0:
-        learned = learned_arm(s, x0, v0, make, timed, max(2, args.steps // 2))
+        learned = learned_arm(s, x0, v0, make, timed, max(2, args.steps // 2), f"cuda:{local}")
 
     replicas = None
     if not args.no_replicas and rank == 0:

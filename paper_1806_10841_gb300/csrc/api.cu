@@ -110,7 +110,7 @@ static cudaError_t realloc_owned(adress_ctx* h, T** p, size_t n) {
 static cudaError_t alloc_pair_buffers(adress_ctx* h) {
   Bufs& b = h->buf;
   const long long pcap = (long long)h->sys.M * h->sys.cap / 2 + 32;
-  cudaError_t e = realloc_owned(h, &b.pfeat, (size_t)pcap * 9);
+  cudaError_t e = realloc_owned(h, &b.pfrag, (size_t)pcap * 10);
   if (e == cudaSuccess) e = realloc_owned(h, &b.pslot, (size_t)pcap);
   if (e == cudaSuccess) e = realloc_owned(h, &b.mirror, (size_t)h->sys.M * h->sys.cap);
   if (e == cudaSuccess && !b.npair) e = dalloc(h, &b.npair, 1);

@@ -138,7 +138,8 @@ struct Bufs {
   long long* nsamples;
   Ctrl* ctrl;
   float* fpair;  // [M*cap] network CG pair force per list slot (CG mode 1)
-  float* pfeat;  // [pcap][9] features of the pairs the network evaluates this step
+  unsigned* pfrag;  // [pcap][10] normalised network inputs of this step's pairs as bf16 pairs:
+                    // words 0-4 the ordering (d, s_a, s_b), 5-9 the ordering (d, s_b, s_a)
   int2* pslot;   // [pcap] the pair's two list slots
   int* mirror;   // [M*cap] (CG mode 1) slot of the same pair in the partner's list, from the last build
   unsigned* npair;  // pairs written this step

@@ -716,7 +716,14 @@ __device__ __forceinline__ bool needs_network(const Sys& s, const Box& X, const 
 }
 
 template <int NA, bool F64>
-__global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s, Bufs b) {
+__global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s, Bufs b, const float* __restrict__ norm) {
+  // input normalisation (mean, 1/std) for the network's A operands
+  __shared__ float sn[2][kIn];
+  if (threadIdx.x < kIn) {
+    sn[0][threadIdx.x] = norm[threadIdx.x];
+    sn[1][threadIdx.x] = norm[2 * kIn + 1 + threadIdx.x];
+  }
+  __syncthreads();
   // four lanes per work item, lane g taking list slots g, g + 4, ...
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2, g = threadIdx.x & 3;
   const int lane = threadIdx.x & 31;
@@ -751,20 +758,32 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
     }
     float f[9];
     pair_features32<NA, F64>(s, b, cur, a, m, f);
+    // both orderings, normalised and packed as the A fragments read them
+    unsigned* out = b.pfrag + p * 10;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) b.pfeat[p * 9 + k] = f[k];
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int w = 0; w < 5; ++w) {
+        float v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = 2 * w + h;
+          const int src = (u == 0 || k == 0) ? k : (k < 5 ? k + 4 : k - 4);
+          v[h] = k < kIn ? (f[src < kIn ? src : 0] - sn[0][k < kIn ? k : 0]) * sn[1][k < kIn ? k : 0] : 0.f;
+        }
+        out[5 * u + w] = pack_bf16(v[0], v[1]);
+      }
     b.pslot[p] = make_int2(t * s.cap + q, b.mirror[(size_t)t * s.cap + q]);
     ++p;
   }
 }
 
-__global__ void __launch_bounds__(128) k_mlp_eval(MlpDev m, const float* __restrict__ pfeat,
-                                                  const int2* __restrict__ pslot, const unsigned* npair,
-                                                  float* __restrict__ fpair) {
-  __shared__ float ft[4][2][16 * kIn];
+__global__ void __launch_bounds__(128, 8) k_mlp_eval(MlpDev m, const unsigned* __restrict__ pfrag,
+                                                     const int2* __restrict__ pslot, const unsigned* npair,
+                                                     float* __restrict__ fpair) {
   __shared__ float yo[4][2][16];
   __shared__ uint2 sW1[kH * 4], sW2[kH * 16];
-  __shared__ float sB[3 * kH], sNorm[2 * kIn];
+  __shared__ float sB[3 * kH];
   for (int i = threadIdx.x; i < kH * 16; i += blockDim.x) {
     const int r = i >> 4, kk = (i >> 2) & 3, tg = i & 3;
     sW2[i] = make_uint2(m.W2p[r * 32 + 8 * kk + tg], m.W2p[r * 32 + 8 * kk + tg + 4]);
@@ -778,12 +797,7 @@ __global__ void __launch_bounds__(128) k_mlp_eval(MlpDev m, const float* __restr
     sB[kH + i] = m.P[ob2 + i];
     sB[2 * kH + i] = m.P[ow3 + i];
   }
-  for (int i = threadIdx.x; i < kIn; i += blockDim.x) {
-    sNorm[i] = m.norm[i];
-    sNorm[kIn + i] = m.norm[2 * kIn + 1 + i];
-  }
   __syncthreads();
-  const MlpView mv{nullptr, nullptr, sB, sB + kH, sB + 2 * kH, m.P[ob3], sNorm, sNorm + kIn};
   const MlpViewQ mq{sW1, sW2, sB, sB + kH, sB + 2 * kH, m.P[ob3]};
   const float scale = m.norm[2 * kIn];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
@@ -791,19 +805,28 @@ __global__ void __launch_bounds__(128) k_mlp_eval(MlpDev m, const float* __restr
   const long long ntiles = (np + 15) / 16;
   for (long long tile = (long long)blockIdx.x * 4 + w; tile < ntiles; tile += (long long)gridDim.x * 4) {
     const long long p0 = tile * 16;
-    for (int e = lane; e < 16 * kIn; e += 32)
-      ft[w][0][e] = p0 + e / kIn < np ? pfeat[p0 * kIn + e] : 0.f;
-    __syncwarp();
-    // the other ordering: (d, s_b, s_a)
-    for (int e = lane; e < 16 * kIn; e += 32) {
-      const int r = e / kIn, k = e % kIn;
-      ft[w][1][e] = ft[w][0][r * kIn + (k == 0 ? 0 : (k < 5 ? k + 4 : k - 4))];
+    // A fragments straight from the pair buffer: rows g, g + 8; words tg (columns 2tg, 2tg+1)
+    // and, for tg = 0, word 4 (columns 8, 9); the other column words are zero padding
+    unsigned ax0[4] = {0u, 0u, 0u, 0u}, ax1[4] = {0u, 0u, 0u, 0u};
+    if (p0 + g < np) {
+      const unsigned* r = pfrag + (p0 + g) * 10;
+      ax0[0] = r[tg];
+      ax1[0] = r[5 + tg];
+      if (tg == 0) {
+        ax0[2] = r[4];
+        ax1[2] = r[9];
+      }
     }
-    __syncwarp();
-    unsigned ax0[4], ax1[4];
+    if (p0 + g + 8 < np) {
+      const unsigned* r = pfrag + (p0 + g + 8) * 10;
+      ax0[1] = r[tg];
+      ax1[1] = r[5 + tg];
+      if (tg == 0) {
+        ax0[3] = r[4];
+        ax1[3] = r[9];
+      }
+    }
     float y[2][2];
-    input_fragment<LdShared>(mv, ft[w][0], ax0);
-    input_fragment<LdShared>(mv, ft[w][1], ax1);
     tile_forward_y2(mq, ax0, ax1, y);
     if (tg == 0) {
       yo[w][0][g] = y[0][0];
@@ -892,8 +915,8 @@ cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* f
   if (e != cudaSuccess) return e;
   const int blocks = ceil_div((long long)s.M * 4, 128);
 #define FEAT(NA_)                                                       \
-  (s.fp64 ? k_mlp_feat<NA_, true><<<blocks, 128, 0, st>>>(s, b)        \
-          : k_mlp_feat<NA_, false><<<blocks, 128, 0, st>>>(s, b))
+  (s.fp64 ? k_mlp_feat<NA_, true><<<blocks, 128, 0, st>>>(s, b, a.norm) \
+          : k_mlp_feat<NA_, false><<<blocks, 128, 0, st>>>(s, b, a.norm))
   switch (s.NA) {
     case 1: FEAT(1); break;
     case 2: FEAT(2); break;
@@ -913,7 +936,7 @@ cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* f
       per_sm = 4;
     grid = per_sm * sms;
   }
-  k_mlp_eval<<<grid, 128, 0, st>>>(m, b.pfeat, b.pslot, b.npair, fpair);
+  k_mlp_eval<<<grid, 128, 0, st>>>(m, b.pfrag, b.pslot, b.npair, fpair);
   return cudaGetLastError();
 }
 
