@@ -36,6 +36,32 @@ RDF_BINS, RDF_DR, RDF_EQ, RDF_SNAPS, RDF_EVERY = 250, 0.02, 500, 5, 100
 CONFIG_NAME = "tetrahedral AdResS fluid, 200k molecules / 800k atoms, 200x100x100 sigma, AT 40 + 2x10 hybrid"
 
 
+def profiled_traffic(profile, sources):
+    """DRAM bytes (read + write) per launch from an ncu summary under profiles/, or None when
+    the kernel's sources changed since the capture (the summary records their hash)."""
+    import hashlib
+    import re
+
+    path = os.path.join(ROOT, "profiles", profile)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"sha256\[:16\] = `([0-9a-f]+)`", txt)
+    h = hashlib.sha256()
+    for name in sources:
+        h.update(open(os.path.join(ROOT, "paper_1806_10841_gb300", "csrc", name), "rb").read())
+    if not m or m.group(1) != h.hexdigest()[:16]:
+        return None
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    total = 0.0
+    for metric in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        r = re.search(r"`" + re.escape(metric) + r"` \| ([0-9.]+) \| (\w+) \|", txt)
+        if not r:
+            return None
+        total += float(r.group(1)) * scale.get(r.group(2), float("nan"))
+    return total
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -402,7 +428,11 @@ def main():
             train_network(sim, feat, t)
             sim.set_cg_mode(1)
         sim.compute_forces(energies=False)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("md_steps")  # ncu --nvtx --nvtx-include md_steps/ selects these launches
         sim.run(args.profile, sample_every=SAMPLE_EVERY, tf_update=True, alpha=TF_ALPHA)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         sim.check()
         print(json.dumps({"profile_steps": args.profile, "atoms": s.N, "lists": sim.list_stats()}))
         sim.close()
@@ -562,7 +592,11 @@ def main():
     roofline = {"bound": "hbm" if bname == "hbm" else "alu", "resource": bname,
                 "kernel": "k_step fused (forces + bonded + TF + Langevin + kicks + drift + mapping)",
                 "achieved": b["achieved"], "peak": b["peak"], "unit": b["unit"], "frac": b["frac"],
-                "traffic": None, "all": cand, "ms_per_launch": kt["step"],
+                "traffic": profiled_traffic("k_step_fused_c2_800k_fp32.md", ("step.cu", "internal.cuh"))
+                if args.precision == "fp32" else None,
+                "traffic_source": "profiles/k_step_fused_c2_800k_fp32.md (one ncu capture, cold cache; "
+                                  "null when the kernel's sources changed since)",
+                "all": cand, "ms_per_launch": kt["step"],
                 "peak_source": {"hbm": f"{src} HBM copy bandwidth",
                                 "alu_fp64": f"152 SMs x 2 DFMA/clk x 2 x {sm_mhz:.0f} MHz (sampled)",
                                 "alu_fp32": f"152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz (sampled)"}}
