@@ -48,6 +48,11 @@ class orc_sys(C.Structure):
         ("kT", C.c_double), ("gamma", C.c_double), ("dt", C.c_double),
         ("seed", C.c_uint64), ("replica", C.c_int64),
         ("mlp", C.POINTER(orc_mlp)),
+        ("nb_model", C.c_int), ("charge", C.POINTER(C.c_double)), ("lj_eps", C.POINTER(C.c_double)),
+        ("lj_sig", C.POINTER(C.c_double)), ("coulomb_f", C.c_double), ("eps_rf", C.c_double),
+        ("bond_model", C.c_int), ("bond_k", C.c_double), ("bond_r0", C.c_double),
+        ("n_angles", C.c_int), ("angles", C.POINTER(C.c_int)), ("angle_k", C.c_double),
+        ("angle_theta0", C.c_double),
     ]
 
 
@@ -134,6 +139,16 @@ class Oracle:
             cgV=np.ascontiguousarray(s.cg_V, dtype=np.float64),
             tf=np.ascontiguousarray(s.tf if s.tf is not None else np.zeros(0), dtype=np.float64),
         )
+        nb_model = int(getattr(s, "nb_model", 0))
+        zeros = np.zeros(self.na)
+        self._keep.update(
+            charge=np.ascontiguousarray(s.charge if nb_model else zeros, dtype=np.float64),
+            lj_eps=np.ascontiguousarray(s.lj_eps if nb_model else zeros, dtype=np.float64),
+            lj_sig=np.ascontiguousarray(s.lj_sig if nb_model else zeros, dtype=np.float64),
+            angles=np.ascontiguousarray(
+                np.asarray(s.angles if getattr(s, "angles", None) is not None else np.zeros((0, 3)),
+                           dtype=np.int32).reshape(-1)),
+        )
         k = self._keep
         self.sys = orc_sys(
             M=self.M, na=self.na, mass=_ptr(k["mass"]), L=(C.c_double * 3)(*s.box),
@@ -142,7 +157,13 @@ class Oracle:
             fene_k=s.fene_k, fene_r0=s.fene_r0, intra_wca=int(s.intra_wca),
             cgF=_ptr(k["cgF"]), cgV=_ptr(k["cgV"]), cg_n=len(k["cgF"]) - 1, cg_dr=s.cg_dr,
             rc_cg=s.rc_cg, tf=_ptr(k["tf"]), tf_n=len(k["tf"]), tf_dx=s.tf_dx,
-            kT=s.kT, gamma=s.gamma, dt=s.dt, seed=int(s.seed), replica=int(replica))
+            kT=s.kT, gamma=s.gamma, dt=s.dt, seed=int(s.seed), replica=int(replica),
+            nb_model=nb_model, charge=_ptr(k["charge"]), lj_eps=_ptr(k["lj_eps"]), lj_sig=_ptr(k["lj_sig"]),
+            coulomb_f=float(getattr(s, "coulomb_f", 0.0)), eps_rf=float(getattr(s, "eps_rf", 1.0)),
+            bond_model=int(getattr(s, "bond_model", 0)), bond_k=float(getattr(s, "bond_k", 0.0)),
+            bond_r0=float(getattr(s, "bond_r0", 0.0)), n_angles=len(k["angles"]) // 3,
+            angles=_ptr(k["angles"], C.c_int), angle_k=float(getattr(s, "angle_k", 0.0)),
+            angle_theta0=float(getattr(s, "angle_theta0", 0.0)))
 
     def set_mlp(self, net):
         """Use the learned CG pair force of `net` (an OracleMLP) in place of the table, or

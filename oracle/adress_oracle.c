@@ -125,6 +125,34 @@ static double wca_fr(const orc_sys* s, double r2, double* V) {
   return 24.0 * s->eps * (2.0 * sr6 * sr6 - sr6) / r2;
 }
 
+/* Atom pair (site i of one molecule, site j of another) of the water-like model:
+ * Lennard-Jones with eps = sqrt(eps_i eps_j), sigma = (sigma_i + sigma_j)/2, potential
+ * shifted so that V(rc) = 0, and reaction-field Coulomb
+ * V = f q_i q_j (1/r + k_rf r^2 - c_rf), k_rf = (eps_rf - 1)/((2 eps_rf + 1) rc^3),
+ * c_rf = 1/rc + k_rf rc^2 (so V(rc) = 0).  Returns F/r, sets V. */
+static double ljrf_fr(const orc_sys* s, int si, int sj, double r2, double* V) {
+  const double rc = s->rc_at;
+  double fr = 0.0, v = 0.0;
+  const double eps = sqrt(s->lj_eps[si] * s->lj_eps[sj]);
+  if (eps > 0.0) {
+    const double sg = 0.5 * (s->lj_sig[si] + s->lj_sig[sj]);
+    const double sr2 = sg * sg / r2, sr6 = sr2 * sr2 * sr2;
+    const double sc2 = sg * sg / (rc * rc), sc6 = sc2 * sc2 * sc2;
+    v += 4.0 * eps * (sr6 * sr6 - sr6) - 4.0 * eps * (sc6 * sc6 - sc6);
+    fr += 24.0 * eps * (2.0 * sr6 * sr6 - sr6) / r2;
+  }
+  const double qq = s->coulomb_f * s->charge[si] * s->charge[sj];
+  if (qq != 0.0) {
+    const double krf = (s->eps_rf - 1.0) / ((2.0 * s->eps_rf + 1.0) * rc * rc * rc);
+    const double crf = 1.0 / rc + krf * rc * rc;
+    const double r = sqrt(r2);
+    v += qq * (1.0 / r + krf * r2 - crf);
+    fr += qq * (1.0 / (r2 * r) - 2.0 * krf);
+  }
+  *V = v;
+  return fr;
+}
+
 /* Linear interpolation in the CG table: returns F(r) (positive = repulsive), sets V. */
 static double cg_table(const orc_sys* s, double r, double* V) {
   double u = r / s->cg_dr;
@@ -166,7 +194,7 @@ static void pair_ab(const orc_sys* s, const double* x, const double* R, const do
           r2 += r[d] * r[d];
         }
         if (r2 >= rc2) continue;
-        double V, fr = wca_fr(s, r2, &V);
+        double V, fr = s->nb_model == 1 ? ljrf_fr(s, i - a * na, j - b * na, r2, &V) : wca_fr(s, r2, &V);
         for (int d = 0; d < 3; ++d) {
           f[3 * i + d] += wab * fr * r[d];
           f[3 * j + d] -= wab * fr * r[d];
@@ -204,16 +232,66 @@ static void pair_ab(const orc_sys* s, const double* x, const double* R, const do
   }
 }
 
-/* Bonded terms of molecule a: FENE (+ optional WCA) on every listed pair, unweighted. */
+/* Harmonic angle (i, vertex j, k) of molecule a: V = k/2 (theta - theta0)^2 with
+ * cos theta = u.v / (|u||v|), u = x_i - x_j, v = x_k - x_j.  F_i = -dV/dtheta dtheta/dx_i,
+ * dtheta/dx_i = -(v/(|u||v|) - cos theta u/|u|^2) / sin theta; F_j = -(F_i + F_k). */
+static void angle_mol(const orc_sys* s, const double* x, int a, double* f, double* e) {
+  const int na = s->na;
+  for (int q = 0; q < s->n_angles; ++q) {
+    const int i = a * na + s->angles[3 * q], j = a * na + s->angles[3 * q + 1], k = a * na + s->angles[3 * q + 2];
+    double u[3], v[3], uu = 0, vv = 0, uv = 0;
+    for (int d = 0; d < 3; ++d) {
+      u[d] = minimg(x[3 * i + d] - x[3 * j + d], s->L[d]);
+      v[d] = minimg(x[3 * k + d] - x[3 * j + d], s->L[d]);
+      uu += u[d] * u[d];
+      vv += v[d] * v[d];
+      uv += u[d] * v[d];
+    }
+    const double nu = sqrt(uu), nv = sqrt(vv);
+    double c = uv / (nu * nv);
+    if (c > 1.0) c = 1.0;
+    if (c < -1.0) c = -1.0;
+    const double th = acos(c), sn = sqrt(1.0 - c * c);
+    const double dV = s->angle_k * (th - s->angle_theta0);
+    e[2] += 0.5 * s->angle_k * (th - s->angle_theta0) * (th - s->angle_theta0);
+    if (sn <= 0.0) continue;
+    const double g = dV / sn;
+    double fi[3], fk[3];
+    for (int d = 0; d < 3; ++d) {
+      fi[d] = g * (v[d] / (nu * nv) - c * u[d] / uu);
+      fk[d] = g * (u[d] / (nu * nv) - c * v[d] / vv);
+      f[3 * i + d] += fi[d];
+      f[3 * k + d] += fk[d];
+      f[3 * j + d] -= fi[d] + fk[d];
+      e[3] += u[d] * fi[d] + v[d] * fk[d];
+    }
+  }
+}
+
+/* Bonded terms of molecule a, unweighted: FENE (+ optional WCA) or harmonic bonds on every
+ * listed pair, and harmonic angles. */
 static int bonded_mol(const orc_sys* s, const double* x, int a, double* f, double* e) {
   const int na = s->na;
   const double R02 = s->fene_r0 * s->fene_r0;
+  if (s->n_angles > 0) angle_mol(s, x, a, f, e);
   for (int q = 0; q < s->nb; ++q) {
     int i = a * na + s->bonds[2 * q], j = a * na + s->bonds[2 * q + 1];
     double r[3], r2 = 0;
     for (int d = 0; d < 3; ++d) {
       r[d] = minimg(x[3 * i + d] - x[3 * j + d], s->L[d]);
       r2 += r[d] * r[d];
+    }
+    if (s->bond_model == 1) {
+      /* harmonic: V = k/2 (r - r0)^2, F/r = -k (r - r0)/r */
+      const double rr = sqrt(r2);
+      const double fr = -s->bond_k * (rr - s->bond_r0) / rr;
+      for (int d = 0; d < 3; ++d) {
+        f[3 * i + d] += fr * r[d];
+        f[3 * j + d] -= fr * r[d];
+      }
+      e[2] += 0.5 * s->bond_k * (rr - s->bond_r0) * (rr - s->bond_r0);
+      e[3] += fr * r2;
+      continue;
     }
     if (r2 >= R02) return ORC_ERR_BOND;
     double g = 1.0 - r2 / R02;
@@ -546,7 +624,7 @@ void orc_pair_features(const orc_sys* s, const double* x, int a, int b, double* 
           r2 += r[d] * r[d];
         }
         if (r2 >= rc2) continue;
-        double V, fr = wca_fr(s, r2, &V);
+        double V, fr = s->nb_model == 1 ? ljrf_fr(s, i - a * s->na, j - b * s->na, r2, &V) : wca_fr(s, r2, &V);
         for (int d = 0; d < 3; ++d) F[d] += fr * r[d];
       }
     *target = -(F[0] * e[0] + F[1] * e[1] + F[2] * e[2]);

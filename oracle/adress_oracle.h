@@ -39,6 +39,17 @@ typedef struct {
   uint64_t seed;
   int64_t replica;
   const orc_mlp* mlp; /* when non-NULL the CG force of Eq. 1 is the learned pair force */
+  /* water-like molecules (nb_model 1): between atoms of different molecules, Lennard-Jones
+   * with Lorentz-Berthelot site pairs, shifted to zero at rc_at, plus reaction-field
+   * Coulomb; bond_model 1: harmonic bonds on the listed pairs; harmonic angles */
+  int nb_model;
+  const double *charge, *lj_eps, *lj_sig; /* na each */
+  double coulomb_f, eps_rf;
+  int bond_model;
+  double bond_k, bond_r0;
+  int n_angles;
+  const int* angles; /* 3 * n_angles local indices (i, vertex, k) */
+  double angle_k, angle_theta0;
 } orc_sys;
 
 void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

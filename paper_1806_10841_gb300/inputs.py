@@ -1,4 +1,4 @@
-"""Seeded synthetic inputs for the tetrahedral AdResS fluid.
+"""Seeded synthetic inputs for the tetrahedral AdResS fluid and the water-like fluid.
 
 This module only *builds inputs*: the molecular geometry, the initial lattice with
 jitter, Maxwell-Boltzmann velocities, the tabulated coarse-grained (CG) pair potential
@@ -57,6 +57,21 @@ class System:
     seed: int = 20180628
     skin: float = 0.3
     r_ext: float = 0.75         # bound on atom-to-COM distance used for list cutoffs
+    # water-like molecules: nb_model 1 = Lennard-Jones (per-site eps/sigma, Lorentz-Berthelot)
+    # + reaction-field Coulomb between atoms of different molecules, cutoff rc_at;
+    # bond_model 1 = harmonic bonds (bond_k, bond_r0); harmonic angles
+    nb_model: int = 0
+    charge: np.ndarray = None   # (na,) site charges (e)
+    lj_eps: np.ndarray = None   # (na,) site LJ epsilon
+    lj_sig: np.ndarray = None   # (na,) site LJ sigma
+    coulomb_f: float = 0.0      # 1/(4 pi eps0) in the model's units
+    eps_rf: float = 1.0         # reaction-field dielectric constant
+    bond_model: int = 0
+    bond_k: float = 0.0
+    bond_r0: float = 0.0
+    angles: np.ndarray = None   # (n_angles, 3) int32 local indices (i, vertex, k)
+    angle_k: float = 0.0
+    angle_theta0: float = 0.0
 
     @property
     def N(self) -> int:
@@ -178,7 +193,7 @@ def _close_pairs(pos, occ, n, L, active, thr):
 
 
 def tetra_state(s: System, *, edge: float = 0.97, jitter: float = 0.1, seed: int | None = None,
-                min_contact: float = 1.0, max_rounds: int = 200):
+                min_contact: float = 1.0, max_rounds: int = 200, body: np.ndarray | None = None):
     """Initial positions and velocities, both (N, 3) float64.
 
     Molecule centres sit on a simple-cubic lattice filling the box (M sites chosen at
@@ -203,7 +218,8 @@ def tetra_state(s: System, *, edge: float = 0.97, jitter: float = 0.1, seed: int
     sites = (site_idx + 0.5) * (L / n)
     occ = -np.ones(tuple(n), dtype=np.int64)
     occ[tuple(site_idx.T)] = np.arange(s.M)
-    body = tetra_sites(edge) if s.na == 4 else np.zeros((s.na, 3))
+    if body is None:
+        body = tetra_sites(edge) if s.na == 4 else np.zeros((s.na, 3))
     com = sites + rng.uniform(-jitter, jitter, size=(s.M, 3))
     pos = com[:, None, :] + np.einsum("mij,kj->mki", random_rotations(rng, s.M), body)
     if min_contact > 0 and s.M > 1:
@@ -229,6 +245,77 @@ def tetra_state(s: System, *, edge: float = 0.97, jitter: float = 0.1, seed: int
 
 
 # --- named workloads ---------------------------------------------------------------
+
+# --- water-like fluid (flexible three-site model, reaction-field electrostatics) -------
+# Units: nm, ps, atomic mass units, kJ/mol, elementary charges.
+
+WATER_MASS = np.array([15.9994, 1.008, 1.008])      # O, H, H
+WATER_CHARGE = np.array([-0.8476, 0.4238, 0.4238])
+WATER_R0 = 0.1                                      # O-H bond length (nm)
+WATER_THETA0 = math.radians(109.47)                 # H-O-H angle
+COULOMB_F = 138.935458                              # 1 / (4 pi eps0) in kJ mol^-1 nm e^-2
+KB = 0.0083144626                                   # kJ mol^-1 K^-1
+
+
+def water_sites() -> np.ndarray:
+    """O and the two H of the equilibrium geometry, relative to the centre of mass (3, 3)."""
+    h = 0.5 * WATER_THETA0
+    x = np.array([[0.0, 0.0, 0.0],
+                  [WATER_R0 * math.sin(h), WATER_R0 * math.cos(h), 0.0],
+                  [-WATER_R0 * math.sin(h), WATER_R0 * math.cos(h), 0.0]])
+    return x - (WATER_MASS[:, None] * x).sum(0) / WATER_MASS.sum()
+
+
+def water_system(M: int, box, at_width: float, hy_width: float, *, tf_bins: int | None = None,
+                 **kw) -> System:
+    """Flexible three-site water-like fluid: O-H bonds harmonic (k = 345000 kJ mol^-1 nm^-2,
+    r0 = 0.1 nm), H-O-H angle harmonic at 109.47 degrees (k_theta = 383 kJ mol^-1 rad^-2),
+    Lennard-Jones on O (sigma = 0.3166 nm, eps = 0.65 kJ/mol) and reaction-field Coulomb
+    (rc = 0.9 nm, eps_rf = 80) between atoms of different molecules; a tabulated single-bead
+    COM potential for the CG model (placeholder Lennard-Jones-like table unless `cg_F`/`cg_V`
+    are given); Langevin at 300 K (gamma = 5 / ps), dt = 0.5 fs.  Slab as in tetra_system."""
+    box = tuple(float(b) for b in box)
+    rc_cg = kw.pop("rc_cg", 0.9)
+    dr = kw.pop("cg_dr", 0.0005)
+    cg = {k: kw.pop(k) for k in ("cg_F", "cg_V") if k in kw}
+    if not cg:
+        F, V = lj_cg_table(0.65, 0.3166, rc_cg, dr, r_min=0.2)
+        cg = dict(cg_F=F, cg_V=V)
+    tf_dx = kw.pop("tf_dx", 0.05)
+    d_at, d_hy = 0.5 * at_width, hy_width
+    if tf_bins is None:
+        tf_bins = int(math.ceil((d_at + d_hy) / tf_dx)) + 2
+    params = dict(eps=0.0, sigma=1.0, rc_at=0.9, fene_k=0.0, fene_r0=1.0, intra_wca=0, cg_dr=dr, rc_cg=rc_cg,
+                  tf_dx=tf_dx, kT=KB * 300.0, gamma=5.0, dt=0.0005, skin=0.1, r_ext=0.15,
+                  nb_model=1, charge=WATER_CHARGE.copy(), lj_eps=np.array([0.65, 0.0, 0.0]),
+                  lj_sig=np.array([0.3166, 0.0, 0.0]), coulomb_f=COULOMB_F, eps_rf=80.0,
+                  bond_model=1, bond_k=345000.0, bond_r0=WATER_R0,
+                  angles=np.array([[1, 0, 2]], dtype=np.int32), angle_k=383.0, angle_theta0=WATER_THETA0)
+    params.update(kw)
+    return System(M=M, na=3, box=box, mass=WATER_MASS.copy(), bonds=np.array([[0, 1], [0, 2]], dtype=np.int32),
+                  xc=0.5 * box[0], d_at=d_at, d_hy=d_hy, tf=np.zeros(tf_bins), **cg, **params)
+
+
+def water_state(s: System, *, seed: int | None = None, jitter: float = 0.01, min_contact: float = 0.17):
+    """Initial state of the water-like fluid: molecules at lattice sites in random
+    orientations (orientations redrawn until no atom of another molecule is closer than
+    min_contact), Maxwell-Boltzmann velocities at kT."""
+    return tetra_state(s, seed=seed, jitter=jitter, min_contact=min_contact, body=water_sites())
+
+
+def c3_water(**kw) -> System:
+    """64,000 water-like molecules (192,000 atoms) at 33.4 molecules/nm^3 in 19.72 x 9.86 x
+    9.86 nm; AT width 3 nm, hybrid 1.5 nm each side."""
+    return water_system(64_000, (19.72, 9.86, 9.86), 3.0, 1.5, **kw)
+
+
+def scaled_c3(M: int, **kw) -> System:
+    """The water workload's shape (33.4 molecules/nm^3, box 2:1:1, AT 15% / hybrid 2x7.6% of
+    Lx) at M molecules."""
+    Ly = (M / 33.4 / 2.0) ** (1.0 / 3.0)
+    Lx = 2 * Ly
+    return water_system(M, (Lx, Ly, Ly), 3.0 / 19.72 * Lx, 1.5 / 19.72 * Lx, **kw)
+
 
 def c1_literal(**kw) -> System:
     """1000 tetrahedra (4000 atoms) in a 20x10x10 box, AT width 5, hybrid 2.5 (density 0.5/sigma^3)."""
