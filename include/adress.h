@@ -99,6 +99,25 @@ typedef struct {
   double skin, r_ext;
   int32_t max_neighbors; /* initial list capacity per molecule; 0 = automatic */
   int32_t precision;     /* adress_precision */
+  /* ---- water-like molecules (all zero: the WCA/FENE model above) ----
+   * nb_model 1 (three atoms per molecule): between atoms of different molecules within rc_at,
+   * Lennard-Jones with eps_ij = sqrt(lj_eps_i lj_eps_j), sigma_ij = (lj_sigma_i + lj_sigma_j)/2,
+   * shifted so that V(rc_at) = 0, plus reaction-field Coulomb
+   * V = coulomb_f q_i q_j (1/r + k_rf r^2 - c_rf), k_rf = (eps_rf - 1)/((2 eps_rf + 1) rc_at^3),
+   * c_rf = 1/rc_at + k_rf rc_at^2 (wca_eps, wca_sigma unused).  Intramolecular nonbonded
+   * pairs are excluded. */
+  int32_t nb_model;
+  const double* charge;   /* host [na] site charges */
+  const double* lj_eps;   /* host [na] >= 0 */
+  const double* lj_sigma; /* host [na] */
+  double coulomb_f, eps_rf;
+  /* bond_model 1: harmonic V = bond_k/2 (r - bond_r0)^2 on the listed pairs (fene_* unused);
+   * angles: V = angle_k/2 (theta - angle_theta0)^2 for each (i, vertex j, k), at most 4 */
+  int32_t bond_model;
+  double bond_k, bond_r0;
+  int32_t n_angles;
+  const int32_t* angles; /* host [3*n_angles] local atom indices */
+  double angle_k, angle_theta0;
 } adress_config;
 
 /* Validate `cfg`, copy its tables, allocate the handle's device buffers on the current

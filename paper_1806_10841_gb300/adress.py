@@ -55,6 +55,11 @@ class adress_config(C.Structure):
         ("seed", C.c_uint64), ("replica", C.c_int64),
         ("skin", C.c_double), ("r_ext", C.c_double),
         ("max_neighbors", C.c_int32), ("precision", C.c_int32),
+        ("nb_model", C.c_int32), ("charge", C.POINTER(C.c_double)), ("lj_eps", C.POINTER(C.c_double)),
+        ("lj_sigma", C.POINTER(C.c_double)), ("coulomb_f", C.c_double), ("eps_rf", C.c_double),
+        ("bond_model", C.c_int32), ("bond_k", C.c_double), ("bond_r0", C.c_double),
+        ("n_angles", C.c_int32), ("angles", C.POINTER(C.c_int32)), ("angle_k", C.c_double),
+        ("angle_theta0", C.c_double),
     ]
 
 
@@ -134,6 +139,14 @@ def _config(s, keep, replica, max_neighbors, precision):
         cgV=np.ascontiguousarray(s.cg_V, dtype=np.float64),
         tf=np.ascontiguousarray(s.tf if s.tf is not None else np.zeros(0), dtype=np.float64),
     )
+    nb_model = int(getattr(s, "nb_model", 0))
+    ang = getattr(s, "angles", None)
+    arrs.update(
+        charge=np.ascontiguousarray(s.charge if nb_model else np.zeros(s.na), dtype=np.float64),
+        lj_eps=np.ascontiguousarray(s.lj_eps if nb_model else np.zeros(s.na), dtype=np.float64),
+        lj_sig=np.ascontiguousarray(s.lj_sig if nb_model else np.zeros(s.na), dtype=np.float64),
+        angles=np.ascontiguousarray(np.asarray(ang if ang is not None else np.zeros((0, 3)), dtype=np.int32).reshape(-1)),
+    )
     keep.append(arrs)
     tf_n = len(arrs["tf"])
     return adress_config(
@@ -146,7 +159,13 @@ def _config(s, keep, replica, max_neighbors, precision):
         tf=_dptr(arrs["tf"]) if tf_n else None, tf_n=tf_n, tf_dx=s.tf_dx,
         kT=s.kT, gamma=s.gamma, dt=s.dt, seed=int(s.seed), replica=int(replica), skin=s.skin,
         r_ext=s.r_ext, max_neighbors=int(max_neighbors),
-        precision=ADRESS_FP64 if precision == "fp64" else ADRESS_FP32_MIXED)
+        precision=ADRESS_FP64 if precision == "fp64" else ADRESS_FP32_MIXED,
+        nb_model=nb_model, charge=_dptr(arrs["charge"]), lj_eps=_dptr(arrs["lj_eps"]), lj_sigma=_dptr(arrs["lj_sig"]),
+        coulomb_f=float(getattr(s, "coulomb_f", 0.0)), eps_rf=float(getattr(s, "eps_rf", 1.0)),
+        bond_model=int(getattr(s, "bond_model", 0)), bond_k=float(getattr(s, "bond_k", 0.0)),
+        bond_r0=float(getattr(s, "bond_r0", 0.0)), n_angles=len(arrs["angles"]) // 3,
+        angles=arrs["angles"].ctypes.data_as(C.POINTER(C.c_int32)), angle_k=float(getattr(s, "angle_k", 0.0)),
+        angle_theta0=float(getattr(s, "angle_theta0", 0.0)))
 
 
 class AdResS:

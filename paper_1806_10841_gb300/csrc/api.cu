@@ -183,6 +183,26 @@ static std::string config_error(const adress_config* c) {
   if (!(c->dt > 0) || c->gamma < 0 || c->kT < 0) return "dt, gamma, kT invalid";
   if (c->precision != ADRESS_FP64 && c->precision != ADRESS_FP32_MIXED) return "unknown precision";
   if (!(c->skin >= 0) || !(c->r_ext >= 0) || !(c->rc_at > 0) || !(c->rc_cg > 0)) return "cutoffs invalid";
+  if (c->nb_model != 0 && c->nb_model != 1) return "nb_model must be 0 or 1";
+  if (c->nb_model == 1) {
+    if (c->atoms_per_mol != 3) return "nb_model 1 needs three atoms per molecule";
+    if (!c->charge || !c->lj_eps || !c->lj_sigma) return "nb_model 1 needs charge, lj_eps and lj_sigma";
+    for (int k = 0; k < c->atoms_per_mol; ++k)
+      if (!(c->lj_eps[k] >= 0) || !(c->lj_sigma[k] >= 0) || !(c->charge[k] == c->charge[k]))
+        return "lj_eps, lj_sigma must be >= 0 and charges finite";
+    if (!(c->coulomb_f >= 0) || !(c->eps_rf >= 1)) return "coulomb_f must be >= 0 and eps_rf >= 1";
+  }
+  if (c->bond_model != 0 && c->bond_model != 1) return "bond_model must be 0 or 1";
+  if (c->bond_model == 1 && (!(c->bond_k >= 0) || !(c->bond_r0 > 0))) return "bond_k >= 0 and bond_r0 > 0 needed";
+  if (c->n_angles < 0 || c->n_angles > kMaxAngles || (c->n_angles > 0 && !c->angles)) return "n_angles must be 0..4 with an angle array";
+  for (int q = 0; q < c->n_angles; ++q) {
+    const int* t = c->angles + 3 * q;
+    if (t[0] < 0 || t[1] < 0 || t[2] < 0 || t[0] >= c->atoms_per_mol || t[1] >= c->atoms_per_mol ||
+        t[2] >= c->atoms_per_mol || t[0] == t[1] || t[1] == t[2] || t[0] == t[2])
+      return "angle indices out of range or repeated";
+  }
+  if (c->n_angles > 0 && (!(c->angle_k >= 0) || !(c->angle_theta0 > 0) || !(c->angle_theta0 <= M_PI)))
+    return "angle_k >= 0 and 0 < angle_theta0 <= pi needed";
   return "";
 }
 
@@ -205,6 +225,15 @@ static std::string shared_mismatch(const adress_config* a, const adress_config* 
   if (c->kT != a->kT || c->gamma != a->gamma || c->dt != a->dt || c->seed != a->seed) return "thermostat";
   if (c->skin != a->skin || c->r_ext != a->r_ext || c->max_neighbors != a->max_neighbors) return "list parameters";
   if (c->precision != a->precision) return "precision";
+  if (c->nb_model != a->nb_model || c->coulomb_f != a->coulomb_f || c->eps_rf != a->eps_rf) return "nonbonded model";
+  for (int k = 0; k < a->atoms_per_mol && a->nb_model == 1; ++k)
+    if (c->charge[k] != a->charge[k] || c->lj_eps[k] != a->lj_eps[k] || c->lj_sigma[k] != a->lj_sigma[k])
+      return "site parameters";
+  if (c->bond_model != a->bond_model || c->bond_k != a->bond_k || c->bond_r0 != a->bond_r0 ||
+      c->n_angles != a->n_angles || c->angle_k != a->angle_k || c->angle_theta0 != a->angle_theta0)
+    return "bonded model";
+  for (int q = 0; q < 3 * a->n_angles; ++q)
+    if (c->angles[q] != a->angles[q]) return "angle list";
   return "";
 }
 
@@ -407,6 +436,38 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   s.f.fene_k = (float)s.fene_k;
   s.f.fene_r02 = (float)s.fene_r02;
   s.f.tf_inv_dx = (float)s.tf_inv_dx;
+  s.nb_model = c->nb_model;
+  if (c->nb_model == 1) {
+    const double rc = c->rc_at;
+    s.krf = (c->eps_rf - 1.0) / ((2.0 * c->eps_rf + 1.0) * rc * rc * rc);
+    s.crf = 1.0 / rc + s.krf * rc * rc;
+    for (int i = 0; i < s.NA; ++i)
+      for (int j = 0; j < s.NA; ++j) {
+        const double e = sqrt(c->lj_eps[i] * c->lj_eps[j]);
+        const double sg = 0.5 * (c->lj_sigma[i] + c->lj_sigma[j]);
+        const double s6 = sg * sg * sg * sg * sg * sg;
+        s.c12[i][j] = 4.0 * e * s6 * s6;
+        s.c6[i][j] = 4.0 * e * s6;
+        const double ir6 = 1.0 / (rc * rc * rc * rc * rc * rc);
+        s.vsh[i][j] = -(s.c12[i][j] * ir6 - s.c6[i][j]) * ir6;
+        s.qq[i][j] = c->coulomb_f * c->charge[i] * c->charge[j];
+        s.f.c12[i][j] = (float)s.c12[i][j];
+        s.f.c6[i][j] = (float)s.c6[i][j];
+        s.f.qq[i][j] = (float)s.qq[i][j];
+      }
+    s.f.krf2 = (float)(2.0 * s.krf);
+  }
+  s.bond_model = c->bond_model;
+  s.bond_k = c->bond_k;
+  s.bond_r0 = c->bond_r0;
+  s.n_angles = c->n_angles;
+  for (int q = 0; q < 3 * kMaxAngles; ++q) s.angles[q] = q < 3 * c->n_angles ? c->angles[q] : 0;
+  s.angle_k = c->angle_k;
+  s.angle_theta0 = c->angle_theta0;
+  s.f.bond_k = (float)c->bond_k;
+  s.f.bond_r0 = (float)c->bond_r0;
+  s.f.angle_k = (float)c->angle_k;
+  s.f.angle_theta0 = (float)c->angle_theta0;
 
   std::vector<int> nmol(nbox);
   h->boxes.resize(nbox);
@@ -454,6 +515,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   }
   A(b.mcell, M);
   A(b.sorted, M);
+  A(b.fill_tmp, M);
   A(b.flag, M);
   A(b.pos, M + 1);
   A(b.items, M);

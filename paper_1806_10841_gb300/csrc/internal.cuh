@@ -12,6 +12,7 @@ namespace adress {
 
 constexpr int kMaxNA = 4;
 constexpr int kMaxBonds = 6;
+constexpr int kMaxAngles = 4;
 constexpr int kGroup = 4;  // threads per molecule in the force kernel
 
 // Device control block: list-validity trackers, error word, counters.
@@ -87,13 +88,27 @@ struct Sys {
   int force_block;  // threads per block of the mapping and force kernels
   int cg_mode;  // 0: tabulated F^CG, 1: learned network (pair forces in Bufs::fpair)
   double dt_m[kMaxNA];  // dt / m (both half kicks of a fused step)
+  // water-like model (nb_model 1): site-pair Lennard-Jones c12 = 4 eps sigma^12,
+  // c6 = 4 eps sigma^6, LJ energy shift, f q_i q_j; reaction field k_rf, c_rf
+  int nb_model;
+  double c12[kMaxNA][kMaxNA], c6[kMaxNA][kMaxNA], vsh[kMaxNA][kMaxNA], qq[kMaxNA][kMaxNA];
+  double krf, crf;
+  // bonded: bond_model 0 FENE (+ WCA), 1 harmonic (bond_k, bond_r0); harmonic angles
+  int bond_model;
+  double bond_k, bond_r0;
+  int n_angles;
+  int angles[3 * kMaxAngles];
+  double angle_k, angle_theta0;
   // float copies of the parameters the FP32 path uses (no run-time double->float work)
   struct {
     float eps, sig2, rc_at, rc_at2, rc_cg2, cg_inv_dr, fene_k, fene_r02;
     float tf_inv_dx;
     float frac[kMaxNA];
+    float c12[kMaxNA][kMaxNA], c6[kMaxNA][kMaxNA], qq[kMaxNA][kMaxNA];
+    float krf2, bond_k, bond_r0, angle_k, angle_theta0;
   } f;
 };
+static_assert(sizeof(Sys) <= 4096, "Sys is passed by value as a kernel parameter");
 
 // Device buffers owned by the handle.
 struct Bufs {
@@ -115,7 +130,8 @@ struct Bufs {
   int* cell_count;  // [ncell]
   int* cell_fill;   // [ncell]
   int* cell_start;  // [ncell+1]
-  int* sorted;      // molecules grouped by cell, cells in Morton order
+  int* sorted;      // molecules grouped by cell, cells in Morton order, each cell in id order
+  int* fill_tmp;    // [M] cell-grouped molecules in fill (arbitrary) order
   int* flag;        // [M] high-resolution candidate flag at sorted positions
   int* pos;         // [M] exclusive scan of flag
   int* items;       // [M] work items: high-resolution candidates first, then CG

@@ -1,8 +1,8 @@
 // Neighbour search on the GPU: a linked-cell list over molecule centres of mass (the
 // paper's linked-cell-list neighbour search, Sec. "Heterogeneous Spatial Domain
 // Decomposition Algorithm", here on one GPU).  Cells are ranked in Morton order;
-// molecules are counting-sorted by cell and each cell's members are taken in id order
-// when lists are built, so every list is deterministic; molecules are split into two work lists — high-resolution
+// molecules are counting-sorted by cell and each cell's members are then put in id order,
+// so every list is deterministic; molecules are split into two work lists — high-resolution
 // candidates (|dxc| < d_at + d_hy + skin/2) first, then coarse-grained molecules —
 // and each work item gets a full Verlet list of molecules within r_list.
 #include "internal.cuh"
@@ -143,7 +143,23 @@ __global__ void k_rb_fill(const __grid_constant__ Sys s, Bufs b) {
   if (a >= s.M) return;
   const int r = b.mcell[a];
   const int p = b.cell_start[r] + atomicAdd(&b.cell_fill[r], 1);
-  b.sorted[p] = a;
+  b.fill_tmp[p] = a;
+}
+
+// One warp per cell: each member's position in the cell is the number of members with a
+// smaller id (ids are distinct), so the cell's slice of `sorted` is in increasing id.
+constexpr int kSortWarps = 4;
+__global__ void __launch_bounds__(32 * kSortWarps) k_rb_sortcell(const __grid_constant__ Sys s, Bufs b) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kSortWarps + (threadIdx.x >> 5);
+  if (r >= s.ncell) return;
+  const int ps = b.cell_start[r], pe = b.cell_start[r + 1];
+  for (int p = ps + lane; p < pe; p += 32) {
+    const int a = b.fill_tmp[p];
+    int rank = 0;
+    for (int q = ps; q < pe; ++q) rank += b.fill_tmp[q] < a;
+    b.sorted[ps + rank] = a;
+  }
 }
 
 __global__ void k_rb_flag(const __grid_constant__ Sys s, Bufs b) {
@@ -169,62 +185,20 @@ __global__ void k_rb_items(const __grid_constant__ Sys s, Bufs b) {
   b.item_of[a] = t;
 }
 
-// Verlet list of one molecule a (work item t) scanned directly from global memory: every
-// other molecule whose centre lies within r_list, over the 27 neighbour cells (fewer when
-// a dimension has < 3 cells) in fixed order, each cell's members in id order.
-__device__ void scan_neighbours(const Sys& s, const Bufs& b, const int4* com, int a, int t) {
-  const int4 C = com[a];
-  const Box& B = box_of(s, b, a);
-  const int c0 = cell_of((unsigned)C.x, B.nc[0]), c1 = cell_of((unsigned)C.y, B.nc[1]),
-            c2 = cell_of((unsigned)C.z, B.nc[2]);
-  const float rl2 = (float)s.r_list2;
-  int cnt = 0;
-  const int lo0 = B.nc[0] >= 3 ? -1 : 0, lo1 = B.nc[1] >= 3 ? -1 : 0, lo2 = B.nc[2] >= 3 ? -1 : 0;
-  const int hi0 = B.nc[0] >= 2 ? 1 : 0, hi1 = B.nc[1] >= 2 ? 1 : 0, hi2 = B.nc[2] >= 2 ? 1 : 0;
-  for (int o0 = lo0; o0 <= hi0; ++o0) {
-    const int x = (c0 + o0 + B.nc[0]) % B.nc[0];
-    for (int o1 = lo1; o1 <= hi1; ++o1) {
-      const int y = (c1 + o1 + B.nc[1]) % B.nc[1];
-      for (int o2 = lo2; o2 <= hi2; ++o2) {
-        const int z = (c2 + o2 + B.nc[2]) % B.nc[2];
-        const int r = b.cell_rank[B.cell0 + (x * B.nc[1] + y) * B.nc[2] + z];
-        const int ps = b.cell_start[r], pe = b.cell_start[r + 1];
-        // members in increasing id (cells are filled in no fixed order)
-        int last = -1;
-        for (int rep = ps; rep < pe; ++rep) {
-          int m = 0x7fffffff;
-          for (int p = ps; p < pe; ++p) {
-            const int id = b.sorted[p];
-            if (id > last && id < m) m = id;
-          }
-          last = m;
-          if (m == a) continue;
-          const int4 D = com[m];
-          const float d0 = (float)(int)((unsigned)C.x - (unsigned)D.x) * B.fx_scale[0];
-          const float d1 = (float)(int)((unsigned)C.y - (unsigned)D.y) * B.fx_scale[1];
-          const float d2 = (float)(int)((unsigned)C.z - (unsigned)D.z) * B.fx_scale[2];
-          if (d0 * d0 + d1 * d1 + d2 * d2 < rl2) {
-            if (cnt < s.cap) b.nbr[(size_t)t * s.cap + cnt] = m;
-            ++cnt;
-          }
-        }
-      }
-    }
-  }
-  b.nn[t] = cnt < s.cap ? cnt : s.cap;
-  b.com_ref[a] = C;
-  if (cnt > s.cap) set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, cnt);
-}
-
 // One warp per cell (cells in Morton order).  Lanes 0..26 take the 27 neighbour cells in
-// the fixed (ox, oy, oz) order, a warp scan gives each cell's offset in the candidate
-// list, and the candidates (centre + id) are staged in shared memory once; each molecule
-// of the cell then tests all candidates in parallel and appends its neighbours in
-// candidate order with ballot/popc compaction — the same lists scan_neighbours builds.
+// the fixed (ox, oy, oz) order and a warp scan gives each cell's offset in the candidate
+// list.  Candidates (centre + id) are staged in shared memory kMaxCand at a time; each
+// molecule of the home cell tests a staged chunk in parallel and appends its neighbours in
+// candidate order with ballot/popc compaction, its running count kept in shared memory
+// (home molecules in batches of kMaxHome): lists in candidate order for any density.
 constexpr int kNbrWarps = 4;
-constexpr int kMaxCand = 256;  // typical neighbourhoods hold ~70 (denser ones use the scan)
+constexpr int kMaxCand = 256;  // candidates staged per chunk
+constexpr int kMaxHome = 128;  // home-cell molecules per batch
 __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant__ Sys s, Bufs b) {
   __shared__ int4 stage[kNbrWarps][kMaxCand];
+  __shared__ int4 home[kNbrWarps][kMaxHome];  // centre + work item
+  __shared__ int hitem[kNbrWarps][kMaxHome];
+  __shared__ int hcnt[kNbrWarps][kMaxHome];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * kNbrWarps + w;
   if (r >= s.ncell) return;  // warp-uniform
@@ -257,58 +231,68 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
   const int n_home = __shfl_sync(0xffffffffu, cnt, 13);
   const int home_start = __shfl_sync(0xffffffffu, start, 13);
   if (n_home == 0) return;
-  if (total > kMaxCand) {  // over-dense neighbourhood: per-molecule scan
-    for (int h = lane; h < n_home; h += 32) {
-      const int a = b.sorted[home_start + h];
-      scan_neighbours(s, b, com, a, b.item_of[a]);
-    }
-    return;
-  }
-  // lane j stages the members of neighbour cell j at its offset in the candidate list,
-  // in increasing molecule id (the cell's fill order is not deterministic)
-  for (int q = 0; q < cnt; ++q) {
-    const int m = b.sorted[start + q];
-    const int4 C = com[m];
-    int p = pre + q;
-    while (p > pre && stage[w][p - 1].w > m) {
-      stage[w][p] = stage[w][p - 1];
-      --p;
-    }
-    stage[w][p] = make_int4(C.x, C.y, C.z, m);
-  }
-  __syncwarp();
-  // the home cell is neighbour 13: its molecules, centres and work items, fetched at once
-  const int home_pre = __shfl_sync(0xffffffffu, pre, 13);
-  int my_item = 0;
-  if (lane < n_home) my_item = b.item_of[stage[w][home_pre + lane].w];
   const float rl2 = (float)s.r_list2;
-  for (int h = 0; h < n_home; ++h) {
-    const int4 H = stage[w][home_pre + h];
-    const int a = H.w;
-    const int t = h < 32 ? __shfl_sync(0xffffffffu, my_item, h) : b.item_of[a];
-    int count = 0;
-    for (int k0 = 0; k0 < total; k0 += 32) {
-      const int k = k0 + lane;
-      bool hit = false;
-      int m = 0;
-      if (k < total) {
-        const int4 D = stage[w][k];
-        m = D.w;
-        const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * B.fx_scale[0];
-        const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * B.fx_scale[1];
-        const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * B.fx_scale[2];
-        hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < rl2;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, hit);
-      if (hit) {
-        const int p = count + __popc(bal & ((1u << lane) - 1u));
-        if (p < s.cap) b.nbr[(size_t)t * s.cap + p] = m;
-      }
-      count += __popc(bal);
+  // home molecules in batches of kMaxHome (one batch unless the cell is over-dense)
+  for (int hb = 0; hb < n_home; hb += kMaxHome) {
+    const int nh = min(kMaxHome, n_home - hb);
+    __syncwarp();
+    for (int h = lane; h < nh; h += 32) {
+      const int a = b.sorted[home_start + hb + h];
+      const int4 C = com[a];
+      home[w][h] = make_int4(C.x, C.y, C.z, a);
+      hitem[w][h] = b.item_of[a];
+      hcnt[w][h] = 0;
     }
-    if (lane == 0) {
-      b.nn[t] = count < s.cap ? count : s.cap;
-      b.com_ref[a] = make_int4(H.x, H.y, H.z, 0);
+    for (int c0 = 0; c0 < total; c0 += kMaxCand) {
+      __syncwarp();
+      // lane j stages the part of neighbour cell j's members (in id order) inside the window
+      if (lane < 27) {
+        const int lo = max(pre, c0), hi = min(pre + cnt, c0 + kMaxCand);
+#pragma unroll 1
+        for (int k = lo; k < hi; ++k) {
+          const int m = b.sorted[start + (k - pre)];
+          const int4 C = com[m];
+          stage[w][k - c0] = make_int4(C.x, C.y, C.z, m);
+        }
+      }
+      __syncwarp();
+      const int nc = min(kMaxCand, total - c0);
+#pragma unroll 1
+      for (int h = 0; h < nh; ++h) {
+        const int4 H = home[w][h];
+        const int a = H.w;
+        const int tt = hitem[w][h];
+        int count = hcnt[w][h];
+        for (int k0 = 0; k0 < nc; k0 += 32) {
+          const int k = k0 + lane;
+          bool hit = false;
+          int m = 0;
+          if (k < nc) {
+            const int4 D = stage[w][k];
+            m = D.w;
+            const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * B.fx_scale[0];
+            const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * B.fx_scale[1];
+            const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * B.fx_scale[2];
+            hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < rl2;
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, hit);
+          if (hit) {
+            const int p = count + __popc(bal & ((1u << lane) - 1u));
+            if (p < s.cap) b.nbr[(size_t)tt * s.cap + p] = m;
+          }
+          count += __popc(bal);
+        }
+        if (lane == 0) hcnt[w][h] = count;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    for (int h = lane; h < nh; h += 32) {
+      const int4 H = home[w][h];
+      const int count = hcnt[w][h];
+      const int tt = hitem[w][h];
+      b.nn[tt] = count < s.cap ? count : s.cap;
+      b.com_ref[H.w] = make_int4(H.x, H.y, H.z, 0);
       if (count > s.cap) set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, count);
     }
   }
@@ -367,6 +351,7 @@ cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st) {
       cudaSuccess)
     return e;
   k_rb_fill<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
+  k_rb_sortcell<<<ceil_div(s.ncell, kSortWarps), 32 * kSortWarps, 0, st>>>(s, b);
   k_rb_flag<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   if ((e = exclusive_scan(b.flag, b.pos, s.M, b.scan_tmp, b.pos + s.M, st)) != cudaSuccess) return e;
   k_rb_items<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
