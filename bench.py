@@ -328,6 +328,32 @@ def learned_arm(s, x0, v0, make, timed, steps, device):
                                  "L2 = sqrt(sum (g1 - g2)^2 dr)"}}
 
 
+def water_arm(timed, steps, local):
+    """The water-like fluid (64,000 flexible three-site molecules, 192,000 atoms; Lennard-Jones
+    + reaction-field Coulomb, harmonic bonds and angle; AT 3 nm + 2 x 1.5 nm hybrid), FP32
+    mixed and FP64 paths timed on the same bench step, force error of both against the
+    oracle on the initial state."""
+    import oracle
+    from paper_1806_10841_gb300 import adress, inputs
+
+    s = inputs.c3_water()
+    x, v = inputs.water_state(s)
+    out = {"atoms": s.N, "molecules": s.M, "box_nm": list(s.box), "dt_ps": s.dt}
+    f_ref, _ = oracle.Oracle(s).forces(x)
+    for prec in ("fp32", "fp64"):
+        sim = adress.AdResS(s, precision=prec, device=f"cuda:{local}")
+        sim.set_state(x, v)
+        fg, _ = sim.forces()
+        err = math.sqrt(((fg - f_ref) ** 2).sum() / (f_ref ** 2).sum())
+        sim.set_state(x, v)
+        sim.compute_forces(energies=False)
+        tot, _, _ = timed(sim, steps, 2)
+        out[prec] = {"value": s.N * MD_PER_BLOCK * steps / tot, "unit": "atom-steps/s",
+                     "force_rel_rms_vs_fp64_oracle": err, "lists": sim.list_stats()}
+        sim.close()
+    return out
+
+
 def replicas_arm(timed, steps, local):
     """64 independent replicas (log-uniform 500..20000 molecules, AT width U(3, 15), hybrid
     U(1, 5)) in one handle: every MD step is one launch over all replicas' molecules, the
@@ -390,6 +416,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 GPU comparison arm")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-CG-force arm")
     ap.add_argument("--no-replicas", action="store_true", help="skip the 64-replica batch arm")
+    ap.add_argument("--no-water", action="store_true", help="skip the water-like fluid arm")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up, run this many MD steps, exit (no timing output)")
     ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1],
@@ -555,6 +582,9 @@ def main():
     replicas = None
     if not args.no_replicas and rank == 0:
         replicas = replicas_arm(timed, max(2, args.steps // 2), local)
+    water = None
+    if not args.no_water and rank == 0:
+        water = water_arm(timed, max(2, args.steps // 2), local)
 
     if rank != 0:
         if dist:
@@ -621,6 +651,7 @@ def main():
         "compare": compare,
         "learned_cg": learned,
         "replicas_64": replicas,
+        "water_64k": water,
         "per_step_ms": ms,
     }
     if not args.no_cpu_baseline:
