@@ -301,6 +301,7 @@ static adress_status setup_cells(adress_ctx* h, double skin) {
     if (e == cudaSuccess) e = realloc_owned(h, &h->cell_rank, s.ncell);
     if (e == cudaSuccess) e = realloc_owned(h, &h->rank_cell, s.ncell);
     if (e == cudaSuccess && s.nbox > 1) e = realloc_owned(h, &h->cell_box, s.ncell);
+    if (e == cudaSuccess) e = realloc_owned(h, &h->buf.dense_cells, s.ncell);
     b.cell_count = cc;
     b.cell_fill = cf;
     b.cell_start = cs;

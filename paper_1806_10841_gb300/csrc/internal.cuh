@@ -29,6 +29,7 @@ struct Ctrl {
   int parity;          // which half of the double-buffered molecule arrays is current
   unsigned maxext2;    // float bits: largest squared atom-to-COM distance of the last mapping
   unsigned maxdisp2;   // float bits: largest squared COM displacement since the last build
+  int n_dense;         // cells passed to the dense-cell list builder in this build
 };
 
 // Decision taken after a mapping (see decide_after_map in observe.cu).
@@ -164,6 +165,7 @@ struct Bufs {
   const Box* boxes;    // [nbox]
   const int* mol_box;  // [M] box of each molecule
   const int* cell_box; // [ncell] box of each global cell rank
+  int* dense_cells;     // [ncell] cells the dense-cell list builder handles
 };
 
 // Box of molecule a (the single box unless the system holds batched replicas).

@@ -5,6 +5,8 @@
 // so every list is deterministic; molecules are split into two work lists — high-resolution
 // candidates (|dxc| < d_at + d_hy + skin/2) first, then coarse-grained molecules —
 // and each work item gets a full Verlet list of molecules within r_list.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace adress {
@@ -19,6 +21,7 @@ __device__ __forceinline__ int cell_of(unsigned int X, int nc) {
 }
 
 __global__ void k_rb_zero(const __grid_constant__ Sys s, Bufs b) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) b.ctrl->n_dense = 0;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.ncell; c += gridDim.x * blockDim.x) {
     b.cell_count[c] = 0;
     b.cell_fill[c] = 0;
@@ -146,20 +149,18 @@ __global__ void k_rb_fill(const __grid_constant__ Sys s, Bufs b) {
   b.fill_tmp[p] = a;
 }
 
-// One warp per cell: each member's position in the cell is the number of members with a
-// smaller id (ids are distinct), so the cell's slice of `sorted` is in increasing id.
-constexpr int kSortWarps = 4;
-__global__ void __launch_bounds__(32 * kSortWarps) k_rb_sortcell(const __grid_constant__ Sys s, Bufs b) {
-  const int lane = threadIdx.x & 31;
-  const int r = blockIdx.x * kSortWarps + (threadIdx.x >> 5);
-  if (r >= s.ncell) return;
+// Each molecule's position in its cell is the number of the cell's members with a smaller
+// id (ids are distinct), so every cell's slice of `sorted` is in increasing id.  One thread
+// per molecule.
+__global__ void k_rb_sortcell(const __grid_constant__ Sys s, Bufs b) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= s.M) return;
+  const int a = b.fill_tmp[p];
+  const int r = b.mcell[a];
   const int ps = b.cell_start[r], pe = b.cell_start[r + 1];
-  for (int p = ps + lane; p < pe; p += 32) {
-    const int a = b.fill_tmp[p];
-    int rank = 0;
-    for (int q = ps; q < pe; ++q) rank += b.fill_tmp[q] < a;
-    b.sorted[ps + rank] = a;
-  }
+  int rank = 0;
+  for (int q = ps; q < pe; ++q) rank += b.fill_tmp[q] < a;
+  b.sorted[ps + rank] = a;
 }
 
 __global__ void k_rb_flag(const __grid_constant__ Sys s, Bufs b) {
@@ -186,19 +187,15 @@ __global__ void k_rb_items(const __grid_constant__ Sys s, Bufs b) {
 }
 
 // One warp per cell (cells in Morton order).  Lanes 0..26 take the 27 neighbour cells in
-// the fixed (ox, oy, oz) order and a warp scan gives each cell's offset in the candidate
-// list.  Candidates (centre + id) are staged in shared memory kMaxCand at a time; each
-// molecule of the home cell tests a staged chunk in parallel and appends its neighbours in
-// candidate order with ballot/popc compaction, its running count kept in shared memory
-// (home molecules in batches of kMaxHome): lists in candidate order for any density.
+// the fixed (ox, oy, oz) order, a warp scan gives each cell's offset in the candidate list,
+// and the candidates (centre + id; each cell's members already in id order) are staged in
+// shared memory once; each molecule of the cell then tests all candidates in parallel and
+// appends its neighbours in candidate order with ballot/popc compaction.  A cell with more
+// than kMaxCand candidates or 32 molecules is passed to k_rb_nbr_dense.
 constexpr int kNbrWarps = 4;
-constexpr int kMaxCand = 256;  // candidates staged per chunk
-constexpr int kMaxHome = 128;  // home-cell molecules per batch
+constexpr int kMaxCand = 256;  // candidates staged at once
 __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant__ Sys s, Bufs b) {
   __shared__ int4 stage[kNbrWarps][kMaxCand];
-  __shared__ int4 home[kNbrWarps][kMaxHome];  // centre + work item
-  __shared__ int hitem[kNbrWarps][kMaxHome];
-  __shared__ int hcnt[kNbrWarps][kMaxHome];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * kNbrWarps + w;
   if (r >= s.ncell) return;  // warp-uniform
@@ -229,71 +226,160 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
   const int pre = incl - cnt;
   const int total = __shfl_sync(0xffffffffu, incl, 31);
   const int n_home = __shfl_sync(0xffffffffu, cnt, 13);
-  const int home_start = __shfl_sync(0xffffffffu, start, 13);
   if (n_home == 0) return;
+  if (total > kMaxCand || n_home > 32) {
+    if (lane == 0) b.dense_cells[atomicAdd(&b.ctrl->n_dense, 1)] = r;
+    return;
+  }
+  for (int q = 0; q < cnt; ++q) {
+    const int m = b.sorted[start + q];
+    const int4 C = com[m];
+    stage[w][pre + q] = make_int4(C.x, C.y, C.z, m);
+  }
+  __syncwarp();
+  // the home cell is neighbour 13: its molecules and their work items
+  const int home_pre = __shfl_sync(0xffffffffu, pre, 13);
+  const int my_item = lane < n_home ? b.item_of[stage[w][home_pre + lane].w] : 0;
   const float rl2 = (float)s.r_list2;
-  // home molecules in batches of kMaxHome (one batch unless the cell is over-dense)
-  for (int hb = 0; hb < n_home; hb += kMaxHome) {
-    const int nh = min(kMaxHome, n_home - hb);
-    __syncwarp();
-    for (int h = lane; h < nh; h += 32) {
-      const int a = b.sorted[home_start + hb + h];
-      const int4 C = com[a];
-      home[w][h] = make_int4(C.x, C.y, C.z, a);
-      hitem[w][h] = b.item_of[a];
-      hcnt[w][h] = 0;
-    }
-    for (int c0 = 0; c0 < total; c0 += kMaxCand) {
-      __syncwarp();
-      // lane j stages the part of neighbour cell j's members (in id order) inside the window
-      if (lane < 27) {
-        const int lo = max(pre, c0), hi = min(pre + cnt, c0 + kMaxCand);
-#pragma unroll 1
-        for (int k = lo; k < hi; ++k) {
-          const int m = b.sorted[start + (k - pre)];
-          const int4 C = com[m];
-          stage[w][k - c0] = make_int4(C.x, C.y, C.z, m);
-        }
+  for (int h = 0; h < n_home; ++h) {
+    const int4 H = stage[w][home_pre + h];
+    const int a = H.w;
+    const int t = __shfl_sync(0xffffffffu, my_item, h);
+    int count = 0;
+    for (int k0 = 0; k0 < total; k0 += 32) {
+      const int k = k0 + lane;
+      bool hit = false;
+      int m = 0;
+      if (k < total) {
+        const int4 D = stage[w][k];
+        m = D.w;
+        const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * B.fx_scale[0];
+        const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * B.fx_scale[1];
+        const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * B.fx_scale[2];
+        hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < rl2;
       }
-      __syncwarp();
-      const int nc = min(kMaxCand, total - c0);
-#pragma unroll 1
-      for (int h = 0; h < nh; ++h) {
-        const int4 H = home[w][h];
-        const int a = H.w;
-        const int tt = hitem[w][h];
-        int count = hcnt[w][h];
-        for (int k0 = 0; k0 < nc; k0 += 32) {
-          const int k = k0 + lane;
-          bool hit = false;
-          int m = 0;
-          if (k < nc) {
-            const int4 D = stage[w][k];
-            m = D.w;
-            const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * B.fx_scale[0];
-            const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * B.fx_scale[1];
-            const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * B.fx_scale[2];
-            hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < rl2;
-          }
-          const unsigned bal = __ballot_sync(0xffffffffu, hit);
-          if (hit) {
-            const int p = count + __popc(bal & ((1u << lane) - 1u));
-            if (p < s.cap) b.nbr[(size_t)tt * s.cap + p] = m;
-          }
-          count += __popc(bal);
-        }
-        if (lane == 0) hcnt[w][h] = count;
-        __syncwarp();
+      const unsigned bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) {
+        const int p = count + __popc(bal & ((1u << lane) - 1u));
+        if (p < s.cap) b.nbr[(size_t)t * s.cap + p] = m;
       }
+      count += __popc(bal);
     }
-    __syncwarp();
-    for (int h = lane; h < nh; h += 32) {
-      const int4 H = home[w][h];
-      const int count = hcnt[w][h];
-      const int tt = hitem[w][h];
-      b.nn[tt] = count < s.cap ? count : s.cap;
-      b.com_ref[H.w] = make_int4(H.x, H.y, H.z, 0);
+    if (lane == 0) {
+      b.nn[t] = count < s.cap ? count : s.cap;
+      b.com_ref[a] = make_int4(H.x, H.y, H.z, 0);
       if (count > s.cap) set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, count);
+    }
+  }
+}
+
+// Dense cells (those k_rb_nbr passed on): one warp per listed cell, persistent grid.
+// Candidates (centre + id) are staged in shared memory kMaxCand at a time; each molecule of
+// the home cell tests a staged chunk in parallel and appends its neighbours in candidate
+// order with ballot/popc compaction, its running count kept in shared memory (home
+// molecules in batches of kMaxHome): the same lists for any density.
+constexpr int kMaxHome = 128;  // home-cell molecules per batch
+__global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_constant__ Sys s, Bufs b) {
+  __shared__ int4 stage[kNbrWarps][kMaxCand];
+  __shared__ int4 home[kNbrWarps][kMaxHome];  // centre + work item
+  __shared__ int hitem[kNbrWarps][kMaxHome];
+  __shared__ int hcnt[kNbrWarps][kMaxHome];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_dense = b.ctrl->n_dense;
+  const int4* com = b.com_fx[b.ctrl->parity];
+  for (int di = blockIdx.x * kNbrWarps + w; di < n_dense; di += gridDim.x * kNbrWarps) {  // warp-uniform
+    const int r = b.dense_cells[di];
+    const Box& B = s.nbox > 1 ? b.boxes[b.cell_box[r]] : s.bx;
+    const int lin = b.rank_cell[r] - B.cell0;
+    const int cz = lin % B.nc[2], cy = (lin / B.nc[2]) % B.nc[1], cx = lin / (B.nc[1] * B.nc[2]);
+    int cnt = 0, start = 0;
+    if (lane < 27) {
+      const int o0 = lane / 9 - 1, o1 = (lane / 3) % 3 - 1, o2 = lane % 3 - 1;
+      const bool ok = (o0 >= (B.nc[0] >= 3 ? -1 : 0)) && (o0 <= (B.nc[0] >= 2 ? 1 : 0)) &&
+                      (o1 >= (B.nc[1] >= 3 ? -1 : 0)) && (o1 <= (B.nc[1] >= 2 ? 1 : 0)) &&
+                      (o2 >= (B.nc[2] >= 3 ? -1 : 0)) && (o2 <= (B.nc[2] >= 2 ? 1 : 0));
+      if (ok) {
+        const int x = (cx + o0 + B.nc[0]) % B.nc[0], y = (cy + o1 + B.nc[1]) % B.nc[1],
+                  z = (cz + o2 + B.nc[2]) % B.nc[2];
+        const int rr = b.cell_rank[B.cell0 + (x * B.nc[1] + y) * B.nc[2] + z];
+        start = b.cell_start[rr];
+        cnt = b.cell_start[rr + 1] - start;
+      }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int pre = incl - cnt;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int n_home = __shfl_sync(0xffffffffu, cnt, 13);
+    const int home_start = __shfl_sync(0xffffffffu, start, 13);
+    const float rl2 = (float)s.r_list2;
+    // home molecules in batches of kMaxHome (one batch unless the cell is over-dense)
+    for (int hb = 0; hb < n_home; hb += kMaxHome) {
+      const int nh = min(kMaxHome, n_home - hb);
+      __syncwarp();
+      for (int h = lane; h < nh; h += 32) {
+        const int a = b.sorted[home_start + hb + h];
+        const int4 C = com[a];
+        home[w][h] = make_int4(C.x, C.y, C.z, a);
+        hitem[w][h] = b.item_of[a];
+        hcnt[w][h] = 0;
+      }
+      for (int c0 = 0; c0 < total; c0 += kMaxCand) {
+        __syncwarp();
+        // lane j stages the part of neighbour cell j's members (in id order) inside the window
+        if (lane < 27) {
+          const int lo = max(pre, c0), hi = min(pre + cnt, c0 + kMaxCand);
+#pragma unroll 1
+          for (int k = lo; k < hi; ++k) {
+            const int m = b.sorted[start + (k - pre)];
+            const int4 C = com[m];
+            stage[w][k - c0] = make_int4(C.x, C.y, C.z, m);
+          }
+        }
+        __syncwarp();
+        const int nc = min(kMaxCand, total - c0);
+#pragma unroll 1
+        for (int h = 0; h < nh; ++h) {
+          const int4 H = home[w][h];
+          const int a = H.w;
+          const int tt = hitem[w][h];
+          int count = hcnt[w][h];
+          for (int k0 = 0; k0 < nc; k0 += 32) {
+            const int k = k0 + lane;
+            bool hit = false;
+            int m = 0;
+            if (k < nc) {
+              const int4 D = stage[w][k];
+              m = D.w;
+              const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * B.fx_scale[0];
+              const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * B.fx_scale[1];
+              const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * B.fx_scale[2];
+              hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < rl2;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) {
+              const int p = count + __popc(bal & ((1u << lane) - 1u));
+              if (p < s.cap) b.nbr[(size_t)tt * s.cap + p] = m;
+            }
+            count += __popc(bal);
+          }
+          if (lane == 0) hcnt[w][h] = count;
+          __syncwarp();
+        }
+      }
+      __syncwarp();
+      for (int h = lane; h < nh; h += 32) {
+        const int4 H = home[w][h];
+        const int count = hcnt[w][h];
+        const int tt = hitem[w][h];
+        b.nn[tt] = count < s.cap ? count : s.cap;
+        b.com_ref[H.w] = make_int4(H.x, H.y, H.z, 0);
+        if (count > s.cap) set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, count);
+      }
     }
   }
 }
@@ -351,11 +437,12 @@ cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st) {
       cudaSuccess)
     return e;
   k_rb_fill<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
-  k_rb_sortcell<<<ceil_div(s.ncell, kSortWarps), 32 * kSortWarps, 0, st>>>(s, b);
+  k_rb_sortcell<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   k_rb_flag<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   if ((e = exclusive_scan(b.flag, b.pos, s.M, b.scan_tmp, b.pos + s.M, st)) != cudaSuccess) return e;
   k_rb_items<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   k_rb_nbr<<<ceil_div(s.ncell, kNbrWarps), 32 * kNbrWarps, 0, st>>>(s, b);
+  k_rb_nbr_dense<<<std::min(ceil_div(s.ncell, kNbrWarps), 152 * 8), 32 * kNbrWarps, 0, st>>>(s, b);
   if (s.cg_mode && b.mirror) return launch_mirror(s, b, st);
   return cudaGetLastError();
 }
