@@ -179,6 +179,20 @@ def pair_statistics(s, x):
 FLOPS = {"at_pair": 35, "cg_pair": 55, "bond": 40}  # FP32 flops per interaction
 
 
+def job_throughput(seconds, atom_steps, dist=None, device=None):
+    """Whole-job throughput: every rank runs its own replica; the job's time is the slowest
+    rank's, its work the sum over ranks.  Returns (atom-steps/s, max seconds)."""
+    if dist is not None and dist.is_initialized():
+        import torch
+
+        t = torch.tensor([seconds, float(atom_steps)], dtype=torch.float64, device=device)
+        tmax, tsum = t.clone(), t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        seconds, atom_steps = float(tmax[0]), float(tsum[1])
+    return atom_steps / seconds, seconds
+
+
 def reference_arm(args, world, rank):
     """The FP64 CPU oracle on the host cores (a bounded sample of the same workload)."""
     if rank != 0:
@@ -511,12 +525,7 @@ def main():
     # + 10 density samples + 1 TF update; 14 kernels per list rebuild
     per_block = 1 + (MD_PER_BLOCK - 1) + 1 + MD_PER_BLOCK + MD_PER_BLOCK // SAMPLE_EVERY + 1
     launches = args.steps * per_block + 14 * rebuilds
-    if dist:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    atom_steps = s.N * MD_PER_BLOCK * args.steps * world
-    value = atom_steps / total_s
+    value, total_s = job_throughput(total_s, s.N * MD_PER_BLOCK * args.steps, dist, dev)
 
     # ---- live kernel timing (CUDA events on the library's stream) + roofline ----
     kt = sim.time_kernels(reps=20)
