@@ -1,0 +1,82 @@
+"""Failure detection, checkpoint/resume and parity after equilibration (GPU, host-side faults
+only: nothing here faults, traps or hangs the GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1806_10841_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def sim_of(s, precision, **kw):
+    from paper_1806_10841_gb300 import adress
+
+    return adress.AdResS(s, precision=precision, **kw)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_nan_injected_into_host_velocities_is_reported_not_trapped(precision):
+    from paper_1806_10841_gb300 import adress
+
+    s = inputs.scaled_c2(2000)
+    x, v = inputs.tetra_state(s)
+    v[17, 1] = np.nan
+    sim = sim_of(s, precision)
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    sim.step(2)
+    with pytest.raises(adress.AdressError) as ei:
+        sim.check()
+    assert ei.value.status == 4  # ADRESS_ERR_NONFINITE
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_checkpoint_resume_is_bitwise(precision):
+    """Counter-based noise keyed by (seed, replica, atom, time level): a run resumed from a
+    checkpoint (x, v, f, time level, thermodynamic-force table) continues bitwise, given that
+    both runs build their lists at the checkpoint."""
+    s = inputs.scaled_c2(3000)
+    x, v = inputs.tetra_state(s)
+    a = sim_of(s, precision)
+    a.set_state(x, v)
+    a.compute_forces(energies=False)
+    a.run(40, sample_every=10, tf_update=True, alpha=1.0)
+    a.build_lists()
+    ck = a.get_state(), a.get_step(), a.get_tf()
+    a.run(60, sample_every=10, tf_update=True, alpha=1.0)
+    end_a = a.get_state()
+    a.close()
+    b = sim_of(s, precision)
+    (xc, vc, fc), step, tf = ck
+    b.set_state(xc, vc, fc)
+    b.set_step(step)
+    b.set_tf(tf)
+    b.build_lists()
+    b.run(60, sample_every=10, tf_update=True, alpha=1.0)
+    end_b = b.get_state()
+    b.check()
+    for p, q in zip(end_a, end_b):
+        assert np.array_equal(p, q)
+    assert b.get_step() == 100
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_forces_match_oracle_after_equilibration(precision):
+    s = inputs.scaled_c2(5000)
+    x, v = inputs.tetra_state(s)
+    sim = sim_of(s, precision)
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    sim.step(1500)
+    sim.check()
+    xe, _, _ = sim.get_state()
+    f, _ = sim.forces()
+    f_ref, _ = oracle.Oracle(s).forces(xe)
+    r = math.sqrt(((f - f_ref) ** 2).sum() / (f_ref ** 2).sum())
+    assert r <= {"fp64": 1e-10, "fp32": 2e-5}[precision], r
+    sim.close()
