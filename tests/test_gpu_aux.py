@@ -30,7 +30,10 @@ def test_nan_injected_into_host_velocities_is_reported_not_trapped(precision):
     sim.step(2)
     with pytest.raises(adress.AdressError) as ei:
         sim.check()
-    assert ei.value.status == 4  # ADRESS_ERR_NONFINITE
+    # reported as a non-finite force, or as a broken bond when the centre-of-mass mapping
+    # (fixed point in the FP32 path) sends the NaN coordinate to a finite but distant point
+    assert ei.value.status in (4, 5)
+    sim.check()  # cleared after being reported
     sim.close()
 
 
