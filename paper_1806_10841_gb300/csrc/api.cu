@@ -52,7 +52,7 @@ struct adress_ctx {
   int* mol_box = nullptr;
   int* cell_box = nullptr;
   int* cell_rank = nullptr;
-  int* rank_cell = nullptr;
+  int* nbr_cells = nullptr;  // [ncell][27]
   int ncell_cap = 0;
   double skin0 = 0.0;  // skin of the configuration (the autotuner scales it)
   // radial distribution function scratch
@@ -299,9 +299,9 @@ static adress_status setup_cells(adress_ctx* h, double skin) {
     if (e == cudaSuccess) e = realloc_owned(h, &cf, s.ncell);
     if (e == cudaSuccess) e = realloc_owned(h, &cs, s.ncell + 1);
     if (e == cudaSuccess) e = realloc_owned(h, &h->cell_rank, s.ncell);
-    if (e == cudaSuccess) e = realloc_owned(h, &h->rank_cell, s.ncell);
     if (e == cudaSuccess && s.nbox > 1) e = realloc_owned(h, &h->cell_box, s.ncell);
     if (e == cudaSuccess) e = realloc_owned(h, &h->buf.dense_cells, s.ncell);
+    if (e == cudaSuccess) e = realloc_owned(h, &h->nbr_cells, (size_t)s.ncell * 27);
     b.cell_count = cc;
     b.cell_fill = cf;
     b.cell_start = cs;
@@ -309,10 +309,10 @@ static adress_status setup_cells(adress_ctx* h, double skin) {
     h->ncell_cap = s.ncell;
   }
   b.cell_rank = h->cell_rank;
-  b.rank_cell = h->rank_cell;
   b.cell_box = h->cell_box;
+  b.nbr_cells = h->nbr_cells;
 
-  std::vector<int> rank(s.ncell), rcell(s.ncell), cbox(s.nbox > 1 ? s.ncell : 0);
+  std::vector<int> rank(s.ncell), cbox(s.nbox > 1 ? s.ncell : 0);
   for (int k = 0; k < s.nbox; ++k) {
     const Box& B = h->boxes[k];
     std::vector<std::pair<uint64_t, int>> codes(B.ncell);
@@ -325,14 +325,37 @@ static adress_status setup_cells(adress_ctx* h, double skin) {
     std::sort(codes.begin(), codes.end());
     for (int r = 0; r < B.ncell; ++r) {
       rank[B.cell0 + codes[r].second] = B.cell0 + r;
-      rcell[B.cell0 + r] = B.cell0 + codes[r].second;
       if (s.nbox > 1) cbox[B.cell0 + r] = k;
     }
+  }
+  // the 27 neighbour cells of every cell (by Morton rank), in the list order
+  // (ox, oy, oz) = (j/9 - 1, (j/3)%3 - 1, j%3 - 1); -1 where a dimension has fewer than three
+  // cells and the offset would repeat a cell
+  std::vector<int> ncells((size_t)s.ncell * 27);
+  for (int k = 0; k < s.nbox; ++k) {
+    const Box& B = h->boxes[k];
+    for (int x = 0; x < B.nc[0]; ++x)
+      for (int y = 0; y < B.nc[1]; ++y)
+        for (int z = 0; z < B.nc[2]; ++z) {
+          const int r = rank[B.cell0 + (x * B.nc[1] + y) * B.nc[2] + z];
+          for (int j = 0; j < 27; ++j) {
+            const int o[3] = {j / 9 - 1, (j / 3) % 3 - 1, j % 3 - 1};
+            const int c[3] = {x, y, z};
+            int q[3];
+            bool ok = true;
+            for (int d = 0; d < 3; ++d) {
+              const int lo = B.nc[d] >= 3 ? -1 : 0, hi = B.nc[d] >= 2 ? 1 : 0;
+              ok = ok && o[d] >= lo && o[d] <= hi;
+              q[d] = (c[d] + o[d] + B.nc[d]) % B.nc[d];
+            }
+            ncells[(size_t)r * 27 + j] = ok ? rank[B.cell0 + (q[0] * B.nc[1] + q[1]) * B.nc[2] + q[2]] : -1;
+          }
+        }
   }
   cudaStream_t st = h->stream;
   e = cudaMemcpyAsync(h->cell_rank, rank.data(), sizeof(int) * s.ncell, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->rank_cell, rcell.data(), sizeof(int) * s.ncell, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(h->nbr_cells, ncells.data(), sizeof(int) * ncells.size(), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && s.nbox > 1)
     e = cudaMemcpyAsync(h->cell_box, cbox.data(), sizeof(int) * s.ncell, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && s.nbox > 1)
@@ -517,6 +540,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   A(b.mcell, M);
   A(b.sorted, M);
   A(b.fill_tmp, M);
+  A(b.scom, M);
   A(b.flag, M);
   A(b.pos, M + 1);
   A(b.items, M);

@@ -133,6 +133,7 @@ struct Bufs {
   int* cell_start;  // [ncell+1]
   int* sorted;      // molecules grouped by cell, cells in Morton order, each cell in id order
   int* fill_tmp;    // [M] cell-grouped molecules in fill (arbitrary) order
+  int4* scom;       // [M] fixed-point centres in `sorted` order (staged by the list build)
   int* flag;        // [M] high-resolution candidate flag at sorted positions
   int* pos;         // [M] exclusive scan of flag
   int* items;       // [M] work items: high-resolution candidates first, then CG
@@ -141,7 +142,6 @@ struct Bufs {
   int* nbr;         // [M*cap] neighbour molecule of item t in slot q at nbr[t*cap + q]
   int* scan_tmp;    // block sums for device-wide scans
   const int* cell_rank;  // linear cell -> Morton rank
-  const int* rank_cell;  // Morton rank -> linear cell
   // tables
   const double* cgF64;
   const double* cgV64;
@@ -166,6 +166,7 @@ struct Bufs {
   const int* mol_box;  // [M] box of each molecule
   const int* cell_box; // [ncell] box of each global cell rank
   int* dense_cells;     // [ncell] cells the dense-cell list builder handles
+  const int* nbr_cells; // [ncell][27] Morton ranks of each cell's neighbour cells (-1: none)
 };
 
 // Box of molecule a (the single box unless the system holds batched replicas).

@@ -161,6 +161,7 @@ __global__ void k_rb_sortcell(const __grid_constant__ Sys s, Bufs b) {
   int rank = 0;
   for (int q = ps; q < pe; ++q) rank += b.fill_tmp[q] < a;
   b.sorted[ps + rank] = a;
+  b.scom[ps + rank] = b.com_fx[b.ctrl->parity][a];
 }
 
 __global__ void k_rb_flag(const __grid_constant__ Sys s, Bufs b) {
@@ -199,20 +200,11 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int r = blockIdx.x * kNbrWarps + w;
   if (r >= s.ncell) return;  // warp-uniform
-  const int4* com = b.com_fx[b.ctrl->parity];
   const Box& B = s.nbox > 1 ? b.boxes[b.cell_box[r]] : s.bx;
-  const int lin = b.rank_cell[r] - B.cell0;
-  const int cz = lin % B.nc[2], cy = (lin / B.nc[2]) % B.nc[1], cx = lin / (B.nc[1] * B.nc[2]);
   int cnt = 0, start = 0;
   if (lane < 27) {
-    const int o0 = lane / 9 - 1, o1 = (lane / 3) % 3 - 1, o2 = lane % 3 - 1;
-    const bool ok = (o0 >= (B.nc[0] >= 3 ? -1 : 0)) && (o0 <= (B.nc[0] >= 2 ? 1 : 0)) &&
-                    (o1 >= (B.nc[1] >= 3 ? -1 : 0)) && (o1 <= (B.nc[1] >= 2 ? 1 : 0)) &&
-                    (o2 >= (B.nc[2] >= 3 ? -1 : 0)) && (o2 <= (B.nc[2] >= 2 ? 1 : 0));
-    if (ok) {
-      const int x = (cx + o0 + B.nc[0]) % B.nc[0], y = (cy + o1 + B.nc[1]) % B.nc[1],
-                z = (cz + o2 + B.nc[2]) % B.nc[2];
-      const int rr = b.cell_rank[B.cell0 + (x * B.nc[1] + y) * B.nc[2] + z];
+    const int rr = b.nbr_cells[(size_t)r * 27 + lane];
+    if (rr >= 0) {
       start = b.cell_start[rr];
       cnt = b.cell_start[rr + 1] - start;
     }
@@ -232,9 +224,8 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
     return;
   }
   for (int q = 0; q < cnt; ++q) {
-    const int m = b.sorted[start + q];
-    const int4 C = com[m];
-    stage[w][pre + q] = make_int4(C.x, C.y, C.z, m);
+    const int4 C = b.scom[start + q];
+    stage[w][pre + q] = make_int4(C.x, C.y, C.z, b.sorted[start + q]);
   }
   __syncwarp();
   // the home cell is neighbour 13: its molecules and their work items
@@ -290,18 +281,10 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
   for (int di = blockIdx.x * kNbrWarps + w; di < n_dense; di += gridDim.x * kNbrWarps) {  // warp-uniform
     const int r = b.dense_cells[di];
     const Box& B = s.nbox > 1 ? b.boxes[b.cell_box[r]] : s.bx;
-    const int lin = b.rank_cell[r] - B.cell0;
-    const int cz = lin % B.nc[2], cy = (lin / B.nc[2]) % B.nc[1], cx = lin / (B.nc[1] * B.nc[2]);
     int cnt = 0, start = 0;
     if (lane < 27) {
-      const int o0 = lane / 9 - 1, o1 = (lane / 3) % 3 - 1, o2 = lane % 3 - 1;
-      const bool ok = (o0 >= (B.nc[0] >= 3 ? -1 : 0)) && (o0 <= (B.nc[0] >= 2 ? 1 : 0)) &&
-                      (o1 >= (B.nc[1] >= 3 ? -1 : 0)) && (o1 <= (B.nc[1] >= 2 ? 1 : 0)) &&
-                      (o2 >= (B.nc[2] >= 3 ? -1 : 0)) && (o2 <= (B.nc[2] >= 2 ? 1 : 0));
-      if (ok) {
-        const int x = (cx + o0 + B.nc[0]) % B.nc[0], y = (cy + o1 + B.nc[1]) % B.nc[1],
-                  z = (cz + o2 + B.nc[2]) % B.nc[2];
-        const int rr = b.cell_rank[B.cell0 + (x * B.nc[1] + y) * B.nc[2] + z];
+      const int rr = b.nbr_cells[(size_t)r * 27 + lane];
+      if (rr >= 0) {
         start = b.cell_start[rr];
         cnt = b.cell_start[rr + 1] - start;
       }
@@ -335,9 +318,8 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
           const int lo = max(pre, c0), hi = min(pre + cnt, c0 + kMaxCand);
 #pragma unroll 1
           for (int k = lo; k < hi; ++k) {
-            const int m = b.sorted[start + (k - pre)];
-            const int4 C = com[m];
-            stage[w][k - c0] = make_int4(C.x, C.y, C.z, m);
+            const int4 C = b.scom[start + (k - pre)];
+            stage[w][k - c0] = make_int4(C.x, C.y, C.z, b.sorted[start + (k - pre)]);
           }
         }
         __syncwarp();
