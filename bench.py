@@ -631,7 +631,7 @@ def main():
     roofline = {"bound": "hbm" if bname == "hbm" else "alu", "resource": bname,
                 "kernel": "k_step fused (forces + bonded + TF + Langevin + kicks + drift + mapping)",
                 "achieved": b["achieved"], "peak": b["peak"], "unit": b["unit"], "frac": b["frac"],
-                "traffic": profiled_traffic("k_step_fused_c2_800k_fp32.md", ("step.cu", "internal.cuh"))
+                "traffic": profiled_traffic("k_step_fused_c2_800k_fp32.md", ("step_impl.cuh", "step.cu", "internal.cuh"))
                 if args.precision == "fp32" else None,
                 "traffic_source": "profiles/k_step_fused_c2_800k_fp32.md (one ncu capture, cold cache; "
                                   "null when the kernel's sources changed since)",
