@@ -434,7 +434,9 @@ def main():
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up, run this many MD steps, exit (no timing output)")
     ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1],
-                    help="for --profile: 1 = learned CG force (untrained network of the production shape)")
+                    help="for --profile: 1 = learned CG force (network trained on atomistic samples first)")
+    ap.add_argument("--water", action="store_true",
+                    help="for --profile: the water-like fluid (64k molecules, or --molecules at its density)")
     ap.add_argument("--molecules", type=int, default=200_000,
                     help="system size for --profile (same density, shape and slab proportions)")
     args = ap.parse_args()
@@ -458,8 +460,12 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
 
     if args.profile:
-        s = inputs.c2_800k() if args.molecules == 200_000 else inputs.scaled_c2(args.molecules)
-        x0, v0 = inputs.tetra_state(s)
+        if args.water:
+            s = inputs.c3_water() if args.molecules == 200_000 else inputs.scaled_c3(args.molecules)
+            x0, v0 = inputs.water_state(s)
+        else:
+            s = inputs.c2_800k() if args.molecules == 200_000 else inputs.scaled_c2(args.molecules)
+            x0, v0 = inputs.tetra_state(s)
         sim = adress.AdResS(s, precision=args.precision, device=f"cuda:{local}")
         sim.set_state(x0, v0)
         if args.cg_mode:

@@ -264,12 +264,13 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
   }
 }
 
-// Dense cells (those k_rb_nbr passed on): one warp per listed cell, persistent grid.
-// Candidates (centre + id) are staged in shared memory kMaxCand at a time; each molecule of
-// the home cell tests a staged chunk in parallel and appends its neighbours in candidate
-// order with ballot/popc compaction, its running count kept in shared memory (home
-// molecules in batches of kMaxHome): the same lists for any density.
-constexpr int kMaxHome = 128;  // home-cell molecules per batch
+// Dense cells (those k_rb_nbr passed on): kHomeParts warps per listed cell, each taking
+// batches of kMaxHome of its molecules, persistent grid.  Candidates (centre + id) are
+// staged in shared memory kMaxCand at a time; each home molecule of the batch tests a staged
+// chunk in parallel and appends its neighbours in candidate order with ballot/popc
+// compaction, its running count kept in shared memory: the same lists for any density.
+constexpr int kMaxHome = 16;   // home-cell molecules per batch
+constexpr int kHomeParts = 8;  // warps that share one dense cell's home molecules
 __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_constant__ Sys s, Bufs b) {
   __shared__ int4 stage[kNbrWarps][kMaxCand];
   __shared__ int4 home[kNbrWarps][kMaxHome];  // centre + work item
@@ -278,7 +279,10 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_dense = b.ctrl->n_dense;
   const int4* com = b.com_fx[b.ctrl->parity];
-  for (int di = blockIdx.x * kNbrWarps + w; di < n_dense; di += gridDim.x * kNbrWarps) {  // warp-uniform
+  // task = (dense cell, part): part j takes the home batches j, j + kHomeParts, ... so that
+  // the molecules of one dense cell are shared by kHomeParts warps
+  for (int task = blockIdx.x * kNbrWarps + w; task < n_dense * kHomeParts; task += gridDim.x * kNbrWarps) {
+    const int di = task / kHomeParts, part = task % kHomeParts;
     const int r = b.dense_cells[di];
     const Box& B = s.nbox > 1 ? b.boxes[b.cell_box[r]] : s.bx;
     int cnt = 0, start = 0;
@@ -300,8 +304,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
     const int n_home = __shfl_sync(0xffffffffu, cnt, 13);
     const int home_start = __shfl_sync(0xffffffffu, start, 13);
     const float rl2 = (float)s.r_list2;
-    // home molecules in batches of kMaxHome (one batch unless the cell is over-dense)
-    for (int hb = 0; hb < n_home; hb += kMaxHome) {
+    for (int hb = part * kMaxHome; hb < n_home; hb += kHomeParts * kMaxHome) {
       const int nh = min(kMaxHome, n_home - hb);
       __syncwarp();
       for (int h = lane; h < nh; h += 32) {
@@ -424,7 +427,7 @@ cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st) {
   if ((e = exclusive_scan(b.flag, b.pos, s.M, b.scan_tmp, b.pos + s.M, st)) != cudaSuccess) return e;
   k_rb_items<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   k_rb_nbr<<<ceil_div(s.ncell, kNbrWarps), 32 * kNbrWarps, 0, st>>>(s, b);
-  k_rb_nbr_dense<<<std::min(ceil_div(s.ncell, kNbrWarps), 152 * 8), 32 * kNbrWarps, 0, st>>>(s, b);
+  k_rb_nbr_dense<<<std::min(ceil_div((long long)s.ncell * kHomeParts, kNbrWarps), 152 * 16), 32 * kNbrWarps, 0, st>>>(s, b);
   if (s.cg_mode && b.mirror) return launch_mirror(s, b, st);
   return cudaGetLastError();
 }
