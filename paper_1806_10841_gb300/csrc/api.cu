@@ -516,7 +516,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   {
     int warps = 0;
     for (int blk = 32; blk <= kMaxForceBlock; blk *= 2)
-      warps = std::max(warps, ceil_div((long long)M * kGroup, blk) * (blk / 32));
+      warps = std::max(warps, ceil_div((long long)M * step_lanes(s), blk) * (blk / 32));
     h->nparts = std::max(warps, ceil_div(N, 256));
   }
   const int ntf = std::max(1, nbox * s.tf_n);

@@ -273,9 +273,13 @@ adress_status set_global_error(adress_status s, const std::string& msg);
 // registers and ~4% time at 128 threads).
 constexpr int kMaxForceBlock = 128;
 
+// Threads per molecule the force kernel is launched with: four, or eight for the water-like
+// model, whose high-resolution items split their neighbour lists over two lane groups.
+inline int step_lanes(const Sys& s) { return s.nb_model == 1 ? 2 * kGroup : kGroup; }
+
 // Warps launched by the force kernel (one energy partial each).
 inline int force_warps(const Sys& s) {
-  return ceil_div((long long)s.M * kGroup, s.force_block) * (s.force_block / 32);
+  return ceil_div((long long)s.M * step_lanes(s), s.force_block) * (s.force_block / 32);
 }
 
 }  // namespace adress

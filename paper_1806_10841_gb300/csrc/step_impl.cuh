@@ -384,9 +384,24 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
   using real = typename Q::real;
   const int lane = threadIdx.x & 31, g = threadIdx.x & 3, base = lane & ~3;
   const unsigned gmask = 0xFu << base;
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
-  const bool live = t < s.M;
+  // SPLIT = 2 (water): a high-resolution item takes two groups of four lanes (eight lanes in
+  // the same warp), each group half of the neighbour list; CG items keep one group.
+  constexpr int SPLIT = MODEL == 1 ? 2 : 1;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  int t = gtid >> 2, sub = 0;
+  if (SPLIT == 2) {
+    const int n_hr0 = b.ctrl->n_hr;
+    if (gtid < 8 * n_hr0) {
+      t = gtid >> 3;
+      sub = (gtid >> 2) & 1;
+    } else {
+      t = n_hr0 + ((gtid - 8 * n_hr0) >> 2);
+    }
+  }
+  const bool live_item = t < s.M;
+  const bool live = live_item && sub == 0;  // the group that integrates and maps the molecule
   const bool own = live && g < NA;
+  const bool own_pair = live_item && g < NA;  // lanes that evaluate pair forces
   const int cur = b.ctrl->parity;
 
   const real eps = par<real>(s.eps, s.f.eps), sig2 = par<real>(s.sig2, s.f.sig2);
@@ -412,34 +427,35 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
   real fx = 0, fy = 0, fz = 0;
   double e_at = 0.0, e_cg = 0.0, e_b = 0.0, vir = 0.0;
 
-  const int a = live ? b.items[t] : 0;
+  const int a = live_item ? b.items[t] : 0;
   const Box& B = box_t<MULTI>(s, b, a);
   const int i = a * NA + (g < NA ? g : 0);
   const auto Ca = Q::com(b, cur, a);
   const real wa = Q::w(Ca);
   const auto oi = Q::off(b, cur, i);
-  const int nnb = live ? b.nn[t] : 0;
+  const int nnb = live_item ? b.nn[t] : 0;
 
   if (t < b.ctrl->n_hr) {
-    // high-resolution item: Eq. 1 for atom i against every listed neighbour; the next
-    // neighbour's index and centre are fetched while the current one is evaluated
+    // high-resolution item: Eq. 1 for atom i against every listed neighbour (of this lane
+    // group's share); the next neighbour's index and centre are fetched while the current
+    // one is evaluated
     int m_n = 0;
     auto C_n = Ca;
-    if (nnb > 0) {
-      m_n = b.nbr[(size_t)t * s.cap];
+    if (sub < nnb) {
+      m_n = b.nbr[(size_t)t * s.cap + sub];
       C_n = Q::com(b, cur, m_n);
     }
-    for (int q = 0; q < nnb; ++q) {
+    for (int q = sub; q < nnb; q += SPLIT) {
       const int m = m_n;
       const auto Cb = C_n;
-      if (q + 1 < nnb) {
-        m_n = b.nbr[(size_t)t * s.cap + q + 1];
+      if (q + SPLIT < nnb) {
+        m_n = b.nbr[(size_t)t * s.cap + q + SPLIT];
         C_n = Q::com(b, cur, m_n);
       }
       const auto R = Q::dR(B, Ca, Cb);
       const real r2 = pair_r2(R.x, R.y, R.z);
       const real wab = wa * Q::w(Cb);
-      if (own && wab > (real)0 && r2 < reach_at2) {
+      if (own_pair && wab > (real)0 && r2 < reach_at2) {
         const real px = R.x + (real)oi.x, py = R.y + (real)oi.y, pz = R.z + (real)oi.z;
         typename P::off_t oj[NA];
 #pragma unroll
@@ -474,7 +490,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
           }
         }
       }
-      if (own && wab < (real)1 && r2 < rc_cg2) {
+      if (own_pair && wab < (real)1 && r2 < rc_cg2) {
         const real r = Q::sqrt_(r2);
         real V = 0;
         const real F = s.cg_mode ? (real)b.fpair[(size_t)t * s.cap + q] : Q::cg(b, s.cg_n, r, inv_dr, &V);
@@ -487,6 +503,12 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
           vir += 0.5 * (double)(c * r2);
         }
       }
+    }
+    if (SPLIT == 2) {  // the two groups' shares of the force (energies are summed per warp)
+      const unsigned m8 = 0xFFu << (lane & 24);
+      fx += __shfl_xor_sync(m8, fx, 4);
+      fy += __shfl_xor_sync(m8, fy, 4);
+      fz += __shfl_xor_sync(m8, fz, 4);
     }
   } else {
     // coarse-grained item (l_a = 0, so w_ab = 0): neighbour list split over the group,
@@ -777,7 +799,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
 
 template <class P, int NA, int MODEL>
 static void launch_step_na(const Sys& s, const Bufs& b, int mode, int energy, cudaStream_t st) {
-  const int blocks = ceil_div((long long)s.M * kGroup, s.force_block);
+  const int blocks = ceil_div((long long)s.M * step_lanes(s), s.force_block);
   const bool multi = s.nbox > 1;
   switch (mode) {
     case MODE_FORCES:
