@@ -53,6 +53,7 @@ class orc_sys(C.Structure):
         ("bond_model", C.c_int), ("bond_k", C.c_double), ("bond_r0", C.c_double),
         ("n_angles", C.c_int), ("angles", C.POINTER(C.c_int)), ("angle_k", C.c_double),
         ("angle_theta0", C.c_double),
+        ("n_centers", C.c_int), ("centers", C.POINTER(C.c_double)),
     ]
 
 
@@ -164,6 +165,7 @@ class Oracle:
             bond_r0=float(getattr(s, "bond_r0", 0.0)), n_angles=len(k["angles"]) // 3,
             angles=_ptr(k["angles"], C.c_int), angle_k=float(getattr(s, "angle_k", 0.0)),
             angle_theta0=float(getattr(s, "angle_theta0", 0.0)))
+        self.set_centers(getattr(s, "centers", None))
 
     def set_mlp(self, net):
         """Use the learned CG pair force of `net` (an OracleMLP) in place of the table, or
@@ -175,6 +177,13 @@ class Oracle:
         self._keep["tf"] = np.ascontiguousarray(tf, dtype=np.float64)
         self.sys.tf = _ptr(self._keep["tf"])
         self.sys.tf_n = len(self._keep["tf"])
+
+    def set_centers(self, centers):
+        """Resolution centres (n, 3) of the self-adjusting geometry, or None for the slab."""
+        c = np.zeros((0, 3)) if centers is None else np.asarray(centers, dtype=np.float64).reshape(-1, 3)
+        self._keep["centers"] = np.ascontiguousarray(c.reshape(-1))
+        self.sys.n_centers = len(c)
+        self.sys.centers = _ptr(self._keep["centers"])
 
     def weight(self, d: float) -> float:
         return self.lib.orc_weight(C.byref(self.sys), float(d))

@@ -93,8 +93,31 @@ static double mol_mass(const orc_sys* s) {
   return m;
 }
 
+/* Distance of a centre of mass to the nearest resolution centre (3D minimum image) and the
+ * index of that centre (the first one on ties). */
+static double nearest_center(const orc_sys* s, const double* R, int* kmin) {
+  double best = INFINITY;
+  int kb = 0;
+  for (int k = 0; k < s->n_centers; ++k) {
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double t = minimg(R[d] - s->centers[3 * k + d], s->L[d]);
+      r2 += t * t;
+    }
+    const double r = sqrt(r2);
+    if (r < best) {
+      best = r;
+      kb = k;
+    }
+  }
+  if (kmin) *kmin = kb;
+  return best;
+}
+
 /* Centre of mass of every molecule (minimum-image unwrap relative to its first atom,
- * result wrapped into [0,L)), signed x-distance to the slab centre, |d| and lambda. */
+ * result wrapped into [0,L)), the distance d that the resolution function takes (slab: the
+ * signed x-distance to the slab centre, so |d|; spheres: the non-negative distance to the
+ * nearest centre) and lambda. */
 void orc_com_lambda(const orc_sys* s, const double* x, double* R, double* dx_c, double* w) {
   const double Mt = mol_mass(s);
   for (int a = 0; a < s->M; ++a) {
@@ -110,7 +133,7 @@ void orc_com_lambda(const orc_sys* s, const double* x, double* R, double* dx_c, 
       if (r >= s->L[d]) r -= s->L[d];
       R[3 * a + d] = r;
     }
-    double dxc = minimg(R[3 * a] - s->xc, s->L[0]);
+    double dxc = s->n_centers > 0 ? nearest_center(s, R + 3 * a, NULL) : minimg(R[3 * a] - s->xc, s->L[0]);
     if (dx_c) dx_c[a] = dxc;
     if (w) w[a] = orc_weight(s, fabs(dxc));
   }
@@ -312,15 +335,23 @@ static int bonded_mol(const orc_sys* s, const double* x, int a, double* f, doubl
   return ORC_OK;
 }
 
-/* Thermodynamic force on hybrid-layer molecules, along x, away from the centre when
- * positive, spread over the atoms by mass fraction. */
-static void tf_forces(const orc_sys* s, const double* dxc, double* f) {
+/* Thermodynamic force on hybrid-layer molecules, away from the AT region when positive
+ * (slab: along x; spheres: along the direction from the nearest centre), spread over the
+ * atoms by mass fraction. */
+static void tf_forces(const orc_sys* s, const double* R, const double* dxc, double* f) {
   const double Mt = mol_mass(s);
   for (int a = 0; a < s->M; ++a) {
     double d = fabs(dxc[a]);
     if (d < s->d_at || d >= s->d_at + s->d_hy) continue;
-    double F = tf_table(s, d) * (dxc[a] < 0 ? -1.0 : 1.0);
-    for (int k = 0; k < s->na; ++k) f[3 * (a * s->na + k)] += s->mass[k] / Mt * F;
+    double dir[3] = {dxc[a] < 0 ? -1.0 : 1.0, 0.0, 0.0};
+    if (s->n_centers > 0) {
+      int kc;
+      nearest_center(s, R + 3 * a, &kc);
+      for (int q = 0; q < 3; ++q) dir[q] = minimg(R[3 * a + q] - s->centers[3 * kc + q], s->L[q]) / d;
+    }
+    const double F = tf_table(s, d);
+    for (int k = 0; k < s->na; ++k)
+      for (int q = 0; q < 3; ++q) f[3 * (a * s->na + k) + q] += s->mass[k] / Mt * F * dir[q];
   }
 }
 
@@ -401,7 +432,7 @@ int orc_forces(const orc_sys* s, const double* x, int method, const double* w_ov
     free(head); free(next); free(cell);
   }
   for (int a = 0; a < M && st == ORC_OK; ++a) st = bonded_mol(s, x, a, f, acc);
-  tf_forces(s, dxc, f);
+  tf_forces(s, R, dxc, f);
   if (e) memcpy(e, acc, sizeof(acc));
   free(R); free(dxc); free(w);
   return st;
@@ -505,16 +536,24 @@ void orc_rdf(const orc_sys* s, const double* x, int nbins, double dr, int64_t* c
 }
 
 /* Thermodynamic-force iteration: tf_k <- tf_k - alpha * g_k for hybrid-layer nodes,
- * where rho_k = counts_d[k] / (nsamples * 2 tf_dx Ly Lz) is the folded COM density in
- * bin [k dx, (k+1) dx), g_k = (rho_k - rho_{k-1}) / dx is its gradient at node d_k
+ * where rho_k = counts_d[k] / (nsamples * V_k) is the folded COM density in
+ * bin [k dx, (k+1) dx) (V_k: two slabs 2 dx Ly Lz, or n_centers spherical shells),
+ * g_k = (rho_k - rho_{k-1}) / dx is its gradient at node d_k
  * (g_0 = 0 by symmetry, g at the last node one-sided), smoothed by a three-point moving
  * average.  Parity unpinned beyond zero-gradient and linear-profile cases. */
 void orc_tf_update(const orc_sys* s, double* tf, int n, const int64_t* counts_d, int nd,
                    double nsamples, double alpha) {
   double* rho = (double*)calloc(n + 1, sizeof(double));
   double* g = (double*)calloc(n, sizeof(double));
-  double vol = nsamples * 2.0 * s->tf_dx * s->L[1] * s->L[2];
-  for (int k = 0; k < n && k < nd; ++k) rho[k] = counts_d[k] / vol;
+  const double dx = s->tf_dx;
+  for (int k = 0; k < n && k < nd; ++k) {
+    /* bin volume: two slabs of width dx, or a spherical shell around each centre (exact
+     * when the spheres do not overlap) */
+    const double vol = s->n_centers > 0
+                           ? nsamples * s->n_centers * 4.0 / 3.0 * M_PI * ((k + 1.0) * (k + 1.0) * (k + 1.0) - (double)k * k * k) * dx * dx * dx
+                           : nsamples * 2.0 * dx * s->L[1] * s->L[2];
+    rho[k] = counts_d[k] / vol;
+  }
   for (int k = 1; k < n; ++k) g[k] = (k < nd ? (rho[k] - rho[k - 1]) : 0.0) / s->tf_dx;
   for (int k = 0; k < n; ++k) {
     double sum = 0;

@@ -50,6 +50,12 @@ typedef struct {
   int n_angles;
   const int* angles; /* 3 * n_angles local indices (i, vertex, k) */
   double angle_k, angle_theta0;
+  /* self-adjusting geometry (Sec. "Self-adjusting adaptive resolution simulations"): with
+   * n_centers > 0 the AT region is the union of spheres of radius d_at around the centres,
+   * d is the distance of the COM to the nearest centre (3D minimum image) and the
+   * thermodynamic force acts along the direction from that centre */
+  int n_centers;
+  const double* centers; /* 3 * n_centers */
 } orc_sys;
 
 void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

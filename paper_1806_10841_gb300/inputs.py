@@ -72,6 +72,9 @@ class System:
     angles: np.ndarray = None   # (n_angles, 3) int32 local indices (i, vertex, k)
     angle_k: float = 0.0
     angle_theta0: float = 0.0
+    # self-adjusting geometry: resolution centres (n, 3); the AT region is the union of
+    # spheres of radius d_at around them and the hybrid shells have width d_hy (None: slab)
+    centers: np.ndarray = None
 
     @property
     def N(self) -> int:
