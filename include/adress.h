@@ -118,6 +118,17 @@ typedef struct {
   int32_t n_angles;
   const int32_t* angles; /* host [3*n_angles] local atom indices */
   double angle_k, angle_theta0;
+  /* ---- self-adjusting geometry (Sec. "Self-adjusting adaptive resolution simulations") ----
+   * n_centers > 0 (at most 1024, single-system handles only): the AT region is the union of
+   * spheres of radius d_at_half around the resolution centres and the hybrid layer the shells
+   * of width d_hy around them; the resolution function takes the distance of the centre of
+   * mass to the nearest centre (3D minimum image; the first of equal distances) instead of
+   * the slab distance (x_center unused).  The thermodynamic force acts along the direction
+   * from that centre; the density profile bins that distance, and the thermodynamic-force
+   * update divides the counts by the shell volume around every centre (exact when the
+   * spheres do not overlap).  0: the slab. */
+  int32_t n_centers;
+  const double* centers; /* host [3*n_centers] */
 } adress_config;
 
 /* Validate `cfg`, copy its tables, allocate the handle's device buffers on the current
@@ -179,6 +190,11 @@ adress_status adress_step(adress_handle h, int32_t nsteps);
  * one captured CUDA graph (cached per argument set, nsteps <= 1000).  Asynchronous. */
 adress_status adress_run(adress_handle h, int32_t nsteps, int32_t sample_every, int32_t tf_update,
                          double alpha);
+
+/* Move the resolution centres of the self-adjusting geometry (n must equal the configured
+ * n_centers > 0; host [3n], wrapped into the box): the AT region follows them from the next
+ * mapping on, e.g. to track a solute between step calls.  Synchronises. */
+adress_status adress_set_centers(adress_handle h, const double* centers, int32_t n);
 
 /* Radial distribution function numerator of the bound positions: counts (host int64
  * [n_replicas][nbins]) = number of molecule pairs a < b (of the same replica) whose

@@ -20,7 +20,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "neighbour list ov
           7: "invalid state", 8: "molecule wider than the list cutoff allows"}
 
 # Every symbol include/adress.h declares (checked by the CPU test suite).
-EXPORTS = ["adress_init", "adress_init_batch", "adress_rdf", "adress_set_tuning", "adress_get_tuning", "adress_autotune",
+EXPORTS = ["adress_init", "adress_init_batch", "adress_rdf", "adress_set_centers", "adress_set_tuning", "adress_get_tuning", "adress_autotune",
            "adress_bind_state", "adress_build_lists", "adress_compute_forces",
            "adress_step", "adress_run", "adress_set_step", "adress_get_step", "adress_com_lambda", "adress_kinetic",
            "adress_density_accumulate", "adress_density_get", "adress_density_reset",
@@ -60,6 +60,7 @@ class adress_config(C.Structure):
         ("bond_model", C.c_int32), ("bond_k", C.c_double), ("bond_r0", C.c_double),
         ("n_angles", C.c_int32), ("angles", C.POINTER(C.c_int32)), ("angle_k", C.c_double),
         ("angle_theta0", C.c_double),
+        ("n_centers", C.c_int32), ("centers", C.POINTER(C.c_double)),
     ]
 
 
@@ -82,6 +83,7 @@ def load_library(path: str = LIB_PATH):
         "adress_init_batch": ([C.POINTER(adress_config), C.c_int32, vp, C.POINTER(H)], C.c_int),
         "adress_set_tuning": ([H, C.c_int32, C.c_double], C.c_int),
         "adress_rdf": ([H, C.c_int32, C.c_double, i64p], C.c_int),
+        "adress_set_centers": ([H, d, C.c_int32], C.c_int),
         "adress_get_tuning": ([H, C.POINTER(C.c_int32), d], C.c_int),
         "adress_autotune": ([H, C.c_int32, d, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
         "adress_bind_state": ([H, vp, vp, vp], C.c_int),
@@ -146,6 +148,8 @@ def _config(s, keep, replica, max_neighbors, precision):
         lj_eps=np.ascontiguousarray(s.lj_eps if nb_model else np.zeros(s.na), dtype=np.float64),
         lj_sig=np.ascontiguousarray(s.lj_sig if nb_model else np.zeros(s.na), dtype=np.float64),
         angles=np.ascontiguousarray(np.asarray(ang if ang is not None else np.zeros((0, 3)), dtype=np.int32).reshape(-1)),
+        centers=np.ascontiguousarray(np.asarray(getattr(s, "centers", None) if getattr(s, "centers", None) is not None
+                                                else np.zeros((0, 3)), dtype=np.float64).reshape(-1)),
     )
     keep.append(arrs)
     tf_n = len(arrs["tf"])
@@ -165,7 +169,8 @@ def _config(s, keep, replica, max_neighbors, precision):
         bond_model=int(getattr(s, "bond_model", 0)), bond_k=float(getattr(s, "bond_k", 0.0)),
         bond_r0=float(getattr(s, "bond_r0", 0.0)), n_angles=len(arrs["angles"]) // 3,
         angles=arrs["angles"].ctypes.data_as(C.POINTER(C.c_int32)), angle_k=float(getattr(s, "angle_k", 0.0)),
-        angle_theta0=float(getattr(s, "angle_theta0", 0.0)))
+        angle_theta0=float(getattr(s, "angle_theta0", 0.0)),
+        n_centers=len(arrs["centers"]) // 3, centers=_dptr(arrs["centers"]) if len(arrs["centers"]) else None)
 
 
 class AdResS:
@@ -337,6 +342,11 @@ class AdResS:
         tf = np.zeros(self.tf_n)
         self._call("adress_get_tf", _dptr(tf), self.tf_n)
         return tf
+
+    def set_centers(self, centers):
+        """Move the resolution centres (n, 3) of the self-adjusting geometry."""
+        c = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1))
+        self._call("adress_set_centers", _dptr(c), C.c_int32(len(c) // 3))
 
     def set_tuning(self, force_block: int, skin: float):
         self._call("adress_set_tuning", C.c_int32(int(force_block)), C.c_double(float(skin)))

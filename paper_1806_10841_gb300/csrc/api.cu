@@ -54,6 +54,8 @@ struct adress_ctx {
   int* cell_rank = nullptr;
   int* nbr_cells = nullptr;  // [ncell][27]
   int ncell_cap = 0;
+  double4_32a* cen64 = nullptr;  // resolution centres (self-adjusting geometry)
+  int4* cen32 = nullptr;
   double skin0 = 0.0;  // skin of the configuration (the autotuner scales it)
   // radial distribution function scratch
   double* rdf_com = nullptr;
@@ -203,6 +205,10 @@ static std::string config_error(const adress_config* c) {
   }
   if (c->n_angles > 0 && (!(c->angle_k >= 0) || !(c->angle_theta0 > 0) || !(c->angle_theta0 <= M_PI)))
     return "angle_k >= 0 and 0 < angle_theta0 <= pi needed";
+  if (c->n_centers < 0 || c->n_centers > kMaxCenters || (c->n_centers > 0 && !c->centers))
+    return "n_centers must be 0..1024 with a centre array";
+  for (int q = 0; q < 3 * c->n_centers; ++q)
+    if (!(c->centers[q] == c->centers[q]) || isinf(c->centers[q])) return "resolution centres must be finite";
   return "";
 }
 
@@ -367,6 +373,27 @@ static adress_status setup_cells(adress_ctx* h, double skin) {
   return ADRESS_OK;
 }
 
+// Resolution centres wrapped into the box, in double and in 32-bit fixed point.
+static adress_status upload_centers(adress_ctx* h, const double* c, int n) {
+  const Box& B = h->boxes[0];
+  std::vector<double4_32a> c64(n);
+  std::vector<int4> c32(n);
+  for (int k = 0; k < n; ++k) {
+    double w[3];
+    for (int d = 0; d < 3; ++d) {
+      w[d] = c[3 * k + d] - B.L[d] * floor(c[3 * k + d] / B.L[d]);
+      if (w[d] >= B.L[d]) w[d] -= B.L[d];
+    }
+    c64[k] = make_double4_32a(w[0], w[1], w[2], 0.0);
+    c32[k] = make_int4((int)fixed32_host(w[0], B.fxK[0], B.fxq[0]), (int)fixed32_host(w[1], B.fxK[1], B.fxq[1]),
+                       (int)fixed32_host(w[2], B.fxK[2], B.fxq[2]), 0);
+  }
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->cen64, c64.data(), sizeof(double4_32a) * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(h->cen32, c32.data(), sizeof(int4) * n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
+}
+
 static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream, adress_handle* out) {
   if (!out) return fail(nullptr, ADRESS_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -390,6 +417,10 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
                         "box edge shorter than twice the list cutoff");
     mtot += cfgs[k].n_mols;
   }
+  if (nbox > 1)
+    for (int k = 0; k < nbox; ++k)
+      if (cfgs[k].n_centers > 0)
+        return fail(nullptr, ADRESS_ERR_ARG, "resolution centres are supported for single-system handles only");
   if (mtot > 4096 * 2048 - 1)
     return fail(nullptr, ADRESS_ERR_ARG, "too many molecules for the device scans (max 8388607)");
   const adress_config* c = &cfgs[0];
@@ -481,6 +512,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
       }
     s.f.krf2 = (float)(2.0 * s.krf);
   }
+  s.n_centers = c->n_centers;
   s.bond_model = c->bond_model;
   s.bond_k = c->bond_k;
   s.bond_r0 = c->bond_r0;
@@ -536,6 +568,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
       A(b.molf[p], M);
       A(b.off32[p], N);
     }
+    if (c->n_centers > 0) A(b.kcen[p], M);
   }
   A(b.mcell, M);
   A(b.sorted, M);
@@ -564,6 +597,10 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   A(b.hist, ntf);
   A(b.nsamples, 1);
   A(b.ctrl, 1);
+  if (c->n_centers > 0) {
+    A(h->cen64, c->n_centers);
+    A(h->cen32, c->n_centers);
+  }
   if (nbox > 1) {
     A(h->d_boxes, nbox);
     A(h->mol_box, M);
@@ -571,6 +608,8 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
 #undef A
   b.boxes = h->d_boxes;
   b.mol_box = h->mol_box;
+  b.cen64 = h->cen64;
+  b.cen32 = h->cen32;
   if (e != cudaSuccess) {
     adress_destroy(h);
     return fail(nullptr, ADRESS_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
@@ -618,6 +657,14 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
     std::string msg = std::string("init upload: ") + cudaGetErrorString(e);
     adress_destroy(h);
     return fail(nullptr, ADRESS_ERR_CUDA, msg);
+  }
+  if (c->n_centers > 0) {
+    adress_status st2 = upload_centers(h, c->centers, c->n_centers);
+    if (st2 != ADRESS_OK) {
+      const std::string msg = h->err;
+      adress_destroy(h);
+      return fail(nullptr, st2, msg);
+    }
   }
   *out = h;
   return ADRESS_OK;
@@ -917,6 +964,15 @@ adress_status adress_com_lambda(adress_handle h, double* com, double* w) {
   CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream, DecideArgs{0, 0, 0, 0}));
   CUDA_OR_FAIL(h, launch_export_com(h->sys, h->buf, h->precision, com, w, h->stream));
   return ADRESS_OK;
+}
+
+adress_status adress_set_centers(adress_handle h, const double* centers, int32_t n) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (h->sys.n_centers == 0 || n != h->sys.n_centers || !centers)
+    return fail(h, ADRESS_ERR_ARG, "set_centers needs the configured number of resolution centres");
+  for (int q = 0; q < 3 * n; ++q)
+    if (!(centers[q] == centers[q]) || isinf(centers[q])) return fail(h, ADRESS_ERR_ARG, "resolution centres must be finite");
+  return upload_centers(h, centers, n);
 }
 
 adress_status adress_rdf(adress_handle h, int32_t nbins, double dr, int64_t* counts) {

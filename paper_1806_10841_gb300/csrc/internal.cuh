@@ -13,6 +13,7 @@ namespace adress {
 constexpr int kMaxNA = 4;
 constexpr int kMaxBonds = 6;
 constexpr int kMaxAngles = 4;
+constexpr int kMaxCenters = 1024;  // resolution centres of the self-adjusting geometry
 constexpr int kGroup = 4;  // threads per molecule in the force kernel
 
 // Device control block: list-validity trackers, error word, counters.
@@ -100,6 +101,9 @@ struct Sys {
   int n_angles;
   int angles[3 * kMaxAngles];
   double angle_k, angle_theta0;
+  // self-adjusting geometry: n_centers > 0 makes the AT region the union of spheres of
+  // radius d_at around the centres (Bufs::cen64 / cen32); d is the distance to the nearest
+  int n_centers;
   // float copies of the parameters the FP32 path uses (no run-time double->float work)
   struct {
     float eps, sig2, rc_at, rc_at2, rc_cg2, cg_inv_dr, fene_k, fene_r02;
@@ -121,8 +125,11 @@ struct Bufs {
   int4* com_fx[2];         // fixed-point COM (uint32 bits) + float bits of w
   int4* com_ref;           // fixed-point COM at the last list build
   double4_32a* com64[2];   // FP64 path: COM + w
-  double* dxc64[2];        // FP64 path: signed x distance to the slab centre
-  float2* molf[2];         // FP32 path: (signed x distance, 1 if in the hybrid layer)
+  double* dxc64[2];        // FP64 path: signed x distance to the slab centre (spheres: distance
+                           // to the nearest centre)
+  float2* molf[2];         // FP32 path: (signed x distance or distance to the nearest centre,
+                           // 1 if in the hybrid layer)
+  int* kcen[2];            // spheres: index of the nearest centre
   // per atom, double-buffered
   double4_32a* off64[2];   // COM-relative atom offsets (FP64 path)
   float4* off32[2];        // (FP32 path)
@@ -166,6 +173,8 @@ struct Bufs {
   const int* mol_box;  // [M] box of each molecule
   const int* cell_box; // [ncell] box of each global cell rank
   int* dense_cells;     // [ncell] cells the dense-cell list builder handles
+  const double4_32a* cen64;  // [n_centers] resolution centres (spheres)
+  const int4* cen32;         // the same in 32-bit fixed point
   const int* nbr_cells; // [ncell][27] Morton ranks of each cell's neighbour cells (-1: none)
 };
 

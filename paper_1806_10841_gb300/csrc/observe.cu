@@ -106,6 +106,33 @@ __device__ double com_x64(const Sys& s, const Box& B, const double* x, int a) {
   return r;
 }
 
+// Distance of molecule a's centre of mass (in double, from x, as the definition forms it) to
+// the nearest resolution centre (the first of equal distances).
+template <int NA>
+__device__ double center_d64(const Sys& s, const Box& B, const Bufs& b, int a) {
+  const size_t N = (size_t)s.N;
+  double R[3];
+  for (int d = 0; d < 3; ++d) {
+    const double x0 = b.x[d * N + a * NA];
+    double acc = 0.0;
+    for (int k = 0; k < NA; ++k) acc += s.mass[k] * (x0 + minimg_cmp(b.x[d * N + a * NA + k] - x0, B.L[d], B.halfL[d]));
+    double r = acc / s.Mtot;
+    r -= B.L[d] * floor(r / B.L[d]);
+    if (r >= B.L[d]) r -= B.L[d];
+    R[d] = r;
+  }
+  double best = INFINITY;
+  for (int k = 0; k < s.n_centers; ++k) {
+    const double4_32a C = b.cen64[k];
+    const double t0 = minimg_cmp(R[0] - C.x, B.L[0], B.halfL[0]);
+    const double t1 = minimg_cmp(R[1] - C.y, B.L[1], B.halfL[1]);
+    const double t2 = minimg_cmp(R[2] - C.z, B.L[2], B.halfL[2]);
+    const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(t0, t0), __dmul_rn(t1, t1)), __dmul_rn(t2, t2)));
+    if (r < best) best = r;
+  }
+  return best;
+}
+
 // COM histogram folded about the slab centre: bin floor(|dxc| / tf_dx), integer atomics
 // (one histogram of tf_n bins per box).  The FP32 path takes |dxc| from its float mapping
 // and recomputes it in double for the few molecules within 1e-4 of a bin edge, so the bin
@@ -129,7 +156,9 @@ __global__ void __launch_bounds__(1024) k_density(const __grid_constant__ Sys s,
       const float u = fabsf(b.molf[cur][a].x) * s.f.tf_inv_dx, fr = u - floorf(u);
       k = (int)floorf(u);
       if (fr < 1e-4f || fr > 1.f - 1e-4f)
-        k = (int)floor(fabs(minimg_cmp(com_x64<NA>(s, B, b.x, a) - B.xc, B.L[0], B.halfL[0])) / s.tf_dx);
+        k = (int)floor((s.n_centers > 0 ? center_d64<NA>(s, B, b, a)
+                                        : fabs(minimg_cmp(com_x64<NA>(s, B, b.x, a) - B.xc, B.L[0], B.halfL[0]))) /
+                       s.tf_dx);
     }
     if (k < s.tf_n) {
       if (multi) atomicAdd(&b.hist[B.tf0 + k], 1ull);
@@ -144,7 +173,8 @@ __global__ void __launch_bounds__(1024) k_density(const __grid_constant__ Sys s,
 }
 
 // Thermodynamic-force iteration on the accumulated profile, one block per box (tf_n nodes):
-// rho_k = counts_k / (nsamples 2 dx Ly Lz), g_k = (rho_k - rho_{k-1})/dx, g_0 = 0,
+// rho_k = counts_k / (nsamples V_k) (V_k: 2 dx Ly Lz, or the shells around the resolution
+// centres), g_k = (rho_k - rho_{k-1})/dx, g_0 = 0,
 // three-point moving average, tf_k -= alpha g_k on hybrid-layer nodes, then the box's
 // histogram is cleared (the sample count is cleared by the launcher afterwards).
 __global__ void k_tf_update(const __grid_constant__ Sys s, Bufs b, double alpha) {
@@ -152,10 +182,16 @@ __global__ void k_tf_update(const __grid_constant__ Sys s, Bufs b, double alpha)
   const Box& B = s.nbox > 1 ? b.boxes[blockIdx.x] : s.bx;
   const int n = s.tf_n, o = B.tf0;
   const double ns = (double)(*b.nsamples);
-  const double vol = ns * 2.0 * s.tf_dx * B.L[1] * B.L[2];
+  // bin volume: two slabs, or a spherical shell around each resolution centre
+  auto vol = [&](int k) {
+    const double dx = s.tf_dx;
+    return s.n_centers > 0
+               ? ns * s.n_centers * 4.0 / 3.0 * M_PI * ((k + 1.0) * (k + 1.0) * (k + 1.0) - (double)k * k * k) * dx * dx * dx
+               : ns * 2.0 * dx * B.L[1] * B.L[2];
+  };
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     double gk = 0.0;
-    if (k > 0 && ns > 0) gk = ((double)b.hist[o + k] / vol - (double)b.hist[o + k - 1] / vol) / s.tf_dx;
+    if (k > 0 && ns > 0) gk = ((double)b.hist[o + k] / vol(k) - (double)b.hist[o + k - 1] / vol(k - 1)) / s.tf_dx;
     g[k] = gk;
   }
   __syncthreads();

@@ -200,6 +200,85 @@ __device__ __forceinline__ double com_x_fp64(const Sys& s, const Box& B, unsigne
   return r;
 }
 
+// Nearest resolution centre of a molecule (self-adjusting geometry): the group's four lanes
+// take every fourth centre, then reduce (distance, index) so that the first of equal
+// distances wins, as the definition states.  FP32: from the fixed-point centres.
+__device__ __forceinline__ float nearest_center32(const Sys& s, const Box& B, const Bufs& b, unsigned gmask, int g,
+                                                  const unsigned R[3], int& kmin) {
+  float best = INFINITY;
+  int kb = 0x7fffffff;
+  for (int k = g; k < s.n_centers; k += 4) {
+    const int4 C = b.cen32[k];
+    const float r = sqrtf(pair_r2((float)(int)(R[0] - (unsigned)C.x) * B.fx_scale[0],
+                                  (float)(int)(R[1] - (unsigned)C.y) * B.fx_scale[1],
+                                  (float)(int)(R[2] - (unsigned)C.z) * B.fx_scale[2]));
+    if (r < best) {
+      best = r;
+      kb = k;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    const float ob = __shfl_xor_sync(gmask, best, o);
+    const int ok = __shfl_xor_sync(gmask, kb, o);
+    if (ob < best || (ob == best && ok < kb)) {
+      best = ob;
+      kb = ok;
+    }
+  }
+  kmin = kb;
+  return best;
+}
+
+// FP64: from a double centre of mass, the sum of squares in the definition's order.
+__device__ __forceinline__ double nearest_center64(const Sys& s, const Box& B, const Bufs& b, unsigned gmask, int g,
+                                                   const double R[3], int& kmin) {
+  double best = INFINITY;
+  int kb = 0x7fffffff;
+  for (int k = g; k < s.n_centers; k += 4) {
+    const double4_32a C = b.cen64[k];
+    const double t0 = minimg_cmp(R[0] - C.x, B.L[0], B.halfL[0]);
+    const double t1 = minimg_cmp(R[1] - C.y, B.L[1], B.halfL[1]);
+    const double t2 = minimg_cmp(R[2] - C.z, B.L[2], B.halfL[2]);
+    const double r = sqrt(__dadd_rn(__dadd_rn(__dmul_rn(t0, t0), __dmul_rn(t1, t1)), __dmul_rn(t2, t2)));
+    if (r < best) {
+      best = r;
+      kb = k;
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1) {
+    const double ob = shfl_xor_d(gmask, best, o);
+    const int ok = __shfl_xor_sync(gmask, kb, o);
+    if (ob < best || (ob == best && ok < kb)) {
+      best = ob;
+      kb = ok;
+    }
+  }
+  kmin = kb;
+  return best;
+}
+
+// Centre of mass in double exactly as the definition forms it (all lanes of the group get it).
+template <int NA>
+__device__ __forceinline__ void com_fp64(const Sys& s, const Box& B, unsigned gmask, int base, const double x[3],
+                                         double R[3]) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double x0 = shfl_d(gmask, x[d], base);
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      const double xkk = shfl_d(gmask, x[d], base + k);
+      acc += s.mass[k] * (x0 + minimg_cmp(xkk - x0, B.L[d], B.halfL[d]));
+    }
+    double r = acc / s.Mtot;
+    r -= B.L[d] * floor(r / B.L[d]);
+    if (r >= B.L[d]) r -= B.L[d];
+    R[d] = r;
+  }
+}
+
 // Map one molecule: fixed-point centre, resolution value, offsets, region flag.
 // P32: integer fixed-point arithmetic (exact, periodic) on the bits of the doubles.
 template <int NA>
@@ -229,14 +308,25 @@ __device__ __forceinline__ void map_group32(const Sys& s, const Box& B, const Bu
     b.off32[nxt][a * NA + g] = o;
     ext2 = fmaxf(ext2, o.x * o.x + o.y * o.y + o.z * o.z);
   }
-  // signed x distance to the slab centre; region decided in FP64 near a boundary
-  const float dxc = (float)(int)(R[0] - B.xc32) * B.fx_scale[0];
+  // signed x distance to the slab centre (spheres: distance to the nearest centre); region
+  // decided in FP64 near a boundary
+  int kmin = 0;
+  const float dxc = s.n_centers > 0 ? nearest_center32(s, B, b, gmask, g, R, kmin)
+                                    : (float)(int)(R[0] - B.xc32) * B.fx_scale[0];
   float dd = fabsf(dxc);
   const bool near = fabsf(dd - B.d_at_f) < B.near_at || fabsf(dd - B.d_hyend_f) < B.near_hyend;
   int region;  // 0 AT, 1 hybrid, 2 CG
   if (__any_sync(gmask, live && near)) {
-    const double rx = com_x_fp64<NA>(s, B, gmask, base, g, x[0]);
-    const double dxd = fabs(minimg_cmp(rx - B.xc, B.L[0], B.halfL[0]));
+    double dxd;
+    if (s.n_centers > 0) {
+      double R64[3];
+      com_fp64<NA>(s, B, gmask, base, x, R64);
+      int k64;
+      dxd = nearest_center64(s, B, b, gmask, g, R64, k64);
+    } else {
+      const double rx = com_x_fp64<NA>(s, B, gmask, base, g, x[0]);
+      dxd = fabs(minimg_cmp(rx - B.xc, B.L[0], B.halfL[0]));
+    }
     region = dxd < B.d_at ? 0 : (dxd >= B.d_at + B.d_hy ? 2 : 1);
   } else {
     region = dd < B.d_at_f ? 0 : (dd >= B.d_hyend_f ? 2 : 1);
@@ -249,6 +339,7 @@ __device__ __forceinline__ void map_group32(const Sys& s, const Box& B, const Bu
     }
     b.com_fx[nxt][a] = make_int4((int)R[0], (int)R[1], (int)R[2], __float_as_int(w));
     b.molf[nxt][a] = make_float2(dxc, region == 1 ? 1.f : 0.f);
+    if (s.n_centers > 0) b.kcen[nxt][a] = kmin;
     const int4 ref = b.com_ref[a];
     const float d0 = (float)(int)(R[0] - (unsigned)ref.x) * B.fx_scale[0];
     const float d1 = (float)(int)(R[1] - (unsigned)ref.y) * B.fx_scale[1];
@@ -281,8 +372,10 @@ __device__ __forceinline__ void map_group64(const Sys& s, const Box& B, const Bu
     b.off64[nxt][a * NA + g] = make_double4_32a(o0, o1, o2, 0.0);
     ext2 = fmaxf(ext2, (float)(o0 * o0 + o1 * o1 + o2 * o2));
   }
+  int kmin = 0;
+  const double dxc = s.n_centers > 0 ? nearest_center64(s, B, b, gmask, g, R, kmin)
+                                     : minimg_cmp(R[0] - B.xc, B.L[0], B.halfL[0]);
   if (live && g == 0) {
-    const double dxc = minimg_cmp(R[0] - B.xc, B.L[0], B.halfL[0]);
     const double dd = fabs(dxc);
     double w;
     if (dd < B.d_at) w = 1.0;
@@ -293,6 +386,7 @@ __device__ __forceinline__ void map_group64(const Sys& s, const Box& B, const Bu
     }
     b.com64[nxt][a] = make_double4_32a(R[0], R[1], R[2], w);
     b.dxc64[nxt][a] = dxc;
+    if (s.n_centers > 0) b.kcen[nxt][a] = kmin;
     unsigned X[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) X[d] = (unsigned)(unsigned long long)llrint(R[d] * B.fx_inv[d]);
@@ -682,7 +776,30 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
         } else if (k + 1 == s.tf_n && u == (real)k) {
           F = Q::tf(b, B.tf0 + k);
         }
-        fx += frac_g * (dxc < (real)0 ? -F : F);
+        if (s.n_centers > 0) {
+          // along the direction from the nearest centre
+          const int kc = b.kcen[cur][a];
+          real ux, uy, uz;
+          if (P::fp64) {
+            const double4_32a C = b.cen64[kc];
+            const auto& R64 = Ca;
+            ux = (real)minimg_cmp(R64.x - C.x, B.L[0], B.halfL[0]);
+            uy = (real)minimg_cmp(R64.y - C.y, B.L[1], B.halfL[1]);
+            uz = (real)minimg_cmp(R64.z - C.z, B.L[2], B.halfL[2]);
+          } else {
+            const int4 C = b.cen32[kc];
+            const auto& R32 = Ca;
+            ux = (real)((float)(int)((unsigned)R32.x - (unsigned)C.x) * B.fx_scale[0]);
+            uy = (real)((float)(int)((unsigned)R32.y - (unsigned)C.y) * B.fx_scale[1]);
+            uz = (real)((float)(int)((unsigned)R32.z - (unsigned)C.z) * B.fx_scale[2]);
+          }
+          const real fd = frac_g * Q::div_(F, d);
+          fx += fd * ux;
+          fy += fd * uy;
+          fz += fd * uz;
+        } else {
+          fx += frac_g * (dxc < (real)0 ? -F : F);
+        }
       }
     }
   }
