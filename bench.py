@@ -368,6 +368,45 @@ def water_arm(timed, steps, local):
     return out
 
 
+def spheres_arm(timed, steps, local):
+    """Self-adjusting geometry on the 800k-atom fluid: the AT region is the union of 16
+    spheres (radius 10, hybrid shell 5) around centres drawn in the box, which move by a
+    random displacement of 1 sigma between bench steps (adress_set_centers), FP32 mixed."""
+    import torch
+
+    from paper_1806_10841_gb300 import adress, inputs
+
+    s = inputs.c2_800k()
+    s.d_at, s.d_hy = 10.0, 5.0
+    s.tf = np.zeros(int(math.ceil((s.d_at + s.d_hy) / s.tf_dx)) + 2)
+    rng = np.random.default_rng(20180628)
+    L = np.array(s.box)
+    s.centers = rng.uniform(0, 1, (16, 3)) * L
+    x, v = inputs.tetra_state(s)
+    sim = adress.AdResS(s, precision="fp32", device=f"cuda:{local}")
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    for _ in range(2):
+        run_block(sim)
+    sim.check()
+    c = s.centers.copy()
+    ms = []
+    for _ in range(steps):
+        c = c + rng.normal(0, 1.0 / math.sqrt(3.0), c.shape)
+        sim.set_centers(c)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        run_block(sim)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    sim.check()
+    st = sim.list_stats()
+    sim.close()
+    return {"value": s.N * MD_PER_BLOCK * steps / (sum(ms) / 1e3), "unit": "atom-steps/s", "centers": 16,
+            "radius": s.d_at, "hybrid_shell": s.d_hy, "hr_molecules": st["n_hr"], "ms_per_bench_step": ms}
+
+
 def replicas_arm(timed, steps, local):
     """64 independent replicas (log-uniform 500..20000 molecules, AT width U(3, 15), hybrid
     U(1, 5)) in one handle: every MD step is one launch over all replicas' molecules, the
@@ -431,6 +470,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-CG-force arm")
     ap.add_argument("--no-replicas", action="store_true", help="skip the 64-replica batch arm")
     ap.add_argument("--no-water", action="store_true", help="skip the water-like fluid arm")
+    ap.add_argument("--no-spheres", action="store_true", help="skip the self-adjusting-geometry arm")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up, run this many MD steps, exit (no timing output)")
     ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1],
@@ -600,6 +640,9 @@ def main():
     water = None
     if not args.no_water and rank == 0:
         water = water_arm(timed, max(2, args.steps // 2), local)
+    spheres = None
+    if not args.no_spheres and rank == 0:
+        spheres = spheres_arm(timed, max(2, args.steps // 2), local)
 
     if rank != 0:
         if dist:
@@ -667,6 +710,7 @@ def main():
         "learned_cg": learned,
         "replicas_64": replicas,
         "water_64k": water,
+        "spheres_16": spheres,
         "per_step_ms": ms,
     }
     if not args.no_cpu_baseline:
