@@ -54,6 +54,7 @@ class orc_sys(C.Structure):
         ("n_angles", C.c_int), ("angles", C.POINTER(C.c_int)), ("angle_k", C.c_double),
         ("angle_theta0", C.c_double),
         ("n_centers", C.c_int), ("centers", C.POINTER(C.c_double)),
+        ("scheme", C.c_int),
     ]
 
 
@@ -166,6 +167,7 @@ class Oracle:
             angles=_ptr(k["angles"], C.c_int), angle_k=float(getattr(s, "angle_k", 0.0)),
             angle_theta0=float(getattr(s, "angle_theta0", 0.0)))
         self.set_centers(getattr(s, "centers", None))
+        self.sys.scheme = int(getattr(s, "scheme", 0))
 
     def set_mlp(self, net):
         """Use the learned CG pair force of `net` (an OracleMLP) in place of the table, or

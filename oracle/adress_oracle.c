@@ -202,10 +202,13 @@ static double tf_table(const orc_sys* s, double d) {
 /* Accumulators: e[0]=E_AT (weighted), e[1]=E_CG (weighted), e[2]=E_bond,
  * e[3]=virial sum r.f (nonbonded + bonded). */
 
-/* Interaction of molecules a and b (a != b), Eq. 1, added to both (Newton's 3rd law). */
+/* Interaction of molecules a and b (a != b), added to both (Newton's 3rd law): Eq. 1 with
+ * w_ab = l_a l_b, or (energy interpolation) the pair terms of Eq. Hmix with
+ * w_ab = (l_a + l_b)/2.  vat / vcg (may be NULL) collect the single-molecule potentials of
+ * Eq. Hmix: half of every pair's unweighted AT and CG energy to each molecule. */
 static void pair_ab(const orc_sys* s, const double* x, const double* R, const double* w, int a,
-                    int b, double* f, double* e) {
-  const double wab = w[a] * w[b];
+                    int b, double* f, double* e, double* vat, double* vcg) {
+  const double wab = s->scheme == 1 ? 0.5 * (w[a] + w[b]) : w[a] * w[b];
   const int na = s->na;
   if (wab > 0.0) {
     const double rc2 = s->rc_at * s->rc_at;
@@ -224,6 +227,10 @@ static void pair_ab(const orc_sys* s, const double* x, const double* R, const do
         }
         e[0] += wab * V;
         e[3] += wab * fr * r2;
+        if (vat) {
+          vat[a] += 0.5 * V;
+          vat[b] += 0.5 * V;
+        }
       }
   }
   if (wab < 1.0) {
@@ -250,6 +257,10 @@ static void pair_ab(const orc_sys* s, const double* x, const double* R, const do
           f[3 * (b * na + k) + d] -= s->mass[k] / Mt * c * Rab[d];
         }
       e[1] += (1.0 - wab) * V;
+      if (vcg) {
+        vcg[a] += 0.5 * V;
+        vcg[b] += 0.5 * V;
+      }
       e[3] += c * r2;
     }
   }
@@ -355,6 +366,31 @@ static void tf_forces(const orc_sys* s, const double* R, const double* dxc, doub
   }
 }
 
+/* Drift force of energy interpolation (Eq. Hmix): the position derivative of l(R_a) in
+ * l_a V_AT_a + (1 - l_a) V_CG_a gives F_i = -(V_AT_a - V_CG_a) l'(d_a) (m_i/M) grad d_a on
+ * the atoms of molecule a, with l'(d) = -(pi/(2 d_hy)) sin(pi (d - d_at)/d_hy) in the hybrid
+ * layer and 0 elsewhere, grad d = sign(x - x_c) x (slab) or (R - c)/d (nearest centre).
+ * vat == NULL (lambda held fixed) gives no drift force. */
+static void drift_forces(const orc_sys* s, const double* R, const double* dxc, const double* vat,
+                         const double* vcg, double* f) {
+  if (!vat || s->d_hy <= 0.0) return;
+  const double Mt = mol_mass(s);
+  for (int a = 0; a < s->M; ++a) {
+    const double d = fabs(dxc[a]);
+    if (d <= s->d_at || d >= s->d_at + s->d_hy) continue;
+    const double dl = -(M_PI / (2.0 * s->d_hy)) * sin(M_PI * (d - s->d_at) / s->d_hy);
+    double dir[3] = {dxc[a] < 0 ? -1.0 : 1.0, 0.0, 0.0};
+    if (s->n_centers > 0) {
+      int kc;
+      nearest_center(s, R + 3 * a, &kc);
+      for (int q = 0; q < 3; ++q) dir[q] = minimg(R[3 * a + q] - s->centers[3 * kc + q], s->L[q]) / d;
+    }
+    const double F = -(vat[a] - vcg[a]) * dl;
+    for (int k = 0; k < s->na; ++k)
+      for (int q = 0; q < 3; ++q) f[3 * (a * s->na + k) + q] += s->mass[k] / Mt * F * dir[q];
+  }
+}
+
 /* Largest atom-to-COM distance over all molecules. */
 static double max_extent(const orc_sys* s, const double* x, const double* R) {
   double m = 0;
@@ -384,10 +420,12 @@ int orc_forces(const orc_sys* s, const double* x, int method, const double* w_ov
   memset(f, 0, sizeof(double) * 3 * (size_t)M * s->na);
   double acc[4] = {0, 0, 0, 0};
   int st = ORC_OK;
+  double* vat = s->scheme == 1 ? (double*)calloc(M, sizeof(double)) : NULL;
+  double* vcg = s->scheme == 1 ? (double*)calloc(M, sizeof(double)) : NULL;
 
   if (method == 0) {
     for (int a = 0; a < M; ++a)
-      for (int b = a + 1; b < M; ++b) pair_ab(s, x, R, w, a, b, f, acc);
+      for (int b = a + 1; b < M; ++b) pair_ab(s, x, R, w, a, b, f, acc, vat, vcg);
   } else {
     double ext = max_extent(s, x, R);
     double reach = s->rc_cg > s->rc_at + 2 * ext ? s->rc_cg : s->rc_at + 2 * ext;
@@ -426,13 +464,18 @@ int orc_forces(const orc_sys* s, const double* x, int method, const double* w_ov
             if (dup) continue;
             seen[ns++] = nbc;
             for (int b = head[nbc]; b >= 0; b = next[b])
-              if (b > a) pair_ab(s, x, R, w, a, b, f, acc);
+              if (b > a) pair_ab(s, x, R, w, a, b, f, acc, vat, vcg);
           }
     }
     free(head); free(next); free(cell);
   }
   for (int a = 0; a < M && st == ORC_OK; ++a) st = bonded_mol(s, x, a, f, acc);
   tf_forces(s, R, dxc, f);
+  if (vat) {
+    drift_forces(s, R, dxc, w_override ? NULL : vat, vcg, f);
+    free(vat);
+    free(vcg);
+  }
   if (e) memcpy(e, acc, sizeof(acc));
   free(R); free(dxc); free(w);
   return st;

@@ -56,6 +56,10 @@ typedef struct {
    * thermodynamic force acts along the direction from that centre */
   int n_centers;
   const double* centers; /* 3 * n_centers */
+  /* scheme 0: force interpolation (Eq. 1); scheme 1: energy interpolation (Eq. Hmix,
+   * H-AdResS): pair terms weighted by (l_a + l_b)/2 and the drift force
+   * -(V_AT_a - V_CG_a) grad l_a on the atoms of each hybrid molecule */
+  int scheme;
 } orc_sys;
 
 void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -75,6 +75,8 @@ class System:
     # self-adjusting geometry: resolution centres (n, 3); the AT region is the union of
     # spheres of radius d_at around them and the hybrid shells have width d_hy (None: slab)
     centers: np.ndarray = None
+    # 0: force interpolation (Eq. 1); 1: energy interpolation (H-AdResS, Eq. Hmix)
+    scheme: int = 0
 
     @property
     def N(self) -> int:
