@@ -55,6 +55,7 @@ class orc_sys(C.Structure):
         ("angle_theta0", C.c_double),
         ("n_centers", C.c_int), ("centers", C.POINTER(C.c_double)),
         ("scheme", C.c_int),
+        ("fec_n", C.c_int), ("fec", C.POINTER(C.c_double)),
     ]
 
 
@@ -168,6 +169,10 @@ class Oracle:
             angle_theta0=float(getattr(s, "angle_theta0", 0.0)))
         self.set_centers(getattr(s, "centers", None))
         self.sys.scheme = int(getattr(s, "scheme", 0))
+        fec = getattr(s, "fec", None)
+        self._fec = np.ascontiguousarray(np.asarray(fec if fec is not None else [], dtype=np.float64))
+        self.sys.fec_n = len(self._fec)
+        self.sys.fec = _ptr(self._fec) if len(self._fec) else None
 
     def set_mlp(self, net):
         """Use the learned CG pair force of `net` (an OracleMLP) in place of the table, or

@@ -366,13 +366,25 @@ static void tf_forces(const orc_sys* s, const double* R, const double* dxc, doub
   }
 }
 
+/* Free-energy correction derivative g(l) = dDF/dl: linear between the nodes l_k = k/(n-1). */
+double orc_fec_g(const orc_sys* s, double l) {
+  if (s->fec_n < 2) return 0.0;
+  const double u = l * (s->fec_n - 1);
+  int k = (int)floor(u);
+  if (k >= s->fec_n - 1) return s->fec[s->fec_n - 1];
+  if (k < 0) k = 0;
+  const double t = u - k;
+  return s->fec[k] * (1.0 - t) + s->fec[k + 1] * t;
+}
+
 /* Drift force of energy interpolation (Eq. Hmix): the position derivative of l(R_a) in
  * l_a V_AT_a + (1 - l_a) V_CG_a gives F_i = -(V_AT_a - V_CG_a) l'(d_a) (m_i/M) grad d_a on
  * the atoms of molecule a, with l'(d) = -(pi/(2 d_hy)) sin(pi (d - d_at)/d_hy) in the hybrid
  * layer and 0 elsewhere, grad d = sign(x - x_c) x (slab) or (R - c)/d (nearest centre).
- * vat == NULL (lambda held fixed) gives no drift force. */
-static void drift_forces(const orc_sys* s, const double* R, const double* dxc, const double* vat,
-                         const double* vcg, double* f) {
+ * The free-energy correction -DF(l_a) adds +g(l_a) l'(d_a) grad d_a.  vat == NULL (lambda
+ * held fixed) gives neither. */
+static void drift_forces(const orc_sys* s, const double* R, const double* dxc, const double* w,
+                         const double* vat, const double* vcg, double* f) {
   if (!vat || s->d_hy <= 0.0) return;
   const double Mt = mol_mass(s);
   for (int a = 0; a < s->M; ++a) {
@@ -385,7 +397,7 @@ static void drift_forces(const orc_sys* s, const double* R, const double* dxc, c
       nearest_center(s, R + 3 * a, &kc);
       for (int q = 0; q < 3; ++q) dir[q] = minimg(R[3 * a + q] - s->centers[3 * kc + q], s->L[q]) / d;
     }
-    const double F = -(vat[a] - vcg[a]) * dl;
+    const double F = -(vat[a] - vcg[a] - orc_fec_g(s, w[a])) * dl;
     for (int k = 0; k < s->na; ++k)
       for (int q = 0; q < 3; ++q) f[3 * (a * s->na + k) + q] += s->mass[k] / Mt * F * dir[q];
   }
@@ -472,7 +484,7 @@ int orc_forces(const orc_sys* s, const double* x, int method, const double* w_ov
   for (int a = 0; a < M && st == ORC_OK; ++a) st = bonded_mol(s, x, a, f, acc);
   tf_forces(s, R, dxc, f);
   if (vat) {
-    drift_forces(s, R, dxc, w_override ? NULL : vat, vcg, f);
+    drift_forces(s, R, dxc, w, w_override ? NULL : vat, vcg, f);
     free(vat);
     free(vcg);
   }

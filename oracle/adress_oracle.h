@@ -60,11 +60,17 @@ typedef struct {
    * H-AdResS): pair terms weighted by (l_a + l_b)/2 and the drift force
    * -(V_AT_a - V_CG_a) grad l_a on the atoms of each hybrid molecule */
   int scheme;
+  /* free-energy correction of energy interpolation (Sec. "Free energy corrections and the
+   * thermodynamic force"): g(l) = dDF/dl per molecule at fec_n >= 2 equidistant nodes on
+   * [0, 1], linear in between; H gains -sum_a DF(l_a), DF(l) = int_0^l g.  fec_n = 0: none */
+  int fec_n;
+  const double* fec;
 } orc_sys;
 
 void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void orc_uniform3(uint64_t seed, int64_t replica, int64_t gid, int64_t step, double u[3]);
 double orc_weight(const orc_sys* s, double d);
+double orc_fec_g(const orc_sys* s, double l);
 void orc_com_lambda(const orc_sys* s, const double* x, double* R, double* dx_c, double* w);
 int orc_forces(const orc_sys* s, const double* x, int method, const double* w_override, double* f,
                double* e);

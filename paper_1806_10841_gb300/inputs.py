@@ -77,6 +77,8 @@ class System:
     centers: np.ndarray = None
     # 0: force interpolation (Eq. 1); 1: energy interpolation (H-AdResS, Eq. Hmix)
     scheme: int = 0
+    # energy interpolation's free-energy correction dDF/dl at equidistant nodes on [0, 1]
+    fec: np.ndarray = None
 
     @property
     def N(self) -> int:

@@ -7,8 +7,9 @@ oracle's pair weighting), F = -grad H by central differences with lambda followi
 centres of mass (which pins the drift force, its sign, its COM mass-fraction spread and its
 direction in the slab and in the sphere geometry), F = -grad E at fixed lambda with pair
 weight (l_a + l_b)/2, energy conservation of velocity Verlet to second order in a hybrid
-system without thermostat, and the reductions at lambda = 1 and lambda = 0 where the two
-schemes coincide.
+system without thermostat, the reductions at lambda = 1 and lambda = 0 where the two
+schemes coincide, and, for the free-energy correction, F = -grad (V - sum_a DF(l_a)) with
+DF integrated in numpy from the tabulated dDF/dl.
 """
 import math
 
@@ -171,3 +172,65 @@ def test_schemes_coincide_at_full_and_zero_resolution(at, hy):
     assert np.array_equal(f1, f0)
     for k in ("E_at", "E_cg", "E_bond"):
         assert e1[k] == e0[k]
+
+
+def free_energy(g, lam):
+    """DF(l) = int_0^l g for g linear between equidistant nodes on [0, 1] (exact)."""
+    n = len(g)
+    u = np.asarray(lam) * (n - 1)
+    k = np.minimum(np.floor(u).astype(int), n - 2)
+    t = u - k
+    cum = np.concatenate([[0.0], np.cumsum(0.5 * (g[:-1] + g[1:]))]) / (n - 1)
+    gk = g[k] + (g[k + 1] - g[k]) * t
+    return cum[k] + 0.5 * (g[k] + gk) * t / (n - 1)
+
+
+def test_free_energy_integral_helper():
+    g = np.array([1.0, 3.0, -2.0, 0.5])
+    assert free_energy(g, 0.0) == 0.0
+    assert free_energy(g, 1.0) == pytest.approx((0.5 * (1 + 3) + 0.5 * (3 - 2) + 0.5 * (-2 + 0.5)) / 3)
+    lam = np.linspace(0, 1, 3001)
+    gl = np.interp(lam, np.linspace(0, 1, 4), g)
+    num = np.concatenate([[0.0], np.cumsum(0.5 * (gl[1:] + gl[:-1]) * np.diff(lam))])
+    assert np.allclose(free_energy(g, lam), num, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed,centers", [(21, None), (22, [[2.0, 2.5, 3.0], [6.6, 5.0, 0.3]])])
+def test_free_energy_correction_is_gradient_of_its_potential(seed, centers):
+    """With a tabulated dDF/dl the forces are -grad (V - sum_a DF(l_a)): the correction adds
+    +g(l_a) grad l_a to the drift force, in the slab and the sphere geometry."""
+    if centers is None:
+        s, x, _ = hybrid_system(seed=seed)
+    else:
+        s, x, _ = hybrid_system(M=40, box=(7.0, 7.0, 6.0), at=1.2, hy=1.5, seed=seed)
+        s.centers = np.array(centers)
+    rng = np.random.default_rng(seed)
+    s.fec = rng.uniform(-20, 20, 9)
+    o = oracle.Oracle(s)
+    _, _, w = o.com_lambda(x)
+    hyb = np.flatnonzero((w > 0.02) & (w < 0.98))
+    assert len(hyb) >= 3
+    f, _ = o.forces(x)
+    f_nofec, _ = oracle.Oracle(_without_fec(s)).forces(x)
+    assert np.abs(f - f_nofec).max() > 1e-2
+
+    def pot(xx):
+        _, _, ww = o.com_lambda(xx)
+        return potential(o, xx) - free_energy(s.fec, ww).sum()
+
+    fmax = np.abs(f).max()
+    for i in 4 * hyb[:6] + rng.integers(0, 4, min(6, len(hyb))):
+        for d in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, d] += 1e-6
+            xm[i, d] -= 1e-6
+            gnum = -(pot(xp) - pot(xm)) / 2e-6
+            assert f[i, d] == pytest.approx(gnum, rel=2e-4, abs=2e-4 * (1 + fmax * 1e-3)), (i, d)
+
+
+def _without_fec(s):
+    import copy
+
+    s2 = copy.copy(s)
+    s2.fec = None
+    return s2
