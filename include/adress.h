@@ -129,6 +129,21 @@ typedef struct {
    * spheres do not overlap).  0: the slab. */
   int32_t n_centers;
   const double* centers; /* host [3*n_centers] */
+  /* ---- coupling scheme (Sec. "Potential energy interpolation", Eq. Hmix) ----
+   * scheme 0: force interpolation (Eq. 1).  scheme 1: energy interpolation (H-AdResS): the
+   * pair terms are weighted by (l_a + l_b)/2 instead of l_a l_b, and each hybrid molecule
+   * feels the drift force -(V_AT_a - V_CG_a) grad l_a, V_AT_a and V_CG_a being half of its
+   * unweighted AT and CG pair energies, spread over its atoms by m_i/M (along x in the slab,
+   * along the direction from the nearest centre with resolution centres).  Molecules within
+   * r_list of the hybrid layer are then handled as high-resolution work items.  Scheme 1
+   * needs the tabulated CG model (no learned CG force).
+   * fec_n >= 2 (scheme 1 only): free-energy correction dDF/dl per molecule at fec_n
+   * equidistant nodes on l in [0, 1], linear in between; the Hamiltonian gains
+   * -sum_a DF(l_a), i.e. the force +g(l_a) grad l_a (not included in the reported
+   * energies, like the thermodynamic force).  0: none. */
+  int32_t scheme;
+  int32_t fec_n;
+  const double* fec; /* host [fec_n] */
 } adress_config;
 
 /* Validate `cfg`, copy its tables, allocate the handle's device buffers on the current

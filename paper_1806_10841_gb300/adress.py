@@ -61,6 +61,7 @@ class adress_config(C.Structure):
         ("n_angles", C.c_int32), ("angles", C.POINTER(C.c_int32)), ("angle_k", C.c_double),
         ("angle_theta0", C.c_double),
         ("n_centers", C.c_int32), ("centers", C.POINTER(C.c_double)),
+        ("scheme", C.c_int32), ("fec_n", C.c_int32), ("fec", C.POINTER(C.c_double)),
     ]
 
 
@@ -150,6 +151,8 @@ def _config(s, keep, replica, max_neighbors, precision):
         angles=np.ascontiguousarray(np.asarray(ang if ang is not None else np.zeros((0, 3)), dtype=np.int32).reshape(-1)),
         centers=np.ascontiguousarray(np.asarray(getattr(s, "centers", None) if getattr(s, "centers", None) is not None
                                                 else np.zeros((0, 3)), dtype=np.float64).reshape(-1)),
+        fec=np.ascontiguousarray(np.asarray(getattr(s, "fec", None) if getattr(s, "fec", None) is not None
+                                            else np.zeros(0), dtype=np.float64).reshape(-1)),
     )
     keep.append(arrs)
     tf_n = len(arrs["tf"])
@@ -170,7 +173,9 @@ def _config(s, keep, replica, max_neighbors, precision):
         bond_r0=float(getattr(s, "bond_r0", 0.0)), n_angles=len(arrs["angles"]) // 3,
         angles=arrs["angles"].ctypes.data_as(C.POINTER(C.c_int32)), angle_k=float(getattr(s, "angle_k", 0.0)),
         angle_theta0=float(getattr(s, "angle_theta0", 0.0)),
-        n_centers=len(arrs["centers"]) // 3, centers=_dptr(arrs["centers"]) if len(arrs["centers"]) else None)
+        n_centers=len(arrs["centers"]) // 3, centers=_dptr(arrs["centers"]) if len(arrs["centers"]) else None,
+        scheme=int(getattr(s, "scheme", 0)), fec_n=len(arrs["fec"]),
+        fec=_dptr(arrs["fec"]) if len(arrs["fec"]) else None)
 
 
 class AdResS:

@@ -209,6 +209,12 @@ static std::string config_error(const adress_config* c) {
     return "n_centers must be 0..1024 with a centre array";
   for (int q = 0; q < 3 * c->n_centers; ++q)
     if (!(c->centers[q] == c->centers[q]) || isinf(c->centers[q])) return "resolution centres must be finite";
+  if (c->scheme != 0 && c->scheme != 1) return "scheme must be 0 (force) or 1 (energy interpolation)";
+  if (c->fec_n < 0 || c->fec_n == 1 || c->fec_n > 4096 || (c->fec_n > 0 && !c->fec))
+    return "fec_n must be 0 or 2..4096 with a table";
+  if (c->fec_n > 0 && c->scheme != 1) return "the free-energy correction needs scheme 1";
+  for (int k = 0; k < c->fec_n; ++k)
+    if (!(c->fec[k] == c->fec[k]) || isinf(c->fec[k])) return "free-energy correction must be finite";
   return "";
 }
 
@@ -240,6 +246,9 @@ static std::string shared_mismatch(const adress_config* a, const adress_config* 
     return "bonded model";
   for (int q = 0; q < 3 * a->n_angles; ++q)
     if (c->angles[q] != a->angles[q]) return "angle list";
+  if (c->scheme != a->scheme || c->fec_n != a->fec_n) return "coupling scheme";
+  for (int k = 0; k < a->fec_n; ++k)
+    if (c->fec[k] != a->fec[k]) return "free-energy correction";
   return "";
 }
 
@@ -295,7 +304,9 @@ static adress_status setup_cells(adress_ctx* h, double skin) {
   s.r_list = r_list;
   s.r_list2 = r_list * r_list;
   s.ncell = (int)total;
-  for (Box& B : h->boxes) B.d_hr = B.d_at + B.d_hy + 0.5 * skin;
+  // energy interpolation: a molecule within r_list of the hybrid layer may pair with a
+  // hybrid one (weight (l_a + l_b)/2 > 0), so it is a high-resolution item too
+  for (Box& B : h->boxes) B.d_hr = B.d_at + B.d_hy + (s.scheme == 1 ? r_list : 0.5 * skin);
   s.bx = h->boxes[0];
 
   cudaError_t e = cudaSuccess;
@@ -511,7 +522,15 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
         s.f.qq[i][j] = (float)s.qq[i][j];
       }
     s.f.krf2 = (float)(2.0 * s.krf);
+    s.f.krf = (float)s.krf;
+    s.f.crf = (float)s.crf;
+    for (int i = 0; i < s.NA; ++i)
+      for (int j = 0; j < s.NA; ++j) s.f.vsh[i][j] = (float)s.vsh[i][j];
   }
+  s.scheme = c->scheme;
+  s.fec_n = c->fec_n;
+  s.fec_scale = c->fec_n > 1 ? (double)(c->fec_n - 1) : 0.0;
+  s.f.fec_scale = (float)s.fec_scale;
   s.n_centers = c->n_centers;
   s.bond_model = c->bond_model;
   s.bond_k = c->bond_k;
@@ -592,6 +611,14 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   b.cgFV32 = cgFV;
   A(b.tf64, ntf);
   A(b.tf32, ntf);
+  if (c->fec_n > 0) {
+    double* f64 = nullptr;
+    float* f32 = nullptr;
+    A(f64, c->fec_n);
+    A(f32, c->fec_n);
+    b.fec64 = f64;
+    b.fec32 = f32;
+  }
   A(b.part, (size_t)h->nparts * 4);
   A(b.result, 8);
   A(b.hist, ntf);
@@ -627,6 +654,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   for (int k = 0; k <= s.cg_n; ++k) fv[k] = make_float2((float)c->cg_F[k], (float)c->cg_V[k]);
   std::vector<double> tf(ntf, 0.0);
   std::vector<float> tff(ntf, 0.f);
+  std::vector<float> fecf(c->fec, c->fec + c->fec_n);  // staged until the stream synchronises
   for (int r = 0; r < nbox; ++r)
     for (int k = 0; k < s.tf_n; ++k) {
       tf[r * s.tf_n + k] = cfgs[r].tf[k];
@@ -645,6 +673,10 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   H2D(cgFV, fv.data(), sizeof(float2) * (s.cg_n + 1));
   H2D(b.tf64, tf.data(), sizeof(double) * tf.size());
   H2D(b.tf32, tff.data(), sizeof(float) * tff.size());
+  if (c->fec_n > 0) {
+    H2D(b.fec64, c->fec, sizeof(double) * c->fec_n);
+    H2D(b.fec32, fecf.data(), sizeof(float) * c->fec_n);
+  }
   if (nbox > 1) H2D(h->mol_box, mb.data(), sizeof(int) * M);
 #undef H2D
   if (e == cudaSuccess) e = cudaMemsetAsync(b.ctrl, 0, sizeof(Ctrl), st);
@@ -1305,6 +1337,7 @@ adress_status adress_set_cg_mode(adress_handle h, int32_t mode) {
   if (!h || mode < 0 || mode > 1) return ADRESS_ERR_ARG;
   if (mode == 1) {
     if (!h->mlp_ready) return fail(h, ADRESS_ERR_STATE, "set the network parameters first");
+    if (h->sys.scheme == 1) return fail(h, ADRESS_ERR_STATE, "energy interpolation needs the tabulated CG energy");
     if (h->sys.NA != 4 && h->sys.NA != 3 && h->sys.NA != 2 && h->sys.NA != 1) return ADRESS_ERR_ARG;
     if (!h->buf.fpair) {
       CUDA_OR_FAIL(h, dalloc(h, &h->buf.fpair, (size_t)h->sys.cap * h->sys.M));

@@ -104,6 +104,11 @@ struct Sys {
   // self-adjusting geometry: n_centers > 0 makes the AT region the union of spheres of
   // radius d_at around the centres (Bufs::cen64 / cen32); d is the distance to the nearest
   int n_centers;
+  // coupling: 0 force interpolation, 1 energy interpolation (pair weight (l_a + l_b)/2, drift
+  // force); free-energy correction g(l) at fec_n nodes (Bufs::fec64 / fec32), fec_n - 1
+  int scheme;
+  int fec_n;
+  double fec_scale;
   // float copies of the parameters the FP32 path uses (no run-time double->float work)
   struct {
     float eps, sig2, rc_at, rc_at2, rc_cg2, cg_inv_dr, fene_k, fene_r02;
@@ -111,6 +116,7 @@ struct Sys {
     float frac[kMaxNA];
     float c12[kMaxNA][kMaxNA], c6[kMaxNA][kMaxNA], qq[kMaxNA][kMaxNA];
     float krf2, bond_k, bond_r0, angle_k, angle_theta0;
+    float vsh[kMaxNA][kMaxNA], krf, crf, fec_scale;
   } f;
 };
 static_assert(sizeof(Sys) <= 4096, "Sys is passed by value as a kernel parameter");
@@ -155,6 +161,8 @@ struct Bufs {
   const float2* cgFV32;
   double* tf64;
   float* tf32;
+  const double* fec64;  // [fec_n] free-energy correction dDF/dl (energy interpolation)
+  const float* fec32;
   // reductions
   double* part;      // per-warp partials
   double* result;    // reduced results [8]

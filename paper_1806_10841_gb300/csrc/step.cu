@@ -1,11 +1,12 @@
 // Launchers of the MD-step kernels (step_impl.cuh): the prologue for every molecule size
-// and the force/step kernels of the WCA model; the water-like model's kernels are
-// instantiated in step_ljrf.cu.
+// and the force-interpolation step kernels of the WCA model; the water-like model's kernels
+// are instantiated in step_ljrf.cu and the energy-interpolation ones in step_hadress.cu.
 #include "step_impl.cuh"
 
 namespace adress {
 
 cudaError_t launch_step_ljrf(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st);
+cudaError_t launch_step_hadress(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st);
 
 template <class P, int NA>
 static void launch_prologue_na(const Sys& s, const Bufs& b, int integrate, cudaStream_t st) {
@@ -39,17 +40,19 @@ cudaError_t launch_com(const Sys& s, const Bufs& b, int precision, int integrate
 template <class P>
 static void launch_step_p(const Sys& s, const Bufs& b, int mode, int energy, cudaStream_t st) {
   switch (s.NA) {
-    case 1: launch_step_na<P, 1, 0>(s, b, mode, energy, st); break;
-    case 2: launch_step_na<P, 2, 0>(s, b, mode, energy, st); break;
-    case 3: launch_step_na<P, 3, 0>(s, b, mode, energy, st); break;
-    default: launch_step_na<P, 4, 0>(s, b, mode, energy, st); break;
+    case 1: launch_step_na<P, 1, 0, false>(s, b, mode, energy, st); break;
+    case 2: launch_step_na<P, 2, 0, false>(s, b, mode, energy, st); break;
+    case 3: launch_step_na<P, 3, 0, false>(s, b, mode, energy, st); break;
+    default: launch_step_na<P, 4, 0, false>(s, b, mode, energy, st); break;
   }
 }
 
 cudaError_t launch_step(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st,
                         DecideArgs da) {
   cudaError_t e;
-  if (s.nb_model == 1) {
+  if (s.scheme == 1) {
+    e = launch_step_hadress(s, b, precision, mode, energy, st);
+  } else if (s.nb_model == 1) {
     e = launch_step_ljrf(s, b, precision, mode, energy, st);
   } else {
     if (precision == ADRESS_FP64) launch_step_p<P64>(s, b, mode, energy, st);

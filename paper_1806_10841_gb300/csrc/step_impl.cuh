@@ -133,6 +133,8 @@ struct Prec<P64> {
     return b.cgF64[k] * (1.0 - t) + b.cgF64[k + 1] * t;
   }
   static __device__ __forceinline__ double tf(const Bufs& b, int k) { return b.tf64[k]; }
+  static __device__ __forceinline__ double fec(const Bufs& b, int k) { return b.fec64[k]; }
+  static __device__ __forceinline__ double sin_(double x) { return sin(x); }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
@@ -165,6 +167,8 @@ struct Prec<P32> {
     return fmaf(t, hi.x - lo.x, lo.x);
   }
   static __device__ __forceinline__ float tf(const Bufs& b, int k) { return b.tf32[k]; }
+  static __device__ __forceinline__ float fec(const Bufs& b, int k) { return b.fec32[k]; }
+  static __device__ __forceinline__ float sin_(float x) { return sinf(x); }
   // hardware approximations (a few ulp): the FP32 path's error budget is 2e-5 relative
   static __device__ __forceinline__ float sqrt_(float x) { return x * rsqrtf(x); }
   static __device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
@@ -472,7 +476,7 @@ constexpr int step_min_blocks() {
   return P::fp64 ? 1 : (MODEL == 0 && !MULTI ? 10 : 8);
 }
 
-template <class P, int NA, int MODE, bool ENERGY, bool MULTI, int MODEL>
+template <class P, int NA, int MODE, bool ENERGY, bool MULTI, int MODEL, bool HS>
 __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULTI>()) k_step(const __grid_constant__ Sys s, Bufs b) {
   using Q = Prec<P>;
   using real = typename Q::real;
@@ -528,6 +532,11 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
   const real wa = Q::w(Ca);
   const auto oi = Q::off(b, cur, i);
   const int nnb = live_item ? b.nn[t] : 0;
+  // energy interpolation: a hybrid molecule sums its unweighted pair energies (AT per atom
+  // lane, CG on lane 0 of its group) for the drift force
+  constexpr bool hs = HS;
+  const bool drift = hs && wa > (real)0 && wa < (real)1;
+  real dv = 0;
 
   if (t < b.ctrl->n_hr) {
     // high-resolution item: Eq. 1 for atom i against every listed neighbour (of this lane
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
       }
       const auto R = Q::dR(B, Ca, Cb);
       const real r2 = pair_r2(R.x, R.y, R.z);
-      const real wab = wa * Q::w(Cb);
+      const real wab = hs ? (real)0.5 * (wa + Q::w(Cb)) : wa * Q::w(Cb);
       if (own_pair && wab > (real)0 && r2 < reach_at2) {
         const real px = R.x + (real)oi.x, py = R.y + (real)oi.y, pz = R.z + (real)oi.z;
         typename P::off_t oj[NA];
@@ -566,6 +575,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
               const real sr6 = sr2 * sr2 * sr2;
               fr = (real)24 * eps * ((real)2 * sr6 * sr6 - sr6) * ir2 * wab;
               if (ENERGY) e_at += 0.5 * (double)wab * (double)((real)4 * eps * (sr6 * sr6 - sr6) + eps);
+              if (drift) dv += (real)4 * eps * (sr6 * sr6 - sr6) + eps;
             } else {
               // LJ (c12 r^-12 - c6 r^-6, shifted) + reaction field q_i q_j f (1/r + k_rf r^2 - c_rf)
               const real ir = Q::rsqrt_(d2);
@@ -576,6 +586,9 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
                 e_at += 0.5 * (double)wab *
                         ((double)((c12r[j] * ir6 - c6r[j]) * ir6) + s.vsh[gg0][j] +
                          (double)qqr[j] * ((double)ir + s.krf * (double)d2 - s.crf));
+              if (drift)
+                dv += (c12r[j] * ir6 - c6r[j]) * ir6 + par<real>(s.vsh[gg0][j], s.f.vsh[gg0][j]) +
+                      qqr[j] * (ir + par<real>(s.krf, s.f.krf) * d2 - par<real>(s.crf, s.f.crf));
             }
             fx += fr * dx;
             fy += fr * dy;
@@ -596,6 +609,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
           e_cg += 0.5 * (double)(((real)1 - wab) * V);
           vir += 0.5 * (double)(c * r2);
         }
+        if (drift && g == 0) dv -= V;
       }
     }
     if (SPLIT == 2) {  // the two groups' shares of the force (energies are summed per warp)
@@ -603,6 +617,12 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
       fx += __shfl_xor_sync(m8, fx, 4);
       fy += __shfl_xor_sync(m8, fy, 4);
       fz += __shfl_xor_sync(m8, fz, 4);
+      if (hs) dv += __shfl_xor_sync(m8, dv, 4);
+    }
+    if (hs) {  // V_AT_a - V_CG_a = half the group's sum (every pair is listed from both sides)
+      dv += __shfl_xor_sync(gmask, dv, 1);
+      dv += __shfl_xor_sync(gmask, dv, 2);
+      dv *= (real)0.5;
     }
   } else {
     // coarse-grained item (l_a = 0, so w_ab = 0): neighbour list split over the group,
@@ -752,8 +772,9 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
       }
     }
     }
-    // thermodynamic force on hybrid-layer molecules (region decided at mapping time)
-    if (s.tf_n > 0) {
+    // thermodynamic force on hybrid-layer molecules (region decided at mapping time), and
+    // energy interpolation's drift force -(V_AT_a - V_CG_a - g(l_a)) l'(d) along grad d
+    if (s.tf_n > 0 || hs) {
       real dxc;
       bool hy;
       if (P::fp64) {
@@ -767,14 +788,33 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
       }
       if (hy) {
         const real d = dxc < (real)0 ? -dxc : dxc;
-        const real u = d * par<real>(s.tf_inv_dx, s.f.tf_inv_dx);
-        const int k = (int)u;
         real F = 0;
-        if (k + 1 < s.tf_n) {
-          const real tt = u - (real)k;
-          F = Q::tf(b, B.tf0 + k) * ((real)1 - tt) + Q::tf(b, B.tf0 + k + 1) * tt;
-        } else if (k + 1 == s.tf_n && u == (real)k) {
-          F = Q::tf(b, B.tf0 + k);
+        if (s.tf_n > 0) {
+          const real u = d * par<real>(s.tf_inv_dx, s.f.tf_inv_dx);
+          const int k = (int)u;
+          if (k + 1 < s.tf_n) {
+            const real tt = u - (real)k;
+            F = Q::tf(b, B.tf0 + k) * ((real)1 - tt) + Q::tf(b, B.tf0 + k + 1) * tt;
+          } else if (k + 1 == s.tf_n && u == (real)k) {
+            F = Q::tf(b, B.tf0 + k);
+          }
+        }
+        if (hs) {
+          real gl = 0;
+          if (s.fec_n > 0) {  // free-energy correction dDF/dl at l_a
+            const real ul = wa * par<real>(s.fec_scale, s.f.fec_scale);
+            const int kl = (int)ul;
+            if (kl + 1 < s.fec_n) {
+              const real tl = ul - (real)kl;
+              gl = Q::fec(b, kl) * ((real)1 - tl) + Q::fec(b, kl + 1) * tl;
+            } else {
+              gl = Q::fec(b, s.fec_n - 1);
+            }
+          }
+          // l'(d) = -(pi/(2 d_hy)) sin(pi (d - d_at)/d_hy)
+          const real c = par<real>(B.pi_half_over_dhy, B.pi_half_over_dhy_f);
+          const real sn = Q::sin_((real)2 * c * (d - par<real>(B.d_at, B.d_at_f)));
+          F += (dv - gl) * c * sn;
         }
         if (s.n_centers > 0) {
           // along the direction from the nearest centre
@@ -914,27 +954,27 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
 
 // ---------------- launchers ----------------------------------------------------------
 
-template <class P, int NA, int MODEL>
+template <class P, int NA, int MODEL, bool HS>
 static void launch_step_na(const Sys& s, const Bufs& b, int mode, int energy, cudaStream_t st) {
   const int blocks = ceil_div((long long)s.M * step_lanes(s), s.force_block);
   const bool multi = s.nbox > 1;
   switch (mode) {
     case MODE_FORCES:
       if (multi) {
-        if (energy) k_step<P, NA, MODE_FORCES, true, true, MODEL><<<blocks, s.force_block, 0, st>>>(s, b);
-        else k_step<P, NA, MODE_FORCES, false, true, MODEL><<<blocks, s.force_block, 0, st>>>(s, b);
+        if (energy) k_step<P, NA, MODE_FORCES, true, true, MODEL, HS><<<blocks, s.force_block, 0, st>>>(s, b);
+        else k_step<P, NA, MODE_FORCES, false, true, MODEL, HS><<<blocks, s.force_block, 0, st>>>(s, b);
       } else {
-        if (energy) k_step<P, NA, MODE_FORCES, true, false, MODEL><<<blocks, s.force_block, 0, st>>>(s, b);
-        else k_step<P, NA, MODE_FORCES, false, false, MODEL><<<blocks, s.force_block, 0, st>>>(s, b);
+        if (energy) k_step<P, NA, MODE_FORCES, true, false, MODEL, HS><<<blocks, s.force_block, 0, st>>>(s, b);
+        else k_step<P, NA, MODE_FORCES, false, false, MODEL, HS><<<blocks, s.force_block, 0, st>>>(s, b);
       }
       break;
     case MODE_LAST:
-      if (multi) k_step<P, NA, MODE_LAST, false, true, MODEL><<<blocks, s.force_block, 0, st>>>(s, b);
-      else k_step<P, NA, MODE_LAST, false, false, MODEL><<<blocks, s.force_block, 0, st>>>(s, b);
+      if (multi) k_step<P, NA, MODE_LAST, false, true, MODEL, HS><<<blocks, s.force_block, 0, st>>>(s, b);
+      else k_step<P, NA, MODE_LAST, false, false, MODEL, HS><<<blocks, s.force_block, 0, st>>>(s, b);
       break;
     default:
-      if (multi) k_step<P, NA, MODE_FUSED, false, true, MODEL><<<blocks, s.force_block, 0, st>>>(s, b);
-      else k_step<P, NA, MODE_FUSED, false, false, MODEL><<<blocks, s.force_block, 0, st>>>(s, b);
+      if (multi) k_step<P, NA, MODE_FUSED, false, true, MODEL, HS><<<blocks, s.force_block, 0, st>>>(s, b);
+      else k_step<P, NA, MODE_FUSED, false, false, MODEL, HS><<<blocks, s.force_block, 0, st>>>(s, b);
       break;
   }
 }

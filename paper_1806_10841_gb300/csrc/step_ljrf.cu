@@ -7,8 +7,8 @@ namespace adress {
 
 cudaError_t launch_step_ljrf(const Sys& s, const Bufs& b, int precision, int mode, int energy, cudaStream_t st) {
   if (s.NA != 3) return cudaErrorInvalidValue;
-  if (precision == ADRESS_FP64) launch_step_na<P64, 3, 1>(s, b, mode, energy, st);
-  else launch_step_na<P32, 3, 1>(s, b, mode, energy, st);
+  if (precision == ADRESS_FP64) launch_step_na<P64, 3, 1, false>(s, b, mode, energy, st);
+  else launch_step_na<P32, 3, 1, false>(s, b, mode, energy, st);
   return cudaGetLastError();
 }
 

@@ -98,3 +98,30 @@ def test_oracle_and_cuda_path_share_no_code():
             txt = open(os.path.join(ROOT, "oracle", fn)).read()
             assert "paper_1806_10841_gb300" not in txt, fn
             assert "adress.h" not in txt, fn
+
+
+def test_init_rejects_bad_coupling_scheme_without_touching_the_gpu(lib):
+    """Energy interpolation's switches are validated on the host: the scheme number, a
+    free-energy correction without scheme 1 or with a single node, and replicas of a batch
+    that disagree on the scheme."""
+    import numpy as np
+
+    from paper_1806_10841_gb300 import adress, inputs
+
+    L = adress.load_library()
+    keep = []
+    h = ctypes.c_void_p()
+    s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, tf_bins=20)
+    for scheme, fec, msg in ((2, None, b"scheme must be"), (0, np.zeros(5), b"needs scheme 1"),
+                             (1, np.zeros(1), b"fec_n must be"), (1, np.array([0.0, np.nan]), b"finite")):
+        s.scheme, s.fec = scheme, fec
+        cfg = adress._config(s, keep, 0, 0, "fp32")
+        assert L.adress_init(ctypes.byref(cfg), None, ctypes.byref(h)) == 1
+        assert msg in L.adress_last_error(None), msg
+        assert not h.value
+    a = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, tf_bins=20)
+    b = inputs.tetra_system(300, (30.0, 15.0, 15.0), 3.0, 1.0, tf_bins=20)
+    b.scheme = 1
+    cfgs = (adress.adress_config * 2)(adress._config(a, keep, 0, 0, "fp32"), adress._config(b, keep, 1, 0, "fp32"))
+    assert L.adress_init_batch(cfgs, 2, None, ctypes.byref(h)) == 1
+    assert b"coupling scheme" in L.adress_last_error(None)
