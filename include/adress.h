@@ -211,6 +211,26 @@ adress_status adress_run(adress_handle h, int32_t nsteps, int32_t sample_every, 
  * mapping on, e.g. to track a solute between step calls.  Synchronises. */
 adress_status adress_set_centers(adress_handle h, const double* centers, int32_t n);
 
+/* Uniform resolution for Kirkwood thermodynamic integration (Sec. "Free energy corrections
+ * and the thermodynamic force"): on != 0 gives every molecule l = lambda in [0, 1],
+ * independent of its position, so no thermodynamic force, drift force or free-energy
+ * correction acts; with energy interpolation H(l) = K + l V_AT + (1 - l) V_CG + V_bond, and
+ * the reported E_at and E_cg are l V_AT and (1 - l) V_CG.  on = 0 restores the geometry.
+ * The lists must be rebuilt afterwards (adress_build_lists or adress_compute_forces). */
+adress_status adress_set_uniform_lambda(adress_handle h, int32_t on, double lambda);
+
+/* Kirkwood thermodynamic integration of energy interpolation (scheme 1, tabulated CG): for
+ * each node l_k (host [n], strictly inside (0, 1)): uniform l = l_k, fresh lists and
+ * forces, n_equil steps, then n_samples samples every `every` steps of
+ * dH/dl = V_AT - V_CG = E_at / l - E_cg / (1 - l); each sample recomputes the conservative
+ * force (adress_compute_forces) and the next steps start from it.  dhdl (host [n]) gets the
+ * mean per molecule (over all molecules of all replicas), the integrand of
+ * DF(l) = int_0^l <V_AT - V_CG>_l' dl' and so a free-energy correction table (fec).  The
+ * state advances by n (n_equil + n_samples every) steps; the geometry's resolution, lists
+ * and forces are restored at the end. */
+adress_status adress_kirkwood(adress_handle h, const double* lambdas, int32_t n, int32_t n_equil,
+                              int32_t n_samples, int32_t every, double* dhdl);
+
 /* Radial distribution function numerator of the bound positions: counts (host int64
  * [n_replicas][nbins]) = number of molecule pairs a < b (of the same replica) whose
  * minimum-image centre-of-mass distance r (centres in FP64 as adress_com_lambda computes

@@ -56,6 +56,7 @@ class orc_sys(C.Structure):
         ("n_centers", C.c_int), ("centers", C.POINTER(C.c_double)),
         ("scheme", C.c_int),
         ("fec_n", C.c_int), ("fec", C.POINTER(C.c_double)),
+        ("lam_uniform_on", C.c_int), ("lam_uniform", C.c_double),
     ]
 
 
@@ -194,6 +195,35 @@ class Oracle:
 
     def weight(self, d: float) -> float:
         return self.lib.orc_weight(C.byref(self.sys), float(d))
+
+    def set_uniform_lambda(self, lam):
+        """Every molecule at l = lam (None: l follows the geometry again)."""
+        self.sys.lam_uniform_on = 0 if lam is None else 1
+        self.sys.lam_uniform = 0.0 if lam is None else float(lam)
+
+    def kirkwood(self, x, v, lambdas, n_equil, n_samples, every, step0=0):
+        """Kirkwood thermodynamic integration of energy interpolation (Sec. "Free energy
+        corrections and the thermodynamic force"): at each uniform l in `lambdas` (strictly
+        inside (0, 1)), n_equil Langevin steps, then n_samples samples every `every` steps of
+        dH/dl per molecule = (V_AT - V_CG) / M = (E_at / l - E_cg / (1 - l)) / M.  Each sample
+        recomputes the conservative force, which the next steps start from.  Returns (g, x,
+        v, step) with g[k] the mean at lambdas[k]."""
+        g = []
+        step = step0
+        for lam in lambdas:
+            self.set_uniform_lambda(lam)
+            f, _ = self.forces(x)
+            x, v, f = self.run(x, v, f, step, n_equil)
+            step += n_equil
+            acc = 0.0
+            for _ in range(n_samples):
+                x, v, f = self.run(x, v, f, step, every)
+                step += every
+                f, e = self.forces(x)
+                acc += e["E_at"] / lam - e["E_cg"] / (1.0 - lam)
+            g.append(acc / (n_samples * self.M))
+        self.set_uniform_lambda(None)
+        return np.array(g), x, v, step
 
     def com_lambda(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64)

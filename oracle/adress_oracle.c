@@ -135,7 +135,7 @@ void orc_com_lambda(const orc_sys* s, const double* x, double* R, double* dx_c, 
     }
     double dxc = s->n_centers > 0 ? nearest_center(s, R + 3 * a, NULL) : minimg(R[3 * a] - s->xc, s->L[0]);
     if (dx_c) dx_c[a] = dxc;
-    if (w) w[a] = orc_weight(s, fabs(dxc));
+    if (w) w[a] = s->lam_uniform_on ? s->lam_uniform : orc_weight(s, fabs(dxc));
   }
 }
 
@@ -350,6 +350,7 @@ static int bonded_mol(const orc_sys* s, const double* x, int a, double* f, doubl
  * (slab: along x; spheres: along the direction from the nearest centre), spread over the
  * atoms by mass fraction. */
 static void tf_forces(const orc_sys* s, const double* R, const double* dxc, double* f) {
+  if (s->lam_uniform_on) return;
   const double Mt = mol_mass(s);
   for (int a = 0; a < s->M; ++a) {
     double d = fabs(dxc[a]);
@@ -385,7 +386,7 @@ double orc_fec_g(const orc_sys* s, double l) {
  * held fixed) gives neither. */
 static void drift_forces(const orc_sys* s, const double* R, const double* dxc, const double* w,
                          const double* vat, const double* vcg, double* f) {
-  if (!vat || s->d_hy <= 0.0) return;
+  if (!vat || s->d_hy <= 0.0 || s->lam_uniform_on) return;
   const double Mt = mol_mass(s);
   for (int a = 0; a < s->M; ++a) {
     const double d = fabs(dxc[a]);

@@ -65,6 +65,10 @@ typedef struct {
    * [0, 1], linear in between; H gains -sum_a DF(l_a), DF(l) = int_0^l g.  fec_n = 0: none */
   int fec_n;
   const double* fec;
+  /* Kirkwood thermodynamic integration: lam_uniform_on != 0 gives every molecule
+   * l = lam_uniform (no position dependence, hence no thermodynamic or drift force) */
+  int lam_uniform_on;
+  double lam_uniform;
 } orc_sys;
 
 void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

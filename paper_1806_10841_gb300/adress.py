@@ -20,7 +20,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "neighbour list ov
           7: "invalid state", 8: "molecule wider than the list cutoff allows"}
 
 # Every symbol include/adress.h declares (checked by the CPU test suite).
-EXPORTS = ["adress_init", "adress_init_batch", "adress_rdf", "adress_set_centers", "adress_set_tuning", "adress_get_tuning", "adress_autotune",
+EXPORTS = ["adress_init", "adress_init_batch", "adress_rdf", "adress_set_centers", "adress_set_uniform_lambda",
+           "adress_kirkwood", "adress_set_tuning", "adress_get_tuning", "adress_autotune",
            "adress_bind_state", "adress_build_lists", "adress_compute_forces",
            "adress_step", "adress_run", "adress_set_step", "adress_get_step", "adress_com_lambda", "adress_kinetic",
            "adress_density_accumulate", "adress_density_get", "adress_density_reset",
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH):
         "adress_set_tuning": ([H, C.c_int32, C.c_double], C.c_int),
         "adress_rdf": ([H, C.c_int32, C.c_double, i64p], C.c_int),
         "adress_set_centers": ([H, d, C.c_int32], C.c_int),
+        "adress_set_uniform_lambda": ([H, C.c_int32, C.c_double], C.c_int),
+        "adress_kirkwood": ([H, d, C.c_int32, C.c_int32, C.c_int32, C.c_int32, d], C.c_int),
         "adress_get_tuning": ([H, C.POINTER(C.c_int32), d], C.c_int),
         "adress_autotune": ([H, C.c_int32, d, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
         "adress_bind_state": ([H, vp, vp, vp], C.c_int),
@@ -352,6 +355,19 @@ class AdResS:
         """Move the resolution centres (n, 3) of the self-adjusting geometry."""
         c = np.ascontiguousarray(np.asarray(centers, dtype=np.float64).reshape(-1))
         self._call("adress_set_centers", _dptr(c), C.c_int32(len(c) // 3))
+
+    def set_uniform_lambda(self, lam):
+        """Every molecule at resolution lam (None: the geometry decides again); rebuild the
+        lists (build_lists / compute_forces) before stepping."""
+        self._call("adress_set_uniform_lambda", C.c_int32(0 if lam is None else 1), C.c_double(0.0 if lam is None else lam))
+
+    def kirkwood(self, lambdas, n_equil: int, n_samples: int, every: int):
+        """Kirkwood thermodynamic integration: mean dH/dl per molecule at each uniform l."""
+        lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).reshape(-1))
+        out = np.zeros(len(lam))
+        self._call("adress_kirkwood", _dptr(lam), C.c_int32(len(lam)), C.c_int32(n_equil), C.c_int32(n_samples),
+                   C.c_int32(every), _dptr(out))
+        return out
 
     def set_tuning(self, force_block: int, skin: float):
         self._call("adress_set_tuning", C.c_int32(int(force_block)), C.c_double(float(skin)))

@@ -532,6 +532,8 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   s.fec_scale = c->fec_n > 1 ? (double)(c->fec_n - 1) : 0.0;
   s.f.fec_scale = (float)s.fec_scale;
   s.n_centers = c->n_centers;
+  s.lam_uniform_on = 0;
+  s.lam_uniform = 0.0;
   s.bond_model = c->bond_model;
   s.bond_k = c->bond_k;
   s.bond_r0 = c->bond_r0;
@@ -996,6 +998,49 @@ adress_status adress_com_lambda(adress_handle h, double* com, double* w) {
   CUDA_OR_FAIL(h, launch_com(h->sys, h->buf, h->precision, 0, h->stream, DecideArgs{0, 0, 0, 0}));
   CUDA_OR_FAIL(h, launch_export_com(h->sys, h->buf, h->precision, com, w, h->stream));
   return ADRESS_OK;
+}
+
+adress_status adress_set_uniform_lambda(adress_handle h, int32_t on, double lambda) {
+  if (!h) return ADRESS_ERR_ARG;
+  if (on && !(lambda >= 0.0 && lambda <= 1.0)) return fail(h, ADRESS_ERR_ARG, "uniform lambda must be in [0, 1]");
+  h->sys.lam_uniform_on = on ? 1 : 0;
+  h->sys.lam_uniform = on ? lambda : 0.0;
+  h->sys.f.lam_uniform = (float)h->sys.lam_uniform;
+  free_graphs(h);
+  h->lists_built = false;  // the work-item classes change
+  return ADRESS_OK;
+}
+
+adress_status adress_kirkwood(adress_handle h, const double* lambdas, int32_t n, int32_t n_equil, int32_t n_samples,
+                              int32_t every, double* dhdl) {
+  if (!h || !lambdas || !dhdl || n < 1 || n_equil < 0 || n_samples < 1 || every < 1)
+    return fail(h, ADRESS_ERR_ARG, "kirkwood needs lambdas, n >= 1, n_equil >= 0, n_samples >= 1, every >= 1");
+  if (h->sys.scheme != 1) return fail(h, ADRESS_ERR_STATE, "Kirkwood integration needs energy interpolation");
+  if (h->sys.cg_mode) return fail(h, ADRESS_ERR_STATE, "Kirkwood integration needs the tabulated CG energy");
+  if (!h->bound) return fail(h, ADRESS_ERR_STATE, "no state bound");
+  for (int k = 0; k < n; ++k)
+    if (!(lambdas[k] > 0.0 && lambdas[k] < 1.0)) return fail(h, ADRESS_ERR_ARG, "Kirkwood nodes must lie inside (0, 1)");
+  adress_status st = ADRESS_OK;
+  for (int k = 0; k < n && st == ADRESS_OK; ++k) {
+    const double lam = lambdas[k];
+    st = adress_set_uniform_lambda(h, 1, lam);
+    if (st == ADRESS_OK) st = adress_compute_forces(h, nullptr);
+    if (st == ADRESS_OK) st = adress_step(h, n_equil);
+    double acc = 0.0;
+    for (int j = 0; j < n_samples && st == ADRESS_OK; ++j) {
+      double e[4];
+      st = adress_step(h, every);
+      if (st == ADRESS_OK) st = adress_compute_forces(h, e);
+      acc += e[0] / lam - e[1] / (1.0 - lam);  // dH/dl = V_AT - V_CG
+    }
+    dhdl[k] = acc / ((double)n_samples * h->sys.M);
+  }
+  // back to position-dependent resolution, lists and forces of the current state
+  const adress_status st2 = adress_set_uniform_lambda(h, 0, 0.0);
+  if (st == ADRESS_OK) st = st2;
+  if (st == ADRESS_OK) st = adress_compute_forces(h, nullptr);
+  if (st == ADRESS_OK) st = adress_check(h);
+  return st;
 }
 
 adress_status adress_set_centers(adress_handle h, const double* centers, int32_t n) {

@@ -109,6 +109,10 @@ struct Sys {
   int scheme;
   int fec_n;
   double fec_scale;
+  // Kirkwood thermodynamic integration: lam_uniform_on != 0 gives every molecule
+  // l = lam_uniform (no thermodynamic or drift force; high-resolution items iff l > 0)
+  int lam_uniform_on;
+  double lam_uniform;
   // float copies of the parameters the FP32 path uses (no run-time double->float work)
   struct {
     float eps, sig2, rc_at, rc_at2, rc_cg2, cg_inv_dr, fene_k, fene_r02;
@@ -116,7 +120,7 @@ struct Sys {
     float frac[kMaxNA];
     float c12[kMaxNA][kMaxNA], c6[kMaxNA][kMaxNA], qq[kMaxNA][kMaxNA];
     float krf2, bond_k, bond_r0, angle_k, angle_theta0;
-    float vsh[kMaxNA][kMaxNA], krf, crf, fec_scale;
+    float vsh[kMaxNA][kMaxNA], krf, crf, fec_scale, lam_uniform;
   } f;
 };
 static_assert(sizeof(Sys) <= 4096, "Sys is passed by value as a kernel parameter");

@@ -169,7 +169,8 @@ __global__ void k_rb_flag(const __grid_constant__ Sys s, Bufs b) {
   if (k >= s.M) return;
   const int a = b.sorted[k], cur = b.ctrl->parity;
   const double d = s.fp64 ? fabs(b.dxc64[cur][a]) : (double)fabsf(b.molf[cur][a].x);
-  b.flag[k] = d < box_of(s, b, a).d_hr + (s.fp64 ? 0.0 : 1e-3) ? 1 : 0;
+  if (s.lam_uniform_on) b.flag[k] = s.lam_uniform > 0.0 ? 1 : 0;
+  else b.flag[k] = d < box_of(s, b, a).d_hr + (s.fp64 ? 0.0 : 1e-3) ? 1 : 0;
 }
 
 __global__ void k_rb_items(const __grid_constant__ Sys s, Bufs b) {

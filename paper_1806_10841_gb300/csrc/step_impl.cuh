@@ -341,6 +341,10 @@ __device__ __forceinline__ void map_group32(const Sys& s, const Box& B, const Bu
       const float c = cosf((dd - B.d_at_f) * B.pi_half_over_dhy_f);
       w = c * c;
     }
+    if (s.lam_uniform_on) {
+      w = s.f.lam_uniform;
+      region = 0;  // no hybrid-layer forces
+    }
     b.com_fx[nxt][a] = make_int4((int)R[0], (int)R[1], (int)R[2], __float_as_int(w));
     b.molf[nxt][a] = make_float2(dxc, region == 1 ? 1.f : 0.f);
     if (s.n_centers > 0) b.kcen[nxt][a] = kmin;
@@ -388,6 +392,7 @@ __device__ __forceinline__ void map_group64(const Sys& s, const Box& B, const Bu
       const double cs = cos((dd - B.d_at) * B.pi_half_over_dhy);
       w = cs * cs;
     }
+    if (s.lam_uniform_on) w = s.lam_uniform;
     b.com64[nxt][a] = make_double4_32a(R[0], R[1], R[2], w);
     b.dxc64[nxt][a] = dxc;
     if (s.n_centers > 0) b.kcen[nxt][a] = kmin;
@@ -535,7 +540,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
   // energy interpolation: a hybrid molecule sums its unweighted pair energies (AT per atom
   // lane, CG on lane 0 of its group) for the drift force
   constexpr bool hs = HS;
-  const bool drift = hs && wa > (real)0 && wa < (real)1;
+  const bool drift = hs && wa > (real)0 && wa < (real)1 && !s.lam_uniform_on;
   real dv = 0;
 
   if (t < b.ctrl->n_hr) {
@@ -780,7 +785,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
       if (P::fp64) {
         const double dd = b.dxc64[cur][a], ad = fabs(dd);
         dxc = (real)dd;
-        hy = ad >= B.d_at && ad < B.d_at + B.d_hy;
+        hy = ad >= B.d_at && ad < B.d_at + B.d_hy && !s.lam_uniform_on;
       } else {
         const float2 mf = b.molf[cur][a];
         dxc = (real)mf.x;

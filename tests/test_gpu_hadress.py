@@ -176,3 +176,58 @@ def test_learned_cg_force_is_refused_with_energy_interpolation():
     with pytest.raises(adress.AdressError):
         sim.set_cg_mode(1)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("lam", [0.0, 0.35, 1.0])
+def test_uniform_lambda_forces_match_oracle(precision, lam):
+    """Kirkwood mode: every molecule at the same l; the thermodynamic force and the
+    free-energy correction configured on the system must not act."""
+    s, x, _ = tetra_case("slab", True, M=4000, seed=9)
+    s.tf = np.full(len(s.tf), 2.0)
+    o = oracle.Oracle(s)
+    o.set_uniform_lambda(lam)
+    f_ref, e_ref = o.forces(x)
+    sim = sim_of(s, precision)
+    sim.set_state(x)
+    sim.set_uniform_lambda(lam)
+    f, e = sim.forces()
+    sim.check()
+    assert rel_rms(f, f_ref) <= TOL[precision]
+    scale = abs(e_ref["E_at"]) + abs(e_ref["E_cg"]) + abs(e_ref["E_bond"])
+    for k in ("E_at", "E_cg", "E_bond"):
+        assert abs(e[k] - e_ref[k]) <= TOL[precision] * scale, k
+    _, w = sim.com_lambda()
+    assert np.all(w == (lam if precision == "fp64" else np.float32(lam)))
+    st = sim.list_stats()
+    assert st["n_hr"] == (s.M if lam > 0 else 0)
+    sim.set_uniform_lambda(None)
+    sim.build_lists()
+    _, w = sim.com_lambda()
+    assert ((w > 0) & (w < 1)).any()
+    sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_kirkwood_integration_follows_the_oracle_protocol(precision):
+    s, x, v = tetra_case("slab", False, M=1000, seed=12)
+    lams = [0.3, 0.7]
+    o = oracle.Oracle(s)
+    g_ref, x_ref, _, step_ref = o.kirkwood(x, v, lams, n_equil=10, n_samples=3, every=5)
+    sim = sim_of(s, precision)
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    g = sim.kirkwood(lams, n_equil=10, n_samples=3, every=5)
+    sim.check()
+    assert sim.get_step() == step_ref
+    tol = 1e-8 if precision == "fp64" else 1e-3
+    assert np.allclose(g, g_ref, rtol=tol, atol=tol * np.abs(g_ref).max())
+    xg, _, _ = sim.get_state()
+    L = np.array(s.box)
+    dx = xg - x_ref
+    dx -= L * np.rint(dx / L)
+    assert np.abs(dx).max() < (1e-9 if precision == "fp64" else 1e-2)
+    # resolution follows the geometry again
+    _, w = sim.com_lambda()
+    assert ((w > 0) & (w < 1)).any() and (w == 1).any()
+    sim.close()

@@ -234,3 +234,79 @@ def _without_fec(s):
     s2 = copy.copy(s)
     s2.fec = None
     return s2
+
+
+# --- uniform lambda and Kirkwood thermodynamic integration --------------------------------
+
+def one_site_fluid(M=125, L=6.0, seed=4, cg_scale=1.0, **kw):
+    """One-site molecules on a jittered lattice; the CG table is cg_scale x WCA (the force-
+    shifted LJ at its minimum is WCA), so AT and CG differ by a known factor."""
+    rc = 2 ** (1 / 6)
+    n = 112246
+    F, V = inputs.lj_cg_table(1.0, 1.0, rc, rc / n, r_min=0.5)
+    s = inputs.tetra_system(M, (L, L, L), 2.0, 1.0, rc_cg=rc, cg_dr=rc / n, seed=seed, **kw)
+    s.na, s.mass, s.bonds = 1, np.ones(1), np.zeros((0, 2), np.int32)
+    s.cg_F, s.cg_V = cg_scale * F, cg_scale * V
+    s.scheme = 1
+    k = round(M ** (1 / 3))
+    g = np.stack(np.meshgrid(*[np.arange(k)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    rng = np.random.default_rng(seed)
+    x = np.mod((g + 0.5) * (L / k) + rng.uniform(-0.12, 0.12, (M, 3)), L)
+    v = rng.normal(0, 1, (M, 3))
+    v -= v.mean(0)
+    return s, x, v
+
+
+def _wca_all_pairs(x, L):
+    r = x[:, None] - x[None]
+    r -= L * np.rint(r / L)
+    r2 = (r ** 2).sum(-1)
+    np.fill_diagonal(r2, np.inf)
+    inside = r2 < 2 ** (1 / 3)
+    ir6 = np.where(inside, 1 / np.where(inside, r2, 1) ** 3, 0)
+    V = 0.5 * np.where(inside, 4 * (ir6 ** 2 - ir6) + 1, 0).sum()
+    F = (np.where(inside, 24 * (2 * ir6 ** 2 - ir6) / np.where(inside, r2, 1), 0)[:, :, None] * r).sum(1)
+    return F, V
+
+
+@pytest.mark.parametrize("lam", [0.2, 0.5, 0.9])
+def test_uniform_lambda_mixes_the_two_models_linearly(lam):
+    """Every molecule at l = lam: H's potential is lam V_AT + (1 - lam) V_CG and the force
+    the same mix of the plain all-atom and all-CG forces (numpy, WCA and 0.5 x WCA), with
+    no thermodynamic force, drift force or correction although all three are configured."""
+    s, x, _ = one_site_fluid(cg_scale=0.5)
+    s.tf = np.full(8, 3.0)
+    s.fec = np.linspace(-5, 5, 6)
+    o = oracle.Oracle(s)
+    o.set_uniform_lambda(lam)
+    _, _, w = o.com_lambda(x)
+    assert np.all(w == lam)
+    f, e = o.forces(x)
+    F, V = _wca_all_pairs(x, np.array(s.box))
+    assert e["E_at"] == pytest.approx(lam * V, rel=1e-12)
+    assert e["E_cg"] == pytest.approx((1 - lam) * 0.5 * V, rel=1e-8)
+    assert np.allclose(f, (lam + 0.5 * (1 - lam)) * F, rtol=1e-8, atol=1e-8 * np.abs(F).max())
+    # dH/dl at fixed configuration = V_AT - V_CG
+    assert e["E_at"] / lam - e["E_cg"] / (1 - lam) == pytest.approx(0.5 * V, rel=1e-8)
+
+
+def test_kirkwood_integrand_vanishes_for_identical_models():
+    """AT and CG the same potential: dH/dl = V_AT - V_CG = 0 at every l and every sampled
+    configuration (up to the CG table's interpolation error)."""
+    s, x, v = one_site_fluid(cg_scale=1.0, gamma=1.0, dt=0.002)
+    o = oracle.Oracle(s)
+    g, x1, v1, step = o.kirkwood(x, v, [0.25, 0.5, 0.75], n_equil=20, n_samples=4, every=10)
+    assert step == 3 * (20 + 40)
+    _, V = _wca_all_pairs(x1, np.array(s.box))
+    assert np.abs(g).max() < 1e-8 * (1 + V / s.M)
+    assert np.abs(x1 - x).max() > 1e-3  # the configurations moved
+
+
+def test_kirkwood_integrand_for_half_strength_cg_model():
+    """CG = 0.5 x AT: the integrand is half the AT energy per molecule of the sampled
+    configurations, and the dynamics at l samples the potential ((1 + l)/2) V_WCA."""
+    s, x, v = one_site_fluid(cg_scale=0.5, gamma=1.0, dt=0.002)
+    o = oracle.Oracle(s)
+    g, x1, _, _ = o.kirkwood(x, v, [0.6], n_equil=0, n_samples=1, every=15)
+    _, V = _wca_all_pairs(x1, np.array(s.box))
+    assert g[0] == pytest.approx(0.5 * V / s.M, rel=1e-8)
