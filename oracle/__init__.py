@@ -57,6 +57,7 @@ class orc_sys(C.Structure):
         ("scheme", C.c_int),
         ("fec_n", C.c_int), ("fec", C.POINTER(C.c_double)),
         ("lam_uniform_on", C.c_int), ("lam_uniform", C.c_double),
+        ("respa_n", C.c_int),
     ]
 
 
@@ -98,6 +99,7 @@ def _load(path: str | None = None):
     lib.orc_forces.argtypes = [S, d, C.c_int, d, d, d]
     lib.orc_forces.restype = C.c_int
     lib.orc_run.argtypes = [S, d, d, d, C.c_int64, C.c_int, C.c_int]
+    lib.orc_forces_step.argtypes = [S, d, C.c_int64, d, d]
     lib.orc_run.restype = C.c_int
     lib.orc_langevin_force.argtypes = [S, d, C.c_int64, d]
     lib.orc_kinetic.argtypes = [S, d, d]
@@ -170,6 +172,7 @@ class Oracle:
             angle_theta0=float(getattr(s, "angle_theta0", 0.0)))
         self.set_centers(getattr(s, "centers", None))
         self.sys.scheme = int(getattr(s, "scheme", 0))
+        self.sys.respa_n = int(getattr(s, "respa_n", 1))
         fec = getattr(s, "fec", None)
         self._fec = np.ascontiguousarray(np.asarray(fec if fec is not None else [], dtype=np.float64))
         self.sys.fec_n = len(self._fec)
@@ -233,13 +236,17 @@ class Oracle:
         self.lib.orc_com_lambda(C.byref(self.sys), _ptr(x), _ptr(R), _ptr(dxc), _ptr(w))
         return R, dxc, w
 
-    def forces(self, x, method: int = 1, w_override=None):
-        """Conservative forces (N,3) and energies {E_at, E_cg, E_bond, virial}."""
+    def forces(self, x, method: int = 1, w_override=None, step=None):
+        """Conservative forces (N,3) and energies {E_at, E_cg, E_bond, virial}.  With `step`
+        (multiple time stepping) the slow part carries its weight at that time level."""
         x = np.ascontiguousarray(x, dtype=np.float64)
         f = np.empty((self.N, 3))
         e = np.zeros(4)
         wo = None if w_override is None else np.ascontiguousarray(w_override, dtype=np.float64)
-        st = self.lib.orc_forces(C.byref(self.sys), _ptr(x), int(method), _ptr(wo), _ptr(f), _ptr(e))
+        if step is not None:
+            st = self.lib.orc_forces_step(C.byref(self.sys), _ptr(x), int(step), _ptr(f), _ptr(e))
+        else:
+            st = self.lib.orc_forces(C.byref(self.sys), _ptr(x), int(method), _ptr(wo), _ptr(f), _ptr(e))
         if st != ORC_OK:
             raise RuntimeError(f"oracle forces failed with status {st}")
         return f, dict(E_at=e[0], E_cg=e[1], E_bond=e[2], virial=e[3])

@@ -207,7 +207,7 @@ static double tf_table(const orc_sys* s, double d) {
  * w_ab = (l_a + l_b)/2.  vat / vcg (may be NULL) collect the single-molecule potentials of
  * Eq. Hmix: half of every pair's unweighted AT and CG energy to each molecule. */
 static void pair_ab(const orc_sys* s, const double* x, const double* R, const double* w, int a,
-                    int b, double* f, double* e, double* vat, double* vcg) {
+                    int b, double* f, double* e, double* vat, double* vcg, double sw) {
   const double wab = s->scheme == 1 ? 0.5 * (w[a] + w[b]) : w[a] * w[b];
   const int na = s->na;
   if (wab > 0.0) {
@@ -249,12 +249,13 @@ static void pair_ab(const orc_sys* s, const double* x, const double* R, const do
         F = cg_table(s, r, &V);
       }
       double c = (1.0 - wab) * F / r;
+      const double cs = sw * c;  /* slow-force weight of multiple time stepping */
       const double Mt = mol_mass(s);
       /* the COM force reaches each atom in proportion m_i / M (dR/dx_i = m_i/M) */
       for (int k = 0; k < na; ++k)
         for (int d = 0; d < 3; ++d) {
-          f[3 * (a * na + k) + d] += s->mass[k] / Mt * c * Rab[d];
-          f[3 * (b * na + k) + d] -= s->mass[k] / Mt * c * Rab[d];
+          f[3 * (a * na + k) + d] += s->mass[k] / Mt * cs * Rab[d];
+          f[3 * (b * na + k) + d] -= s->mass[k] / Mt * cs * Rab[d];
         }
       e[1] += (1.0 - wab) * V;
       if (vcg) {
@@ -349,7 +350,7 @@ static int bonded_mol(const orc_sys* s, const double* x, int a, double* f, doubl
 /* Thermodynamic force on hybrid-layer molecules, away from the AT region when positive
  * (slab: along x; spheres: along the direction from the nearest centre), spread over the
  * atoms by mass fraction. */
-static void tf_forces(const orc_sys* s, const double* R, const double* dxc, double* f) {
+static void tf_forces(const orc_sys* s, const double* R, const double* dxc, double* f, double sw) {
   if (s->lam_uniform_on) return;
   const double Mt = mol_mass(s);
   for (int a = 0; a < s->M; ++a) {
@@ -361,7 +362,7 @@ static void tf_forces(const orc_sys* s, const double* R, const double* dxc, doub
       nearest_center(s, R + 3 * a, &kc);
       for (int q = 0; q < 3; ++q) dir[q] = minimg(R[3 * a + q] - s->centers[3 * kc + q], s->L[q]) / d;
     }
-    const double F = tf_table(s, d);
+    const double F = sw * tf_table(s, d);
     for (int k = 0; k < s->na; ++k)
       for (int q = 0; q < 3; ++q) f[3 * (a * s->na + k) + q] += s->mass[k] / Mt * F * dir[q];
   }
@@ -385,7 +386,7 @@ double orc_fec_g(const orc_sys* s, double l) {
  * The free-energy correction -DF(l_a) adds +g(l_a) l'(d_a) grad d_a.  vat == NULL (lambda
  * held fixed) gives neither. */
 static void drift_forces(const orc_sys* s, const double* R, const double* dxc, const double* w,
-                         const double* vat, const double* vcg, double* f) {
+                         const double* vat, const double* vcg, double* f, double sw) {
   if (!vat || s->d_hy <= 0.0 || s->lam_uniform_on) return;
   const double Mt = mol_mass(s);
   for (int a = 0; a < s->M; ++a) {
@@ -398,7 +399,8 @@ static void drift_forces(const orc_sys* s, const double* R, const double* dxc, c
       nearest_center(s, R + 3 * a, &kc);
       for (int q = 0; q < 3; ++q) dir[q] = minimg(R[3 * a + q] - s->centers[3 * kc + q], s->L[q]) / d;
     }
-    const double F = -(vat[a] - vcg[a] - orc_fec_g(s, w[a])) * dl;
+    /* fast part -V_AT l', slow part +(V_CG + g) l' (weighted by sw) */
+    const double F = -(vat[a] - sw * (vcg[a] + orc_fec_g(s, w[a]))) * dl;
     for (int k = 0; k < s->na; ++k)
       for (int q = 0; q < 3; ++q) f[3 * (a * s->na + k) + q] += s->mass[k] / Mt * F * dir[q];
   }
@@ -422,8 +424,10 @@ static double max_extent(const orc_sys* s, const double* x, const double* R) {
 /* Conservative forces (no thermostat).  method 0: every molecule pair a<b;
  * method 1: a linked-cell scan over COM cells no smaller than the largest pair reach.
  * w_override (may be NULL) replaces lambda for every molecule. */
-int orc_forces(const orc_sys* s, const double* x, int method, const double* w_override, double* f,
-               double* e) {
+/* Forces with the slow (CG) part weighted by sw: 1 for the plain force; with multiple time
+ * stepping n at outer steps and 0 in between (energies and virial stay unweighted). */
+static int forces_sw(const orc_sys* s, const double* x, int method, const double* w_override, double* f,
+                     double* e, double sw) {
   const int M = s->M;
   double* R = (double*)malloc(sizeof(double) * 3 * M);
   double* dxc = (double*)malloc(sizeof(double) * M);
@@ -438,7 +442,7 @@ int orc_forces(const orc_sys* s, const double* x, int method, const double* w_ov
 
   if (method == 0) {
     for (int a = 0; a < M; ++a)
-      for (int b = a + 1; b < M; ++b) pair_ab(s, x, R, w, a, b, f, acc, vat, vcg);
+      for (int b = a + 1; b < M; ++b) pair_ab(s, x, R, w, a, b, f, acc, vat, vcg, sw);
   } else {
     double ext = max_extent(s, x, R);
     double reach = s->rc_cg > s->rc_at + 2 * ext ? s->rc_cg : s->rc_at + 2 * ext;
@@ -477,15 +481,15 @@ int orc_forces(const orc_sys* s, const double* x, int method, const double* w_ov
             if (dup) continue;
             seen[ns++] = nbc;
             for (int b = head[nbc]; b >= 0; b = next[b])
-              if (b > a) pair_ab(s, x, R, w, a, b, f, acc, vat, vcg);
+              if (b > a) pair_ab(s, x, R, w, a, b, f, acc, vat, vcg, sw);
           }
     }
     free(head); free(next); free(cell);
   }
   for (int a = 0; a < M && st == ORC_OK; ++a) st = bonded_mol(s, x, a, f, acc);
-  tf_forces(s, R, dxc, f);
+  tf_forces(s, R, dxc, f, sw);
   if (vat) {
-    drift_forces(s, R, dxc, w, w_override ? NULL : vat, vcg, f);
+    drift_forces(s, R, dxc, w, w_override ? NULL : vat, vcg, f, sw);
     free(vat);
     free(vcg);
   }
@@ -511,6 +515,23 @@ static void langevin(const orc_sys* s, const double* v, int64_t step, double* f)
 /* Velocity Verlet with the thermostat force evaluated with the half-step velocity:
  *   v += dt/2 f/m;  x += dt v;  wrap;  f = F(x) + F_L(v; step+1);  v += dt/2 f/m.
  * (x, v, f) hold time level `step0` on entry and step0+nsteps on return. */
+/* Slow-force weight at time level `step`: multiple time stepping (Sec. "Multiple time
+ * stepping in adaptive resolution simulations", impulse r-RESPA) applies the CG forces as an
+ * impulse of n inner steps at every n-th time level and not in between. */
+static double slow_weight(const orc_sys* s, int64_t step) {
+  if (s->respa_n <= 1) return 1.0;
+  return step % s->respa_n == 0 ? (double)s->respa_n : 0.0;
+}
+
+int orc_forces(const orc_sys* s, const double* x, int method, const double* w_override, double* f,
+               double* e) {
+  return forces_sw(s, x, method, w_override, f, e, 1.0);
+}
+
+int orc_forces_step(const orc_sys* s, const double* x, int64_t step, double* f, double* e) {
+  return forces_sw(s, x, 1, NULL, f, e, slow_weight(s, step));
+}
+
 int orc_run(const orc_sys* s, double* x, double* v, double* f, int64_t step0, int nsteps, int method) {
   const int N = s->M * s->na;
   for (int n = 0; n < nsteps; ++n) {
@@ -524,7 +545,7 @@ int orc_run(const orc_sys* s, double* x, double* v, double* f, int64_t step0, in
         x[3 * i + d] = y;
       }
     }
-    int st = orc_forces(s, x, method, NULL, f, NULL);
+    int st = forces_sw(s, x, method, NULL, f, NULL, slow_weight(s, step0 + n + 1));
     if (st != ORC_OK) return st;
     if (s->gamma != 0.0) langevin(s, v, step0 + n + 1, f);
     for (int i = 0; i < N; ++i) {

@@ -69,6 +69,10 @@ typedef struct {
    * l = lam_uniform (no position dependence, hence no thermodynamic or drift force) */
   int lam_uniform_on;
   double lam_uniform;
+  /* multiple time stepping (impulse r-RESPA): respa_n > 1 applies the slow forces (CG pair
+   * forces, thermodynamic force, the CG part of the drift force and the free-energy
+   * correction) as n dt impulses at time levels divisible by n; dt is the inner step */
+  int respa_n;
 } orc_sys;
 
 void orc_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -79,6 +83,7 @@ void orc_com_lambda(const orc_sys* s, const double* x, double* R, double* dx_c, 
 int orc_forces(const orc_sys* s, const double* x, int method, const double* w_override, double* f,
                double* e);
 int orc_run(const orc_sys* s, double* x, double* v, double* f, int64_t step0, int nsteps, int method);
+int orc_forces_step(const orc_sys* s, const double* x, int64_t step, double* f, double* e);
 void orc_langevin_force(const orc_sys* s, const double* v, int64_t step, double* f);
 void orc_kinetic(const orc_sys* s, const double* v, double* out);
 void orc_density(const orc_sys* s, const double* x, int nd, int64_t* counts_d, int nx,

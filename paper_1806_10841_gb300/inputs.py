@@ -79,6 +79,8 @@ class System:
     scheme: int = 0
     # energy interpolation's free-energy correction dDF/dl at equidistant nodes on [0, 1]
     fec: np.ndarray = None
+    # multiple time stepping: CG (slow) forces every respa_n inner steps of dt (1: off)
+    respa_n: int = 1
 
     @property
     def N(self) -> int:
