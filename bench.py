@@ -407,6 +407,52 @@ def spheres_arm(timed, steps, local):
             "radius": s.d_at, "hybrid_shell": s.d_hy, "hr_molecules": st["n_hr"], "ms_per_bench_step": ms}
 
 
+def hadress_arm(timed, steps, local):
+    """Energy interpolation (H-AdResS) on the 800k-atom fluid: pair weight (l_a + l_b)/2,
+    drift force on hybrid molecules, high-resolution band widened by r_list; FP32 mixed,
+    the same bench step (thermodynamic-force iteration block), force error against the
+    oracle on the initial state."""
+    import oracle
+    from paper_1806_10841_gb300 import adress, inputs
+
+    s = inputs.c2_800k()
+    s.scheme = 1
+    x, v = inputs.tetra_state(s)
+    f_ref, _ = oracle.Oracle(s).forces(x)
+    sim = adress.AdResS(s, precision="fp32", device=f"cuda:{local}")
+    sim.set_state(x, v)
+    fg, _ = sim.forces()
+    err = math.sqrt(((fg - f_ref) ** 2).sum() / (f_ref ** 2).sum())
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    tot, _, _ = timed(sim, steps, 2)
+    st = sim.list_stats()
+    sim.close()
+    return {"value": s.N * MD_PER_BLOCK * steps / tot, "unit": "atom-steps/s", "precision": "fp32",
+            "force_rel_rms_vs_fp64_oracle": err, "hr_molecules": st["n_hr"], "cg_molecules": st["n_cg"]}
+
+
+def respa_arm(timed, steps, local):
+    """Multiple time stepping on the 800k-atom fluid (force interpolation, FP32 mixed): the
+    CG pair forces and the thermodynamic force every n-th step with weight n, n = 2 and 4,
+    the same bench step; throughput counts inner (atomistic) steps."""
+    from paper_1806_10841_gb300 import adress, inputs
+
+    out = {}
+    for n in (2, 4):
+        s = inputs.c2_800k()
+        s.respa_n = n
+        x, v = inputs.tetra_state(s)
+        sim = adress.AdResS(s, precision="fp32", device=f"cuda:{local}")
+        sim.set_state(x, v)
+        sim.compute_forces(energies=False)
+        tot, _, _ = timed(sim, steps, 2)
+        sim.check()
+        sim.close()
+        out[f"n{n}"] = {"value": s.N * MD_PER_BLOCK * steps / tot, "unit": "atom-steps/s"}
+    return out
+
+
 def replicas_arm(timed, steps, local):
     """64 independent replicas (log-uniform 500..20000 molecules, AT width U(3, 15), hybrid
     U(1, 5)) in one handle: every MD step is one launch over all replicas' molecules, the
@@ -471,6 +517,8 @@ def main():
     ap.add_argument("--no-replicas", action="store_true", help="skip the 64-replica batch arm")
     ap.add_argument("--no-water", action="store_true", help="skip the water-like fluid arm")
     ap.add_argument("--no-spheres", action="store_true", help="skip the self-adjusting-geometry arm")
+    ap.add_argument("--no-hadress", action="store_true", help="skip the energy-interpolation arm")
+    ap.add_argument("--no-respa", action="store_true", help="skip the multiple-time-stepping arm")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling driver: set up, run this many MD steps, exit (no timing output)")
     ap.add_argument("--cg-mode", type=int, default=0, choices=[0, 1],
@@ -643,6 +691,12 @@ def main():
     spheres = None
     if not args.no_spheres and rank == 0:
         spheres = spheres_arm(timed, max(2, args.steps // 2), local)
+    hadress = None
+    if not args.no_hadress and rank == 0:
+        hadress = hadress_arm(timed, max(2, args.steps // 2), local)
+    respa = None
+    if not args.no_respa and rank == 0:
+        respa = respa_arm(timed, max(2, args.steps // 2), local)
 
     if rank != 0:
         if dist:
@@ -711,6 +765,8 @@ def main():
         "replicas_64": replicas,
         "water_64k": water,
         "spheres_16": spheres,
+        "energy_interpolation": hadress,
+        "multiple_time_stepping": respa,
         "per_step_ms": ms,
     }
     if not args.no_cpu_baseline:

@@ -144,6 +144,14 @@ typedef struct {
   int32_t scheme;
   int32_t fec_n;
   const double* fec; /* host [fec_n] */
+  /* ---- multiple time stepping (Sec. "Multiple time stepping in adaptive resolution
+   * simulations"), impulse r-RESPA ----
+   * respa_n > 1 (at most 64): dt is the inner (atomistic) step; the slow forces (CG pair
+   * forces, the thermodynamic force and, with energy interpolation, the CG share
+   * +(V_CG_a + g(l_a)) grad l_a of the drift force) act as impulses of respa_n dt at every
+   * time level divisible by respa_n and not in between.  The force stored in f is
+   * F_fast + w F_slow with that weight w; reported energies are unweighted.  0 or 1: off. */
+  int32_t respa_n;
 } adress_config;
 
 /* Validate `cfg`, copy its tables, allocate the handle's device buffers on the current

@@ -63,6 +63,7 @@ class adress_config(C.Structure):
         ("angle_theta0", C.c_double),
         ("n_centers", C.c_int32), ("centers", C.POINTER(C.c_double)),
         ("scheme", C.c_int32), ("fec_n", C.c_int32), ("fec", C.POINTER(C.c_double)),
+        ("respa_n", C.c_int32),
     ]
 
 
@@ -178,7 +179,7 @@ def _config(s, keep, replica, max_neighbors, precision):
         angle_theta0=float(getattr(s, "angle_theta0", 0.0)),
         n_centers=len(arrs["centers"]) // 3, centers=_dptr(arrs["centers"]) if len(arrs["centers"]) else None,
         scheme=int(getattr(s, "scheme", 0)), fec_n=len(arrs["fec"]),
-        fec=_dptr(arrs["fec"]) if len(arrs["fec"]) else None)
+        fec=_dptr(arrs["fec"]) if len(arrs["fec"]) else None, respa_n=int(getattr(s, "respa_n", 1)))
 
 
 class AdResS:

@@ -213,6 +213,7 @@ static std::string config_error(const adress_config* c) {
   if (c->fec_n < 0 || c->fec_n == 1 || c->fec_n > 4096 || (c->fec_n > 0 && !c->fec))
     return "fec_n must be 0 or 2..4096 with a table";
   if (c->fec_n > 0 && c->scheme != 1) return "the free-energy correction needs scheme 1";
+  if (c->respa_n < 0 || c->respa_n > 64) return "respa_n must be 0..64";
   for (int k = 0; k < c->fec_n; ++k)
     if (!(c->fec[k] == c->fec[k]) || isinf(c->fec[k])) return "free-energy correction must be finite";
   return "";
@@ -247,6 +248,7 @@ static std::string shared_mismatch(const adress_config* a, const adress_config* 
   for (int q = 0; q < 3 * a->n_angles; ++q)
     if (c->angles[q] != a->angles[q]) return "angle list";
   if (c->scheme != a->scheme || c->fec_n != a->fec_n) return "coupling scheme";
+  if (std::max(1, c->respa_n) != std::max(1, a->respa_n)) return "multiple time stepping";
   for (int k = 0; k < a->fec_n; ++k)
     if (c->fec[k] != a->fec[k]) return "free-energy correction";
   return "";
@@ -534,6 +536,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   s.n_centers = c->n_centers;
   s.lam_uniform_on = 0;
   s.lam_uniform = 0.0;
+  s.respa_n = std::max(1, c->respa_n);
   s.bond_model = c->bond_model;
   s.bond_k = c->bond_k;
   s.bond_r0 = c->bond_r0;

@@ -113,6 +113,10 @@ struct Sys {
   // l = lam_uniform (no thermodynamic or drift force; high-resolution items iff l > 0)
   int lam_uniform_on;
   double lam_uniform;
+  // multiple time stepping (impulse r-RESPA): respa_n > 1 applies the slow forces (CG pairs,
+  // thermodynamic force, CG share of the drift force) with weight respa_n at time levels
+  // divisible by respa_n and skips them in between
+  int respa_n;
   // float copies of the parameters the FP32 path uses (no run-time double->float work)
   struct {
     float eps, sig2, rc_at, rc_at2, rc_cg2, cg_inv_dr, fene_k, fene_r02;

@@ -542,6 +542,10 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
   constexpr bool hs = HS;
   const bool drift = hs && wa > (real)0 && wa < (real)1 && !s.lam_uniform_on;
   real dv = 0;
+  // slow-force weight at this time level (1 without multiple time stepping)
+  real sw = 1;
+  if (s.respa_n > 1) sw = b.ctrl->step % s.respa_n == 0 ? (real)s.respa_n : (real)0;
+  const bool slow = sw != (real)0 || ENERGY;
 
   if (t < b.ctrl->n_hr) {
     // high-resolution item: Eq. 1 for atom i against every listed neighbour (of this lane
@@ -602,19 +606,20 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
           }
         }
       }
-      if (own_pair && wab < (real)1 && r2 < rc_cg2) {
+      if (own_pair && wab < (real)1 && r2 < rc_cg2 && slow) {
         const real r = Q::sqrt_(r2);
         real V = 0;
         const real F = s.cg_mode ? (real)b.fpair[(size_t)t * s.cap + q] : Q::cg(b, s.cg_n, r, inv_dr, &V);
-        const real c = Q::div_(((real)1 - wab) * F, r);
+        const real fw = ((real)1 - wab) * F;
+        const real c = Q::div_(fw * sw, r);
         fx += frac_g * c * R.x;
         fy += frac_g * c * R.y;
         fz += frac_g * c * R.z;
         if (ENERGY && g == 0) {
           e_cg += 0.5 * (double)(((real)1 - wab) * V);
-          vir += 0.5 * (double)(c * r2);
+          vir += 0.5 * (double)(Q::div_(fw, r) * r2);
         }
-        if (drift && g == 0) dv -= V;
+        if (drift && g == 0) dv -= sw * V;
       }
     }
     if (SPLIT == 2) {  // the two groups' shares of the force (energies are summed per warp)
@@ -635,10 +640,11 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
     if (live && g == 0 && wa != (real)0) set_error(b.ctrl, ADRESS_ERR_STATE, a);
     real Fx = 0, Fy = 0, Fz = 0;
     auto C_n = Ca;
-    if (g < nnb) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + g]);
-    for (int q = g; q < nnb; q += kGroup) {
+    const int nnb_cg = slow ? nnb : 0;  // no CG force at inner levels of multiple time stepping
+    if (g < nnb_cg) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + g]);
+    for (int q = g; q < nnb_cg; q += kGroup) {
       const auto Cb = C_n;
-      if (q + kGroup < nnb) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + q + kGroup]);
+      if (q + kGroup < nnb_cg) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + q + kGroup]);
       const auto R = Q::dR(B, Ca, Cb);
       const real r2 = pair_r2(R.x, R.y, R.z);
       if (r2 < rc_cg2) {
@@ -661,9 +667,10 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
     Fx += __shfl_xor_sync(gmask, Fx, 2);
     Fy += __shfl_xor_sync(gmask, Fy, 2);
     Fz += __shfl_xor_sync(gmask, Fz, 2);
-    fx = frac_g * Fx;
-    fy = frac_g * Fy;
-    fz = frac_g * Fz;
+    const real fs = frac_g * sw;
+    fx = fs * Fx;
+    fy = fs * Fy;
+    fz = fs * Fz;
   }
 
   // own state for the update, fetched before the bonded terms so the loads overlap them
@@ -803,6 +810,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
           } else if (k + 1 == s.tf_n && u == (real)k) {
             F = Q::tf(b, B.tf0 + k);
           }
+          F *= sw;
         }
         if (hs) {
           real gl = 0;
@@ -819,7 +827,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
           // l'(d) = -(pi/(2 d_hy)) sin(pi (d - d_at)/d_hy)
           const real c = par<real>(B.pi_half_over_dhy, B.pi_half_over_dhy_f);
           const real sn = Q::sin_((real)2 * c * (d - par<real>(B.d_at, B.d_at_f)));
-          F += (dv - gl) * c * sn;
+          F += (dv - sw * gl) * c * sn;
         }
         if (s.n_centers > 0) {
           // along the direction from the nearest centre

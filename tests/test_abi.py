@@ -125,3 +125,23 @@ def test_init_rejects_bad_coupling_scheme_without_touching_the_gpu(lib):
     cfgs = (adress.adress_config * 2)(adress._config(a, keep, 0, 0, "fp32"), adress._config(b, keep, 1, 0, "fp32"))
     assert L.adress_init_batch(cfgs, 2, None, ctypes.byref(h)) == 1
     assert b"coupling scheme" in L.adress_last_error(None)
+
+
+def test_init_rejects_bad_multiple_time_stepping(lib):
+    from paper_1806_10841_gb300 import adress, inputs
+
+    L = adress.load_library()
+    keep = []
+    h = ctypes.c_void_p()
+    s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, tf_bins=20)
+    for n in (-1, 65):
+        s.respa_n = n
+        cfg = adress._config(s, keep, 0, 0, "fp32")
+        assert L.adress_init(ctypes.byref(cfg), None, ctypes.byref(h)) == 1
+        assert b"respa_n" in L.adress_last_error(None)
+    a = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, tf_bins=20)
+    b = inputs.tetra_system(300, (30.0, 15.0, 15.0), 3.0, 1.0, tf_bins=20)
+    b.respa_n = 2
+    cfgs = (adress.adress_config * 2)(adress._config(a, keep, 0, 0, "fp32"), adress._config(b, keep, 1, 0, "fp32"))
+    assert L.adress_init_batch(cfgs, 2, None, ctypes.byref(h)) == 1
+    assert b"multiple time stepping" in L.adress_last_error(None)
