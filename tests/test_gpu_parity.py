@@ -362,3 +362,36 @@ def test_neighbour_lists_are_complete_and_exact():
     assert expect  # non-trivial
     got = sim.neighbour_pairs()
     assert expect <= got and got <= expect | maybe
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_energy_trace_of_all_atomistic_nve_follows_the_oracle(precision):
+    """lambda = 1, no thermostat: the total energy after every 10 of 100 velocity-Verlet steps
+    equals the oracle's (FP64: 1e-10 relative), and stays conserved."""
+    s = inputs.tetra_system(1000, (34.20, 17.10, 17.10), 1e3, 1.0, gamma=0.0, dt=0.001)
+    x, v = inputs.tetra_state(s)
+    o = oracle.Oracle(s)
+    sim = gpu(s, precision)
+    sim.set_state(x, v)
+    sim.compute_forces(energies=False)
+    f = o.forces(x)[0]
+    xo, vo = x, v
+
+    def total_ref(xx, vv):
+        _, e = o.forces(xx)
+        return o.kinetic(vv)[0] + e["E_at"] + e["E_cg"] + e["E_bond"]
+
+    def total_gpu():
+        _, e = sim.forces()
+        return sim.kinetic()[0] + e["E_at"] + e["E_cg"] + e["E_bond"]
+
+    E0 = total_ref(x, v)
+    tol = {"fp64": 1e-10, "fp32": 1e-5}[precision]
+    for k in range(10):
+        sim.step(10)
+        xo, vo, f = o.run(xo, vo, f, 10 * k, 10)
+        Eg, Er = total_gpu(), total_ref(xo, vo)
+        assert abs(Eg - Er) <= tol * abs(Er), (k, Eg, Er)
+        assert abs(Er - E0) <= 1e-3 * s.N
+    sim.check()
+    sim.close()
