@@ -506,6 +506,12 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
   const bool own = live && g < NA;
   const bool own_pair = live_item && g < NA;  // lanes that evaluate pair forces
   const int cur = b.ctrl->parity;
+  // the first list slot this lane reads is fetched together with the item, before the count
+  // is known (slots below the capacity lie inside the list array; the value is used only
+  // when the count covers the slot)
+  const bool hr_item = t < b.ctrl->n_hr;
+  const int j0 = hr_item ? sub : g;
+  const int m_first = live_item && j0 < s.cap ? b.nbr[(size_t)t * s.cap + j0] : 0;
 
   const real eps = par<real>(s.eps, s.f.eps), sig2 = par<real>(s.sig2, s.f.sig2);
   const real rc_at2 = par<real>(s.rc_at2, s.f.rc_at2), rc_cg2 = par<real>(s.rc_cg2, s.f.rc_cg2);
@@ -547,14 +553,14 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
   if (s.respa_n > 1) sw = b.ctrl->step % s.respa_n == 0 ? (real)s.respa_n : (real)0;
   const bool slow = sw != (real)0 || ENERGY;
 
-  if (t < b.ctrl->n_hr) {
+  if (hr_item) {
     // high-resolution item: Eq. 1 for atom i against every listed neighbour (of this lane
     // group's share); the next neighbour's index and centre are fetched while the current
     // one is evaluated
     int m_n = 0;
     auto C_n = Ca;
     if (sub < nnb) {
-      m_n = b.nbr[(size_t)t * s.cap + sub];
+      m_n = m_first;
       C_n = Q::com(b, cur, m_n);
     }
     for (int q = sub; q < nnb; q += SPLIT) {
@@ -641,7 +647,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
     real Fx = 0, Fy = 0, Fz = 0;
     auto C_n = Ca;
     const int nnb_cg = slow ? nnb : 0;  // no CG force at inner levels of multiple time stepping
-    if (g < nnb_cg) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + g]);
+    if (g < nnb_cg) C_n = Q::com(b, cur, m_first);
     for (int q = g; q < nnb_cg; q += kGroup) {
       const auto Cb = C_n;
       if (q + kGroup < nnb_cg) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + q + kGroup]);
