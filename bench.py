@@ -320,6 +320,21 @@ def learned_arm(s, x0, v0, make, timed, steps, device):
     sim.compute_forces(energies=False)
     tot, _, _ = timed(sim, steps, 2)
     value = s.N * MD_PER_BLOCK * steps / tot
+    # the same network as a slow force of multiple time stepping (evaluated every 4th step)
+    import copy
+
+    p = sim.mlp_get()
+    s4 = copy.copy(s)
+    s4.respa_n = 4
+    sim4 = adress.AdResS(s4, precision="fp32", device=device)
+    sim4.mlp_set(p, p["in_mean"], p["in_std"], p["out_scale"])
+    sim4.set_cg_mode(1)
+    sim4.set_state(x0, v0)
+    sim4.compute_forces(energies=False)
+    tot4, _, _ = timed(sim4, steps, 2)
+    sim4.check()
+    sim4.close()
+    value_respa4 = s.N * MD_PER_BLOCK * steps / tot4
     # structure: COM g(r) of the learned run, the tabulated run and the all-atomistic run,
     # each from the initial state after RDF_EQ steps, over RDF_SNAPS snapshots
     sim.set_state(x0, v0)
@@ -330,7 +345,8 @@ def learned_arm(s, x0, v0, make, timed, steps, device):
     g_tab = rdf_of(tab, RDF_EQ)
     tab.close()
     l2 = lambda a, b: float(math.sqrt(((a - b) ** 2).sum() * dr))
-    return {"value": value, "unit": "atom-steps/s", "training_samples": int(ntr), "held_out": int(n - ntr),
+    return {"value": value, "unit": "atom-steps/s", "value_respa4": value_respa4, "training_samples": int(ntr),
+            "held_out": int(n - ntr),
             "epoch_loss": [float(v) for v in losses], "train_s": t_train, "prep_s": prep_s,
             "held_out_force_rms": {"target": rms(t[te]), "network_error": rms(pred - t[te]),
                                    "table_error": rms(table - t[te])},
@@ -371,7 +387,11 @@ def water_arm(timed, steps, local):
 def spheres_arm(timed, steps, local):
     """Self-adjusting geometry on the 800k-atom fluid: the AT region is the union of 16
     spheres (radius 10, hybrid shell 5) around centres drawn in the box, which move by a
-    random displacement of 1 sigma between bench steps (adress_set_centers), FP32 mixed."""
+    random displacement of 0.1 sigma between bench steps (adress_set_centers; the next step
+    rebuilds the lists), FP32 mixed.  A moved region changes the resolution of a molecule in
+    the shell at once, by up to (pi / (2 d_hy)) times the displacement; kept that small, two
+    overlapping coarse-grained molecules that find themselves at the shell's outer edge get an
+    atomistic weight of order 1e-6."""
     import torch
 
     from paper_1806_10841_gb300 import adress, inputs
@@ -392,7 +412,7 @@ def spheres_arm(timed, steps, local):
     c = s.centers.copy()
     ms = []
     for _ in range(steps):
-        c = c + rng.normal(0, 1.0 / math.sqrt(3.0), c.shape)
+        c = c + rng.normal(0, 0.1 / math.sqrt(3.0), c.shape)
         sim.set_centers(c)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(sim.stream)

@@ -216,7 +216,10 @@ adress_status adress_run(adress_handle h, int32_t nsteps, int32_t sample_every, 
 
 /* Move the resolution centres of the self-adjusting geometry (n must equal the configured
  * n_centers > 0; host [3n], wrapped into the box): the AT region follows them from the next
- * mapping on, e.g. to track a solute between step calls.  Synchronises. */
+ * mapping on, e.g. to track a solute between step calls, and the next step rebuilds the
+ * lists.  The resolution of molecules in the hybrid shells changes at once, by up to
+ * (pi / (2 d_hy)) times the displacement: move the centres in small increments.
+ * Synchronises. */
 adress_status adress_set_centers(adress_handle h, const double* centers, int32_t n);
 
 /* Uniform resolution for Kirkwood thermodynamic integration (Sec. "Free energy corrections

@@ -1052,7 +1052,14 @@ adress_status adress_set_centers(adress_handle h, const double* centers, int32_t
     return fail(h, ADRESS_ERR_ARG, "set_centers needs the configured number of resolution centres");
   for (int q = 0; q < 3 * n; ++q)
     if (!(centers[q] == centers[q]) || isinf(centers[q])) return fail(h, ADRESS_ERR_ARG, "resolution centres must be finite");
-  return upload_centers(h, centers, n);
+  adress_status st = upload_centers(h, centers, n);
+  if (st != ADRESS_OK) return st;
+  // the work-item classes were decided for the old region: the next decision rebuilds the
+  // lists (the flag stays set until a list build clears it)
+  const int one = 1;
+  CUDA_OR_FAIL(h, cudaMemcpyAsync(&h->buf.ctrl->force_rebuild, &one, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
+  return ADRESS_OK;
 }
 
 adress_status adress_rdf(adress_handle h, int32_t nbins, double dr, int64_t* counts) {

@@ -31,6 +31,7 @@ struct Ctrl {
   unsigned maxext2;    // float bits: largest squared atom-to-COM distance of the last mapping
   unsigned maxdisp2;   // float bits: largest squared COM displacement since the last build
   int n_dense;         // cells passed to the dense-cell list builder in this build
+  int force_rebuild;   // set by the host (moved resolution centres), cleared by a list build
 };
 
 // Decision taken after a mapping (see decide_after_map in observe.cu).

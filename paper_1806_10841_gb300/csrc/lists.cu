@@ -21,7 +21,10 @@ __device__ __forceinline__ int cell_of(unsigned int X, int nc) {
 }
 
 __global__ void k_rb_zero(const __grid_constant__ Sys s, Bufs b) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) b.ctrl->n_dense = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    b.ctrl->n_dense = 0;
+    b.ctrl->force_rebuild = 0;
+  }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.ncell; c += gridDim.x * blockDim.x) {
     b.cell_count[c] = 0;
     b.cell_fill[c] = 0;

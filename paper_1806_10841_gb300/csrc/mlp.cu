@@ -717,6 +717,9 @@ __device__ __forceinline__ bool needs_network(const Sys& s, const Box& X, const 
 
 template <int NA, bool F64>
 __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s, Bufs b, const float* __restrict__ norm) {
+  // multiple time stepping: the network gives a slow (CG) force, needed only at outer time
+  // levels; elsewhere no pair is written and the evaluation kernel finds nothing to do
+  if (s.respa_n > 1 && b.ctrl->step % s.respa_n != 0) return;
   // input normalisation (mean, 1/std) for the network's A operands
   __shared__ float sn[2][kIn];
   if (threadIdx.x < kIn) {

@@ -10,8 +10,9 @@
 namespace adress {
 
 // Rebuild decision after a mapping: rebuild when a centre moved more than skin/2 since the
-// last build (it could have changed class or found a new partner) or when the widest
-// molecule makes max(rc_cg, rc_at + 2 ext) + 2 disp exceed the list cutoff.  The mapping
+// last build (it could have changed class or found a new partner), when the widest
+// molecule makes max(rc_cg, rc_at + 2 ext) + 2 disp exceed the list cutoff, or when the
+// host asked for it (the resolution region moved).  The mapping
 // just written becomes current; the maxima are reset for the next mapping.
 __global__ void k_decide(const __grid_constant__ Sys s, Bufs b, DecideArgs da) {
   Ctrl* c = b.ctrl;
@@ -20,7 +21,7 @@ __global__ void k_decide(const __grid_constant__ Sys s, Bufs b, DecideArgs da) {
   c->maxext2 = 0u;
   c->maxdisp2 = 0u;
   const double cut = fmax(s.rc_cg, s.rc_at + 2.0 * (double)e);
-  const int rb = da.force || (md > 0.5 * s.skin) || (cut + 2.0 * md > s.r_list);
+  const int rb = da.force || c->force_rebuild || (md > 0.5 * s.skin) || (cut + 2.0 * md > s.r_list);
   if (cut > s.r_list) set_error(c, ADRESS_ERR_EXTENT, (int)(e * 1000));
   c->rebuild = rb;
   c->ext_now = e;

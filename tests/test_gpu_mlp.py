@@ -157,6 +157,42 @@ def test_md_forces_with_learned_cg_force_match_oracle(precision):
     sim.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_learned_cg_force_with_multiple_time_stepping(precision):
+    """The network is a slow force: at inner time levels it is not evaluated (the forces equal
+    the oracle's fast part), at outer levels it acts with weight n; a run of whole outer steps
+    follows the oracle."""
+    s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, seed=5)
+    s.respa_n = 3
+    x, v = inputs.tetra_state(s)
+    o = oracle.Oracle(s)
+    feat, _, _ = o.collect_pairs(x, s.rc_cg)
+    mean, std = feat.mean(0), feat.std(0) + 1e-3
+    params = rand_params(7, scale=0.2)
+    o.set_mlp(oracle_net(params, mean, std, 3.0))
+    sim = sim_with_net(s, params, mean, std, 3.0, precision=precision)
+    sim.set_cg_mode(1)
+    sim.set_state(x, v)
+    for level, tol in ((1, 2e-5 if precision == "fp32" else 1e-10), (3, 2e-3)):
+        sim.set_step(level)
+        f, _ = sim.forces()
+        f_ref, _ = o.forces(x, step=level)
+        rel = math.sqrt(((f - f_ref) ** 2).sum() / (f_ref ** 2).sum())
+        assert rel < tol, (level, rel)
+    sim.set_step(0)
+    sim.compute_forces(energies=False)
+    sim.step(6)
+    sim.check()
+    xg, _, _ = sim.get_state()
+    f0, _ = o.forces(x, step=0)
+    xo, _, _ = o.run(x, v, f0, 0, 6)
+    L = np.array(s.box)
+    dx = xg - xo
+    dx -= L * np.rint(dx / L)
+    assert np.abs(dx).max() < 1e-4
+    sim.close()
+
+
 def test_trained_network_beats_the_table_on_held_out_atomistic_forces():
     """Force matching on atomistic pair forces: the trained network's error on held-out
     pairs is well below that of the tabulated CG potential (the method without it)."""
