@@ -94,6 +94,19 @@ __device__ __forceinline__ float exp_neg(float z) {
   return r;
 }
 __device__ __forceinline__ float silu_f(float z) { return z * rcp_approx(1.0f + exp_neg(z)); }
+// The MD evaluation's SiLU: z sigma(z) = (z/2) (1 + tanh(z/2)) with the hardware tanh
+// approximation (absolute error about 2^-11): one special-function operation instead of two,
+// the pipe that bounds the network evaluation; the error stays below the bfloat16 resolution
+// the first layer's activations are rounded to.
+__device__ __forceinline__ float tanh_approx(float x) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float silu_t(float z) {
+  const float h = 0.5f * z;
+  return fmaf(h, tanh_approx(h), h);
+}
 __device__ __forceinline__ float dsilu_f(float z) {
   const float sg = rcp_approx(1.0f + exp_neg(z));
   return sg * (1.0f + z * (1.0f - sg));
@@ -238,10 +251,10 @@ __device__ __forceinline__ void tile_forward_y2(const MlpViewQ& m, const unsigne
     }
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      a2[u][kk][0] = pack_bf16(silu_f(z[u][0][0]), silu_f(z[u][0][1]));
-      a2[u][kk][1] = pack_bf16(silu_f(z[u][0][2]), silu_f(z[u][0][3]));
-      a2[u][kk][2] = pack_bf16(silu_f(z[u][1][0]), silu_f(z[u][1][1]));
-      a2[u][kk][3] = pack_bf16(silu_f(z[u][1][2]), silu_f(z[u][1][3]));
+      a2[u][kk][0] = pack_bf16(silu_t(z[u][0][0]), silu_t(z[u][0][1]));
+      a2[u][kk][1] = pack_bf16(silu_t(z[u][0][2]), silu_t(z[u][0][3]));
+      a2[u][kk][2] = pack_bf16(silu_t(z[u][1][0]), silu_t(z[u][1][1]));
+      a2[u][kk][3] = pack_bf16(silu_t(z[u][1][2]), silu_t(z[u][1][3]));
     }
   }
   float p[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
@@ -259,8 +272,8 @@ __device__ __forceinline__ void tile_forward_y2(const MlpViewQ& m, const unsigne
     const float w0 = LdShared::f(m.w3 + o), w1 = LdShared::f(m.w3 + o + 1);
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      p[u][0] += w0 * silu_f(c[u][0]) + w1 * silu_f(c[u][1]);
-      p[u][1] += w0 * silu_f(c[u][2]) + w1 * silu_f(c[u][3]);
+      p[u][0] += w0 * silu_t(c[u][0]) + w1 * silu_t(c[u][1]);
+      p[u][1] += w0 * silu_t(c[u][2]) + w1 * silu_t(c[u][3]);
     }
   }
 #pragma unroll
