@@ -287,7 +287,8 @@ __device__ __forceinline__ void com_fp64(const Sys& s, const Box& B, unsigned gm
 // P32: integer fixed-point arithmetic (exact, periodic) on the bits of the doubles.
 template <int NA>
 __device__ __forceinline__ void map_group32(const Sys& s, const Box& B, const Bufs& b, int nxt, int a, int g, unsigned gmask,
-                                            int base, bool live, const double x[3], float& ext2, float& disp2) {
+                                            int base, bool live, const double x[3], const int4 ref, float& ext2,
+                                            float& disp2) {
   const bool own = live && g < NA;
   unsigned Pk[3], P0[3], R[3];
   int o32[3];
@@ -348,7 +349,6 @@ __device__ __forceinline__ void map_group32(const Sys& s, const Box& B, const Bu
     b.com_fx[nxt][a] = make_int4((int)R[0], (int)R[1], (int)R[2], __float_as_int(w));
     b.molf[nxt][a] = make_float2(dxc, region == 1 ? 1.f : 0.f);
     if (s.n_centers > 0) b.kcen[nxt][a] = kmin;
-    const int4 ref = b.com_ref[a];
     const float d0 = (float)(int)(R[0] - (unsigned)ref.x) * B.fx_scale[0];
     const float d1 = (float)(int)(R[1] - (unsigned)ref.y) * B.fx_scale[1];
     const float d2 = (float)(int)(R[2] - (unsigned)ref.z) * B.fx_scale[2];
@@ -359,7 +359,8 @@ __device__ __forceinline__ void map_group32(const Sys& s, const Box& B, const Bu
 // P64: the plain double-precision mapping (the FP64 reference path).
 template <int NA>
 __device__ __forceinline__ void map_group64(const Sys& s, const Box& B, const Bufs& b, int nxt, int a, int g, unsigned gmask,
-                                            int base, bool live, const double x[3], float& ext2, float& disp2) {
+                                            int base, bool live, const double x[3], const int4 ref, float& ext2,
+                                            float& disp2) {
   const bool own = live && g < NA;
   double dl[3], c[3], R[3];
 #pragma unroll
@@ -400,7 +401,6 @@ __device__ __forceinline__ void map_group64(const Sys& s, const Box& B, const Bu
 #pragma unroll
     for (int d = 0; d < 3; ++d) X[d] = (unsigned)(unsigned long long)llrint(R[d] * B.fx_inv[d]);
     b.com_fx[nxt][a] = make_int4((int)X[0], (int)X[1], (int)X[2], __float_as_int((float)w));
-    const int4 ref = b.com_ref[a];
     const float d0 = (float)(int)(X[0] - (unsigned)ref.x) * B.fx_scale[0];
     const float d1 = (float)(int)(X[1] - (unsigned)ref.y) * B.fx_scale[1];
     const float d2 = (float)(int)(X[2] - (unsigned)ref.z) * B.fx_scale[2];
@@ -445,6 +445,7 @@ __global__ void __launch_bounds__(kMaxForceBlock) k_prologue(const __grid_consta
   const int nxt = b.ctrl->parity ^ 1;
   const Box& B = box_t<MULTI>(s, b, live ? a : 0);
   const size_t N = (size_t)s.N;
+  const int4 ref = live && g == 0 ? b.com_ref[a] : make_int4(0, 0, 0, 0);  // centre at the last build
   double x[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -464,8 +465,8 @@ __global__ void __launch_bounds__(kMaxForceBlock) k_prologue(const __grid_consta
     }
   }
   float ext2 = 0.f, disp2 = 0.f;
-  if (P::fp64) map_group64<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
-  else map_group32<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
+  if (P::fp64) map_group64<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ref, ext2, disp2);
+  else map_group32<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ref, ext2, disp2);
   publish_extent(b, ext2, disp2);
 }
 
@@ -538,6 +539,9 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
 
   const int a = live_item ? b.items[t] : 0;
   const Box& B = box_t<MULTI>(s, b, a);
+  // centre at the last list build, for the displacement the next mapping reports: fetched
+  // now so that its latency hides behind the force loops
+  const int4 ref = MODE == MODE_FUSED && live && g == 0 ? b.com_ref[a] : make_int4(0, 0, 0, 0);
   const int i = a * NA + (g < NA ? g : 0);
   const auto Ca = Q::com(b, cur, a);
   const real wa = Q::w(Ca);
@@ -947,8 +951,8 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
       }
       float ext2 = 0.f, disp2 = 0.f;
       const int nxt = cur ^ 1;
-      if (P::fp64) map_group64<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
-      else map_group32<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ext2, disp2);
+      if (P::fp64) map_group64<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ref, ext2, disp2);
+      else map_group32<NA>(s, B, b, nxt, a, g, gmask, base, live, x, ref, ext2, disp2);
       publish_extent(b, ext2, disp2);
     }
   }
