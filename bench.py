@@ -73,23 +73,25 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 50 ms) started before the warm-up, so that it runs during the
+    timed region; the summary keeps the samples taken inside that region (the one nearest to
+    its middle when the region is shorter than the sampling interval)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}_{index}.csv")
 
     def __enter__(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -104,25 +106,36 @@ class Clocks:
                 self.proc.kill()
             self.fh.close()
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+        if t0 is not None and rows:
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            if not inside:
+                mid = 0.5 * (t0 + t1)
+                inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+            rows = inside
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for n, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+        sm = [r[1] for r in rows]
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "sm_max_mhz": max(r[2] for r in rows) if rows else None, "reasons": sorted(reasons),
                 "samples": len(sm)}
 
 
@@ -527,7 +540,7 @@ def replicas_arm(timed, steps, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
@@ -607,14 +620,15 @@ def main():
 
     def timed(sim, k, w):
         stream = sim.stream
-        for _ in range(w):
-            run_block(sim)
-        sim.check()
-        evs = []
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        with Clocks(local) as clk:
+        with Clocks(local) as clk:  # sampling runs from the warm-up on
+            for _ in range(w):
+                run_block(sim)
+            sim.check()
+            evs = []
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.time()
             for _ in range(k):
                 with torch.cuda.stream(stream):
                     flush.zero_()
@@ -625,11 +639,12 @@ def main():
                 e1.record(stream)
                 evs.append((e0, e1))
             torch.cuda.synchronize()
+            t1 = time.time()
         if dist:
             dist.barrier()
         sim.check()
         ms = [a.elapsed_time(b) for a, b in evs]
-        return sum(ms) / 1e3, ms, clk.summary()
+        return sum(ms) / 1e3, ms, clk.summary(t0, t1)
 
     sim = make(args.precision)
     rb0 = sim.list_stats()["rebuilds"]

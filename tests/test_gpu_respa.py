@@ -98,3 +98,48 @@ def test_hamiltonian_conserved_with_multiple_time_steps():
         sim.close()
     assert amp[0.0015] < 1e-3
     assert 3.0 < amp[0.003] / amp[0.0015] < 5.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_combinations_water_spheres_and_batches(precision):
+    """Multiple time stepping combined with the water model, with energy interpolation in the
+    sphere geometry, and with batched replicas: forces at an inner and an outer level."""
+    from paper_1806_10841_gb300 import adress
+
+    w = inputs.scaled_c3(2000)
+    w.respa_n, w.scheme = 2, 1
+    xw, _ = inputs.water_state(w)
+    sp = inputs.scaled_c2(6000, seed=8)
+    L = np.array(sp.box)
+    sp.d_at, sp.d_hy = 4.0, 4.0
+    sp.centers = np.array([[0.25 * L[0], 0.5 * L[1], 0.5 * L[2]], [0.98 * L[0], 0.1 * L[1], 0.9 * L[2]]])
+    sp.tf = np.linspace(0.3, -0.3, int(math.ceil((sp.d_at + sp.d_hy) / sp.tf_dx)) + 2)
+    sp.respa_n, sp.scheme, sp.fec = 3, 1, np.linspace(-1.0, 1.0, 5)
+    xs, _ = inputs.tetra_state(sp)
+    for s, x in ((w, xw), (sp, xs)):
+        o = oracle.Oracle(s)
+        sim = sim_of(s, precision)
+        sim.set_state(x)
+        for level in (0, 1):
+            sim.set_step(level)
+            f, _ = sim.forces()
+            f_ref, _ = o.forces(x, step=level)
+            assert rel_rms(f, f_ref) <= TOL[precision], (s.na, level)
+        sim.check()
+        sim.close()
+    systems = [case(0, 2, M=M, seed=sd)[0] for M, sd in ((1500, 1), (2500, 1))]
+    nt = max(len(s.tf) for s in systems)
+    for s in systems:
+        s.tf = np.zeros(nt)
+    x, _ = inputs.replica_states(systems)
+    sim = adress.AdResS(systems, precision=precision)
+    sim.set_state(x)
+    for level in (1, 2):
+        sim.set_step(level)
+        f, _ = sim.forces()
+        for r, s in enumerate(systems):
+            a0, a1 = sim.atom0[r], sim.atom0[r + 1]
+            f_ref, _ = oracle.Oracle(s, replica=r).forces(x[a0:a1], step=level)
+            assert rel_rms(f[a0:a1], f_ref) <= TOL[precision], (r, level)
+    sim.check()
+    sim.close()
