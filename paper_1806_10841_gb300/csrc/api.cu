@@ -519,6 +519,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
         const double ir6 = 1.0 / (rc * rc * rc * rc * rc * rc);
         s.vsh[i][j] = -(s.c12[i][j] * ir6 - s.c6[i][j]) * ir6;
         s.qq[i][j] = c->coulomb_f * c->charge[i] * c->charge[j];
+        if (s.c12[i][j] != 0.0 || s.c6[i][j] != 0.0) s.lj_cols |= 1 << j;
         s.f.c12[i][j] = (float)s.c12[i][j];
         s.f.c6[i][j] = (float)s.c6[i][j];
         s.f.qq[i][j] = (float)s.qq[i][j];

@@ -96,6 +96,7 @@ struct Sys {
   int nb_model;
   double c12[kMaxNA][kMaxNA], c6[kMaxNA][kMaxNA], vsh[kMaxNA][kMaxNA], qq[kMaxNA][kMaxNA];
   double krf, crf;
+  int lj_cols;  // bit j: some site has a Lennard-Jones term with site j
   // bonded: bond_model 0 FENE (+ WCA), 1 harmonic (bond_k, bond_r0); harmonic angles
   int bond_model;
   double bond_k, bond_r0;

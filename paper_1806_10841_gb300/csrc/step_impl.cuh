@@ -596,17 +596,22 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
               if (ENERGY) e_at += 0.5 * (double)wab * (double)((real)4 * eps * (sr6 * sr6 - sr6) + eps);
               if (drift) dv += (real)4 * eps * (sr6 * sr6 - sr6) + eps;
             } else {
-              // LJ (c12 r^-12 - c6 r^-6, shifted) + reaction field q_i q_j f (1/r + k_rf r^2 - c_rf)
+              // LJ (c12 r^-12 - c6 r^-6, shifted) + reaction field q_i q_j f (1/r + k_rf r^2 - c_rf);
+              // the LJ term only for partner sites that have one with some site (water: O)
               const real ir = Q::rsqrt_(d2);
               const real ir2 = ir * ir;
-              const real ir6 = ir2 * ir2 * ir2;
-              fr = (((real)12 * c12r[j] * ir6 - (real)6 * c6r[j]) * ir6 * ir2 + qqr[j] * (ir2 * ir - krf2)) * wab;
+              real flj = 0, vlj = 0;
+              if ((s.lj_cols >> j) & 1) {
+                const real ir6 = ir2 * ir2 * ir2;
+                flj = ((real)12 * c12r[j] * ir6 - (real)6 * c6r[j]) * ir6 * ir2;
+                if (ENERGY || drift) vlj = (c12r[j] * ir6 - c6r[j]) * ir6;
+              }
+              fr = (flj + qqr[j] * (ir2 * ir - krf2)) * wab;
               if (ENERGY)
                 e_at += 0.5 * (double)wab *
-                        ((double)((c12r[j] * ir6 - c6r[j]) * ir6) + s.vsh[gg0][j] +
-                         (double)qqr[j] * ((double)ir + s.krf * (double)d2 - s.crf));
+                        ((double)vlj + s.vsh[gg0][j] + (double)qqr[j] * ((double)ir + s.krf * (double)d2 - s.crf));
               if (drift)
-                dv += (c12r[j] * ir6 - c6r[j]) * ir6 + par<real>(s.vsh[gg0][j], s.f.vsh[gg0][j]) +
+                dv += vlj + par<real>(s.vsh[gg0][j], s.f.vsh[gg0][j]) +
                       qqr[j] * (ir + par<real>(s.krf, s.f.krf) * d2 - par<real>(s.crf, s.f.crf));
             }
             fx += fr * dx;
