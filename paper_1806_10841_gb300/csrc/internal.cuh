@@ -302,7 +302,9 @@ constexpr int kMaxForceBlock = 128;
 
 // Threads per molecule the force kernel is launched with: four, or eight for the water-like
 // model, whose high-resolution items split their neighbour lists over two lane groups.
-inline int step_lanes(const Sys& s) { return s.nb_model == 1 ? 2 * kGroup : kGroup; }
+// water-like model: a high-resolution work item takes kSplitWater groups of four lanes
+constexpr int kSplitWater = 2;
+inline int step_lanes(const Sys& s) { return s.nb_model == 1 ? kSplitWater * kGroup : kGroup; }
 
 // Warps launched by the force kernel (one energy partial each).
 inline int force_warps(const Sys& s) {

@@ -488,18 +488,19 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
   using real = typename Q::real;
   const int lane = threadIdx.x & 31, g = threadIdx.x & 3, base = lane & ~3;
   const unsigned gmask = 0xFu << base;
-  // SPLIT = 2 (water): a high-resolution item takes two groups of four lanes (eight lanes in
-  // the same warp), each group half of the neighbour list; CG items keep one group.
-  constexpr int SPLIT = MODEL == 1 ? 2 : 1;
+  // SPLIT > 1 (water): a high-resolution item takes SPLIT groups of four lanes in the same
+  // warp, group `sub` every SPLIT-th neighbour from slot `sub`; CG items keep one group.
+  constexpr int SPLIT = MODEL == 1 ? kSplitWater : 1;
+  static_assert(SPLIT == 1 || SPLIT == 2 || SPLIT == 4, "lane groups per item");
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   int t = gtid >> 2, sub = 0;
-  if (SPLIT == 2) {
+  if (SPLIT > 1) {
     const int n_hr0 = b.ctrl->n_hr;
-    if (gtid < 8 * n_hr0) {
-      t = gtid >> 3;
-      sub = (gtid >> 2) & 1;
+    if (gtid < kGroup * SPLIT * n_hr0) {
+      t = gtid / (kGroup * SPLIT);
+      sub = (gtid >> 2) & (SPLIT - 1);
     } else {
-      t = n_hr0 + ((gtid - 8 * n_hr0) >> 2);
+      t = n_hr0 + ((gtid - kGroup * SPLIT * n_hr0) >> 2);
     }
   }
   const bool live_item = t < s.M;
@@ -637,12 +638,15 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
         if (drift && g == 0) dv -= sw * V;
       }
     }
-    if (SPLIT == 2) {  // the two groups' shares of the force (energies are summed per warp)
-      const unsigned m8 = 0xFFu << (lane & 24);
-      fx += __shfl_xor_sync(m8, fx, 4);
-      fy += __shfl_xor_sync(m8, fy, 4);
-      fz += __shfl_xor_sync(m8, fz, 4);
-      if (hs) dv += __shfl_xor_sync(m8, dv, 4);
+    if (SPLIT > 1) {  // the groups' shares of the force (energies are summed per warp)
+      const unsigned mk = SPLIT == 2 ? 0xFFu << (lane & 24) : 0xFFFFu << (lane & 16);
+#pragma unroll
+      for (int o = kGroup; o < kGroup * SPLIT; o <<= 1) {
+        fx += __shfl_xor_sync(mk, fx, o);
+        fy += __shfl_xor_sync(mk, fy, o);
+        fz += __shfl_xor_sync(mk, fz, o);
+        if (hs) dv += __shfl_xor_sync(mk, dv, o);
+      }
     }
     if (hs) {  // V_AT_a - V_CG_a = half the group's sum (every pair is listed from both sides)
       dv += __shfl_xor_sync(gmask, dv, 1);
