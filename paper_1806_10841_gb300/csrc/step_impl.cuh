@@ -654,16 +654,19 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
       dv *= (real)0.5;
     }
   } else {
-    // coarse-grained item (l_a = 0, so w_ab = 0): neighbour list split over the group,
-    // next centre prefetched
+    // coarse-grained item (l_a = 0, so w_ab = 0): neighbour list split over the group
     if (live && g == 0 && wa != (real)0) set_error(b.ctrl, ADRESS_ERR_STATE, a);
     real Fx = 0, Fy = 0, Fz = 0;
     auto C_n = Ca;
     const int nnb_cg = slow ? nnb : 0;  // no CG force at inner levels of multiple time stepping
+    // centres of the next two neighbours in flight (long lists: the water-like fluid)
     if (g < nnb_cg) C_n = Q::com(b, cur, m_first);
+    auto C_n2 = Ca;
+    if (g + kGroup < nnb_cg) C_n2 = Q::com(b, cur, b.nbr[(size_t)t * s.cap + g + kGroup]);
     for (int q = g; q < nnb_cg; q += kGroup) {
       const auto Cb = C_n;
-      if (q + kGroup < nnb_cg) C_n = Q::com(b, cur, b.nbr[(size_t)t * s.cap + q + kGroup]);
+      C_n = C_n2;
+      if (q + 2 * kGroup < nnb_cg) C_n2 = Q::com(b, cur, b.nbr[(size_t)t * s.cap + q + 2 * kGroup]);
       const auto R = Q::dR(B, Ca, Cb);
       const real r2 = pair_r2(R.x, R.y, R.z);
       if (r2 < rc_cg2) {
