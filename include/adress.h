@@ -1,5 +1,5 @@
 /*
- * adress.h — C ABI of the GB300 (sm_103a) force-interpolation AdResS step.
+ * adress.h — C ABI of the GB300 (sm_103a) AdResS step.
  *
  * One AdResS molecular-dynamics step of the paper's force-interpolation scheme
  * (ESPResSo++ 2.0, Sec. "Force interpolation", Eq. 1):
@@ -10,7 +10,10 @@
  * COM-COM force.  Intramolecular bonds are not interpolated (same section); a
  * thermodynamic force acts in the hybrid layer (Sec. "Free energy corrections and the
  * thermodynamic force"); force interpolation needs a thermostat (Sec. "Potential energy
- * interpolation"), here Langevin inside velocity Verlet.
+ * interpolation"), here Langevin inside velocity Verlet.  The configuration also selects
+ * energy interpolation (H-AdResS, Eq. Hmix, with its drift force, a free-energy
+ * correction and Kirkwood integration for it), a self-adjusting AT region around moving
+ * centres, and multiple time stepping of the CG forces; see adress_config.
  *
  * Conventions for every call:
  *  - All state arrays are caller-owned DEVICE memory in structure-of-arrays layout
@@ -187,8 +190,10 @@ adress_status adress_build_lists(adress_handle h);
 /* Conservative forces of the bound positions (Eq. 1 + bonded + thermodynamic force,
  * no thermostat) into f, with a fresh list build.  If energies != NULL (host, 4
  * doubles) synchronises and writes {E_AT, E_CG, E_bond, virial}: E_AT = sum over
- * molecule pairs of l_a l_b V^AT, E_CG = sum of (1 - l_a l_b) V^CG, virial = sum r.f over
- * pair and bond terms. */
+ * molecule pairs of w_ab V^AT, E_CG = sum of (1 - w_ab) V^CG with w_ab = l_a l_b (energy
+ * interpolation: (l_a + l_b)/2, so that the sum with E_bond is the potential of Eq. Hmix),
+ * virial = sum r.f over pair and bond terms.  With multiple time stepping, f carries the
+ * slow-force weight of the current time level (see respa_n); the energies do not. */
 adress_status adress_compute_forces(adress_handle h, double* energies);
 
 /* Advance the bound state (x, v, f at time level n) by nsteps Langevin velocity-Verlet
