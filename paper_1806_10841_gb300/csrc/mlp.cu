@@ -18,10 +18,14 @@
 // a block, with FP32 accumulation, per-block partials and a fixed-order reduction.
 #include <cuda_bf16.h>
 #include <math.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "internal.cuh"
 
 namespace adress {
+
+cudaError_t launch_mlp_eval_tc(const MlpDevArgs& a, const Bufs& b, float* fpair, cudaStream_t st);
 
 // ---------------- parameters ----------------------------------------------------------
 // Flat FP32 master vector: [W1 (64 x 9) | b1 (64) | W2 (64 x 64) | b2 (64) | w3 (64) | b3]
@@ -942,6 +946,14 @@ cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* f
 #undef FEAT
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  // the tcgen05 / TMEM evaluation (mlp_tc.cu), unless ADRESS_MLP_KERNEL=mma selects the
+  // warp-level MMA kernel below (same network, same results to rounding order)
+  static int tc = -1;
+  if (tc < 0) {
+    const char* v = getenv("ADRESS_MLP_KERNEL");
+    tc = v && strcmp(v, "mma") == 0 ? 0 : 1;
+  }
+  if (tc) return launch_mlp_eval_tc(a, b, fpair, st);
   // persistent grid: as many blocks as fit on the device at once
   static int grid = 0;
   if (!grid) {

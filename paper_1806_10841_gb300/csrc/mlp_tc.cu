@@ -1,0 +1,210 @@
+// Network evaluation of the MD step on the 5th-generation tensor cores (tcgen05): the same
+// 9 -> 64 -> 64 -> 1 SiLU network as k_mlp_eval, with both layers' products issued by one
+// thread as 128-row MMAs whose accumulators live in tensor memory (TMEM).
+//
+// A tile is 64 pairs in both orderings: rows r < 64 hold pair p0 + r with features (d, s_a,
+// s_b), rows r >= 64 the same pairs with (d, s_b, s_a).  Per tile: the pair buffer's bf16
+// inputs go to shared memory (A1, K padded to 16), one MMA gives layer 1 into TMEM columns
+// 0..63; each thread reads its row back (tcgen05.ld), adds the bias, applies SiLU and writes
+// the bf16 activations to shared memory (A2); four MMAs (K = 64) give layer 2 into columns
+// 64..127; each thread forms its row's output w3 . silu(z2 + b2) + b3, and the pair force is
+// the mean over the two orderings times the output scale, written to both list slots.
+// Waits on the MMA completion barrier are bounded: on expiry the kernel records a timeout
+// status and every block leaves after freeing its TMEM.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+#include "umma.cuh"
+
+namespace adress {
+
+namespace {
+
+constexpr int kTcH = 64, kTcIn = 9;
+constexpr int kTcOb1 = kTcH * kTcIn, kTcOb2 = kTcOb1 + kTcH + kTcH * kTcH, kTcOw3 = kTcOb2 + kTcH,
+              kTcOb3 = kTcOw3 + kTcH;
+constexpr uint32_t kWaitPolls = 1u << 22;  // ~tens of ms: far beyond a 128x64x64 product
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ float tanh_hw(float x) {
+  float r;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// z sigma(z) = (z/2)(1 + tanh(z/2)), as in the warp-MMA evaluation
+__device__ __forceinline__ float silu_hw(float z) {
+  const float h = 0.5f * z;
+  return fmaf(h, tanh_hw(h), h);
+}
+
+// byte offset of the 16-byte chunk (row r, K chunk kc) in a K-major no-swizzle operand with
+// nk chunks of 8 elements per row
+__device__ __forceinline__ uint32_t chunk_off(int r, int kc, int nk) {
+  return (uint32_t)((r >> 3) * (nk * 128) + kc * 128 + (r & 7) * 16);
+}
+
+struct __align__(1024) TcSmem {
+  uint8_t A1[128 * 16 * 2];  // 128 rows x 16 bf16
+  uint8_t A2[128 * 64 * 2];  // 128 rows x 64 bf16
+  uint8_t B1[64 * 16 * 2];   // W1: 64 outputs x 16 inputs (K-major)
+  uint8_t B2[64 * 64 * 2];   // W2: 64 outputs x 64 inputs
+  float b1[kTcH], b2[kTcH], w3[kTcH];
+  float y[128];
+  uint64_t mbar;
+  uint32_t taddr;
+  int abort;
+};
+
+__global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict__ P, const unsigned* __restrict__ W1p,
+                                                        const unsigned* __restrict__ W2p, const float* __restrict__ norm,
+                                                        const unsigned* __restrict__ pfrag,
+                                                        const int2* __restrict__ pslot, const unsigned* npair,
+                                                        float* __restrict__ fpair, Ctrl* ctrl) {
+  __shared__ TcSmem S;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // operands that do not change: weights in the K-major core-matrix layout, biases
+  for (int i = tid; i < 64 * 2; i += 128) {  // W1: row n, chunk kc = words 4 kc .. 4 kc + 3
+    const int n = i >> 1, kc = i & 1;
+    const unsigned* w = W1p + n * 8 + 4 * kc;
+    *reinterpret_cast<uint4*>(S.B1 + chunk_off(n, kc, 2)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  for (int i = tid; i < 64 * 8; i += 128) {
+    const int n = i >> 3, kc = i & 7;
+    const unsigned* w = W2p + n * 32 + 4 * kc;
+    *reinterpret_cast<uint4*>(S.B2 + chunk_off(n, kc, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  if (tid < kTcH) {
+    S.b1[tid] = P[kTcOb1 + tid];
+    S.b2[tid] = P[kTcOb2 + tid];
+    S.w3[tid] = P[kTcOw3 + tid];
+  }
+  if (tid == 0) {
+    S.abort = 0;
+    umma::mbar_init(&S.mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    umma::alloc(&S.taddr, 128);
+    umma::relinquish();
+  }
+  umma::fence_proxy_async();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = S.taddr;
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  const float b3 = P[kTcOb3], scale = norm[2 * kTcIn];
+  constexpr uint32_t idesc = umma::idesc_bf16_f32(128, 64);
+  const uint32_t a1 = umma::smem_u32(S.A1), a2 = umma::smem_u32(S.A2), bw1 = umma::smem_u32(S.B1),
+                 bw2 = umma::smem_u32(S.B2);
+  const long long np = *npair;
+  const long long ntiles = (np + 63) / 64;
+  uint32_t phase = 0;
+
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long p0 = tile * 64;
+    // layer-1 inputs of row tid: pair p0 + (tid & 63), ordering tid >> 6 (words 5u .. 5u + 4)
+    {
+      const long long p = p0 + (tid & 63);
+      const int u = tid >> 6;
+      uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0u, 0u, 0u, 0u);
+      if (p < np) {
+        const unsigned* r = pfrag + p * 10 + 5 * u;
+        c0 = make_uint4(r[0], r[1], r[2], r[3]);
+        c1.x = r[4];
+      }
+      *reinterpret_cast<uint4*>(S.A1 + chunk_off(tid, 0, 2)) = c0;
+      *reinterpret_cast<uint4*>(S.A1 + chunk_off(tid, 1, 2)) = c1;
+    }
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      umma::fence_after_sync();
+      umma::mma_bf16(tmem, umma::desc(a1, 128, 256), umma::desc(bw1, 128, 256), idesc, 0u);
+      umma::commit(&S.mbar);
+    }
+    if (!umma::mbar_wait(&S.mbar, phase, kWaitPolls)) atomicExch(&S.abort, 1);
+    phase ^= 1u;
+    umma::fence_after_sync();
+    __syncthreads();
+    if (S.abort) break;
+    // layer 1 -> SiLU -> bf16 activations of row tid
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float z[32];
+      umma::ld32(tmem + lane_base + 32 * half, z);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = 32 * half + 8 * c;
+        uint4 q;
+        q.x = pack2(silu_hw(z[8 * c + 0] + S.b1[j + 0]), silu_hw(z[8 * c + 1] + S.b1[j + 1]));
+        q.y = pack2(silu_hw(z[8 * c + 2] + S.b1[j + 2]), silu_hw(z[8 * c + 3] + S.b1[j + 3]));
+        q.z = pack2(silu_hw(z[8 * c + 4] + S.b1[j + 4]), silu_hw(z[8 * c + 5] + S.b1[j + 5]));
+        q.w = pack2(silu_hw(z[8 * c + 6] + S.b1[j + 6]), silu_hw(z[8 * c + 7] + S.b1[j + 7]));
+        *reinterpret_cast<uint4*>(S.A2 + chunk_off(tid, 4 * half + c, 8)) = q;
+      }
+    }
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      umma::fence_after_sync();
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        umma::mma_bf16(tmem + 64, umma::desc(a2 + 256 * kk, 128, 1024), umma::desc(bw2 + 256 * kk, 128, 1024), idesc,
+                       kk > 0 ? 1u : 0u);
+      umma::commit(&S.mbar);
+    }
+    if (!umma::mbar_wait(&S.mbar, phase, kWaitPolls)) atomicExch(&S.abort, 1);
+    phase ^= 1u;
+    umma::fence_after_sync();
+    __syncthreads();
+    if (S.abort) break;
+    // layer 2 -> SiLU -> output weight: this row's network output
+    float acc = 0.f;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float z[32];
+      umma::ld32(tmem + lane_base + 64 + 32 * half, z);
+#pragma unroll
+      for (int c = 0; c < 32; ++c) acc = fmaf(S.w3[32 * half + c], silu_hw(z[c] + S.b2[32 * half + c]), acc);
+    }
+    S.y[tid] = acc + b3;
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid < 64 && p0 + tid < np) {
+      const float fv = 0.5f * scale * (S.y[tid] + S.y[tid + 64]);
+      const int2 sl = pslot[p0 + tid];
+      fpair[sl.x] = fv;
+      if (sl.y >= 0) fpair[sl.y] = fv;
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && S.abort) set_error(ctrl, ADRESS_ERR_TIMEOUT, 2);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (warp == 0) umma::dealloc(tmem, 128);
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_eval_tc(const MlpDevArgs& a, const Bufs& b, float* fpair, cudaStream_t st) {
+  static int grid = 0;
+  if (!grid) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    // four blocks per SM (the register bound of the kernel keeps a fifth out), 4 x 128 TMEM
+    // columns = all 512; two or three per SM were 20 and 7 us slower per evaluation
+    grid = 4 * sms;
+  }
+  k_mlp_eval_tc<<<grid, 128, 0, st>>>(a.P, a.W1p, a.W2p, a.norm, b.pfrag, b.pslot, b.npair, fpair, b.ctrl);
+  return cudaGetLastError();
+}
+
+}  // namespace adress
