@@ -8,7 +8,9 @@
 // 0..63; each thread reads its row back (tcgen05.ld), adds the bias, applies SiLU and writes
 // the bf16 activations to shared memory (A2); four MMAs (K = 64) give layer 2 into columns
 // 64..127; each thread forms its row's output w3 . silu(z2 + b2) + b3, and the pair force is
-// the mean over the two orderings times the output scale, written to both list slots.
+// the mean over the two orderings times the output scale, written to both list slots.  The
+// layer-2 products of a tile are issued together with the layer-1 product of the block's
+// next tile, so a tile costs one barrier wait.
 // Waits on the MMA completion barrier are bounded: on expiry the kernel records a timeout
 // status and every block leaves after freeing its TMEM.
 #include <cuda_bf16.h>
@@ -104,35 +106,51 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
   const long long ntiles = (np + 63) / 64;
   uint32_t phase = 0;
 
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long p0 = tile * 64;
-    // layer-1 inputs of row tid: pair p0 + (tid & 63), ordering tid >> 6 (words 5u .. 5u + 4)
-    {
-      const long long p = p0 + (tid & 63);
-      const int u = tid >> 6;
-      uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0u, 0u, 0u, 0u);
-      if (p < np) {
-        const unsigned* r = pfrag + p * 10 + 5 * u;
-        c0 = make_uint4(r[0], r[1], r[2], r[3]);
-        c1.x = r[4];
-      }
-      *reinterpret_cast<uint4*>(S.A1 + chunk_off(tid, 0, 2)) = c0;
-      *reinterpret_cast<uint4*>(S.A1 + chunk_off(tid, 1, 2)) = c1;
+  // inputs of a tile's row tid: pair p0 + (tid & 63), ordering tid >> 6 (words 5u .. 5u + 4)
+  auto stage_inputs = [&](long long p0) {
+    const long long p = p0 + (tid & 63);
+    const int u = tid >> 6;
+    uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0u, 0u, 0u, 0u);
+    if (p < np) {
+      const unsigned* r = pfrag + p * 10 + 5 * u;
+      c0 = make_uint4(r[0], r[1], r[2], r[3]);
+      c1.x = r[4];
     }
+    *reinterpret_cast<uint4*>(S.A1 + chunk_off(tid, 0, 2)) = c0;
+    *reinterpret_cast<uint4*>(S.A1 + chunk_off(tid, 1, 2)) = c1;
+  };
+  // make the shared-memory writes and TMEM reads of all threads precede what thread 0 issues
+  auto sync_for_issue = [&]() {
     umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
+  };
+  // wait for every product issued so far; false once any thread of the block gave up
+  auto wait_products = [&]() -> bool {
+    if (!umma::mbar_wait(&S.mbar, phase, kWaitPolls)) atomicExch(&S.abort, 1);
+    phase ^= 1u;
+    umma::fence_after_sync();
+    __syncthreads();
+    return S.abort == 0;
+  };
+
+  // pipeline: layer 1 of the first tile alone, then per tile one barrier wait for layer 2
+  // of this tile together with layer 1 of the next
+  long long tile = blockIdx.x;
+  if (tile < ntiles) {
+    stage_inputs(tile * 64);
+    sync_for_issue();
     if (tid == 0) {
       umma::fence_after_sync();
       umma::mma_bf16(tmem, umma::desc(a1, 128, 256), umma::desc(bw1, 128, 256), idesc, 0u);
       umma::commit(&S.mbar);
     }
-    if (!umma::mbar_wait(&S.mbar, phase, kWaitPolls)) atomicExch(&S.abort, 1);
-    phase ^= 1u;
-    umma::fence_after_sync();
-    __syncthreads();
-    if (S.abort) break;
-    // layer 1 -> SiLU -> bf16 activations of row tid
+    if (!wait_products()) tile = ntiles;
+  }
+  while (tile < ntiles) {
+    const long long p0 = tile * 64, next = tile + gridDim.x;
+    const bool has_next = next < ntiles;
+    // layer 1 (TMEM columns 0..63) -> SiLU -> bf16 activations of row tid
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       float z[32];
@@ -148,23 +166,19 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
         *reinterpret_cast<uint4*>(S.A2 + chunk_off(tid, 4 * half + c, 8)) = q;
       }
     }
-    umma::fence_proxy_async();
-    umma::fence_before_sync();
-    __syncthreads();
+    if (has_next) stage_inputs(next * 64);
+    sync_for_issue();
     if (tid == 0) {
       umma::fence_after_sync();
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
         umma::mma_bf16(tmem + 64, umma::desc(a2 + 256 * kk, 128, 1024), umma::desc(bw2 + 256 * kk, 128, 1024), idesc,
                        kk > 0 ? 1u : 0u);
+      if (has_next) umma::mma_bf16(tmem, umma::desc(a1, 128, 256), umma::desc(bw1, 128, 256), idesc, 0u);
       umma::commit(&S.mbar);
     }
-    if (!umma::mbar_wait(&S.mbar, phase, kWaitPolls)) atomicExch(&S.abort, 1);
-    phase ^= 1u;
-    umma::fence_after_sync();
-    __syncthreads();
-    if (S.abort) break;
-    // layer 2 -> SiLU -> output weight: this row's network output
+    if (!wait_products()) break;
+    // layer 2 (columns 64..127) -> SiLU -> output weight: this row's network output
     float acc = 0.f;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -174,7 +188,6 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
       for (int c = 0; c < 32; ++c) acc = fmaf(S.w3[32 * half + c], silu_hw(z[c] + S.b2[32 * half + c]), acc);
     }
     S.y[tid] = acc + b3;
-    umma::fence_before_sync();
     __syncthreads();
     if (tid < 64 && p0 + tid < np) {
       const float fv = 0.5f * scale * (S.y[tid] + S.y[tid + 64]);
@@ -182,7 +195,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
       fpair[sl.x] = fv;
       if (sl.y >= 0) fpair[sl.y] = fv;
     }
-    __syncthreads();
+    tile = next;
   }
   if (tid == 0 && S.abort) set_error(ctrl, ADRESS_ERR_TIMEOUT, 2);
   umma::fence_before_sync();
