@@ -197,7 +197,11 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
     }
     tile = next;
   }
-  if (tid == 0 && S.abort) set_error(ctrl, ADRESS_ERR_TIMEOUT, 2);
+  if (S.abort) {
+    if (tid == 0) set_error(ctrl, ADRESS_ERR_TIMEOUT, 2);
+    // give the products still in flight a second bounded wait before their TMEM is freed
+    umma::mbar_wait(&S.mbar, phase ^ 1u, kWaitPolls);
+  }
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
