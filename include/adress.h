@@ -269,7 +269,10 @@ adress_status adress_rdf(adress_handle h, int32_t nbins, double dr, int64_t* cou
 adress_status adress_mlp_set(adress_handle h, const float* params, const float* norm);
 adress_status adress_mlp_get(adress_handle h, float* params, float* norm); /* synchronises */
 /* 0: tabulated CG force (default); 1: learned network for every pair with COM distance
- * < rc_cg and l_a l_b < 1 (no CG energy is accumulated in mode 1). */
+ * < rc_cg and l_a l_b < 1 (no CG energy is accumulated in mode 1).  In the MD step the
+ * network runs on the tcgen05 tensor cores (128-row products, accumulators in tensor
+ * memory); the environment variable ADRESS_MLP_KERNEL=mma, read at the first evaluation,
+ * selects the warp-level MMA kernel instead (same results up to summation order). */
 adress_status adress_set_cg_mode(adress_handle h, int32_t mode);
 /* Append training samples from the bound positions (lists rebuilt first): every molecule
  * pair a < b with COM distance < rc_cg gives features (d, s_a[4], s_b[4]), the atomistic
