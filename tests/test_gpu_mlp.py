@@ -286,3 +286,43 @@ def test_learned_cg_run_reproduces_the_atomistic_rdf_better_than_the_table():
     e_net, e_tab = l2(g_net, g_at), l2(g_tab, g_at)
     print(f"RDF L2 vs all-atomistic: network {e_net:.4f}, table {e_tab:.4f}")
     assert e_net < e_tab
+
+
+def test_tcgen05_and_warp_mma_evaluations_agree():
+    """The network evaluation of the MD step runs on tcgen05 (default) or on warp-level MMA
+    (ADRESS_MLP_KERNEL=mma, read once per process): the same forces up to summation order."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = r'''
+import json, sys
+sys.path.insert(0, %r)
+sys.path.insert(0, %r)
+import numpy as np
+from paper_1806_10841_gb300 import inputs
+from test_gpu_mlp import rand_params, sim_with_net
+import oracle
+s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, seed=5)
+x, _ = inputs.tetra_state(s)
+feat, _, _ = oracle.Oracle(s).collect_pairs(x, s.rc_cg)
+sim = sim_with_net(s, rand_params(7, scale=0.2), feat.mean(0), feat.std(0) + 1e-3, 3.0)
+sim.set_cg_mode(1)
+sim.set_state(x)
+f, _ = sim.forces()
+sim.check()
+print(json.dumps(f.reshape(-1).tolist()))
+''' % (root, os.path.join(root, "tests"))
+    out = {}
+    for kind in ("default", "mma"):
+        env = dict(os.environ)
+        env.pop("ADRESS_MLP_KERNEL", None)
+        if kind == "mma":
+            env["ADRESS_MLP_KERNEL"] = "mma"
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out[kind] = np.array(json.loads(r.stdout.strip().splitlines()[-1]))
+    a, b = out["default"], out["mma"]
+    assert math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()) < 1e-5
