@@ -145,3 +145,18 @@ def test_init_rejects_bad_multiple_time_stepping(lib):
     cfgs = (adress.adress_config * 2)(adress._config(a, keep, 0, 0, "fp32"), adress._config(b, keep, 1, 0, "fp32"))
     assert L.adress_init_batch(cfgs, 2, None, ctypes.byref(h)) == 1
     assert b"multiple time stepping" in L.adress_last_error(None)
+
+
+def test_binding_fails_loudly_without_the_library():
+    """No fallback: without the built CUDA library the binding raises (fresh interpreter)."""
+    import subprocess
+    import sys
+
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1806_10841_gb300 import adress\n"
+            "try:\n"
+            "    adress.load_library('/nonexistent/libadress_gb300.so')\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "raised:" in r.stdout and "missing" in r.stdout, r.stdout + r.stderr
