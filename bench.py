@@ -625,6 +625,7 @@ def main():
                 run_block(sim)
             sim.check()
             evs = []
+            timed.rebuilds0 = sim.list_stats()["rebuilds"]
             if dist:
                 dist.barrier()
             torch.cuda.synchronize()
@@ -643,16 +644,17 @@ def main():
         if dist:
             dist.barrier()
         sim.check()
+        timed.rebuilds = sim.list_stats()["rebuilds"] - timed.rebuilds0  # inside the timed steps
         ms = [a.elapsed_time(b) for a, b in evs]
         return sum(ms) / 1e3, ms, clk.summary(t0, t1)
 
     sim = make(args.precision)
-    rb0 = sim.list_stats()["rebuilds"]
     total_s, ms, clocks = timed(sim, args.steps, args.warmup)
-    rebuilds = sim.list_stats()["rebuilds"] - rb0
+    rebuilds = timed.rebuilds
     # kernels per bench step (one graph): 1 prologue + 99 fused + 1 last + 100 decide
-    # + 10 density samples + 1 TF update; 14 kernels per list rebuild
-    per_block = 1 + (MD_PER_BLOCK - 1) + 1 + MD_PER_BLOCK + MD_PER_BLOCK // SAMPLE_EVERY + 1
+    # + 10 density samples + 2 for the TF update (update, sample-count reset); 14 kernels
+    # per list rebuild
+    per_block = 1 + (MD_PER_BLOCK - 1) + 1 + MD_PER_BLOCK + MD_PER_BLOCK // SAMPLE_EVERY + 2
     launches = args.steps * per_block + 14 * rebuilds
     value, total_s = job_throughput(total_s, s.N * MD_PER_BLOCK * args.steps, dist, dev)
 
