@@ -22,11 +22,20 @@
  *     "Potential energy interpolation") with velocity-Verlet integration.
  * Parity unpinned: the thermodynamic-force update rule (orc_tf_update) beyond its
  * identity and closed-form cases; the paper gives no formula for it.
+ *
+ * Built plainly (gcc -O2) every loop runs serially in the order written.  Built with
+ * -fopenmp (the all-core CPU baseline), the per-atom and per-molecule loops run in
+ * parallel and the linked-cell pair scan gives each thread its own force, energy and
+ * per-molecule potential buffers, added in thread order afterwards: the same definition,
+ * with floating-point sums in another order.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include "adress_oracle.h"
 
@@ -120,6 +129,7 @@ static double nearest_center(const orc_sys* s, const double* R, int* kmin) {
  * nearest centre) and lambda. */
 void orc_com_lambda(const orc_sys* s, const double* x, double* R, double* dx_c, double* w) {
   const double Mt = mol_mass(s);
+#pragma omp parallel for schedule(static)
   for (int a = 0; a < s->M; ++a) {
     const double* x0 = x + 3 * (size_t)a * s->na;
     double acc[3] = {0, 0, 0};
@@ -421,6 +431,30 @@ static double max_extent(const orc_sys* s, const double* x, const double* R) {
   return sqrt(m);
 }
 
+/* Every pair (a, b > a) of molecule a with the molecules of its cell and the 26 cells around
+ * it (each distinct cell once, so that a box of two cells along an axis counts no pair
+ * twice). */
+static void cell_scan(const orc_sys* s, const double* x, const double* R, const double* w, int a, const int nc[3],
+                      const int* cell, const int* head, const int* next, double* f, double* acc, double* vat,
+                      double* vcg, double sw) {
+  int c = cell[a];
+  int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
+  int seen[27], ns = 0;
+  for (int ox = -1; ox <= 1; ++ox)
+    for (int oy = -1; oy <= 1; ++oy)
+      for (int oz = -1; oz <= 1; ++oz) {
+        int nx = ((cx + ox) % nc[0] + nc[0]) % nc[0];
+        int ny = ((cy + oy) % nc[1] + nc[1]) % nc[1];
+        int nz = ((cz + oz) % nc[2] + nc[2]) % nc[2];
+        int nbc = (nx * nc[1] + ny) * nc[2] + nz, dup = 0;
+        for (int q = 0; q < ns; ++q) dup |= (seen[q] == nbc);
+        if (dup) continue;
+        seen[ns++] = nbc;
+        for (int b = head[nbc]; b >= 0; b = next[b])
+          if (b > a) pair_ab(s, x, R, w, a, b, f, acc, vat, vcg, sw);
+      }
+}
+
 /* Conservative forces (no thermostat).  method 0: every molecule pair a<b;
  * method 1: a linked-cell scan over COM cells no smaller than the largest pair reach.
  * w_override (may be NULL) replaces lambda for every molecule. */
@@ -466,23 +500,39 @@ static int forces_sw(const orc_sys* s, const double* x, int method, const double
       next[a] = head[cell[a]];
       head[cell[a]] = a;
     }
-    for (int a = 0; a < M; ++a) {
-      int c = cell[a];
-      int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
-      int seen[27], ns = 0;
-      for (int ox = -1; ox <= 1; ++ox)
-        for (int oy = -1; oy <= 1; ++oy)
-          for (int oz = -1; oz <= 1; ++oz) {
-            int nx = ((cx + ox) % nc[0] + nc[0]) % nc[0];
-            int ny = ((cy + oy) % nc[1] + nc[1]) % nc[1];
-            int nz = ((cz + oz) % nc[2] + nc[2]) % nc[2];
-            int nbc = (nx * nc[1] + ny) * nc[2] + nz, dup = 0;
-            for (int q = 0; q < ns; ++q) dup |= (seen[q] == nbc);
-            if (dup) continue;
-            seen[ns++] = nbc;
-            for (int b = head[nbc]; b >= 0; b = next[b])
-              if (b > a) pair_ab(s, x, R, w, a, b, f, acc, vat, vcg, sw);
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    if (nt == 1) {
+      for (int a = 0; a < M; ++a) cell_scan(s, x, R, w, a, nc, cell, head, next, f, acc, vat, vcg, sw);
+    } else {
+      /* all-core build: private buffers per thread, added in thread order */
+      const size_t n3 = (size_t)3 * M * s->na;
+      double* fb = (double*)calloc((size_t)nt * n3, sizeof(double));
+      double* eb = (double*)calloc((size_t)nt * 4, sizeof(double));
+      double* vb = vat ? (double*)calloc((size_t)nt * 2 * M, sizeof(double)) : NULL;
+#pragma omp parallel num_threads(nt)
+      {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        double* vt = vb ? vb + (size_t)t * 2 * M : NULL;
+#pragma omp for schedule(static)
+        for (int a = 0; a < M; ++a)
+          cell_scan(s, x, R, w, a, nc, cell, head, next, fb + (size_t)t * n3, eb + 4 * t, vt, vt ? vt + M : NULL, sw);
+      }
+      for (int t = 0; t < nt; ++t) {
+        for (size_t i = 0; i < n3; ++i) f[i] += fb[(size_t)t * n3 + i];
+        for (int k = 0; k < 4; ++k) acc[k] += eb[4 * t + k];
+        if (vb)
+          for (int a = 0; a < M; ++a) {
+            vat[a] += vb[(size_t)t * 2 * M + a];
+            vcg[a] += vb[(size_t)t * 2 * M + M + a];
           }
+      }
+      free(fb); free(eb); free(vb);
     }
     free(head); free(next); free(cell);
   }
@@ -503,6 +553,7 @@ static int forces_sw(const orc_sys* s, const double* x, int method, const double
  * u uniform in [0,1) from orc_uniform3 (Philox4x32-10). */
 static void langevin(const orc_sys* s, const double* v, int64_t step, double* f) {
   const int N = s->M * s->na;
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < N; ++i) {
     double m = s->mass[i % s->na];
     double amp = sqrt(24.0 * s->gamma * s->kT * m / s->dt);
@@ -535,6 +586,7 @@ int orc_forces_step(const orc_sys* s, const double* x, int64_t step, double* f, 
 int orc_run(const orc_sys* s, double* x, double* v, double* f, int64_t step0, int nsteps, int method) {
   const int N = s->M * s->na;
   for (int n = 0; n < nsteps; ++n) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < N; ++i) {
       double m = s->mass[i % s->na];
       for (int d = 0; d < 3; ++d) {
@@ -548,6 +600,7 @@ int orc_run(const orc_sys* s, double* x, double* v, double* f, int64_t step0, in
     int st = forces_sw(s, x, method, NULL, f, NULL, slow_weight(s, step0 + n + 1));
     if (st != ORC_OK) return st;
     if (s->gamma != 0.0) langevin(s, v, step0 + n + 1, f);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < N; ++i) {
       double m = s->mass[i % s->na];
       for (int d = 0; d < 3; ++d) v[3 * i + d] += 0.5 * s->dt * f[3 * i + d] / m;
