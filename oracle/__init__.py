@@ -11,6 +11,7 @@ Arrays are numpy float64 ``(N, 3)`` row-major.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 
@@ -371,3 +372,54 @@ def uniform3(seed: int, replica: int, gid: int, step: int):
     u = np.zeros(3)
     lib.orc_uniform3(int(seed), int(replica), int(gid), int(step), _ptr(u))
     return u
+
+
+def force_matched_table(d, target, fit_dr: float, n_min: int, cg_dr: float, cg_n: int, rc: float):
+    """Force-matched CG table.  The CG force of Eq. 1 acts between centres of mass (Sec.
+    "Force interpolation"); matched to the atomistic model it is, per COM distance, the mean
+    atomistic pair force projected on the COM axis.  From samples (d_i, t_i) with d the COM
+    distance and t that projected force:
+
+      1. bins j = floor(d / fit_dr) for d < rc, j < ceil(rc / fit_dr); mean_j = sum t / count
+         over the bins holding at least n_min samples;
+      2. F_raw(r) linear between the centres (j + 1/2) fit_dr of those bins, equal to the first
+         (last) mean below (above) the first (last) centre;
+      3. F(r_k) = F_raw(r_k) - F_raw(rc) on the nodes r_k = k cg_dr < rc (the force vanishes
+         continuously at the cutoff), 0 from rc on;
+      4. V(r_k) = sum over m >= k of (F_m + F_{m+1}) cg_dr / 2 (trapezoid rule, V = 0 at the
+         last node).
+
+    Returns F, V as float64 arrays [cg_n + 1]; raises ValueError when no bin holds n_min
+    samples."""
+    d = np.asarray(d, dtype=np.float64).reshape(-1)
+    t = np.asarray(target, dtype=np.float64).reshape(-1)
+    nb = int(math.ceil(rc / fit_dr))
+    u = d / fit_dr
+    keep = (d >= 0) & (u < nb)
+    j = np.floor(u[keep]).astype(np.int64)
+    sums = np.bincount(j, weights=t[keep], minlength=nb)
+    counts = np.bincount(j, minlength=nb)
+    pop = np.nonzero(counts >= n_min)[0]
+    if len(pop) == 0:
+        raise ValueError("no bin holds n_min samples")
+    centre = (pop + 0.5) * fit_dr
+    mean = sums[pop] / counts[pop]
+
+    def raw(r):
+        if r <= centre[0]:
+            return mean[0]
+        if r >= centre[-1]:
+            return mean[-1]
+        k = int(np.searchsorted(centre, r, side="right")) - 1  # centre[k] <= r < centre[k + 1]
+        slope = (mean[k + 1] - mean[k]) / (centre[k + 1] - centre[k])
+        return slope * (r - centre[k]) + mean[k]
+
+    f_rc = raw(rc)
+    r_nodes = np.arange(cg_n + 1, dtype=np.float64) * cg_dr
+    F = np.array([raw(r) - f_rc if r < rc else 0.0 for r in r_nodes])
+    V = np.zeros(cg_n + 1)
+    v = 0.0
+    for k in range(cg_n - 1, -1, -1):
+        v += 0.5 * (F[k] + F[k + 1]) * cg_dr
+        V[k] = v
+    return F, V
