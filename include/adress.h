@@ -176,12 +176,17 @@ adress_status adress_init(const adress_config* cfg, void* stream, adress_handle*
 adress_status adress_init_batch(const adress_config* cfgs, int32_t n_replicas, void* stream,
                                 adress_handle* out);
 
-/* Borrow the caller's device state: x, v double [3][N]; f [3][N] of double
+/* The state of the method's molecular dynamics (Sec. "Force interpolation": atoms grouped
+ * into molecules whose centres of mass carry the resolution).
+ * Borrow the caller's device state: x, v double [3][N]; f [3][N] of double
  * (ADRESS_FP64) or float (ADRESS_FP32_MIXED).  Pointers must stay valid until the next
  * bind or adress_destroy.  Rebinding invalidates captured step graphs. */
 adress_status adress_bind_state(adress_handle h, double* x, double* v, void* f);
 
-/* Map the bound positions to centres of mass and resolution values, then rebuild the
+/* Neighbour search of Sec. "Heterogeneous Spatial Domain Decomposition Algorithm" (a
+ * linked-cell list over the molecule centres; here on one GPU, with the AT/CG load balance
+ * of that section handled by separate work lists instead of non-uniform domains).
+ * Map the bound positions to centres of mass and resolution values, then rebuild the
  * Morton-ordered cell list, the class work lists (high-resolution candidates first,
  * then coarse-grained molecules) and the Verlet lists.  Synchronises: grows the list
  * capacity and rebuilds when a molecule has more neighbours than it holds. */
@@ -196,7 +201,9 @@ adress_status adress_build_lists(adress_handle h);
  * slow-force weight of the current time level (see respa_n); the energies do not. */
 adress_status adress_compute_forces(adress_handle h, double* energies);
 
-/* Advance the bound state (x, v, f at time level n) by nsteps Langevin velocity-Verlet
+/* Thermostatted dynamics of force interpolation (Sec. "Potential energy interpolation": force
+ * interpolation conserves momentum but not energy and needs a thermostat; here Langevin).
+ * Advance the bound state (x, v, f at time level n) by nsteps Langevin velocity-Verlet
  * steps:  v += dt/2 f/m;  x += dt v (wrapped);  f = F(x) + F_L(v; n+1);  v += dt/2 f/m.
  * Lists are rebuilt on the device when a molecule centre moved more than skin/2 or a
  * molecule grew wider than the list allows.  Runs as a captured CUDA graph (cached per
@@ -293,6 +300,24 @@ adress_status adress_mlp_loss_grad(adress_handle h, const float* feat, const flo
  * Synchronises. */
 adress_status adress_mlp_train(adress_handle h, int32_t epochs, int32_t batch, float lr, float* loss);
 
+/* Force-matched CG table.  The CG force of Eq. 1 acts between the centres of mass
+ * (Sec. "Force interpolation"); matched to the atomistic force it is, per COM distance, the
+ * mean of the atomistic pair force projected on the COM axis.  From the held samples
+ * (adress_mlp_collect: every pair a < b with d < rc_cg, target = that force; or
+ * adress_mlp_load_samples):
+ *   bins j = floor(d / fit_dr), j < ceil(rc_cg / fit_dr) <= 4096; mean_j = sum of targets /
+ *   count over the bins with count >= n_min; F_raw(r) linear between the bin centres
+ *   (j + 1/2) fit_dr of those bins, constant below the first and above the last;
+ *   F(r_k) = F_raw(r_k) - F_raw(rc_cg) at the table nodes r_k = k cg_dr < rc_cg (so that the
+ *   force vanishes continuously at the cutoff), 0 from rc_cg on; V(r_k) = sum over m >= k of
+ *   (F_m + F_{m+1}) cg_dr / 2 (trapezoid rule, V = 0 at the last node).
+ * F, V: host double [cg_n + 1] (may be NULL).  install != 0 makes it the handle's CG table
+ * (both precisions) for the tabulated CG force from the next step on.  Sums are exact
+ * (integer accumulation of the targets scaled by 2^48), so the table does not depend on the
+ * order of the samples.  Synchronises; ADRESS_ERR_STATE when no samples are held or no bin
+ * holds n_min of them. */
+adress_status adress_cg_fit(adress_handle h, double fit_dr, int32_t n_min, int32_t install, double* F, double* V);
+
 /* Time level of the bound state (keys the thermostat noise). */
 adress_status adress_set_step(adress_handle h, int64_t step);
 adress_status adress_get_step(adress_handle h, int64_t* step); /* synchronises */
@@ -322,6 +347,24 @@ adress_status adress_density_reset(adress_handle h);
 adress_status adress_tf_update(adress_handle h, double alpha);
 adress_status adress_set_tf(adress_handle h, const double* tf_host, int32_t n);
 adress_status adress_get_tf(adress_handle h, double* tf_host, int32_t n); /* synchronises */
+
+/* Run-time limits of a handle (which, value):
+ *  ADRESS_LIMIT_PAIR_CAPACITY: the learned CG force's pair buffers (set up by
+ *    adress_set_cg_mode, sized for every listed pair once: n_mols * capacity / 2) hold at most
+ *    min(value, allocation) pairs; value <= 0 restores the allocation.  A step that needs more
+ *    pairs evaluates the network for the first `limit` of them only and reports
+ *    ADRESS_ERR_LIST_OVERFLOW at the next adress_check; no kernel reads or writes beyond the
+ *    buffers.  For memory budgets, and to exercise that error path.
+ *  ADRESS_LIMIT_MMA_WAIT_POLLS: polls of the tcgen05 network evaluation's bounded waits for
+ *    its tensor-core products (default 2^22, tens of milliseconds); value < 0 restores the
+ *    default.  A wait that runs out records ADRESS_ERR_TIMEOUT (reported by adress_check),
+ *    the evaluation stops, and each block waits once more with the default limit for the
+ *    products it has in flight before it frees its tensor memory; the next evaluation runs
+ *    normally.  0 makes every such wait give up at once (for testing the error path).
+ * Discards captured graphs.  The paper has no counterpart (resource handling of this
+ * implementation). */
+typedef enum { ADRESS_LIMIT_PAIR_CAPACITY = 0, ADRESS_LIMIT_MMA_WAIT_POLLS = 1 } adress_limit;
+adress_status adress_set_limit(adress_handle h, int32_t which, int64_t value);
 
 /* Copy the current Verlet lists to the host: items host int32 [M] (molecule of each work
  * item, high-resolution candidates first), nn host int32 [M] (neighbour count per item),
@@ -372,7 +415,9 @@ adress_status adress_autotune(adress_handle h, int32_t nsteps, double* results, 
  * threads x 64 atoms per thread); larger sizes return ADRESS_ERR_ARG with a message in
  * adress_last_error(NULL).  The first call on a device looks up the array's device
  * address with that device current (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the one array and it keeps the last call's
+ * any stream capture.  The address is kept for the life of the process, which assumes the
+ * device's primary context is never reset (no cudaDeviceReset) while the library is
+ * loaded.  All calls share the one array and it keeps the last call's
  * contents: calls that overlap on the GPU (other streams, other host threads) race.
  * Asynchronous on `stream`; errors are returned as adress_status. */
 adress_status adress_kinetic_noalloc(const double* v, int64_t n_atoms, int32_t atoms_per_mol,

@@ -26,7 +26,7 @@ EXPORTS = ["adress_init", "adress_init_batch", "adress_rdf", "adress_set_centers
            "adress_step", "adress_run", "adress_set_step", "adress_get_step", "adress_com_lambda", "adress_kinetic",
            "adress_density_accumulate", "adress_density_get", "adress_density_reset",
            "adress_tf_update", "adress_set_tf", "adress_get_tf", "adress_list_stats", "adress_list_export",
-           "adress_time_kernels",
+           "adress_time_kernels", "adress_set_limit", "adress_cg_fit",
            "adress_kinetic_noalloc", "adress_check", "adress_mlp_set", "adress_mlp_get", "adress_set_cg_mode",
            "adress_mlp_collect", "adress_mlp_samples", "adress_mlp_load_samples", "adress_mlp_forward",
            "adress_mlp_loss_grad", "adress_mlp_train",
@@ -109,6 +109,8 @@ def load_library(path: str = LIB_PATH):
         "adress_list_stats": ([H, i64p], C.c_int),
         "adress_list_export": ([H, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)], C.c_int),
         "adress_time_kernels": ([H, C.c_int32, C.POINTER(C.c_float)], C.c_int),
+        "adress_set_limit": ([H, C.c_int32, C.c_int64], C.c_int),
+        "adress_cg_fit": ([H, C.c_double, C.c_int32, C.c_int32, d, d], C.c_int),
         "adress_kinetic_noalloc": ([vp, C.c_int64, C.c_int32, d, vp, vp], C.c_int),
         "adress_check": ([H], C.c_int),
         "adress_mlp_set": ([H, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
@@ -386,6 +388,14 @@ class AdResS:
         self._call("adress_autotune", C.c_int32(int(nsteps)), _dptr(rows), 16, C.byref(n))
         return [(int(r[0]), float(r[1]), float(r[2])) for r in rows[:n.value]]
 
+    LIMIT_PAIR_CAPACITY, LIMIT_MMA_WAIT_POLLS = 0, 1
+
+    def set_limit(self, which: int, value: int):
+        """Run-time limit of the handle (adress_set_limit): LIMIT_PAIR_CAPACITY (pairs the
+        learned force's buffers may hold, <= 0: the allocation) or LIMIT_MMA_WAIT_POLLS (polls
+        of the tcgen05 evaluation's bounded waits, < 0: the default)."""
+        self._call("adress_set_limit", C.c_int32(int(which)), C.c_int64(int(value)))
+
     def list_stats(self):
         out = np.zeros(8, dtype=np.int64)
         self._call("adress_list_stats", out.ctypes.data_as(C.POINTER(C.c_int64)))
@@ -488,6 +498,15 @@ class AdResS:
                    C.c_int64(len(td)), g.ctypes.data_as(C.POINTER(C.c_float)))
         grads = self.mlp_unflatten(g[:-1])
         return float(g[-1]) / len(td), grads
+
+    def cg_fit(self, fit_dr: float, n_min: int = 1, install: bool = False):
+        """Force-matched CG table (F, V on the table's nodes) from the held samples; with
+        install=True it becomes the handle's CG table."""
+        n = len(self.system[0].cg_F) if isinstance(self.system, (list, tuple)) else len(self.system.cg_F)
+        F, V = np.zeros(n), np.zeros(n)
+        self._call("adress_cg_fit", C.c_double(float(fit_dr)), C.c_int32(int(n_min)), C.c_int32(1 if install else 0),
+                   _dptr(F), _dptr(V))
+        return F, V
 
     def mlp_train(self, epochs: int, batch: int = 1024, lr: float = 1e-3):
         loss = np.zeros(epochs, dtype=np.float32)

@@ -57,6 +57,9 @@ struct adress_ctx {
   double4_32a* cen64 = nullptr;  // resolution centres (self-adjusting geometry)
   int4* cen32 = nullptr;
   double skin0 = 0.0;  // skin of the configuration (the autotuner scales it)
+  // network pair buffers: pairs allocated, and the smaller limit set by adress_set_limit (0: none)
+  long long pcap_alloc = 0, pcap_limit = 0;
+  double cg_dr = 0.0;  // node spacing of the CG table
   // radial distribution function scratch
   double* rdf_com = nullptr;
   unsigned long long* rdf_counts = nullptr;
@@ -116,7 +119,10 @@ static cudaError_t alloc_pair_buffers(adress_ctx* h) {
   if (e == cudaSuccess) e = realloc_owned(h, &b.pslot, (size_t)pcap);
   if (e == cudaSuccess) e = realloc_owned(h, &b.mirror, (size_t)h->sys.M * h->sys.cap);
   if (e == cudaSuccess && !b.npair) e = dalloc(h, &b.npair, 1);
-  if (e == cudaSuccess) b.pcap = pcap;
+  if (e == cudaSuccess) {
+    h->pcap_alloc = pcap;
+    b.pcap = h->pcap_limit > 0 ? std::min(h->pcap_limit, pcap) : pcap;
+  }
   return e;
 }
 
@@ -478,6 +484,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   s.intra_wca = c->intra_wca;
   s.cg_n = c->cg_n;
   s.cg_inv_dr = 1.0 / c->cg_dr;
+  h->cg_dr = c->cg_dr;
   s.rc_cg = c->rc_cg;
   s.rc_cg2 = c->rc_cg * c->rc_cg;
   s.tf_n = c->tf_n;
@@ -641,6 +648,7 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
 #undef A
   b.boxes = h->d_boxes;
   b.mol_box = h->mol_box;
+  b.wait_polls = kMmaWaitPolls;
   b.cen64 = h->cen64;
   b.cen32 = h->cen32;
   if (e != cudaSuccess) {
@@ -1324,6 +1332,24 @@ adress_status adress_autotune(adress_handle h, int32_t nsteps, double* results, 
   return build_lists_sync(h);
 }
 
+adress_status adress_set_limit(adress_handle h, int32_t which, int64_t value) {
+  if (!h) return ADRESS_ERR_ARG;
+  switch (which) {
+    case ADRESS_LIMIT_PAIR_CAPACITY:
+      h->pcap_limit = value > 0 ? value : 0;
+      if (h->pcap_alloc > 0) h->buf.pcap = h->pcap_limit > 0 ? std::min(h->pcap_limit, h->pcap_alloc) : h->pcap_alloc;
+      break;
+    case ADRESS_LIMIT_MMA_WAIT_POLLS:
+      if (value > 0xFFFFFFFFll) return fail(h, ADRESS_ERR_ARG, "wait poll limit must be below 2^32");
+      h->buf.wait_polls = value < 0 ? kMmaWaitPolls : (unsigned)value;
+      break;
+    default:
+      return fail(h, ADRESS_ERR_ARG, "unknown limit");
+  }
+  free_graphs(h);  // captured launches hold the old values
+  return ADRESS_OK;
+}
+
 adress_status adress_list_export(adress_handle h, int32_t* items, int32_t* nn, int32_t* nbr) {
   if (!h || !items || !nn || !nbr) return ADRESS_ERR_ARG;
   if (!h->lists_built) return fail(h, ADRESS_ERR_STATE, "no lists built");
@@ -1540,6 +1566,53 @@ adress_status adress_mlp_train(adress_handle h, int32_t epochs, int32_t batch, f
   CUDA_OR_FAIL(h, cudaStreamSynchronize(h->stream));
   if (loss)
     for (int e = 0; e < epochs; ++e) loss[e] = acc[e] / (float)(nb * batch);
+  return ADRESS_OK;
+}
+
+adress_status adress_cg_fit(adress_handle h, double fit_dr, int32_t n_min, int32_t install, double* F, double* V) {
+  if (!h || !(fit_dr > 0) || n_min < 1) return ADRESS_ERR_ARG;
+  if (h->smp_n < 1) return fail(h, ADRESS_ERR_STATE, "cg_fit needs samples (adress_mlp_collect or adress_mlp_load_samples)");
+  const Sys& s = h->sys;
+  const double rc = s.rc_cg;
+  const int nb = (int)ceil(rc / fit_dr);
+  if (nb < 1 || nb > 4096) return fail(h, ADRESS_ERR_ARG, "cg_fit: rc_cg / fit_dr must be at most 4096 bins");
+  const int n = s.cg_n + 1;
+  unsigned long long* acc = nullptr;
+  unsigned* cnt = nullptr;
+  double *dF = nullptr, *dV = nullptr;
+  int* npop = nullptr;
+  cudaError_t e = cudaMalloc(&acc, sizeof(unsigned long long) * 2 * nb);
+  if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(unsigned) * nb);
+  if (e == cudaSuccess) e = cudaMalloc(&dF, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&dV, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&npop, sizeof(int));
+  std::vector<double> hF(n), hV(n);
+  int np = 0;
+  if (e == cudaSuccess)
+    e = cg_fit(h->smp_feat, h->smp_target, h->smp_n, fit_dr, nb, n_min, s.cg_n, h->cg_dr, rc, acc, cnt, dF, dV,
+               npop, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hF.data(), dF, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hV.data(), dV, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&np, npop, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess && np > 0 && install) {
+    std::vector<float2> fv(n);
+    for (int k = 0; k < n; ++k) fv[k] = make_float2((float)hF[k], (float)hV[k]);
+    e = cudaMemcpyAsync((void*)h->buf.cgF64, dF, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync((void*)h->buf.cgV64, dV, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((void*)h->buf.cgFV32, fv.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  }
+  cudaFree(acc);
+  cudaFree(cnt);
+  cudaFree(dF);
+  cudaFree(dV);
+  cudaFree(npop);
+  if (e != cudaSuccess) return fail(h, ADRESS_ERR_CUDA, std::string("cg_fit: ") + cudaGetErrorString(e));
+  if (np == 0) return fail(h, ADRESS_ERR_STATE, "cg_fit: no bin holds n_min samples");
+  if (F) memcpy(F, hF.data(), sizeof(double) * n);
+  if (V) memcpy(V, hV.data(), sizeof(double) * n);
   return ADRESS_OK;
 }
 

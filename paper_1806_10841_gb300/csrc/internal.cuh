@@ -15,6 +15,9 @@ constexpr int kMaxBonds = 6;
 constexpr int kMaxAngles = 4;
 constexpr int kMaxCenters = 1024;  // resolution centres of the self-adjusting geometry
 constexpr int kGroup = 4;  // threads per molecule in the force kernel
+// Default poll limit of a bounded mbarrier wait on tensor-core products: ~tens of ms, far
+// beyond a 128x64x64 product.
+constexpr unsigned kMmaWaitPolls = 1u << 22;
 
 // Device control block: list-validity trackers, error word, counters.
 struct Ctrl {
@@ -185,7 +188,8 @@ struct Bufs {
   int2* pslot;   // [pcap] the pair's two list slots
   int* mirror;   // [M*cap] (CG mode 1) slot of the same pair in the partner's list, from the last build
   unsigned* npair;  // pairs written this step
-  long long pcap;
+  long long pcap;   // pairs the buffers may hold (the allocation, or a smaller limit the host set)
+  unsigned wait_polls;  // poll limit of the tcgen05 evaluation's product waits (kMmaWaitPolls)
   // batched replicas (nbox > 1)
   const Box* boxes;    // [nbox]
   const int* mol_box;  // [M] box of each molecule
@@ -289,6 +293,12 @@ cudaError_t mlp_pack(const MlpDevArgs& a, cudaStream_t st);
 cudaError_t mlp_collect(const Sys& s, const Bufs& b, int pass, const int* offs, long long cap, long long base,
                         float* feat, float* target, int* ids, int* counts, cudaStream_t st);
 cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* fpair, cudaStream_t st);
+// Force-matched CG table from n samples (features [n][9], d = feature 0; targets [n]): bin
+// width h, nb = ceil(rc / h) <= 4096 bins, bins with >= n_min samples; F, V device [cg_n + 1]
+// on nodes k dr; *npop (device) = bins used.  acc [2 nb], cnt [nb] device scratch.
+cudaError_t cg_fit(const float* feat, const float* target, long long n, double h, int nb, int n_min, int cg_n,
+                   double dr, double rc, unsigned long long* acc, unsigned* cnt, double* F, double* V, int* npop,
+                   cudaStream_t st);
 cudaError_t mlp_gather(const float* feat, const float* target, long long n, long long start, long long cnt,
                        long long stride, float* feat_out, float* target_out, cudaStream_t st);
 

@@ -18,6 +18,8 @@
 // a block, with FP32 accumulation, per-block partials and a fixed-order reduction.
 #include <cuda_bf16.h>
 #include <math.h>
+
+#include <algorithm>
 #include <stdlib.h>
 #include <string.h>
 
@@ -25,7 +27,7 @@
 
 namespace adress {
 
-cudaError_t launch_mlp_eval_tc(const MlpDevArgs& a, const Bufs& b, float* fpair, cudaStream_t st);
+cudaError_t launch_mlp_eval_tc(const Sys& s, const MlpDevArgs& a, const Bufs& b, float* fpair, cudaStream_t st);
 
 // ---------------- parameters ----------------------------------------------------------
 // Flat FP32 master vector: [W1 (64 x 9) | b1 (64) | W2 (64 x 64) | b2 (64) | w3 (64) | b3]
@@ -800,7 +802,7 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
 
 __global__ void __launch_bounds__(128, 8) k_mlp_eval(MlpDev m, const unsigned* __restrict__ pfrag,
                                                      const int2* __restrict__ pslot, const unsigned* npair,
-                                                     float* __restrict__ fpair) {
+                                                     long long pcap, long long nslot, float* __restrict__ fpair) {
   __shared__ float yo[4][2][16];
   __shared__ uint2 sW1[kH * 4], sW2[kH * 16];
   __shared__ float sB[3 * kH];
@@ -821,7 +823,7 @@ __global__ void __launch_bounds__(128, 8) k_mlp_eval(MlpDev m, const unsigned* _
   const MlpViewQ mq{sW1, sW2, sB, sB + kH, sB + 2 * kH, m.P[ob3]};
   const float scale = m.norm[2 * kIn];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
-  const long long np = *npair;
+  const long long np = min((long long)*npair, pcap);  // clamped to the buffer (see k_mlp_eval_tc)
   const long long ntiles = (np + 15) / 16;
   for (long long tile = (long long)blockIdx.x * 4 + w; tile < ntiles; tile += (long long)gridDim.x * 4) {
     const long long p0 = tile * 16;
@@ -858,8 +860,8 @@ __global__ void __launch_bounds__(128, 8) k_mlp_eval(MlpDev m, const unsigned* _
     if (lane < 16 && p0 + lane < np) {
       const float fv = 0.5f * scale * (yo[w][0][lane] + yo[w][1][lane]);
       const int2 sl = pslot[p0 + lane];
-      fpair[sl.x] = fv;
-      if (sl.y >= 0) fpair[sl.y] = fv;
+      if (sl.x >= 0 && sl.x < nslot) fpair[sl.x] = fv;
+      if (sl.y >= 0 && sl.y < nslot) fpair[sl.y] = fv;
     }
     __syncwarp();
   }
@@ -875,6 +877,132 @@ __global__ void k_mlp_gather(const float* feat, const float* target, long long n
 #pragma unroll
   for (int k = 0; k < kIn; ++k) fo[i * kIn + k] = feat[src * kIn + k];
   to[i] = target[src];
+}
+
+// ---------------- force-matched CG table ---------------------------------------------------
+// The CG force of Eq. 1 acts between centres of mass (Sec. "Force interpolation").  Its
+// force-matched table is the mean, per distance bin, of the atomistic pair force projected on
+// the COM axis over the collected samples (features[0] = COM distance d, target = that force):
+//   bin j = floor(d / h) (d < rc), mean_j = sum / count for bins with count >= n_min;
+//   F_raw(r) linear between the centres (j + 1/2) h of those bins, constant beyond the first
+//   and the last;  F(r_k) = F_raw(r_k) - F_raw(rc) for r_k = k dr < rc, 0 from rc on;
+//   V(r_k) = sum_{m >= k} (F_m + F_{m+1}) dr / 2  (trapezoid rule from rc down to r_k).
+// Sums are exact integers: each target is scaled by 2^48 and split into a high part
+// (>> 24) and a low part (24 bits), summed with 64-bit integer atomics (order-independent,
+// so the table is deterministic); the mean is formed from them in double.
+
+constexpr double kFitScale = 281474976710656.0;  // 2^48
+
+__global__ void k_fit_bins(const float* __restrict__ feat, const float* __restrict__ target, long long n, double h,
+                           int nb, unsigned long long* __restrict__ acc, unsigned* __restrict__ cnt) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double d = (double)feat[i * kIn];
+    if (!(d >= 0.0)) continue;
+    const double u = d / h;
+    if (u >= (double)nb) continue;
+    const int j = (int)u;
+    const long long q = llrint((double)target[i] * kFitScale);
+    atomicAdd(&acc[2 * j], (unsigned long long)(q >> 24));
+    atomicAdd(&acc[2 * j + 1], (unsigned long long)(q & 0xFFFFFFll));
+    atomicAdd(&cnt[j], 1u);
+  }
+}
+
+constexpr int kFitMaxBins = 4096;
+
+// One block: means of the populated bins (compacted in bin order by a block scan), node
+// values by linear interpolation between their centres, the shift to F(rc) = 0, and V by the
+// trapezoid sum (one thread, from rc down, the definition's order).
+__global__ void __launch_bounds__(1024) k_fit_table(const unsigned long long* __restrict__ acc,
+                                                    const unsigned* __restrict__ cnt, int nb, double h, int n_min,
+                                                    int cg_n, double dr, double rc, double* __restrict__ F,
+                                                    double* __restrict__ V, int* __restrict__ npop_out) {
+  __shared__ double pc[kFitMaxBins], pm[kFitMaxBins];
+  __shared__ int wsum[32], npop;
+  constexpr int per = kFitMaxBins / 1024;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int flag[per], cntp = 0;
+#pragma unroll
+  for (int e = 0; e < per; ++e) {
+    const int j = t * per + e;
+    flag[e] = j < nb && cnt[j] >= (unsigned)n_min;
+    cntp += flag[e];
+  }
+  int incl = cntp;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int x = wsum[lane];
+    int xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += v;
+    }
+    wsum[lane] = xi - x;
+    if (lane == 31) npop = xi;
+  }
+  __syncthreads();
+  int pos = incl - cntp + wsum[w];
+#pragma unroll
+  for (int e = 0; e < per; ++e) {
+    const int j = t * per + e;
+    if (flag[e]) {
+      const double sum = (double)(long long)acc[2 * j] * (1.0 / 16777216.0) + (double)(long long)acc[2 * j + 1] / kFitScale;
+      pc[pos] = __dmul_rn(__dadd_rn((double)j, 0.5), h);
+      pm[pos] = sum / (double)cnt[j];
+      ++pos;
+    }
+  }
+  __syncthreads();
+  const int np = npop;
+  if (t == 0) *npop_out = np;
+  if (np == 0) return;
+  // F_raw(r): clamped linear interpolation between the populated centres
+  auto raw = [&](double r) -> double {
+    if (r <= pc[0]) return pm[0];
+    if (r >= pc[np - 1]) return pm[np - 1];
+    int lo = 0, hi = np - 1;  // pc[lo] < r < pc[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pc[mid] <= r) lo = mid;
+      else hi = mid;
+    }
+    const double slope = __ddiv_rn(__dsub_rn(pm[hi], pm[lo]), __dsub_rn(pc[hi], pc[lo]));
+    return __dadd_rn(__dmul_rn(slope, __dsub_rn(r, pc[lo])), pm[lo]);
+  };
+  const double f_rc = raw(rc);
+  for (int k = t; k <= cg_n; k += blockDim.x) {
+    const double r = __dmul_rn((double)k, dr);
+    F[k] = r < rc ? __dsub_rn(raw(r), f_rc) : 0.0;
+  }
+  __syncthreads();
+  if (t == 0) {
+    double v = 0.0;
+    V[cg_n] = 0.0;
+    for (int k = cg_n - 1; k >= 0; --k) {
+      v = __dadd_rn(v, __dmul_rn(__dmul_rn(0.5, __dadd_rn(F[k], F[k + 1])), dr));
+      V[k] = v;
+    }
+  }
+}
+
+cudaError_t cg_fit(const float* feat, const float* target, long long n, double h, int nb, int n_min, int cg_n,
+                   double dr, double rc, unsigned long long* acc, unsigned* cnt, double* F, double* V, int* npop,
+                   cudaStream_t st) {
+  if (nb > kFitMaxBins) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 2 * nb, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(unsigned) * nb, st);
+  if (e != cudaSuccess) return e;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152 * 8);
+  if (n > 0) k_fit_bins<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, st>>>(feat, target, n, h, nb, acc, cnt);
+  k_fit_table<<<1, 1024, 0, st>>>(acc, cnt, nb, h, n_min, cg_n, dr, rc, F, V, npop);
+  return cudaGetLastError();
 }
 
 // ---------------- launchers ------------------------------------------------------------
@@ -953,7 +1081,7 @@ cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* f
     const char* v = getenv("ADRESS_MLP_KERNEL");
     tc = v && strcmp(v, "mma") == 0 ? 0 : 1;
   }
-  if (tc) return launch_mlp_eval_tc(a, b, fpair, st);
+  if (tc) return launch_mlp_eval_tc(s, a, b, fpair, st);
   // persistent grid: as many blocks as fit on the device at once
   static int grid = 0;
   if (!grid) {
@@ -964,7 +1092,7 @@ cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* f
       per_sm = 4;
     grid = per_sm * sms;
   }
-  k_mlp_eval<<<grid, 128, 0, st>>>(m, b.pfrag, b.pslot, b.npair, fpair);
+  k_mlp_eval<<<grid, 128, 0, st>>>(m, b.pfrag, b.pslot, b.npair, b.pcap, (long long)s.M * s.cap, fpair);
   return cudaGetLastError();
 }
 

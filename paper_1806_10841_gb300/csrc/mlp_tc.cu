@@ -25,7 +25,7 @@ namespace {
 constexpr int kTcH = 64, kTcIn = 9;
 constexpr int kTcOb1 = kTcH * kTcIn, kTcOb2 = kTcOb1 + kTcH + kTcH * kTcH, kTcOw3 = kTcOb2 + kTcH,
               kTcOb3 = kTcOw3 + kTcH;
-constexpr uint32_t kWaitPolls = 1u << 22;  // ~tens of ms: far beyond a 128x64x64 product
+constexpr uint32_t kWaitPolls = kMmaWaitPolls;
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
                                                         const unsigned* __restrict__ W2p, const float* __restrict__ norm,
                                                         const unsigned* __restrict__ pfrag,
                                                         const int2* __restrict__ pslot, const unsigned* npair,
+                                                        long long pcap, long long nslot, uint32_t polls,
                                                         float* __restrict__ fpair, Ctrl* ctrl) {
   __shared__ TcSmem S;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -102,7 +103,9 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
   constexpr uint32_t idesc = umma::idesc_bf16_f32(128, 64);
   const uint32_t a1 = umma::smem_u32(S.A1), a2 = umma::smem_u32(S.A2), bw1 = umma::smem_u32(S.B1),
                  bw2 = umma::smem_u32(S.B2);
-  const long long np = *npair;
+  // the pair buffer holds at most pcap pairs: a count beyond it (an overflow the feature
+  // kernel has reported) is clamped so that no tile reads past the buffer
+  const long long np = min((long long)*npair, pcap);
   const long long ntiles = (np + 63) / 64;
   uint32_t phase = 0;
 
@@ -126,8 +129,9 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
     __syncthreads();
   };
   // wait for every product issued so far; false once any thread of the block gave up
+  // (`polls` bounds these waits; the drain wait before the TMEM is freed keeps kWaitPolls)
   auto wait_products = [&]() -> bool {
-    if (!umma::mbar_wait(&S.mbar, phase, kWaitPolls)) atomicExch(&S.abort, 1);
+    if (!umma::mbar_wait(&S.mbar, phase, polls)) atomicExch(&S.abort, 1);
     phase ^= 1u;
     umma::fence_after_sync();
     __syncthreads();
@@ -192,8 +196,8 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
     if (tid < 64 && p0 + tid < np) {
       const float fv = 0.5f * scale * (S.y[tid] + S.y[tid + 64]);
       const int2 sl = pslot[p0 + tid];
-      fpair[sl.x] = fv;
-      if (sl.y >= 0) fpair[sl.y] = fv;
+      if (sl.x >= 0 && sl.x < nslot) fpair[sl.x] = fv;
+      if (sl.y >= 0 && sl.y < nslot) fpair[sl.y] = fv;
     }
     tile = next;
   }
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
 
 }  // namespace
 
-cudaError_t launch_mlp_eval_tc(const MlpDevArgs& a, const Bufs& b, float* fpair, cudaStream_t st) {
+cudaError_t launch_mlp_eval_tc(const Sys& s, const MlpDevArgs& a, const Bufs& b, float* fpair, cudaStream_t st) {
   static int grid = 0;
   if (!grid) {
     int dev = 0, sms = 0;
@@ -220,7 +224,9 @@ cudaError_t launch_mlp_eval_tc(const MlpDevArgs& a, const Bufs& b, float* fpair,
     // columns = all 512; two or three per SM were 20 and 7 us slower per evaluation
     grid = 4 * sms;
   }
-  k_mlp_eval_tc<<<grid, 128, 0, st>>>(a.P, a.W1p, a.W2p, a.norm, b.pfrag, b.pslot, b.npair, fpair, b.ctrl);
+  k_mlp_eval_tc<<<grid, 128, 0, st>>>(a.P, a.W1p, a.W2p, a.norm, b.pfrag, b.pslot, b.npair, b.pcap,
+                                       (long long)s.M * s.cap, b.wait_polls, fpair,
+                                       b.ctrl);
   return cudaGetLastError();
 }
 

@@ -83,7 +83,9 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_kinetic_final(const double*
     }
 }
 
-// Device address of the scratch array, looked up once per device with that device current.
+// Device address of the scratch array, looked up once per device with that device current
+// and kept for the life of the process (the device's primary context is assumed never to be
+// reset while the library is loaded).
 static std::mutex g_scratch_mutex;
 static double* g_scratch_ptr[kNoAllocMaxDevices] = {};
 

@@ -15,6 +15,22 @@ from paper_1806_10841_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
+# MD forces in network mode against the oracle's network mode (bfloat16 inputs, weights and
+# first-layer activations on both sides): relative RMS over all atoms, and the per-atom
+# bound max_i |F_i - F_ref_i| / (|F_ref_i| + rms|F_ref|).  The GPU forms the first-layer
+# activations in FP32 (hardware tanh in the MD evaluation) before rounding them to bfloat16,
+# the oracle in FP64, so an activation within ~1e-6 of a rounding boundary can round to the
+# neighbouring bfloat16 value (a 2^-8 relative step) on one side only.  Measured on GB300:
+# relative RMS ~3e-6 and per-atom max ~7e-5 at 800k atoms (both kernels), the RMS within the
+# FP32 path's own 2e-5, which is the bound here; the per-atom bound leaves ~8x headroom.
+LEARNED_RMS, LEARNED_MAX = 2e-5, 5e-4
+
+
+def per_atom_max(a, b):
+    d = np.linalg.norm(a - b, axis=1)
+    n = np.linalg.norm(b, axis=1)
+    return float((d / (n + math.sqrt((n ** 2).mean()))).max())
+
 
 def rand_params(seed, scale=0.25):
     rng = np.random.default_rng(seed)
@@ -54,8 +70,10 @@ def test_mlp_forward_matches_oracle_bf16():
     y = sim.mlp_forward(feat)
     ref = oracle_net(params, mean, std, 5.0).forward(feat.astype(np.float32).astype(np.float64))
     err = np.abs(y - ref) / (np.abs(ref) + 0.1 * ref.std())
-    assert np.median(err) < 1e-4
-    assert np.percentile(err, 99) < 1e-2
+    print(f"FORWARD n={len(y)} median={np.median(err):.2e} max={err.max():.2e}")
+    # every output, not a quantile (measured: max ~4e-6, median ~1e-7)
+    assert err.max() < 5e-5
+    assert np.median(err) < 1e-6
     sim.close()
 
 
@@ -71,9 +89,13 @@ def test_mlp_gradient_matches_oracle():
     loss, g = sim.mlp_loss_grad(feat, target)
     loss_ref, g_ref = oracle_net(params, mean, std, 4.0).loss_grad(feat, target.astype(np.float64))
     assert loss == pytest.approx(loss_ref, rel=2e-3)
+    # element by element: |g_k - g_ref_k| <= tol (|g_ref_k| + rms of the tensor), the RMS
+    # floor covering components that are sums of cancelling per-sample terms
     for k in ("W1", "b1", "W2", "b2", "w3"):
         a, r = np.asarray(g[k]).ravel(), np.asarray(g_ref[k]).ravel()
-        assert np.linalg.norm(a - r) <= 3e-2 * np.linalg.norm(r), k
+        e = np.abs(a - r) / (np.abs(r) + math.sqrt((r ** 2).mean()))
+        print(f"GRAD {k} max={e.max():.2e} norm={np.linalg.norm(a - r) / np.linalg.norm(r):.2e}")
+        assert e.max() <= 5e-3, k  # measured max ~1e-3 (W2), bfloat16 operands of the backward products
     assert g["b3"] == pytest.approx(g_ref["b3"], rel=1e-2, abs=1e-4)
     sim.close()
 
@@ -146,7 +168,10 @@ def test_md_forces_with_learned_cg_force_match_oracle(precision):
     f, e = sim.forces()
     sim.check()
     rel = math.sqrt(((f - f_ref) ** 2).sum() / (f_ref ** 2).sum())
-    assert rel < 2e-3, rel
+    mx = per_atom_max(f, f_ref)
+    print(f"LEARNED216 {precision} rms={rel:.2e} max={mx:.2e}")
+    assert rel < LEARNED_RMS, rel
+    assert mx < LEARNED_MAX, mx
     assert np.abs(f.sum(0)).max() <= 1e-5 * np.abs(f).sum()
     # the table is back with mode 0
     sim.set_cg_mode(0)
@@ -173,7 +198,7 @@ def test_learned_cg_force_with_multiple_time_stepping(precision):
     sim = sim_with_net(s, params, mean, std, 3.0, precision=precision)
     sim.set_cg_mode(1)
     sim.set_state(x, v)
-    for level, tol in ((1, 2e-5 if precision == "fp32" else 1e-10), (3, 2e-3)):
+    for level, tol in ((1, 2e-5 if precision == "fp32" else 1e-10), (3, LEARNED_RMS)):
         sim.set_step(level)
         f, _ = sim.forces()
         f_ref, _ = o.forces(x, step=level)
@@ -326,3 +351,153 @@ print(json.dumps(f.reshape(-1).tolist()))
         out[kind] = np.array(json.loads(r.stdout.strip().splitlines()[-1]))
     a, b = out["default"], out["mma"]
     assert math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()) < 1e-5
+
+
+# ---- the learned force at the benchmark's size: every block runs several tiles ----------------
+
+_big = {}
+
+
+def learned_800k_case():
+    """The 800k-atom benchmark state with a random network (normalisation from the 216-molecule
+    box's pairs) and the oracle's network-mode forces (bfloat16 rounding points)."""
+    if not _big:
+        s = inputs.c2_800k()
+        x, _ = inputs.tetra_state(s)
+        s216 = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, seed=5)
+        x216, _ = inputs.tetra_state(s216)
+        feat, _, _ = oracle.Oracle(s216).collect_pairs(x216, s216.rc_cg)
+        mean, std = feat.mean(0), feat.std(0) + 1e-3
+        params = rand_params(7, scale=0.2)
+        o = oracle.Oracle(s)
+        o.set_mlp(oracle_net(params, mean, std, 3.0))
+        f_ref, _ = o.forces(x)
+        # pairs that need the network: COM distance < rc_cg and l_a l_b < 1
+        from scipy.spatial import cKDTree
+
+        R, _, w = o.com_lambda(x)
+        pairs = cKDTree(R, boxsize=np.array(s.box)).query_pairs(s.rc_cg, output_type="ndarray")
+        n_net = int((w[pairs[:, 0]] * w[pairs[:, 1]] < 1.0).sum())
+        _big.update(s=s, x=x, mean=mean, std=std, params=params, f_ref=f_ref, n_net=n_net)
+    return _big
+
+
+_CHILD = r"""
+import sys
+sys.path.insert(0, %r)
+sys.path.insert(0, %r)
+import numpy as np
+from paper_1806_10841_gb300 import inputs
+from test_gpu_mlp import rand_params, sim_with_net
+d = np.load(sys.argv[1])
+s = inputs.c2_800k()
+x, _ = inputs.tetra_state(s)
+sim = sim_with_net(s, rand_params(7, scale=0.2), d["mean"], d["std"], 3.0)
+sim.set_cg_mode(1)
+sim.set_state(x)
+f, _ = sim.forces()
+sim.check()
+np.save(sys.argv[2], f)
+"""
+
+
+@pytest.mark.parametrize("kernel", ["tcgen05", "mma"])
+def test_learned_forces_full_size_800k_atoms(kernel, tmp_path):
+    """Network-mode MD forces on the 800k-atom workload against the oracle, every atom: with
+    ~0.35M network pairs each of the 608 blocks of the tcgen05 evaluation takes several
+    64-pair tiles, so its cross-tile pipeline (the next tile's inputs staged and its first
+    layer issued while the current tile's second layer runs, barrier phases alternating) is
+    what is checked.  The warp-level kernel (ADRESS_MLP_KERNEL=mma, read once per process)
+    runs in a child process."""
+    import os
+    import subprocess
+    import sys
+
+    c = learned_800k_case()
+    assert c["n_net"] > 64 * 608 * 4, c["n_net"]
+    if kernel == "tcgen05" and os.environ.get("ADRESS_MLP_KERNEL", "") != "mma":
+        sim = sim_with_net(c["s"], c["params"], c["mean"], c["std"], 3.0)
+        sim.set_cg_mode(1)
+        sim.set_state(c["x"])
+        f, _ = sim.forces()
+        sim.check()
+        sim.close()
+    else:
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        np.savez(tmp_path / "norm.npz", mean=c["mean"], std=c["std"])
+        env = dict(os.environ)
+        env["ADRESS_MLP_KERNEL"] = "mma" if kernel == "mma" else ""
+        r = subprocess.run([sys.executable, "-c", _CHILD % (root, os.path.join(root, "tests")),
+                            str(tmp_path / "norm.npz"), str(tmp_path / "f.npy")],
+                           capture_output=True, text=True, env=env, timeout=900)
+        assert r.returncode == 0, r.stderr[-3000:]
+        f = np.load(tmp_path / "f.npy")
+    f_ref = c["f_ref"]
+    rel = math.sqrt(((f - f_ref) ** 2).sum() / (f_ref ** 2).sum())
+    mx = per_atom_max(f, f_ref)
+    print(f"LEARNED800K {kernel} pairs={c['n_net']} rms={rel:.2e} max={mx:.2e}")
+    assert rel < LEARNED_RMS, rel
+    assert mx < LEARNED_MAX, mx
+
+
+# ---- host-visible error paths of the network evaluation (no GPU fault) -----------------------
+
+def _net_216():
+    s = inputs.tetra_system(216, (25.8, 12.9, 6.45), 5.0, 2.5, seed=5)
+    x, _ = inputs.tetra_state(s)
+    o = oracle.Oracle(s)
+    feat, _, _ = o.collect_pairs(x, s.rc_cg)
+    mean, std = feat.mean(0), feat.std(0) + 1e-3
+    params = rand_params(7, scale=0.2)
+    o.set_mlp(oracle_net(params, mean, std, 3.0))
+    f_ref, _ = o.forces(x)
+    return s, x, mean, std, params, f_ref
+
+
+def test_pair_buffer_limit_reports_overflow_and_recovers():
+    """A pair buffer smaller than the pairs of a step: the feature kernel reports a list
+    overflow, the evaluation kernels stay inside the buffer, and once the limit is lifted the
+    next evaluation is clean and matches the oracle."""
+    from paper_1806_10841_gb300 import adress
+
+    s, x, mean, std, params, f_ref = _net_216()
+    sim = sim_with_net(s, params, mean, std, 3.0)
+    sim.set_cg_mode(1)
+    sim.set_state(x)
+    sim.set_limit(sim.LIMIT_PAIR_CAPACITY, 5)
+    sim.compute_forces(energies=False)
+    with pytest.raises(adress.AdressError) as ei:
+        sim.check()
+    assert ei.value.status == 3
+    sim.set_limit(sim.LIMIT_PAIR_CAPACITY, 0)
+    f, _ = sim.forces()
+    sim.check()
+    assert math.sqrt(((f - f_ref) ** 2).sum() / (f_ref ** 2).sum()) < LEARNED_RMS
+    sim.close()
+
+
+def test_tensor_core_wait_timeout_is_reported_and_the_next_call_is_clean():
+    """The tcgen05 evaluation's bounded waits for its products, limited to zero polls, give up
+    at once: the evaluation records ADRESS_ERR_TIMEOUT (each block still waits, with the full
+    limit, for the products it has in flight before freeing its tensor memory).  With the
+    default limit again the next call is clean and matches the oracle."""
+    import os
+
+    from paper_1806_10841_gb300 import adress
+
+    if os.environ.get("ADRESS_MLP_KERNEL", "") == "mma":
+        pytest.skip("the warp-level evaluation has no tensor-core waits")
+    s, x, mean, std, params, f_ref = _net_216()
+    sim = sim_with_net(s, params, mean, std, 3.0)
+    sim.set_cg_mode(1)
+    sim.set_state(x)
+    sim.set_limit(sim.LIMIT_MMA_WAIT_POLLS, 0)
+    sim.compute_forces(energies=False)
+    with pytest.raises(adress.AdressError) as ei:
+        sim.check()
+    assert ei.value.status == 6
+    sim.set_limit(sim.LIMIT_MMA_WAIT_POLLS, -1)
+    f, _ = sim.forces()
+    sim.check()
+    assert math.sqrt(((f - f_ref) ** 2).sum() / (f_ref ** 2).sum()) < LEARNED_RMS
+    sim.close()

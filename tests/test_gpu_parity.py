@@ -1,8 +1,10 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances: per-atom force relative RMS  sqrt(sum|F - F_ref|^2 / sum|F_ref|^2)
-<= 1e-10 for the FP64 path and <= 2e-5 for the FP32 mixed path; integer outputs
-(density histogram) bit-exact.
+<= 1e-10 for the FP64 path and <= 2e-5 for the FP32 mixed path; next to it a per-atom
+bound max_i |F_i - F_ref_i| / (|F_ref_i| + rms|F_ref|) (each atom's error relative to its
+own force, with the RMS force as the floor for atoms whose contributions cancel) of
+MAXTOL; integer outputs (density histogram) bit-exact.
 """
 import math
 
@@ -16,10 +18,18 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "fp32": 2e-5}
 ETOL = {"fp64": 1e-10, "fp32": 2e-5}
+MAXTOL = {"fp64": 1e-12, "fp32": 5e-5}  # measured on GB300: <= 7.3e-14 and <= 6.4e-6 (800k atoms)
 
 
 def rel_rms(a, b):
     return math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
+
+
+def per_atom_max(a, b):
+    """max_i |a_i - b_i| / (|b_i| + rms|b|) over atoms (rows of (N, 3) arrays)."""
+    d = np.linalg.norm(a - b, axis=1)
+    n = np.linalg.norm(b, axis=1)
+    return float((d / (n + math.sqrt((n ** 2).mean()))).max())
 
 
 def make(name):
@@ -66,7 +76,10 @@ def check_forces(s, x, f_ref, e_ref, precision):
     f, e = sim.forces()
     sim.check()
     r = rel_rms(f, f_ref)
+    m = per_atom_max(f, f_ref)
+    print(f"PARITY {precision} N={len(f)} rms={r:.3e} max={m:.3e}")
     assert r <= TOL[precision], f"{precision}: force rel RMS {r:.3e}"
+    assert m <= MAXTOL[precision], f"{precision}: per-atom max {m:.3e}"
     scale = abs(e_ref["E_at"]) + abs(e_ref["E_cg"]) + abs(e_ref["E_bond"])
     for k in ("E_at", "E_cg", "E_bond"):
         assert abs(e[k] - e_ref[k]) <= ETOL[precision] * scale, (k, e[k], e_ref[k])
@@ -210,9 +223,10 @@ def test_trajectory_divergence_100_steps(precision):
     sim.check()
     assert sim.get_step() == 100
     env = {"fp64": (1e-11, 1e-9), "fp32": (1e-5, 1e-3)}[precision]
-    print(precision, "divergence curve", [f"{a:.1e}" for a, _ in curve])
+    print(precision, "divergence curve", [f"{a:.1e}" for a, _ in curve], [f"{b:.1e}" for _, b in curve])
     assert curve[0][0] < env[0] / 10
-    assert curve[-1][0] < env[0] * 100 and curve[-1][1] < env[1] * 100
+    # every point of the curve (positions and velocities) stays inside the envelope
+    assert max(a for a, _ in curve) < env[0] and max(b for _, b in curve) < env[1]
     stats = sim.list_stats()
     assert stats["rebuilds"] >= 2 and stats["n_hr"] + stats["n_cg"] == s.M
 

@@ -55,8 +55,42 @@ def test_kinetic_noalloc_matches_adress_kinetic_on_two_calls_in_a_row():
     sim.stream.synchronize()
     m = np.tile(mass, s.M)[:n_small]
     ke_small = 0.5 * float((m[:, None] * v[:n_small] ** 2).sum())
-    assert out.cpu().numpy()[0] == pytest.approx(ke_small, rel=1e-12)
+    p_small = (m[:, None] * v[:n_small]).sum(0)
+    got = out.cpu().numpy()
+    assert got[0] == pytest.approx(ke_small, rel=1e-12)
+    assert np.allclose(got[1:], p_small, rtol=1e-12, atol=1e-13 * float((m[:, None] * np.abs(v[:n_small])).sum()))
     sim.close()
+
+
+def test_kinetic_noalloc_grid_stride_and_block_cap():
+    """Above 1024 blocks x 256 threads (262,144 atoms) every thread sums several atoms in its
+    grid-stride loop and the partial sums fill all 1024 scratch slots: 1,000,003 atoms with
+    three unequal site masses against a numpy sum, twice in a row."""
+    import torch
+
+    from paper_1806_10841_gb300 import adress
+
+    lib = adress.load_library()
+    n = 1_000_003
+    rng = np.random.default_rng(41)
+    v = rng.normal(0.0, 1.0, (3, n))
+    mass = np.array([1.0, 2.5, 0.75])
+    m = np.tile(mass, n // 3 + 1)[:n]
+    ke_ref = 0.5 * float((m * v ** 2).sum())
+    p_ref = (m * v).sum(1)
+    scale = float((m * np.abs(v)).sum())
+    dev = torch.device("cuda:0")
+    vd = torch.from_numpy(np.ascontiguousarray(v)).to(dev)
+    out = torch.zeros(4, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        out.fill_(np.nan)
+        st = _noalloc(lib, vd.data_ptr(), n, 3, mass, stream.cuda_stream, out.data_ptr())
+        assert st == 0, lib.adress_last_error(None)
+        stream.synchronize()
+        got = out.cpu().numpy()
+        assert got[0] == pytest.approx(ke_ref, rel=1e-12)
+        assert np.allclose(got[1:], p_ref, rtol=1e-12, atol=1e-13 * scale)
 
 
 def test_kinetic_noalloc_rejects_sizes_beyond_its_scratch():
