@@ -182,6 +182,8 @@ static std::string config_error(const adress_config* c) {
     return "n_bonds must be 0..6 with a bond array";
   for (int q = 0; q < 2 * c->n_bonds; ++q)
     if (c->bonds[q] < 0 || c->bonds[q] >= c->atoms_per_mol) return "bond index out of range";
+  for (int q = 0; q < c->n_bonds; ++q)
+    if (c->bonds[2 * q] == c->bonds[2 * q + 1]) return "a bond joins an atom to itself";
   if (c->n_bonds > 0 && !(c->fene_r0 > 0)) return "fene_r0 must be > 0";
   if (!c->cg_F || !c->cg_V || c->cg_n < 1 || !(c->cg_dr > 0)) return "CG table missing";
   if (c->rc_cg > c->cg_n * c->cg_dr * (1 + 1e-12)) return "rc_cg beyond the CG table";
@@ -479,6 +481,21 @@ static adress_status init_impl(const adress_config* cfgs, int nbox, void* stream
   s.rc_at2 = c->rc_at * c->rc_at;
   s.nb = c->n_bonds;
   for (int q = 0; q < 2 * kMaxBonds; ++q) s.bonds[q] = q < 2 * c->n_bonds ? c->bonds[q] : 0;
+  // per-atom bond partners in bond order (bit 3: this atom is the bond's first atom)
+  {
+    int cnt[kMaxNA] = {0, 0, 0, 0};
+    for (int g = 0; g < kMaxNA; ++g) s.bond_word[g] = 0;
+    for (int q = 0; q < c->n_bonds; ++q) {
+      const int p0 = c->bonds[2 * q], p1 = c->bonds[2 * q + 1];
+      s.bond_word[p0] |= (unsigned)(p1 | 8) << (4 * cnt[p0]++);
+      s.bond_word[p1] |= (unsigned)p0 << (4 * cnt[p1]++);
+    }
+    s.bmax = 0;
+    for (int g = 0; g < kMaxNA; ++g) {
+      s.bond_word[g] |= (unsigned)cnt[g] << 28;
+      s.bmax = std::max(s.bmax, cnt[g]);
+    }
+  }
   s.fene_k = c->fene_k;
   s.fene_r02 = c->fene_r0 * c->fene_r0;
   s.intra_wca = c->intra_wca;

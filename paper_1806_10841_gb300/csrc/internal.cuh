@@ -78,6 +78,11 @@ struct Sys {
   double eps, sig2, rc_at2;
   int nb;
   int bonds[2 * kMaxBonds];
+  // the same bonds per atom, in bond order, one word per atom: entry q in bits 4q..4q+3 =
+  // partner | 8 when the atom is the bond's first atom (which accounts its energy), the
+  // count in bits 28..31; bmax the largest count
+  unsigned bond_word[kMaxNA];
+  int bmax;
   double fene_k, fene_r02;
   int intra_wca;
   int cg_n;

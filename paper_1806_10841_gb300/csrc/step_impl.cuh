@@ -710,14 +710,17 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
     // bonded terms of atom g: harmonic bonds and angles, or FENE + WCA, on the listed
     // intramolecular pairs
     const real R02 = par<real>(s.fene_r02, s.f.fene_r02), K = par<real>(s.fene_k, s.f.fene_k);
+    // each lane walks its own atom's bonds (bond order), so a warp runs as many bond bodies
+    // as an atom has bonds, not as the molecule has
+    const unsigned bw = s.bond_word[gg0];
     if (s.bond_model == 1) {
       const real kb = par<real>(s.bond_k, s.f.bond_k), r0 = par<real>(s.bond_r0, s.f.bond_r0);
 #pragma unroll
       for (int q = 0; q < kMaxBonds; ++q) {
-        if (q >= s.nb) break;
-        const int p0 = s.bonds[2 * q], p1 = s.bonds[2 * q + 1];
-        if (g != p0 && g != p1) continue;
-        const auto oo = Q::off(b, cur, a * NA + (g == p0 ? p1 : p0));
+        if (q >= s.bmax) break;
+        if (q >= (int)(bw >> 28)) continue;
+        const int e = (bw >> (4 * q)) & 15;
+        const auto oo = Q::off(b, cur, a * NA + (e & 7));
         const real dx = (real)oi.x - (real)oo.x, dy = (real)oi.y - (real)oo.y, dz = (real)oi.z - (real)oo.z;
         const real d2 = dx * dx + dy * dy + dz * dz;
         const real ird = Q::rsqrt_(d2);
@@ -726,7 +729,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
         fx += fr * dx;
         fy += fr * dy;
         fz += fr * dz;
-        if (ENERGY && g == p0) {
+        if (ENERGY && (e & 8)) {
           e_b += 0.5 * (double)kb * (double)(dl - r0) * (double)(dl - r0);
           vir += (double)(fr * d2);
         }
@@ -775,11 +778,10 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
     } else {
 #pragma unroll
     for (int q = 0; q < kMaxBonds; ++q) {
-      if (q >= s.nb) break;
-      const int p0 = s.bonds[2 * q], p1 = s.bonds[2 * q + 1];
-      if (g != p0 && g != p1) continue;
-      const int other = g == p0 ? p1 : p0;
-      const auto oo = Q::off(b, cur, a * NA + other);
+      if (q >= s.bmax) break;
+      if (q >= (int)(bw >> 28)) continue;
+      const int e = (bw >> (4 * q)) & 15;
+      const auto oo = Q::off(b, cur, a * NA + (e & 7));
       const real dx = (real)oi.x - (real)oo.x, dy = (real)oi.y - (real)oo.y, dz = (real)oi.z - (real)oo.z;
       const real d2 = dx * dx + dy * dy + dz * dz;
       if (d2 >= R02) {
@@ -800,7 +802,7 @@ __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULT
       fx += fr * dx;
       fy += fr * dy;
       fz += fr * dz;
-      if (ENERGY && g == p0) {
+      if (ENERGY && (e & 8)) {
         e_b += V;
         vir += (double)(fr * d2);
       }
