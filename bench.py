@@ -32,7 +32,7 @@ MD_PER_BLOCK = 100
 SAMPLE_EVERY = 10
 TF_ALPHA = 0.5
 METRIC = "AdResS atom-steps/s"
-RDF_BINS, RDF_DR, RDF_EQ, RDF_SNAPS, RDF_EVERY = 250, 0.02, 2000, 20, 100
+RDF_BINS, RDF_DR, RDF_EQ, RDF_SNAPS, RDF_EVERY = 250, 0.02, 2000, 50, 100
 FIT_DR, FIT_NMIN = 0.01, 20  # force-matched table: bin width (sigma) and samples a bin needs
 CONFIG_NAME = "tetrahedral AdResS fluid, 200k molecules / 800k atoms, 200x100x100 sigma, AT 40 + 2x10 hybrid"
 
@@ -332,17 +332,21 @@ def held_out_rms(sim, feat, t, scale):
     return float(math.sqrt(np.mean((pred - t) ** 2)))
 
 
-def train_network(sim, feat, t, seed=20180628, max_epochs=300, check_every=5, patience=4):
+def train_network(sim, feat, t, seed=20180628, max_epochs=300, check_every=5, patience=4, radial=False):
     """Standardise, initialise and train the 9-64-64-1 network on 90% of the samples (on the
     GPU, in `sim`), checking the held-out 10% every `check_every` epochs: the learning rate
     halves when the held-out error stops improving, training stops after `patience` checks
-    without improvement (or max_epochs), and the best parameters are kept."""
+    without improvement (or max_epochs), and the best parameters are kept.  radial=True
+    switches the eight orientation inputs off (their standardisation divides by 1e30, so the
+    network sees zeros there): a network of the COM distance alone."""
     n = len(t)
     rng = np.random.default_rng(seed)
     idx = rng.permutation(n)
     ntr = int(0.9 * n)
     tr, te = idx[:ntr], idx[ntr:]
     mean, std = feat[tr].mean(0), feat[tr].std(0) + 1e-3
+    if radial:
+        std[1:] = 1e30
     scale = float(t[tr].std())
     params = dict(W1=rng.normal(0, 1 / 3, (64, 9)), b1=np.zeros(64), W2=rng.normal(0, 1 / 8, (64, 64)),
                   b2=np.zeros(64), w3=rng.normal(0, 1 / 8, 64), b3=float(t[tr].mean() / scale))
@@ -437,16 +441,27 @@ def learned_arm(s, x0, v0, make, timed, steps, device):
     lj = make("fp32")
     g_lj = rdf_of(lj, RDF_EQ)
     lj.close()
+    # the same network on the COM distance alone (orientation inputs off)
+    rad = make("fp32")
+    tn_r = train_network(rad, feat, t, radial=True)
+    rad.set_cg_mode(1)
+    rad.set_state(x0, v0)
+    rad.compute_forces(energies=False)
+    g_rad = rdf_of(rad, RDF_EQ)
+    rad.close()
     l2 = lambda a, b: float(math.sqrt(((a - b) ** 2).sum() * dr))
     return {"value": value, "unit": "atom-steps/s", "value_respa4": value_respa4,
             "samples": int(n), "training_samples": int(len(tr)), "held_out": int(len(te)),
             "epochs": tn["epochs"], "best_epoch": tn["best_epoch"], "train_s": tn["train_s"], "prep_s": prep_s,
             "held_out_force_rms": {"target": rms(t[te]), "network": tn["held_out_rms"],
                                    "force_matched_table": err_fm, "lj_table": err_lj,
-                                   "network_relative": tn["held_out_rms"] / rms(t[te])},
+                                   "network_relative": tn["held_out_rms"] / rms(t[te]),
+                                   "radial_network": tn_r["held_out_rms"]},
             "rdf_l2": {"network_vs_force_matched_table": l2(g_net, g_fm), "network_vs_all_atomistic": l2(g_net, g_at),
                        "force_matched_table_vs_all_atomistic": l2(g_fm, g_at),
                        "lj_table_vs_all_atomistic": l2(g_lj, g_at), "network_vs_lj_table": l2(g_net, g_lj),
+                       "radial_network_vs_force_matched_table": l2(g_rad, g_fm),
+                       "radial_network_vs_all_atomistic": l2(g_rad, g_at),
                        "target": 1e-2,
                        "recipe": f"COM g(r) 0..{nb * dr:g} sigma, dr {dr}, {RDF_SNAPS} snapshots every "
                                  f"{RDF_EVERY} steps after {RDF_EQ} steps from the initial state (AdResS geometry "
