@@ -19,6 +19,9 @@ constexpr int kGroup = 4;  // threads per molecule in the force kernel
 // beyond a 128x64x64 product.
 constexpr unsigned kMmaWaitPolls = 1u << 22;
 
+// Slots the mapping kernels' block maxima are spread over (see publish_extent).
+constexpr int kExtSlots = 32;
+
 // Device control block: list-validity trackers, error word, counters.
 struct Ctrl {
   int rebuild;            // decision for the current step
@@ -31,10 +34,12 @@ struct Ctrl {
   int max_nn;
   int err_info;
   int parity;          // which half of the double-buffered molecule arrays is current
-  unsigned maxext2;    // float bits: largest squared atom-to-COM distance of the last mapping
-  unsigned maxdisp2;   // float bits: largest squared COM displacement since the last build
   int n_dense;         // cells passed to the dense-cell list builder in this build
   int force_rebuild;   // set by the host (moved resolution centres), cleared by a list build
+  // float bits of the last mapping's largest squared atom-to-COM distance [0] and largest
+  // squared COM displacement since the last build [1], as block maxima spread over
+  // kExtSlots slots (block b uses slot b mod kExtSlots); the decide kernel folds and clears them
+  unsigned ext_slot[2][kExtSlots];
 };
 
 // Decision taken after a mapping (see decide_after_map in observe.cu).

@@ -15,11 +15,16 @@ namespace adress {
 // host asked for it (the resolution region moved).  The mapping
 // just written becomes current; the maxima are reset for the next mapping.
 __global__ void k_decide(const __grid_constant__ Sys s, Bufs b, DecideArgs da) {
+  static_assert(kExtSlots == 32, "one slot per lane");
   Ctrl* c = b.ctrl;
-  const float e = sqrtf(__uint_as_float(c->maxext2));
-  const float md = sqrtf(__uint_as_float(c->maxdisp2));
-  c->maxext2 = 0u;
-  c->maxdisp2 = 0u;
+  const int l = threadIdx.x;
+  const unsigned me = __reduce_max_sync(0xffffffffu, c->ext_slot[0][l]);
+  const unsigned mdd = __reduce_max_sync(0xffffffffu, c->ext_slot[1][l]);
+  c->ext_slot[0][l] = 0u;
+  c->ext_slot[1][l] = 0u;
+  if (l != 0) return;
+  const float e = sqrtf(__uint_as_float(me));
+  const float md = sqrtf(__uint_as_float(mdd));
   const double cut = fmax(s.rc_cg, s.rc_at + 2.0 * (double)e);
   const int rb = da.force || c->force_rebuild || (md > 0.5 * s.skin) || (cut + 2.0 * md > s.r_list);
   if (cut > s.r_list) set_error(c, ADRESS_ERR_EXTENT, (int)(e * 1000));
@@ -32,7 +37,7 @@ __global__ void k_decide(const __grid_constant__ Sys s, Bufs b, DecideArgs da) {
 }
 
 cudaError_t launch_decide(const Sys& s, const Bufs& b, DecideArgs da, cudaStream_t st) {
-  k_decide<<<1, 1, 0, st>>>(s, b, da);
+  k_decide<<<1, 32, 0, st>>>(s, b, da);
   return cudaGetLastError();
 }
 

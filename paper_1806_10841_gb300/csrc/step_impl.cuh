@@ -410,7 +410,9 @@ __device__ __forceinline__ void map_group64(const Sys& s, const Box& B, const Bu
 
 // Block maximum of the molecule extent and of the displacement since the last list
 // build, merged into the control block with one fire-and-forget atomic per block (no
-// fence, no returned value, so blocks retire at once); the decide kernel reads them.
+// fence, no returned value, so blocks retire at once) into slot blockIdx mod kExtSlots:
+// spread over 32 slots the blocks' atomics rarely meet at one address (one address for
+// all blocks cost ~2 us of the fused step at 800k atoms); the decide kernel folds them.
 __device__ __forceinline__ void publish_extent(const Bufs& b, float ext2, float disp2) {
   __shared__ unsigned red[2][kMaxForceBlock / 32];
   const unsigned e = __reduce_max_sync(0xffffffffu, __float_as_uint(ext2));
@@ -428,8 +430,8 @@ __device__ __forceinline__ void publish_extent(const Bufs& b, float ext2, float 
       me = max(me, red[0][k]);
       md = max(md, red[1][k]);
     }
-    atomicMax(&b.ctrl->maxext2, me);
-    atomicMax(&b.ctrl->maxdisp2, md);
+    atomicMax(&b.ctrl->ext_slot[0][blockIdx.x & (kExtSlots - 1)], me);
+    atomicMax(&b.ctrl->ext_slot[1][blockIdx.x & (kExtSlots - 1)], md);
   }
 }
 
