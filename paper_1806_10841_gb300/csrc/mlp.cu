@@ -734,46 +734,6 @@ __device__ __forceinline__ bool needs_network(const Sys& s, const Box& X, const 
   return __int_as_float(A.w) * __int_as_float(B.w) < 1.f && r2 < s.f.rc_cg2;
 }
 
-// Features of (a, m) as pair_features32 forms them, from a's centre and offsets already in
-// registers (the same arithmetic, so the same values).
-template <int NA, bool F64>
-__device__ __forceinline__ void pair_features_from(const Bufs& b, const Box& X, int cur, const int4 A,
-                                                   const float4 (&oa)[NA], int m, float feat[9]) {
-  const int4 B = b.com_fx[cur][m];
-  const float ex = (float)(int)((unsigned)B.x - (unsigned)A.x) * X.fx_scale[0];
-  const float ey = (float)(int)((unsigned)B.y - (unsigned)A.y) * X.fx_scale[1];
-  const float ez = (float)(int)((unsigned)B.z - (unsigned)A.z) * X.fx_scale[2];
-  const float d = sqrtf(ex * ex + ey * ey + ez * ez), id = 1.f / d;
-  float sa[4] = {0.f, 0.f, 0.f, 0.f}, sb[4] = {0.f, 0.f, 0.f, 0.f};
-  float4 ob[NA];
-#pragma unroll
-  for (int k = 0; k < NA; ++k) ob[k] = offset_f<F64>(b, cur, m * NA + k);
-#pragma unroll
-  for (int k = 0; k < NA; ++k) {
-    sa[k] = (oa[k].x * ex + oa[k].y * ey + oa[k].z * ez) * id;
-    sb[k] = -(ob[k].x * ex + ob[k].y * ey + ob[k].z * ez) * id;
-  }
-  if (NA == 4) {
-    sort4f(sa);
-    sort4f(sb);
-  } else {
-    for (int i = 1; i < NA; ++i)
-      for (int j = i; j > 0 && sa[j - 1] > sa[j]; --j) {
-        const float t = sa[j]; sa[j] = sa[j - 1]; sa[j - 1] = t;
-      }
-    for (int i = 1; i < NA; ++i)
-      for (int j = i; j > 0 && sb[j - 1] > sb[j]; --j) {
-        const float t = sb[j]; sb[j] = sb[j - 1]; sb[j - 1] = t;
-      }
-  }
-  feat[0] = d;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    feat[1 + k] = sa[k];
-    feat[5 + k] = sb[k];
-  }
-}
-
 template <int NA, bool F64>
 __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s, Bufs b, const float* __restrict__ norm) {
   // multiple time stepping: the network gives a slow (CG) force, needed only at outer time
@@ -795,16 +755,10 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
   const int n = live ? b.nn[t] : 0;
   const Box& X = box_of(s, b, a);
   const int* row = b.nbr + (size_t)t * s.cap;
-  // one pass over the lane's slots decides which pairs need the network (bit k: slot
-  // g + 4k; slots beyond the 32nd are decided again when written)
-  unsigned hits = 0;
   int cnt = 0;
-  for (int q = g, k = 0; q < n; q += 4, ++k) {
+  for (int q = g; q < n; q += 4) {
     const int m = row[q];
-    if (m > a && needs_network<F64>(s, X, b, cur, a, m)) {
-      if (k < 32) hits |= 1u << k;
-      ++cnt;
-    }
+    if (m > a && needs_network<F64>(s, X, b, cur, a, m)) ++cnt;
   }
   int incl = cnt;
 #pragma unroll
@@ -817,21 +771,15 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
   base = __shfl_sync(0xffffffffu, base, 31);
   long long p = (long long)base + (incl - cnt);
   if (cnt == 0) return;
-  // the item's own centre and atom offsets, read once for all its pairs
-  const int4 A = b.com_fx[cur][a];
-  float4 oa[NA];
-#pragma unroll
-  for (int k = 0; k < NA; ++k) oa[k] = offset_f<F64>(b, cur, a * NA + k);
-  for (int q = g, k = 0; q < n; q += 4, ++k) {
+  for (int q = g; q < n; q += 4) {
     const int m = row[q];
-    const bool hit = k < 32 ? ((hits >> k) & 1u) != 0 : (m > a && needs_network<F64>(s, X, b, cur, a, m));
-    if (!hit) continue;
+    if (!(m > a && needs_network<F64>(s, X, b, cur, a, m))) continue;
     if (p >= b.pcap) {
       set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, (int)p);
       return;
     }
     float f[9];
-    pair_features_from<NA, F64>(b, X, cur, A, oa, m, f);
+    pair_features32<NA, F64>(s, b, cur, a, m, f);
     // both orderings, normalised and packed as the A fragments read them
     unsigned* out = b.pfrag + p * 10;
 #pragma unroll
@@ -841,9 +789,9 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
         float v[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const int kk = 2 * w + h;
-          const int src = (u == 0 || kk == 0) ? kk : (kk < 5 ? kk + 4 : kk - 4);
-          v[h] = kk < kIn ? (f[src < kIn ? src : 0] - sn[0][kk < kIn ? kk : 0]) * sn[1][kk < kIn ? kk : 0] : 0.f;
+          const int k = 2 * w + h;
+          const int src = (u == 0 || k == 0) ? k : (k < 5 ? k + 4 : k - 4);
+          v[h] = k < kIn ? (f[src < kIn ? src : 0] - sn[0][k < kIn ? k : 0]) * sn[1][k < kIn ? k : 0] : 0.f;
         }
         out[5 * u + w] = pack_bf16(v[0], v[1]);
       }
