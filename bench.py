@@ -32,7 +32,7 @@ MD_PER_BLOCK = 100
 SAMPLE_EVERY = 10
 TF_ALPHA = 0.5
 METRIC = "AdResS atom-steps/s"
-RDF_BINS, RDF_DR, RDF_EQ, RDF_SNAPS, RDF_EVERY = 250, 0.02, 2000, 50, 100
+RDF_BINS, RDF_DR, RDF_EQ, RDF_SNAPS, RDF_EVERY = 250, 0.02, 2000, 50, 400
 FIT_DR, FIT_NMIN = 0.01, 20  # force-matched table: bin width (sigma) and samples a bin needs
 CONFIG_NAME = "tetrahedral AdResS fluid, 200k molecules / 800k atoms, 200x100x100 sigma, AT 40 + 2x10 hybrid"
 
@@ -602,10 +602,11 @@ def replicas_arm(timed, steps, local):
     sim.compute_forces(energies=False)
     sim.check()
     n_atoms = sim.N
-    t_def, _, _ = timed(sim, steps, 2)
+    t_def, ms_def, _ = timed(sim, steps, 2)
+    tuning0 = sim.get_tuning()
     rows = sim.autotune(nsteps=50)
     tuning = sim.get_tuning()
-    t_tuned, ms, clocks = timed(sim, steps, 2)
+    t_tuned, ms_tuned, clocks = timed(sim, steps, 2)
     sim.close()
     # the same replicas one handle at a time (one graph launch per replica per bench step)
     sims = []
@@ -634,6 +635,11 @@ def replicas_arm(timed, steps, local):
             "molecules_min_median_max": [int(min(q.M for q in systems)), int(statistics.median(q.M for q in systems)),
                                          int(max(q.M for q in systems))],
             "value_default_tuning": per(t_def),
+            "tuned_gain": t_def / t_tuned - 1.0,
+            "bench_step_ms_default": {"min": min(ms_def), "median": statistics.median(ms_def), "max": max(ms_def)},
+            "bench_step_ms_tuned": {"min": min(ms_tuned), "median": statistics.median(ms_tuned), "max": max(ms_tuned)},
+            "autotune_default_row": [r for r in rows if (r[0], r[1]) == tuple(tuning0)][:1],
+            "autotune_chosen_row": [r for r in rows if (r[0], r[1]) == tuple(tuning)][:1],
             "value_one_handle_per_replica": per(t_seq), "tuning": {"force_block": tuning[0], "skin": tuning[1]},
             "autotune_trials": len(rows), "ms_per_bench_step": t_tuned / steps * 1e3}
 

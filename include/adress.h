@@ -391,13 +391,16 @@ adress_status adress_time_kernels(adress_handle h, int32_t reps, float* ms_out);
 adress_status adress_set_tuning(adress_handle h, int32_t force_block, double skin);
 adress_status adress_get_tuning(adress_handle h, int32_t* force_block, double* skin);
 
-/* Autotuner: for every force_block in {32, 64, 128} and skin in {0.5, 1, 1.5, 2} x the
- * configured skin (those the boxes admit), run nsteps (1..100) steps of the bound state once to
- * capture the graph and once timed with CUDA events, and keep the fastest pair.  The bound
- * state (x, v, f, time level) is copied aside first and restored after every trial, and
- * the lists are rebuilt for the chosen pair, so the call leaves the state as it found
- * it.  results (host, may be NULL): up to max_results rows of {force_block, skin,
- * ms per step}; *n_results (may be NULL) = rows written.  Synchronises. */
+/* Autotuner: for every force_block in {32, 64, 128} and skin in {0.5, 0.75, 1, 1.25, 1.5, 2}
+ * x the configured skin (those the boxes admit), run nsteps (1..100) steps of the bound state
+ * once to capture the graph and warm up, then 5 times timed with CUDA events; a trial's time
+ * is the median of the 5.  The trial with the lowest median is kept if that median is below
+ * the fastest of the 5 runs of the setting the call started from; otherwise that setting
+ * stays (no change for a gain inside the run-to-run spread).  The bound state (x, v, f, time
+ * level) is copied aside first and restored after every trial, and the lists are rebuilt
+ * for the chosen pair, so the call leaves the state as it found it.  results (host, may be
+ * NULL): up to max_results rows of {force_block, skin, median ms per step, fastest, slowest};
+ * *n_results (may be NULL) = rows written.  Synchronises. */
 adress_status adress_autotune(adress_handle h, int32_t nsteps, double* results, int32_t max_results,
                               int32_t* n_results);
 

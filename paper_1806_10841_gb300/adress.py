@@ -381,12 +381,13 @@ class AdResS:
         return b.value, sk.value
 
     def autotune(self, nsteps: int = 20):
-        """Pick threads per block and list skin by timing nsteps-step runs (the state is
-        restored); returns the trial table as rows (force_block, skin, ms per step)."""
-        rows = np.zeros((16, 3))
+        """Pick threads per block and list skin by timing nsteps-step runs (5 timed runs per
+        trial, the state restored); returns the trial table as rows (force_block, skin, median
+        ms per step, fastest, slowest)."""
+        rows = np.zeros((32, 5))
         n = C.c_int32()
-        self._call("adress_autotune", C.c_int32(int(nsteps)), _dptr(rows), 16, C.byref(n))
-        return [(int(r[0]), float(r[1]), float(r[2])) for r in rows[:n.value]]
+        self._call("adress_autotune", C.c_int32(int(nsteps)), _dptr(rows), 32, C.byref(n))
+        return [(int(r[0]), float(r[1]), float(r[2]), float(r[3]), float(r[4])) for r in rows[:n.value]]
 
     LIMIT_PAIR_CAPACITY, LIMIT_MMA_WAIT_POLLS = 0, 1
 

@@ -1299,12 +1299,15 @@ adress_status adress_autotune(adress_handle h, int32_t nsteps, double* results, 
   const int block0 = s.force_block;
   const double cur_skin = s.skin;
   std::vector<double> skins;
-  for (double m : {0.5, 1.0, 1.5, 2.0}) {
+  for (double m : {0.5, 0.75, 1.0, 1.25, 1.5, 2.0}) {
     const double sk = m * skin0;
     if (std::find(skins.begin(), skins.end(), sk) == skins.end()) skins.push_back(sk);
   }
+  // each trial: capture + one warm-up run, then kAutotuneRuns timed runs; the trial's time
+  // is their median and its spread their range
+  constexpr int kAutotuneRuns = 5;
   int best_block = block0, rows = 0;
-  double best_skin = cur_skin, best_ms = 1e300;
+  double best_skin = cur_skin, best_med = 1e300, start_med = -1.0, start_min = 0.0;
   adress_status status = ADRESS_OK;
   for (double sk : skins) {
     for (int blk : {32, 64, 128}) {
@@ -1316,27 +1319,44 @@ adress_status adress_autotune(adress_handle h, int32_t nsteps, double* results, 
       }
       status = build_lists_sync(h);
       if (status == ADRESS_OK) status = launch_graph(h, nsteps, 0, 0, 0.0);  // capture + warm-up
-      if (status == ADRESS_OK && cudaEventRecord(ev[0], st) != cudaSuccess) status = ADRESS_ERR_CUDA;
-      if (status == ADRESS_OK) status = launch_graph(h, nsteps, 0, 0, 0.0);
-      if (status == ADRESS_OK && cudaEventRecord(ev[1], st) != cudaSuccess) status = ADRESS_ERR_CUDA;
+      double t[kAutotuneRuns];
+      for (int k = 0; k < kAutotuneRuns && status == ADRESS_OK; ++k) {
+        if (cudaEventRecord(ev[0], st) != cudaSuccess) status = ADRESS_ERR_CUDA;
+        if (status == ADRESS_OK) status = launch_graph(h, nsteps, 0, 0, 0.0);
+        if (status == ADRESS_OK && cudaEventRecord(ev[1], st) != cudaSuccess) status = ADRESS_ERR_CUDA;
+        float ms = 0.f;
+        if (status == ADRESS_OK && cudaEventSynchronize(ev[1]) != cudaSuccess) status = ADRESS_ERR_CUDA;
+        if (status == ADRESS_OK) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        t[k] = ms / nsteps;
+      }
       if (status == ADRESS_OK) status = adress_check(h);
       if (status != ADRESS_OK) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[0], ev[1]);
-      const double per = ms / nsteps;
+      std::sort(t, t + kAutotuneRuns);
+      const double med = t[kAutotuneRuns / 2];
       if (results && rows < max_results) {
-        results[3 * rows + 0] = blk;
-        results[3 * rows + 1] = sk;
-        results[3 * rows + 2] = per;
+        results[5 * rows + 0] = blk;
+        results[5 * rows + 1] = sk;
+        results[5 * rows + 2] = med;
+        results[5 * rows + 3] = t[0];
+        results[5 * rows + 4] = t[kAutotuneRuns - 1];
       }
       ++rows;
-      if (per < best_ms) {
-        best_ms = per;
+      if (blk == block0 && sk == cur_skin) {
+        start_med = med;
+        start_min = t[0];
+      }
+      if (med < best_med) {
+        best_med = med;
         best_block = blk;
         best_skin = sk;
       }
     }
     if (status != ADRESS_OK) break;
+  }
+  // keep the starting setting unless the best trial's median is below every run of it
+  if (status == ADRESS_OK && start_med >= 0.0 && !(best_med < start_min)) {
+    best_block = block0;
+    best_skin = cur_skin;
   }
   if (n_results) *n_results = std::min(rows, std::max(0, max_results));
   adress_status st2 = adress_set_tuning(h, status == ADRESS_OK ? best_block : block0,
