@@ -660,8 +660,15 @@ __device__ __forceinline__ float pair_target32(const Sys& s, const Bufs& b, int 
       const float dx = Rx + oi.x - oj.x, dy = Ry + oi.y - oj.y, dz = Rz + oi.z - oj.z;
       const float d2 = dx * dx + dy * dy + dz * dz;
       if (d2 < s.f.rc_at2) {
-        const float ir2 = 1.f / d2, sr2 = s.f.sig2 * ir2, sr6 = sr2 * sr2 * sr2;
-        const float fr = 24.f * s.f.eps * (2.f * sr6 * sr6 - sr6) * ir2;
+        float fr;
+        if (s.nb_model == 1) {
+          // Lennard-Jones + reaction field of the site pair (the water-like model)
+          const float ir2 = 1.f / d2, ir = sqrtf(ir2), ir6 = ir2 * ir2 * ir2;
+          fr = (12.f * s.f.c12[i][j] * ir6 - 6.f * s.f.c6[i][j]) * ir6 * ir2 + s.f.qq[i][j] * (ir2 * ir - s.f.krf2);
+        } else {
+          const float ir2 = 1.f / d2, sr2 = s.f.sig2 * ir2, sr6 = sr2 * sr2 * sr2;
+          fr = 24.f * s.f.eps * (2.f * sr6 * sr6 - sr6) * ir2;
+        }
         Fx += fr * dx;
         Fy += fr * dy;
         Fz += fr * dz;

@@ -88,3 +88,31 @@ def test_cg_fit_full_size_800k_atoms():
     assert np.abs(F - Fo).max() <= 1e-12 * np.abs(Fo).max()
     assert np.abs(V - Vo).max() <= 1e-12 * np.abs(Vo).max()
     sim.close()
+
+
+def test_water_samples_and_table_match_oracle():
+    """The water-like fluid, all atomistic: the GPU's samples (features, and the site-pair
+    Lennard-Jones + reaction-field force between two molecules projected on their axis) and
+    the force-matched table from them against the oracle's."""
+    from paper_1806_10841_gb300 import adress
+
+    s = inputs.scaled_c3(3000)
+    s.d_at = 1e3
+    x, v = inputs.water_state(s)
+    feat_o, t_o, ids_o = oracle.Oracle(s).collect_pairs(x, s.rc_cg)
+    sim = adress.AdResS(s, precision="fp32")
+    sim.set_state(x, v)
+    n = sim.mlp_collect(cap=2_000_000)
+    feat, t, ids = sim.mlp_samples(n)
+    key_o = {tuple(map(int, p)): k for k, p in enumerate(ids_o)}
+    assert {tuple(map(int, p)) for p in ids} == set(key_o)
+    order = np.array([key_o[tuple(map(int, p))] for p in ids])
+    assert np.abs(feat - feat_o[order]).max() < 2e-5
+    scale = np.abs(t_o).max()
+    print(f"WATER samples={n} max|dt|={np.abs(t - t_o[order]).max():.2e} scale={scale:.2e}")
+    assert np.abs(t - t_o[order]).max() <= 1e-4 * scale
+    h = 0.01
+    F, V, Fo, Vo = fit_both(sim, s, feat, t, h, 5)
+    assert np.abs(F - Fo).max() <= 1e-12 * np.abs(Fo).max()
+    assert np.abs(V - Vo).max() <= 1e-12 * np.abs(Vo).max()
+    sim.close()
