@@ -606,10 +606,11 @@ __device__ __forceinline__ float4 offset_f(const Bufs& b, int cur, int i) {
 }
 
 // Features of (a, b) with e from a to b; feat[9].  Atoms beyond na project to 0 (padding).
+// The first molecule's centre A and atom offsets oa[] come from the caller.
 template <int NA, bool F64>
-__device__ __forceinline__ void pair_features32(const Sys& s, const Bufs& b, int cur, int a, int bb, float feat[9]) {
-  const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][bb];
-  const Box& X = box_of(s, b, a);
+__device__ __forceinline__ void pair_features32(const Box& X, const int4 A, const float4 (&oa)[NA], const Bufs& b,
+                                                int cur, int bb, float feat[9]) {
+  const int4 B = b.com_fx[cur][bb];
   const float ex = (float)(int)((unsigned)B.x - (unsigned)A.x) * X.fx_scale[0];
   const float ey = (float)(int)((unsigned)B.y - (unsigned)A.y) * X.fx_scale[1];
   const float ez = (float)(int)((unsigned)B.z - (unsigned)A.z) * X.fx_scale[2];
@@ -617,8 +618,8 @@ __device__ __forceinline__ void pair_features32(const Sys& s, const Bufs& b, int
   float sa[4] = {0.f, 0.f, 0.f, 0.f}, sb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < NA; ++k) {
-    const float4 oa = offset_f<F64>(b, cur, a * NA + k), ob = offset_f<F64>(b, cur, bb * NA + k);
-    sa[k] = (oa.x * ex + oa.y * ey + oa.z * ez) * id;
+    const float4 ob = offset_f<F64>(b, cur, bb * NA + k);
+    sa[k] = (oa[k].x * ex + oa[k].y * ey + oa[k].z * ez) * id;
     sb[k] = -(ob.x * ex + ob.y * ey + ob.z * ez) * id;
   }
   if (NA == 4) {
@@ -640,6 +641,14 @@ __device__ __forceinline__ void pair_features32(const Sys& s, const Bufs& b, int
     feat[1 + k] = sa[k];
     feat[5 + k] = sb[k];
   }
+}
+
+template <int NA, bool F64>
+__device__ __forceinline__ void pair_features32(const Sys& s, const Bufs& b, int cur, int a, int bb, float feat[9]) {
+  float4 oa[NA];
+#pragma unroll
+  for (int k = 0; k < NA; ++k) oa[k] = offset_f<F64>(b, cur, a * NA + k);
+  pair_features32<NA, F64>(box_of(s, b, a), b.com_fx[cur][a], oa, b, cur, bb, feat);
 }
 
 // Atomistic force on a from b projected on -e (the force-matching target), FP32.
@@ -726,19 +735,41 @@ __global__ void k_mlp_collect(const __grid_constant__ Sys s, Bufs b, int pass, c
 // k_mlp_eval then evaluates the buffer 16 pairs per warp tile (both orderings as two
 // tensor-core tiles, weights staged in shared memory) and writes the force to both slots.
 
+// The first molecule's centre (FP64 or fixed-point, by path) is passed in.
 template <bool F64>
-__device__ __forceinline__ bool needs_network(const Sys& s, const Box& X, const Bufs& b, int cur, int a, int m) {
-  if (F64) {
-    const double4_32a A = b.com64[cur][a], B = b.com64[cur][m];
+struct Centre;
+template <>
+struct Centre<true> {
+  double4_32a c;
+};
+template <>
+struct Centre<false> {
+  int4 c;
+};
+
+template <bool F64>
+__device__ __forceinline__ Centre<F64> centre_of(const Bufs& b, int cur, int a) {
+  if constexpr (F64)
+    return {b.com64[cur][a]};
+  else
+    return {b.com_fx[cur][a]};
+}
+
+template <bool F64>
+__device__ __forceinline__ bool needs_network(const Sys& s, const Box& X, const Bufs& b, int cur, const Centre<F64>& CA,
+                                              int m) {
+  if constexpr (F64) {
+    const double4_32a A = CA.c, B = b.com64[cur][m];
     const double r2 = pair_r2(minimg_cmp(A.x - B.x, X.L[0], X.halfL[0]), minimg_cmp(A.y - B.y, X.L[1], X.halfL[1]),
                               minimg_cmp(A.z - B.z, X.L[2], X.halfL[2]));
     return A.w * B.w < 1.0 && r2 < s.rc_cg2;
+  } else {
+    const int4 A = CA.c, B = b.com_fx[cur][m];
+    const float r2 = pair_r2((float)(int)((unsigned)A.x - (unsigned)B.x) * X.fx_scale[0],
+                             (float)(int)((unsigned)A.y - (unsigned)B.y) * X.fx_scale[1],
+                             (float)(int)((unsigned)A.z - (unsigned)B.z) * X.fx_scale[2]);
+    return __int_as_float(A.w) * __int_as_float(B.w) < 1.f && r2 < s.f.rc_cg2;
   }
-  const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][m];
-  const float r2 = pair_r2((float)(int)((unsigned)A.x - (unsigned)B.x) * X.fx_scale[0],
-                           (float)(int)((unsigned)A.y - (unsigned)B.y) * X.fx_scale[1],
-                           (float)(int)((unsigned)A.z - (unsigned)B.z) * X.fx_scale[2]);
-  return __int_as_float(A.w) * __int_as_float(B.w) < 1.f && r2 < s.f.rc_cg2;
 }
 
 template <int NA, bool F64>
@@ -753,7 +784,9 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
     sn[1][threadIdx.x] = norm[2 * kIn + 1 + threadIdx.x];
   }
   __syncthreads();
-  // four lanes per work item, lane g taking list slots g, g + 4, ...
+  // four lanes per work item, lane g taking list slots g, g + 4, ...; one walk of the list
+  // tests every slot and marks the selected ones in sel (bit j for slot g + 4 j; slots past
+  // bit 31 are tested again when their features are formed)
   const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2, g = threadIdx.x & 3;
   const int lane = threadIdx.x & 31;
   const bool live = t < s.M;
@@ -761,11 +794,16 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
   const int a = live ? b.items[t] : 0;
   const int n = live ? b.nn[t] : 0;
   const Box& X = box_of(s, b, a);
+  const Centre<F64> CA = centre_of<F64>(b, cur, a);
   const int* row = b.nbr + (size_t)t * s.cap;
+  unsigned sel = 0u;
   int cnt = 0;
-  for (int q = g; q < n; q += 4) {
+  for (int q = g, j = 0; q < n; q += 4, ++j) {
     const int m = row[q];
-    if (m > a && needs_network<F64>(s, X, b, cur, a, m)) ++cnt;
+    if (m > a && needs_network<F64>(s, X, b, cur, CA, m)) {
+      ++cnt;
+      if (j < 32) sel |= 1u << j;
+    }
   }
   int incl = cnt;
 #pragma unroll
@@ -778,9 +816,21 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
   base = __shfl_sync(0xffffffffu, base, 31);
   long long p = (long long)base + (incl - cnt);
   if (cnt == 0) return;
-  for (int q = g; q < n; q += 4) {
-    const int m = row[q];
-    if (!(m > a && needs_network<F64>(s, X, b, cur, a, m))) continue;
+  int qx = g + 128;  // where the search for selected slots beyond the mask resumes
+  for (int left = cnt; left > 0; --left) {
+    int q, m = -1;
+    if (sel) {
+      q = g + 4 * (__ffs(sel) - 1);
+      sel &= sel - 1;
+      m = row[q];
+    } else {
+      for (q = qx; q < n; q += 4) {
+        m = row[q];
+        if (m > a && needs_network<F64>(s, X, b, cur, CA, m)) break;
+      }
+      if (q >= n) return;  // not reached: the first walk counted this slot
+      qx = q + 4;
+    }
     if (p >= b.pcap) {
       set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, (int)p);
       return;

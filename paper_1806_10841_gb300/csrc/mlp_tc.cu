@@ -36,11 +36,9 @@ __device__ __forceinline__ float tanh_hw(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-// z sigma(z) = (z/2)(1 + tanh(z/2)), as in the warp-MMA evaluation
-__device__ __forceinline__ float silu_hw(float z) {
-  const float h = 0.5f * z;
-  return fmaf(h, tanh_hw(h), h);
-}
+// z sigma(z) = h (1 + tanh h) with h = z/2, as in the warp-MMA evaluation; the caller forms
+// h = fma(1/2, product, bias/2), which rounds to exactly half of the rounded product + bias
+__device__ __forceinline__ float silu_half(float h) { return fmaf(h, tanh_hw(h), h); }
 
 // byte offset of the 16-byte chunk (row r, K chunk kc) in a K-major no-swizzle operand with
 // nk chunks of 8 elements per row
@@ -53,7 +51,7 @@ struct __align__(1024) TcSmem {
   uint8_t A2[128 * 64 * 2];  // 128 rows x 64 bf16
   uint8_t B1[64 * 16 * 2];   // W1: 64 outputs x 16 inputs (K-major)
   uint8_t B2[64 * 64 * 2];   // W2: 64 outputs x 64 inputs
-  float b1[kTcH], b2[kTcH], w3[kTcH];
+  float hb1[kTcH], hb2[kTcH], w3[kTcH];  // halved biases (see silu_half)
   float y[128];
   uint64_t mbar;
   uint32_t taddr;
@@ -80,8 +78,8 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
     *reinterpret_cast<uint4*>(S.B2 + chunk_off(n, kc, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
   if (tid < kTcH) {
-    S.b1[tid] = P[kTcOb1 + tid];
-    S.b2[tid] = P[kTcOb2 + tid];
+    S.hb1[tid] = 0.5f * P[kTcOb1 + tid];
+    S.hb2[tid] = 0.5f * P[kTcOb2 + tid];
     S.w3[tid] = P[kTcOw3 + tid];
   }
   if (tid == 0) {
@@ -162,11 +160,9 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int j = 32 * half + 8 * c;
-        uint4 q;
-        q.x = pack2(silu_hw(z[8 * c + 0] + S.b1[j + 0]), silu_hw(z[8 * c + 1] + S.b1[j + 1]));
-        q.y = pack2(silu_hw(z[8 * c + 2] + S.b1[j + 2]), silu_hw(z[8 * c + 3] + S.b1[j + 3]));
-        q.z = pack2(silu_hw(z[8 * c + 4] + S.b1[j + 4]), silu_hw(z[8 * c + 5] + S.b1[j + 5]));
-        q.w = pack2(silu_hw(z[8 * c + 6] + S.b1[j + 6]), silu_hw(z[8 * c + 7] + S.b1[j + 7]));
+        const auto act = [&](int k) { return silu_half(fmaf(0.5f, z[8 * c + k], S.hb1[j + k])); };
+        const uint4 q = make_uint4(pack2(act(0), act(1)), pack2(act(2), act(3)), pack2(act(4), act(5)),
+                                   pack2(act(6), act(7)));
         *reinterpret_cast<uint4*>(S.A2 + chunk_off(tid, 4 * half + c, 8)) = q;
       }
     }
@@ -189,7 +185,10 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
       float z[32];
       umma::ld32(tmem + lane_base + 64 + 32 * half, z);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) acc = fmaf(S.w3[32 * half + c], silu_hw(z[c] + S.b2[32 * half + c]), acc);
+      for (int c = 0; c < 32; ++c) {
+        const int j = 32 * half + c;
+        acc = fmaf(S.w3[j], silu_half(fmaf(0.5f, z[c], S.hb2[j])), acc);
+      }
     }
     S.y[tid] = acc + b3;
     __syncthreads();
