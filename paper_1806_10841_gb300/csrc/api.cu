@@ -111,12 +111,13 @@ static cudaError_t realloc_owned(adress_ctx* h, T** p, size_t n) {
 }
 
 // Pair buffers of the network CG force: every unordered listed pair at most once
-// (sum of list lengths / 2 <= M cap / 2).
+// (sum of list lengths / 2 <= M cap / 2), plus 16 bytes of slack each for the evaluation's
+// bulk copies, which round a ragged last tile up to 16 bytes.
 static cudaError_t alloc_pair_buffers(adress_ctx* h) {
   Bufs& b = h->buf;
   const long long pcap = (long long)h->sys.M * h->sys.cap / 2 + 32;
-  cudaError_t e = realloc_owned(h, &b.pfrag, (size_t)pcap * 10);
-  if (e == cudaSuccess) e = realloc_owned(h, &b.pslot, (size_t)pcap);
+  cudaError_t e = realloc_owned(h, &b.pfrag, (size_t)pcap * 10 + 4);
+  if (e == cudaSuccess) e = realloc_owned(h, &b.pslot, (size_t)pcap + 2);
   if (e == cudaSuccess) e = realloc_owned(h, &b.mirror, (size_t)h->sys.M * h->sys.cap);
   if (e == cudaSuccess && !b.npair) e = dalloc(h, &b.npair, 1);
   if (e == cudaSuccess) {

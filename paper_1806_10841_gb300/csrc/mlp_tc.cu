@@ -53,6 +53,13 @@ struct __align__(1024) TcSmem {
   uint8_t B2[64 * 64 * 2];   // W2: 64 outputs x 64 inputs
   float hb1[kTcH], hb2[kTcH], w3[kTcH];  // halved biases (see silu_half)
   float y[128];
+  // pair-buffer rows (inputs, list slots) of three tiles, filled by bulk copies: a tile's
+  // rows land while an earlier tile is evaluated
+  struct alignas(16) In {
+    unsigned frag[64 * 10];
+    int2 slot[64];
+  } in[3];
+  uint64_t mbin[3];
   uint64_t mbar;
   uint32_t taddr;
   int abort;
@@ -85,6 +92,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
   if (tid == 0) {
     S.abort = 0;
     umma::mbar_init(&S.mbar, 1);
+    for (int k = 0; k < 3; ++k) umma::mbar_init(&S.mbin[k], 1);
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -107,13 +115,33 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
   const long long ntiles = (np + 63) / 64;
   uint32_t phase = 0;
 
-  // inputs of a tile's row tid: pair p0 + (tid & 63), ordering tid >> 6 (words 5u .. 5u + 4)
-  auto stage_inputs = [&](long long p0) {
-    const long long p = p0 + (tid & 63);
+  // The block's j-th tile is blockIdx.x + j gridDim.x; its pair-buffer rows go to in[j % 3]
+  // (barrier phase (j / 3) & 1).  Thread 0 requests tile j + 2 once every thread is past
+  // tile j - 1, the last user of that buffer.  The copy of a ragged last tile is rounded up to
+  // 16 bytes (the buffers are allocated with that much slack); its missing rows read as zero.
+  long long issued = 0, landed = 0;  // tiles requested (thread 0) / seen landed (each thread)
+  auto request = [&](long long j) {
+    const long long p0 = ((long long)blockIdx.x + j * gridDim.x) * 64;
+    if (p0 >= np) return;
+    const uint32_t n = (uint32_t)min(64LL, np - p0);
+    const uint32_t bf = (40u * n + 15u) & ~15u, bs = (8u * n + 15u) & ~15u;
+    uint64_t* mb = &S.mbin[j % 3];
+    umma::mbar_arrive_expect_tx(mb, bf + bs);
+    umma::bulk_g2s(S.in[j % 3].frag, pfrag + p0 * 10, bf, mb);
+    umma::bulk_g2s(S.in[j % 3].slot, pslot + p0, bs, mb);
+    issued = j + 1;
+  };
+  // inputs of tile j's row tid: pair p0 + (tid & 63), ordering tid >> 6 (words 5u .. 5u + 4)
+  auto stage_inputs = [&](long long j) {
+    if (umma::mbar_wait(&S.mbin[j % 3], (uint32_t)((j / 3) & 1), kWaitPolls))
+      landed = j + 1;
+    else
+      atomicExch(&S.abort, 1);
+    const long long p = ((long long)blockIdx.x + j * gridDim.x) * 64 + (tid & 63);
     const int u = tid >> 6;
     uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0u, 0u, 0u, 0u);
     if (p < np) {
-      const unsigned* r = pfrag + p * 10 + 5 * u;
+      const unsigned* r = S.in[j % 3].frag + (tid & 63) * 10 + 5 * u;
       c0 = make_uint4(r[0], r[1], r[2], r[3]);
       c1.x = r[4];
     }
@@ -138,9 +166,13 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
 
   // pipeline: layer 1 of the first tile alone, then per tile one barrier wait for layer 2
   // of this tile together with layer 1 of the next
-  long long tile = blockIdx.x;
+  long long tile = blockIdx.x, j = 0;
+  if (tid == 0) {
+    request(0);
+    request(1);
+  }
   if (tile < ntiles) {
-    stage_inputs(tile * 64);
+    stage_inputs(0);
     sync_for_issue();
     if (tid == 0) {
       umma::fence_after_sync();
@@ -166,9 +198,10 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
         *reinterpret_cast<uint4*>(S.A2 + chunk_off(tid, 4 * half + c, 8)) = q;
       }
     }
-    if (has_next) stage_inputs(next * 64);
+    if (has_next) stage_inputs(j + 1);
     sync_for_issue();
     if (tid == 0) {
+      request(j + 2);
       umma::fence_after_sync();
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
@@ -194,17 +227,22 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
     __syncthreads();
     if (tid < 64 && p0 + tid < np) {
       const float fv = 0.5f * scale * (S.y[tid] + S.y[tid + 64]);
-      const int2 sl = pslot[p0 + tid];
+      const int2 sl = S.in[j % 3].slot[tid];
       if (sl.x >= 0 && sl.x < nslot) fpair[sl.x] = fv;
       if (sl.y >= 0 && sl.y < nslot) fpair[sl.y] = fv;
     }
     tile = next;
+    ++j;
   }
   if (S.abort) {
     if (tid == 0) set_error(ctrl, ADRESS_ERR_TIMEOUT, 2);
     // give the products still in flight a second bounded wait before their TMEM is freed
     umma::mbar_wait(&S.mbar, phase ^ 1u, kWaitPolls);
   }
+  // bulk copies still in flight (after an abort) land before the block's shared memory is
+  // released
+  if (tid == 0)
+    for (long long k = landed; k < issued; ++k) umma::mbar_wait(&S.mbin[k % 3], (uint32_t)((k / 3) & 1), kWaitPolls);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();

@@ -86,6 +86,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint3
   return false;
 }
 
+// This thread's arrival on the barrier, which then also waits for `bytes` of bulk-copy data.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+// Untiled bulk copy (TMA) of `bytes` from global to this CTA's shared memory, counted on the
+// barrier as it lands.  Both addresses 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :
+               : "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+
 // 32 consecutive 32-bit TMEM columns of this warp's 32 lanes (lane i of the warp gets TMEM
 // lane base + i), then the wait that makes the registers valid.
 __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
