@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kTcH = 64, kTcIn = 9;
 constexpr int kTcOb1 = kTcH * kTcIn, kTcOb2 = kTcOb1 + kTcH + kTcH * kTcH, kTcOw3 = kTcOb2 + kTcH,
-              kTcOb3 = kTcOw3 + kTcH;
+              kTcOb3 = kTcOw3 + kTcH, kTcOW2 = kTcOb1 + kTcH;
 constexpr uint32_t kWaitPolls = kMmaWaitPolls;
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -36,9 +36,24 @@ __device__ __forceinline__ float tanh_hw(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-// z sigma(z) = h (1 + tanh h) with h = z/2, as in the warp-MMA evaluation; the caller forms
-// h = fma(1/2, product, bias/2), which rounds to exactly half of the rounded product + bias
+// z sigma(z) = h (1 + tanh h) with h = z/2, as in the warp-MMA evaluation.  The products
+// deliver h directly: weights and biases enter halved (exact in bf16 and fp32), and each
+// bias rides in the product as three bf16 terms (hi + lo + lo2, the fp32 value to its last
+// bit) against three input columns of ones.
 __device__ __forceinline__ float silu_half(float h) { return fmaf(h, tanh_hw(h), h); }
+
+__device__ __forceinline__ uint16_t bf16_bits(float v) {
+  const __nv_bfloat16 b = __float2bfloat16_rn(v);
+  return *reinterpret_cast<const uint16_t*>(&b);
+}
+// v as hi + lo + lo2 in bf16 (each the rounding of what the previous ones leave)
+__device__ __forceinline__ void split3(float v, uint16_t (&h)[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    h[k] = bf16_bits(v);
+    v -= __uint_as_float((uint32_t)h[k] << 16);
+  }
+}
 
 // byte offset of the 16-byte chunk (row r, K chunk kc) in a K-major no-swizzle operand with
 // nk chunks of 8 elements per row
@@ -47,11 +62,13 @@ __device__ __forceinline__ uint32_t chunk_off(int r, int kc, int nk) {
 }
 
 struct __align__(1024) TcSmem {
-  uint8_t A1[128 * 16 * 2];  // 128 rows x 16 bf16
+  uint8_t A1[128 * 16 * 2];  // 128 rows x 16 bf16: 9 inputs, three ones (bias), zeros
   uint8_t A2[128 * 64 * 2];  // 128 rows x 64 bf16
-  uint8_t B1[64 * 16 * 2];   // W1: 64 outputs x 16 inputs (K-major)
-  uint8_t B2[64 * 64 * 2];   // W2: 64 outputs x 64 inputs
-  float hb1[kTcH], hb2[kTcH], w3[kTcH];  // halved biases (see silu_half)
+  uint8_t A2b[128 * 16 * 2];  // 128 rows x 16 bf16: three ones (bias of layer 2), zeros
+  uint8_t B1[64 * 16 * 2];   // W1 / 2: 64 outputs x 16 inputs (K-major), b1 / 2 in columns 9..11
+  uint8_t B2[64 * 64 * 2];   // W2 / 2: 64 outputs x 64 inputs
+  uint8_t B2b[64 * 16 * 2];  // b2 / 2 in columns 0..2
+  float w3[kTcH];
   float y[128];
   // pair-buffer rows (inputs, list slots) of three tiles, filled by bulk copies: a tile's
   // rows land while an earlier tile is evaluated
@@ -65,30 +82,41 @@ struct __align__(1024) TcSmem {
   int abort;
 };
 
-__global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict__ P, const unsigned* __restrict__ W1p,
-                                                        const unsigned* __restrict__ W2p, const float* __restrict__ norm,
+__global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict__ P, const float* __restrict__ norm,
                                                         const unsigned* __restrict__ pfrag,
                                                         const int2* __restrict__ pslot, const unsigned* npair,
                                                         long long pcap, long long nslot, uint32_t polls,
                                                         float* __restrict__ fpair, Ctrl* ctrl) {
   __shared__ TcSmem S;
   const int tid = threadIdx.x, warp = tid >> 5;
-  // operands that do not change: weights in the K-major core-matrix layout, biases
-  for (int i = tid; i < 64 * 2; i += 128) {  // W1: row n, chunk kc = words 4 kc .. 4 kc + 3
-    const int n = i >> 1, kc = i & 1;
-    const unsigned* w = W1p + n * 8 + 4 * kc;
-    *reinterpret_cast<uint4*>(S.B1 + chunk_off(n, kc, 2)) = make_uint4(w[0], w[1], w[2], w[3]);
-  }
-  for (int i = tid; i < 64 * 8; i += 128) {
+  // operands that do not change, in the K-major core-matrix layout: halved weights from the
+  // fp32 master (the same bf16 values, halved, as the packed copies of the other kernels),
+  // halved biases split in three, and the columns of ones that multiply them
+  for (int i = tid; i < 64 * 8; i += 128) {  // W2 / 2: row n, chunk kc = inputs 8 kc .. 8 kc + 7
     const int n = i >> 3, kc = i & 7;
-    const unsigned* w = W2p + n * 32 + 4 * kc;
-    *reinterpret_cast<uint4*>(S.B2 + chunk_off(n, kc, 8)) = make_uint4(w[0], w[1], w[2], w[3]);
+    alignas(16) uint16_t e[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) e[k] = bf16_bits(0.5f * P[kTcOW2 + n * kTcH + 8 * kc + k]);
+    *reinterpret_cast<uint4*>(S.B2 + chunk_off(n, kc, 8)) = *reinterpret_cast<const uint4*>(e);
   }
   if (tid < kTcH) {
-    S.hb1[tid] = 0.5f * P[kTcOb1 + tid];
-    S.hb2[tid] = 0.5f * P[kTcOb2 + tid];
-    S.w3[tid] = P[kTcOw3 + tid];
+    const int n = tid;
+    alignas(16) uint16_t e[16] = {};
+    uint16_t hb[3];
+#pragma unroll
+    for (int k = 0; k < kTcIn; ++k) e[k] = bf16_bits(0.5f * P[n * kTcIn + k]);
+    split3(0.5f * P[kTcOb1 + n], hb);
+    e[9] = hb[0], e[10] = hb[1], e[11] = hb[2];
+    *reinterpret_cast<uint4*>(S.B1 + chunk_off(n, 0, 2)) = *reinterpret_cast<const uint4*>(e);
+    *reinterpret_cast<uint4*>(S.B1 + chunk_off(n, 1, 2)) = *reinterpret_cast<const uint4*>(e + 8);
+    split3(0.5f * P[kTcOb2 + n], hb);
+    *reinterpret_cast<uint4*>(S.B2b + chunk_off(n, 0, 2)) = make_uint4(hb[0] | (uint32_t)hb[1] << 16, hb[2], 0u, 0u);
+    *reinterpret_cast<uint4*>(S.B2b + chunk_off(n, 1, 2)) = make_uint4(0u, 0u, 0u, 0u);
+    S.w3[n] = P[kTcOw3 + n];
   }
+  // A2b: ones in columns 0..2 of every row
+  *reinterpret_cast<uint4*>(S.A2b + chunk_off(tid, 0, 2)) = make_uint4(0x3F803F80u, 0x3F80u, 0u, 0u);
+  *reinterpret_cast<uint4*>(S.A2b + chunk_off(tid, 1, 2)) = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     S.abort = 0;
     umma::mbar_init(&S.mbar, 1);
@@ -107,8 +135,8 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
   const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
   const float b3 = P[kTcOb3], scale = norm[2 * kTcIn];
   constexpr uint32_t idesc = umma::idesc_bf16_f32(128, 64);
-  const uint32_t a1 = umma::smem_u32(S.A1), a2 = umma::smem_u32(S.A2), bw1 = umma::smem_u32(S.B1),
-                 bw2 = umma::smem_u32(S.B2);
+  const uint32_t a1 = umma::smem_u32(S.A1), a2 = umma::smem_u32(S.A2), a2b = umma::smem_u32(S.A2b),
+                 bw1 = umma::smem_u32(S.B1), bw2 = umma::smem_u32(S.B2), bw2b = umma::smem_u32(S.B2b);
   // the pair buffer holds at most pcap pairs: a count beyond it (an overflow the feature
   // kernel has reported) is clamped so that no tile reads past the buffer
   const long long np = min((long long)*npair, pcap);
@@ -131,7 +159,8 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
     umma::bulk_g2s(S.in[j % 3].slot, pslot + p0, bs, mb);
     issued = j + 1;
   };
-  // inputs of tile j's row tid: pair p0 + (tid & 63), ordering tid >> 6 (words 5u .. 5u + 4)
+  // inputs of tile j's row tid: pair p0 + (tid & 63), ordering tid >> 6 (words 5u .. 5u + 4),
+  // then ones in columns 9..11 (the bias terms of W1's chunk 1)
   auto stage_inputs = [&](long long j) {
     if (umma::mbar_wait(&S.mbin[j % 3], (uint32_t)((j / 3) & 1), kWaitPolls))
       landed = j + 1;
@@ -139,11 +168,11 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
       atomicExch(&S.abort, 1);
     const long long p = ((long long)blockIdx.x + j * gridDim.x) * 64 + (tid & 63);
     const int u = tid >> 6;
-    uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0u, 0u, 0u, 0u);
+    uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0x3F800000u, 0x3F803F80u, 0u, 0u);
     if (p < np) {
       const unsigned* r = S.in[j % 3].frag + (tid & 63) * 10 + 5 * u;
       c0 = make_uint4(r[0], r[1], r[2], r[3]);
-      c1.x = r[4];
+      c1.x |= r[4] & 0xFFFFu;
     }
     *reinterpret_cast<uint4*>(S.A1 + chunk_off(tid, 0, 2)) = c0;
     *reinterpret_cast<uint4*>(S.A1 + chunk_off(tid, 1, 2)) = c1;
@@ -191,8 +220,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
       umma::ld32(tmem + lane_base + 32 * half, z);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const int j = 32 * half + 8 * c;
-        const auto act = [&](int k) { return silu_half(fmaf(0.5f, z[8 * c + k], S.hb1[j + k])); };
+        const auto act = [&](int k) { return silu_half(z[8 * c + k]); };
         const uint4 q = make_uint4(pack2(act(0), act(1)), pack2(act(2), act(3)), pack2(act(4), act(5)),
                                    pack2(act(6), act(7)));
         *reinterpret_cast<uint4*>(S.A2 + chunk_off(tid, 4 * half + c, 8)) = q;
@@ -207,6 +235,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
       for (int kk = 0; kk < 4; ++kk)
         umma::mma_bf16(tmem + 64, umma::desc(a2 + 256 * kk, 128, 1024), umma::desc(bw2 + 256 * kk, 128, 1024), idesc,
                        kk > 0 ? 1u : 0u);
+      umma::mma_bf16(tmem + 64, umma::desc(a2b, 128, 256), umma::desc(bw2b, 128, 256), idesc, 1u);
       if (has_next) umma::mma_bf16(tmem, umma::desc(a1, 128, 256), umma::desc(bw1, 128, 256), idesc, 0u);
       umma::commit(&S.mbar);
     }
@@ -218,10 +247,7 @@ __global__ void __launch_bounds__(128, 4) k_mlp_eval_tc(const float* __restrict_
       float z[32];
       umma::ld32(tmem + lane_base + 64 + 32 * half, z);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        const int j = 32 * half + c;
-        acc = fmaf(S.w3[j], silu_half(fmaf(0.5f, z[c], S.hb2[j])), acc);
-      }
+      for (int c = 0; c < 32; ++c) acc = fmaf(S.w3[32 * half + c], silu_half(z[c]), acc);
     }
     S.y[tid] = acc + b3;
     __syncthreads();
@@ -261,7 +287,7 @@ cudaError_t launch_mlp_eval_tc(const Sys& s, const MlpDevArgs& a, const Bufs& b,
     // columns = all 512; two or three per SM were 20 and 7 us slower per evaluation
     grid = 4 * sms;
   }
-  k_mlp_eval_tc<<<grid, 128, 0, st>>>(a.P, a.W1p, a.W2p, a.norm, b.pfrag, b.pslot, b.npair, b.pcap,
+  k_mlp_eval_tc<<<grid, 128, 0, st>>>(a.P, a.norm, b.pfrag, b.pslot, b.npair, b.pcap,
                                        (long long)s.M * s.cap, b.wait_polls, fpair,
                                        b.ctrl);
   return cudaGetLastError();
