@@ -336,6 +336,10 @@ static adress_status setup_cells(adress_ctx* h, double skin) {
     if (e != cudaSuccess) return fail(h, ADRESS_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     h->ncell_cap = s.ncell;
   }
+  // the list build expects zero cell counters (it leaves them zero after each build)
+  e = cudaMemsetAsync(b.cell_count, 0, sizeof(int) * (size_t)s.ncell, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.cell_fill, 0, sizeof(int) * (size_t)s.ncell, h->stream);
+  if (e != cudaSuccess) return fail(h, ADRESS_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   b.cell_rank = h->cell_rank;
   b.cell_box = h->cell_box;
   b.nbr_cells = h->nbr_cells;

@@ -20,19 +20,14 @@ __device__ __forceinline__ int cell_of(unsigned int X, int nc) {
   return (int)(((unsigned long long)X * (unsigned long long)nc) >> 32);
 }
 
-__global__ void k_rb_zero(const __grid_constant__ Sys s, Bufs b) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+// Cell populations.  cell_count and cell_fill are zero on entry: zeroed when allocated and
+// again by k_rb_sortcell once this build no longer needs them.
+__global__ void k_rb_count(const __grid_constant__ Sys s, Bufs b) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a == 0) {
     b.ctrl->n_dense = 0;
     b.ctrl->force_rebuild = 0;
   }
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < s.ncell; c += gridDim.x * blockDim.x) {
-    b.cell_count[c] = 0;
-    b.cell_fill[c] = 0;
-  }
-}
-
-__global__ void k_rb_count(const __grid_constant__ Sys s, Bufs b) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= s.M) return;
   const Box& B = box_of(s, b, a);
   const int4 C = b.com_fx[b.ctrl->parity][a];
@@ -43,8 +38,24 @@ __global__ void k_rb_count(const __grid_constant__ Sys s, Bufs b) {
   atomicAdd(&b.cell_count[r], 1);
 }
 
-// ---- exclusive scan: tiles of 2048 ints, a single-block scan of tile sums, add back ----
+// ---- exclusive scan in two launches: tile sums, then every block adds up the sums of the
+// tiles before its own (at most kScanMaxTiles of them) and scans its tile ----
 
+constexpr int kScanMaxTiles = 4096;
+
+// Block-wide sum of v (every thread gets it).
+__device__ __forceinline__ int block_sum(int v) {
+  __shared__ int part[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = __reduce_add_sync(0xffffffffu, v);
+  __syncthreads();  // part[] may still be read by a previous call
+  if (lane == 0) part[w] = v;
+  __syncthreads();
+  int s = lane < (int)(blockDim.x >> 5) ? part[lane] : 0;
+  return __reduce_add_sync(0xffffffffu, s);
+}
+
+// Block-wide exclusive scan of v; *total gets the block's sum.
 __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
   __shared__ int warp_sums[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -73,11 +84,24 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
   return excl;
 }
 
-// Correct block_exclusive_scan's use of slot 31: the warp-0 pass stores exclusive sums in
-// slots 0..nw-1 and the total in slot 31; with 512 threads nw = 16 <= 31, so they never clash.
+// The warp-0 pass stores exclusive sums in slots 0..nw-1 and the total in slot 31; with 512
+// threads nw = 16 <= 31, so they never clash.
 static_assert(kScanThreads / 32 < 32, "scan block too large");
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int* in, int* out, int* tile_sums, int n) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const int* in, int* tile_sums, int n) {
+  const int base = blockIdx.x * kScanTile + threadIdx.x * kScanEPT;
+  int sum = 0;
+#pragma unroll
+  for (int e = 0; e < kScanEPT; ++e) sum += (base + e < n) ? in[base + e] : 0;
+  sum = block_sum(sum);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = sum;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const int* in, int* out, const int* tile_sums, int n,
+                                                             int* grand) {
+  int before = 0;
+  for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) before += tile_sums[k];
+  before = block_sum(before);
   const int base = blockIdx.x * kScanTile + threadIdx.x * kScanEPT;
   int v[kScanEPT], sum = 0;
 #pragma unroll
@@ -86,61 +110,20 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const int* in, int*
     sum += v[e];
   }
   int total;
-  int run = block_exclusive_scan(sum, &total);
+  int run = before + block_exclusive_scan(sum, &total);
 #pragma unroll
   for (int e = 0; e < kScanEPT; ++e) {
     if (base + e < n) out[base + e] = run;
     run += v[e];
   }
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
-}
-
-// One block: exclusive scan of up to 1024*4 tile sums in place; total -> *grand.
-__global__ void __launch_bounds__(1024) k_scan_top(int* tile_sums, int ntiles, int* grand) {
-  const int base = threadIdx.x * 4;
-  int v[4], sum = 0;
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    v[e] = (base + e < ntiles) ? tile_sums[base + e] : 0;
-    sum += v[e];
-  }
-  __shared__ int ws[32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int incl = sum;
-  for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) ws[w] = incl;
-  __syncthreads();
-  if (w == 0) {
-    int x = ws[lane], xi = x;
-    for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, xi, o);
-      if (lane >= o) xi += t;
-    }
-    ws[lane] = xi - x;
-    if (lane == 31) *grand = xi;
-  }
-  __syncthreads();
-  int run = incl - sum + ws[w];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    if (base + e < ntiles) tile_sums[base + e] = run;
-    run += v[e];
-  }
-}
-
-__global__ void k_scan_add(int* out, const int* tile_sums, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] += tile_sums[i / kScanTile];
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *grand = before + total;
 }
 
 static cudaError_t exclusive_scan(const int* in, int* out, int n, int* tmp, int* total, cudaStream_t st) {
-  const int ntiles = ceil_div(n, kScanTile);
-  k_scan_tiles<<<ntiles, kScanThreads, 0, st>>>(in, out, tmp, n);
-  k_scan_top<<<1, 1024, 0, st>>>(tmp, ntiles, total);
-  k_scan_add<<<ceil_div(n, 256), 256, 0, st>>>(out, tmp, n);
+  const int ntiles = std::max(1, ceil_div(n, kScanTile));
+  if (ntiles > kScanMaxTiles) return cudaErrorInvalidValue;
+  k_scan_sums<<<ntiles, kScanThreads, 0, st>>>(in, tmp, n);
+  k_scan_apply<<<ntiles, kScanThreads, 0, st>>>(in, out, tmp, n, total);
   return cudaGetLastError();
 }
 
@@ -154,41 +137,32 @@ __global__ void k_rb_fill(const __grid_constant__ Sys s, Bufs b) {
 
 // Each molecule's position in its cell is the number of the cell's members with a smaller
 // id (ids are distinct), so every cell's slice of `sorted` is in increasing id.  One thread
-// per molecule.
+// per molecule; the molecule's high-resolution flag goes to the same position.  The cell
+// counters, no longer needed by this build, are zeroed for the next one.
 __global__ void k_rb_sortcell(const __grid_constant__ Sys s, Bufs b) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int c = p; c < s.ncell; c += gridDim.x * blockDim.x) {
+    b.cell_count[c] = 0;
+    b.cell_fill[c] = 0;
+  }
   if (p >= s.M) return;
-  const int a = b.fill_tmp[p];
+  const int a = b.fill_tmp[p], cur = b.ctrl->parity;
   const int r = b.mcell[a];
   const int ps = b.cell_start[r], pe = b.cell_start[r + 1];
   int rank = 0;
   for (int q = ps; q < pe; ++q) rank += b.fill_tmp[q] < a;
   b.sorted[ps + rank] = a;
-  b.scom[ps + rank] = b.com_fx[b.ctrl->parity][a];
-}
-
-__global__ void k_rb_flag(const __grid_constant__ Sys s, Bufs b) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= s.M) return;
-  const int a = b.sorted[k], cur = b.ctrl->parity;
+  b.scom[ps + rank] = b.com_fx[cur][a];
   const double d = s.fp64 ? fabs(b.dxc64[cur][a]) : (double)fabsf(b.molf[cur][a].x);
-  if (s.lam_uniform_on) b.flag[k] = s.lam_uniform > 0.0 ? 1 : 0;
-  else b.flag[k] = d < box_of(s, b, a).d_hr + (s.fp64 ? 0.0 : 1e-3) ? 1 : 0;
+  if (s.lam_uniform_on) b.flag[ps + rank] = s.lam_uniform > 0.0 ? 1 : 0;
+  else b.flag[ps + rank] = d < box_of(s, b, a).d_hr + (s.fp64 ? 0.0 : 1e-3) ? 1 : 0;
 }
 
-__global__ void k_rb_items(const __grid_constant__ Sys s, Bufs b) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n_hr = b.pos[s.M];
-  if (k == 0) {
-    b.ctrl->n_hr = n_hr;
-    b.ctrl->n_cg = s.M - n_hr;
-  }
-  if (k >= s.M) return;
-  const int a = b.sorted[k];
+// Work item of the molecule at sorted position k: high-resolution items first, then
+// coarse-grained ones, each in sorted order (pos = exclusive scan of the flags).
+__device__ __forceinline__ int item_at(const Sys& s, const Bufs& b, int k) {
   const int p = b.pos[k];
-  const int t = b.flag[k] ? p : n_hr + (k - p);
-  b.items[t] = a;
-  b.item_of[a] = t;
+  return b.flag[k] ? p : b.pos[s.M] + (k - p);
 }
 
 // One warp per cell (cells in Morton order).  Lanes 0..26 take the 27 neighbour cells in
@@ -222,6 +196,12 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
   const int pre = incl - cnt;
   const int total = __shfl_sync(0xffffffffu, incl, 31);
   const int n_home = __shfl_sync(0xffffffffu, cnt, 13);
+  const int home_start = __shfl_sync(0xffffffffu, start, 13);
+  if (r == 0 && lane == 0) {
+    const int n_hr = b.pos[s.M];
+    b.ctrl->n_hr = n_hr;
+    b.ctrl->n_cg = s.M - n_hr;
+  }
   if (n_home == 0) return;
   if (total > kMaxCand || n_home > 32) {
     if (lane == 0) b.dense_cells[atomicAdd(&b.ctrl->n_dense, 1)] = r;
@@ -232,9 +212,14 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
     stage[w][pre + q] = make_int4(C.x, C.y, C.z, b.sorted[start + q]);
   }
   __syncwarp();
-  // the home cell is neighbour 13: its molecules and their work items
+  // the home cell is neighbour 13: its molecules and their work items, recorded here
   const int home_pre = __shfl_sync(0xffffffffu, pre, 13);
-  const int my_item = lane < n_home ? b.item_of[stage[w][home_pre + lane].w] : 0;
+  const int my_item = lane < n_home ? item_at(s, b, home_start + lane) : 0;
+  if (lane < n_home) {
+    const int a = stage[w][home_pre + lane].w;
+    b.items[my_item] = a;
+    b.item_of[a] = my_item;
+  }
   const float rl2 = (float)s.r_list2;
   for (int h = 0; h < n_home; ++h) {
     const int4 H = stage[w][home_pre + h];
@@ -314,9 +299,12 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
       for (int h = lane; h < nh; h += 32) {
         const int a = b.sorted[home_start + hb + h];
         const int4 C = com[a];
+        const int it = item_at(s, b, home_start + hb + h);
         home[w][h] = make_int4(C.x, C.y, C.z, a);
-        hitem[w][h] = b.item_of[a];
+        hitem[w][h] = it;
         hcnt[w][h] = 0;
+        b.items[it] = a;
+        b.item_of[a] = it;
       }
       for (int c0 = 0; c0 < total; c0 += kMaxCand) {
         __syncwarp();
@@ -420,16 +408,13 @@ cudaError_t device_exclusive_scan(const int* in, int* out, int n, int* tmp, int*
 
 cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st) {
   cudaError_t e;
-  k_rb_zero<<<ceil_div(s.ncell, 256) < 1024 ? ceil_div(s.ncell, 256) : 1024, 256, 0, st>>>(s, b);
   k_rb_count<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   if ((e = exclusive_scan(b.cell_count, b.cell_start, s.ncell, b.scan_tmp, b.cell_start + s.ncell, st)) !=
       cudaSuccess)
     return e;
   k_rb_fill<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   k_rb_sortcell<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
-  k_rb_flag<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   if ((e = exclusive_scan(b.flag, b.pos, s.M, b.scan_tmp, b.pos + s.M, st)) != cudaSuccess) return e;
-  k_rb_items<<<ceil_div(s.M, 256), 256, 0, st>>>(s, b);
   k_rb_nbr<<<ceil_div(s.ncell, kNbrWarps), 32 * kNbrWarps, 0, st>>>(s, b);
   k_rb_nbr_dense<<<std::min(ceil_div((long long)s.ncell * kHomeParts, kNbrWarps), 152 * 16), 32 * kNbrWarps, 0, st>>>(s, b);
   if (s.cg_mode && b.mirror) return launch_mirror(s, b, st);
