@@ -172,7 +172,7 @@ __device__ __forceinline__ int item_at(const Sys& s, const Bufs& b, int k) {
 // appends its neighbours in candidate order with ballot/popc compaction.  A cell with more
 // than kMaxCand candidates or 32 molecules is passed to k_rb_nbr_dense.
 constexpr int kNbrWarps = 4;
-constexpr int kMaxCand = 256;  // candidates staged at once
+constexpr int kMaxCand = 160;  // candidates staged at once (4 warps: 10 KB, 16 blocks per SM)
 __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant__ Sys s, Bufs b) {
   __shared__ int4 stage[kNbrWarps][kMaxCand];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;

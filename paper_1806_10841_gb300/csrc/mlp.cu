@@ -772,6 +772,8 @@ __device__ __forceinline__ bool needs_network(const Sys& s, const Box& X, const 
   }
 }
 
+constexpr int kFeatLanes = 4;  // lanes per work item in k_mlp_feat (a power of two <= 32)
+
 template <int NA, bool F64>
 __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s, Bufs b, const float* __restrict__ norm) {
   // multiple time stepping: the network gives a slow (CG) force, needed only at outer time
@@ -784,10 +786,10 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
     sn[1][threadIdx.x] = norm[2 * kIn + 1 + threadIdx.x];
   }
   __syncthreads();
-  // four lanes per work item, lane g taking list slots g, g + 4, ...; one walk of the list
-  // tests every slot and marks the selected ones in sel (bit j for slot g + 4 j; slots past
-  // bit 31 are tested again when their features are formed)
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2, g = threadIdx.x & 3;
+  // kFeatLanes lanes per work item, lane g taking list slots g, g + kFeatLanes, ...; one walk
+  // of the list tests every slot and marks the selected ones in sel (bit j for slot
+  // g + kFeatLanes j; slots past bit 31 are tested again when their features are formed)
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) / kFeatLanes, g = threadIdx.x & (kFeatLanes - 1);
   const int lane = threadIdx.x & 31;
   const bool live = t < s.M;
   const int cur = b.ctrl->parity;
@@ -798,7 +800,7 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
   const int* row = b.nbr + (size_t)t * s.cap;
   unsigned sel = 0u;
   int cnt = 0;
-  for (int q = g, j = 0; q < n; q += 4, ++j) {
+  for (int q = g, j = 0; q < n; q += kFeatLanes, ++j) {
     const int m = row[q];
     if (m > a && needs_network<F64>(s, X, b, cur, CA, m)) {
       ++cnt;
@@ -816,20 +818,20 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
   base = __shfl_sync(0xffffffffu, base, 31);
   long long p = (long long)base + (incl - cnt);
   if (cnt == 0) return;
-  int qx = g + 128;  // where the search for selected slots beyond the mask resumes
+  int qx = g + 32 * kFeatLanes;  // where the search for selected slots beyond the mask resumes
   for (int left = cnt; left > 0; --left) {
     int q, m = -1;
     if (sel) {
-      q = g + 4 * (__ffs(sel) - 1);
+      q = g + kFeatLanes * (__ffs(sel) - 1);
       sel &= sel - 1;
       m = row[q];
     } else {
-      for (q = qx; q < n; q += 4) {
+      for (q = qx; q < n; q += kFeatLanes) {
         m = row[q];
         if (m > a && needs_network<F64>(s, X, b, cur, CA, m)) break;
       }
       if (q >= n) return;  // not reached: the first walk counted this slot
-      qx = q + 4;
+      qx = q + kFeatLanes;
     }
     if (p >= b.pcap) {
       set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, (int)p);
@@ -1118,7 +1120,7 @@ cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* f
   const MlpDev m{a.P, a.W1p, a.W2p, a.W2Tp, a.norm};
   cudaError_t e = cudaMemsetAsync(b.npair, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  const int blocks = ceil_div((long long)s.M * 4, 128);
+  const int blocks = ceil_div((long long)s.M * kFeatLanes, 128);
 #define FEAT(NA_)                                                       \
   (s.fp64 ? k_mlp_feat<NA_, true><<<blocks, 128, 0, st>>>(s, b, a.norm) \
           : k_mlp_feat<NA_, false><<<blocks, 128, 0, st>>>(s, b, a.norm))

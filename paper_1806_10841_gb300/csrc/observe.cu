@@ -16,6 +16,10 @@ namespace adress {
 // just written becomes current; the maxima are reset for the next mapping.
 __global__ void k_decide(const __grid_constant__ Sys s, Bufs b, DecideArgs da) {
   static_assert(kExtSlots == 32, "one slot per lane");
+  // launched as a programmatic dependent of the mapping kernel: its launch overlaps the
+  // mapping's last blocks, and this wait returns once that grid has completed and its
+  // writes are visible
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   Ctrl* c = b.ctrl;
   const int l = threadIdx.x;
   const unsigned me = __reduce_max_sync(0xffffffffu, c->ext_slot[0][l]);
@@ -37,8 +41,16 @@ __global__ void k_decide(const __grid_constant__ Sys s, Bufs b, DecideArgs da) {
 }
 
 cudaError_t launch_decide(const Sys& s, const Bufs& b, DecideArgs da, cudaStream_t st) {
-  k_decide<<<1, 32, 0, st>>>(s, b, da);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1);
+  cfg.blockDim = dim3(32);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_decide, s, b, da);
 }
 
 // ---- deterministic FP64 reductions: per-block partials, then one fixed-order block ----

@@ -437,8 +437,13 @@ __device__ __forceinline__ void publish_extent(const Bufs& b, float ext2, float 
 
 // ---------------- k_map / k_prologue ---------------------------------------------------
 
+// The decide kernel that follows a mapping kernel may be scheduled once every block of the
+// mapping has started (it waits for the mapping grid's completion itself).
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 template <class P, int NA, bool INTEGRATE, bool MULTI>
 __global__ void __launch_bounds__(kMaxForceBlock) k_prologue(const __grid_constant__ Sys s, Bufs b) {
+  allow_dependent_launch();
   const int lane = threadIdx.x & 31, g = threadIdx.x & 3, base = lane & ~3;
   const unsigned gmask = 0xFu << base;
   const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 2;
@@ -488,6 +493,7 @@ template <class P, int NA, int MODE, bool ENERGY, bool MULTI, int MODEL, bool HS
 __global__ void __launch_bounds__(kMaxForceBlock, step_min_blocks<P, MODEL, MULTI>()) k_step(const __grid_constant__ Sys s, Bufs b) {
   using Q = Prec<P>;
   using real = typename Q::real;
+  if (MODE == MODE_FUSED) allow_dependent_launch();
   const int lane = threadIdx.x & 31, g = threadIdx.x & 3, base = lane & ~3;
   const unsigned gmask = 0xFu << base;
   // SPLIT > 1 (water): a high-resolution item takes SPLIT groups of four lanes in the same
