@@ -314,6 +314,7 @@ static adress_status setup_cells(adress_ctx* h, double skin) {
   s.skin = skin;
   s.r_list = r_list;
   s.r_list2 = r_list * r_list;
+  s.r_cg_list2 = (s.rc_cg + skin) * (s.rc_cg + skin);
   s.ncell = (int)total;
   // energy interpolation: a molecule within r_list of the hybrid layer may pair with a
   // hybrid one (weight (l_a + l_b)/2 > 0), so it is a high-resolution item too

@@ -98,6 +98,9 @@ struct Sys {
   unsigned long long seed;
   unsigned seed_lo, seed_hi;
   double skin, r_ext, r_list, r_list2, reach_at2;  // reach_at: rc_at + 2 r_ext
+  // (rc_cg + skin)^2: list cutoff of pairs with a coarse-grained work item (weight 0 until
+  // the next build, so only the CG force acts); pairs of two high-resolution items use r_list
+  double r_cg_list2;
   double rc_at, rc_cg;
   int ncell;  // cells of all boxes
   int cap;  // neighbour-list capacity per molecule

@@ -4,7 +4,14 @@
 // molecules are counting-sorted by cell and each cell's members are then put in id order,
 // so every list is deterministic; molecules are split into two work lists — high-resolution
 // candidates (|dxc| < d_at + d_hy + skin/2) first, then coarse-grained molecules —
-// and each work item gets a full Verlet list of molecules within r_list.
+// and each work item gets a full Verlet list: partners within r_list when both are
+// high-resolution items, within rc_cg + skin when either is coarse-grained (such a pair has
+// weight 0 until the next build, so only the CG force, cut at rc_cg, acts between them;
+// the lists stay symmetric).
+
+// Staged candidate: centre + (molecule id | high-resolution flag in bit 31).
+__device__ __forceinline__ int tag_id(int id, int hr) { return (int)((unsigned)id | ((unsigned)hr << 31)); }
+__device__ __forceinline__ int id_of(int w) { return w & 0x7fffffff; }
 #include <algorithm>
 
 #include "internal.cuh"
@@ -209,21 +216,21 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
   }
   for (int q = 0; q < cnt; ++q) {
     const int4 C = b.scom[start + q];
-    stage[w][pre + q] = make_int4(C.x, C.y, C.z, b.sorted[start + q]);
+    stage[w][pre + q] = make_int4(C.x, C.y, C.z, tag_id(b.sorted[start + q], b.flag[start + q]));
   }
   __syncwarp();
   // the home cell is neighbour 13: its molecules and their work items, recorded here
   const int home_pre = __shfl_sync(0xffffffffu, pre, 13);
   const int my_item = lane < n_home ? item_at(s, b, home_start + lane) : 0;
   if (lane < n_home) {
-    const int a = stage[w][home_pre + lane].w;
+    const int a = id_of(stage[w][home_pre + lane].w);
     b.items[my_item] = a;
     b.item_of[a] = my_item;
   }
-  const float rl2 = (float)s.r_list2;
+  const float rl2 = (float)s.r_list2, rcl2 = (float)s.r_cg_list2;
   for (int h = 0; h < n_home; ++h) {
     const int4 H = stage[w][home_pre + h];
-    const int a = H.w;
+    const int a = id_of(H.w);
     const int t = __shfl_sync(0xffffffffu, my_item, h);
     int count = 0;
     for (int k0 = 0; k0 < total; k0 += 32) {
@@ -232,11 +239,11 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
       int m = 0;
       if (k < total) {
         const int4 D = stage[w][k];
-        m = D.w;
+        m = id_of(D.w);
         const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * B.fx_scale[0];
         const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * B.fx_scale[1];
         const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * B.fx_scale[2];
-        hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < rl2;
+        hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < ((H.w & D.w) < 0 ? rl2 : rcl2);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, hit);
       if (hit) {
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const int n_home = __shfl_sync(0xffffffffu, cnt, 13);
     const int home_start = __shfl_sync(0xffffffffu, start, 13);
-    const float rl2 = (float)s.r_list2;
+    const float rl2 = (float)s.r_list2, rcl2 = (float)s.r_cg_list2;
     for (int hb = part * kMaxHome; hb < n_home; hb += kHomeParts * kMaxHome) {
       const int nh = min(kMaxHome, n_home - hb);
       __syncwarp();
@@ -300,7 +307,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
         const int a = b.sorted[home_start + hb + h];
         const int4 C = com[a];
         const int it = item_at(s, b, home_start + hb + h);
-        home[w][h] = make_int4(C.x, C.y, C.z, a);
+        home[w][h] = make_int4(C.x, C.y, C.z, tag_id(a, b.flag[home_start + hb + h]));
         hitem[w][h] = it;
         hcnt[w][h] = 0;
         b.items[it] = a;
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
 #pragma unroll 1
           for (int k = lo; k < hi; ++k) {
             const int4 C = b.scom[start + (k - pre)];
-            stage[w][k - c0] = make_int4(C.x, C.y, C.z, b.sorted[start + (k - pre)]);
+            stage[w][k - c0] = make_int4(C.x, C.y, C.z, tag_id(b.sorted[start + (k - pre)], b.flag[start + (k - pre)]));
           }
         }
         __syncwarp();
@@ -322,7 +329,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
 #pragma unroll 1
         for (int h = 0; h < nh; ++h) {
           const int4 H = home[w][h];
-          const int a = H.w;
+          const int a = id_of(H.w);
           const int tt = hitem[w][h];
           int count = hcnt[w][h];
           for (int k0 = 0; k0 < nc; k0 += 32) {
@@ -331,11 +338,11 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
             int m = 0;
             if (k < nc) {
               const int4 D = stage[w][k];
-              m = D.w;
+              m = id_of(D.w);
               const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * B.fx_scale[0];
               const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * B.fx_scale[1];
               const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * B.fx_scale[2];
-              hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < rl2;
+              hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < ((H.w & D.w) < 0 ? rl2 : rcl2);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, hit);
             if (hit) {
@@ -354,7 +361,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
         const int count = hcnt[w][h];
         const int tt = hitem[w][h];
         b.nn[tt] = count < s.cap ? count : s.cap;
-        b.com_ref[H.w] = make_int4(H.x, H.y, H.z, 0);
+        b.com_ref[id_of(H.w)] = make_int4(H.x, H.y, H.z, 0);
         if (count > s.cap) set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, count);
       }
     }

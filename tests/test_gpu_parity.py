@@ -357,25 +357,37 @@ def test_run_block_matches_oracle_sequence(precision):
     assert ns == 0 and not counts_g.any()  # reset by the update
 
 
-def test_neighbour_lists_are_complete_and_exact():
-    """Every molecule pair within the list cutoff is listed (both directions), no pair beyond it."""
-    s, x, v, f, e = case("hybrid_216")
+@pytest.mark.parametrize("name", ["hybrid_216", "c1_stable"])
+def test_neighbour_lists_are_complete_and_exact(name):
+    """Every molecule pair within its list cutoff is listed (both directions), no pair beyond
+    it: r_list = max(rc_cg, rc_at + 2 r_ext) + skin between two high-resolution work items,
+    rc_cg + skin when either is a coarse-grained item (weight 0 until the next build)."""
+    s, x, v, f, e = case(name)
     sim = gpu(s, "fp64")
     sim.set_state(x)
     sim.build_lists()
     st = sim.list_stats()
+    items, _, _ = sim.neighbour_lists()
+    hr = np.zeros(s.M, dtype=bool)
+    hr[items[:st["n_hr"]]] = True
+    assert 0 < st["n_hr"] < s.M  # both kinds present
     com, _ = sim.com_lambda()
     L = np.array(s.box)
     d = com[:, None, :] - com[None, :, :]
     d -= L * np.rint(d / L)
     r = np.sqrt((d ** 2).sum(-1))
     r_list = max(s.rc_cg, s.rc_at + 2 * s.r_ext) + s.skin
-    expect = {(a, b_) for a in range(s.M) for b_ in range(s.M) if a != b_ and r[a, b_] < r_list - 1e-6}
-    maybe = {(a, b_) for a in range(s.M) for b_ in range(s.M) if a != b_ and abs(r[a, b_] - r_list) <= 1e-6}
+    cut = np.where(hr[:, None] & hr[None, :], r_list, s.rc_cg + s.skin)
+    assert r_list > s.rc_cg + s.skin  # the two cutoffs differ in this geometry
+    off = ~np.eye(s.M, dtype=bool)
+    expect = {(int(a), int(b_)) for a, b_ in zip(*np.nonzero(off & (r < cut - 1e-6)))}
+    maybe = {(int(a), int(b_)) for a, b_ in zip(*np.nonzero(off & (np.abs(r - cut) <= 1e-6)))}
     assert st["max_nn"] <= st["capacity"]
     assert expect  # non-trivial
     got = sim.neighbour_pairs()
     assert expect <= got and got <= expect | maybe
+    # symmetric: the mirror slots of the network force rely on it
+    assert {(b_, a) for a, b_ in got} == got
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

@@ -93,7 +93,8 @@ def test_water_trajectory_follows_oracle(precision):
 
 def test_water_lists_are_complete():
     """Dense cells (~70 molecules, ~2000 candidates per neighbourhood) and, with a wide skin,
-    cells of more than 128 molecules (home molecules in batches)."""
+    cells of more than 128 molecules (home molecules in batches).  Cutoff r_list between two
+    high-resolution work items, rc_cg + skin when either is coarse-grained."""
     from paper_1806_10841_gb300 import adress
 
     for skin, M in ((0.1, 3000), (0.8, 8000)):
@@ -106,14 +107,19 @@ def test_water_lists_are_complete():
         L = np.array(s.box)
         r_list = max(s.rc_cg, s.rc_at + 2 * s.r_ext) + s.skin
         items, nn, nbr = sim.neighbour_lists()
+        n_hr = sim.list_stats()["n_hr"]
+        hr = np.zeros(s.M, dtype=bool)
+        hr[items[:n_hr]] = True
+        assert 0 < n_hr < s.M
         for t in range(s.M):
             a = int(items[t])
             d = com - com[a]
             d -= L * np.rint(d / L)
             r = np.sqrt((d ** 2).sum(1))
             r[a] = np.inf
-            expect = np.nonzero(r < r_list - 1e-6)[0]
-            maybe = np.nonzero(np.abs(r - r_list) <= 1e-6)[0]
+            cut = np.where(hr & hr[a], r_list, s.rc_cg + s.skin)
+            expect = np.nonzero(r < cut - 1e-6)[0]
+            maybe = np.nonzero(np.abs(r - cut) <= 1e-6)[0]
             got = np.sort(nbr[t, :nn[t]])
             assert len(np.unique(got)) == len(got)
             assert len(np.setdiff1d(expect, got)) == 0, (skin, M, a)
