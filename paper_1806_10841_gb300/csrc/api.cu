@@ -315,6 +315,8 @@ static adress_status setup_cells(adress_ctx* h, double skin) {
   s.r_list = r_list;
   s.r_list2 = r_list * r_list;
   s.r_cg_list2 = (s.rc_cg + skin) * (s.rc_cg + skin);
+  s.f.r_list2 = (float)s.r_list2;
+  s.f.r_cg_list2 = (float)s.r_cg_list2;
   s.ncell = (int)total;
   // energy interpolation: a molecule within r_list of the hybrid layer may pair with a
   // hybrid one (weight (l_a + l_b)/2 > 0), so it is a high-resolution item too

@@ -143,6 +143,7 @@ struct Sys {
     float c12[kMaxNA][kMaxNA], c6[kMaxNA][kMaxNA], qq[kMaxNA][kMaxNA];
     float krf2, bond_k, bond_r0, angle_k, angle_theta0;
     float vsh[kMaxNA][kMaxNA], krf, crf, fec_scale, lam_uniform;
+    float r_list2, r_cg_list2;  // the list cutoffs, for the list build
   } f;
 };
 static_assert(sizeof(Sys) <= 4096, "Sys is passed by value as a kernel parameter");

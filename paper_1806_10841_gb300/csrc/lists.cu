@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
     b.items[my_item] = a;
     b.item_of[a] = my_item;
   }
-  const float rl2 = (float)s.r_list2, rcl2 = (float)s.r_cg_list2;
+  const float rl2 = s.f.r_list2, rcl2 = s.f.r_cg_list2;
   for (int h = 0; h < n_home; ++h) {
     const int4 H = stage[w][home_pre + h];
     const int a = id_of(H.w);
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const int n_home = __shfl_sync(0xffffffffu, cnt, 13);
     const int home_start = __shfl_sync(0xffffffffu, start, 13);
-    const float rl2 = (float)s.r_list2, rcl2 = (float)s.r_cg_list2;
+    const float rl2 = s.f.r_list2, rcl2 = s.f.r_cg_list2;
     for (int hb = part * kMaxHome; hb < n_home; hb += kHomeParts * kMaxHome) {
       const int nh = min(kMaxHome, n_home - hb);
       __syncwarp();
