@@ -172,6 +172,33 @@ __device__ __forceinline__ int item_at(const Sys& s, const Bufs& b, int k) {
   return b.flag[k] ? p : b.pos[s.M] + (k - p);
 }
 
+// Stage candidates c0 .. c0 + nc - 1 of a 27-cell neighbourhood into st[0 .. nc): lane c < 27
+// holds neighbour cell c's first sorted position `start`, its offset `pre` in the candidate
+// list and the inclusive prefix `incl`.  All lanes copy, 32 candidates at a time; a lane finds
+// the cell of its candidate k as the number of cells whose inclusive prefix is <= k (binary
+// lifting over the monotone prefixes, five shuffles).
+__device__ __forceinline__ void stage_window(const Bufs& b, int lane, int incl, int pre, int start, int c0, int nc,
+                                             int4* st) {
+  for (int k0 = 0; k0 < nc; k0 += 32) {
+    const int k = c0 + k0 + lane;
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+      const int probe = lo + step - 1;
+      const int v = __shfl_sync(0xffffffffu, incl, probe < 27 ? probe : 26);
+      if (probe < 27 && v <= k) lo += step;
+    }
+    const int c = lo < 27 ? lo : 26;
+    const int s0 = __shfl_sync(0xffffffffu, start, c), p0 = __shfl_sync(0xffffffffu, pre, c);
+    if (k0 + lane < nc) {
+      const int g = s0 + (k - p0);
+      const int4 C = b.scom[g];
+      st[k0 + lane] = make_int4(C.x, C.y, C.z, tag_id(b.sorted[g], b.flag[g]));
+    }
+  }
+  __syncwarp();
+}
+
 // One warp per cell (cells in Morton order).  Lanes 0..26 take the 27 neighbour cells in
 // the fixed (ox, oy, oz) order, a warp scan gives each cell's offset in the candidate list,
 // and the candidates (centre + id; each cell's members already in id order) are staged in
@@ -214,11 +241,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
     if (lane == 0) b.dense_cells[atomicAdd(&b.ctrl->n_dense, 1)] = r;
     return;
   }
-  for (int q = 0; q < cnt; ++q) {
-    const int4 C = b.scom[start + q];
-    stage[w][pre + q] = make_int4(C.x, C.y, C.z, tag_id(b.sorted[start + q], b.flag[start + q]));
-  }
-  __syncwarp();
+  stage_window(b, lane, incl, pre, start, 0, total, stage[w]);
   // the home cell is neighbour 13: its molecules and their work items, recorded here
   const int home_pre = __shfl_sync(0xffffffffu, pre, 13);
   const int my_item = lane < n_home ? item_at(s, b, home_start + lane) : 0;
@@ -261,20 +284,17 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr(const __grid_constant
 }
 
 // Dense cells (those k_rb_nbr passed on): kHomeParts warps per listed cell, each taking
-// batches of kMaxHome of its molecules, persistent grid.  Candidates (centre + id) are
-// staged in shared memory kMaxCand at a time; each home molecule of the batch tests a staged
-// chunk in parallel and appends its neighbours in candidate order with ballot/popc
-// compaction, its running count kept in shared memory: the same lists for any density.
-constexpr int kMaxHome = 16;   // home-cell molecules per batch
-constexpr int kHomeParts = 8;  // warps that share one dense cell's home molecules
+// batches of 32 of its molecules (one per lane), persistent grid.  Candidates (centre + id)
+// are staged in shared memory kMaxCand at a time by all lanes; each lane then walks the staged
+// window for its own molecule and appends its neighbours in candidate order (the order of
+// the ballot compaction in k_rb_nbr): the same lists for any density.
+constexpr int kHomeParts = 4;  // warps that share one dense cell's home molecules
 __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_constant__ Sys s, Bufs b) {
   __shared__ int4 stage[kNbrWarps][kMaxCand];
-  __shared__ int4 home[kNbrWarps][kMaxHome];  // centre + work item
-  __shared__ int hitem[kNbrWarps][kMaxHome];
-  __shared__ int hcnt[kNbrWarps][kMaxHome];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_dense = b.ctrl->n_dense;
   const int4* com = b.com_fx[b.ctrl->parity];
+  const float rl2 = s.f.r_list2, rcl2 = s.f.r_cg_list2;
   // task = (dense cell, part): part j takes the home batches j, j + kHomeParts, ... so that
   // the molecules of one dense cell are shared by kHomeParts warps
   for (int task = blockIdx.x * kNbrWarps + w; task < n_dense * kHomeParts; task += gridDim.x * kNbrWarps) {
@@ -299,69 +319,42 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const int n_home = __shfl_sync(0xffffffffu, cnt, 13);
     const int home_start = __shfl_sync(0xffffffffu, start, 13);
-    const float rl2 = s.f.r_list2, rcl2 = s.f.r_cg_list2;
-    for (int hb = part * kMaxHome; hb < n_home; hb += kHomeParts * kMaxHome) {
-      const int nh = min(kMaxHome, n_home - hb);
-      __syncwarp();
-      for (int h = lane; h < nh; h += 32) {
-        const int a = b.sorted[home_start + hb + h];
-        const int4 C = com[a];
-        const int it = item_at(s, b, home_start + hb + h);
-        home[w][h] = make_int4(C.x, C.y, C.z, tag_id(a, b.flag[home_start + hb + h]));
-        hitem[w][h] = it;
-        hcnt[w][h] = 0;
-        b.items[it] = a;
-        b.item_of[a] = it;
+    for (int hb = part * 32; hb < n_home; hb += kHomeParts * 32) {
+      // this lane's home molecule (lanes past the cell's end take none)
+      const bool mine = hb + lane < n_home;
+      const int kh = home_start + hb + (mine ? lane : 0);
+      const int a = b.sorted[kh];
+      const int4 C = com[a];
+      const int H = tag_id(a, b.flag[kh]);
+      const int tt = mine ? item_at(s, b, kh) : 0;
+      if (mine) {
+        b.items[tt] = a;
+        b.item_of[a] = tt;
       }
+      int count = 0;
+      int* row = b.nbr + (size_t)tt * s.cap;
       for (int c0 = 0; c0 < total; c0 += kMaxCand) {
-        __syncwarp();
-        // lane j stages the part of neighbour cell j's members (in id order) inside the window
-        if (lane < 27) {
-          const int lo = max(pre, c0), hi = min(pre + cnt, c0 + kMaxCand);
-#pragma unroll 1
-          for (int k = lo; k < hi; ++k) {
-            const int4 C = b.scom[start + (k - pre)];
-            stage[w][k - c0] = make_int4(C.x, C.y, C.z, tag_id(b.sorted[start + (k - pre)], b.flag[start + (k - pre)]));
-          }
-        }
-        __syncwarp();
         const int nc = min(kMaxCand, total - c0);
-#pragma unroll 1
-        for (int h = 0; h < nh; ++h) {
-          const int4 H = home[w][h];
-          const int a = id_of(H.w);
-          const int tt = hitem[w][h];
-          int count = hcnt[w][h];
-          for (int k0 = 0; k0 < nc; k0 += 32) {
-            const int k = k0 + lane;
-            bool hit = false;
-            int m = 0;
-            if (k < nc) {
-              const int4 D = stage[w][k];
-              m = id_of(D.w);
-              const float d0 = (float)(int)((unsigned)H.x - (unsigned)D.x) * B.fx_scale[0];
-              const float d1 = (float)(int)((unsigned)H.y - (unsigned)D.y) * B.fx_scale[1];
-              const float d2 = (float)(int)((unsigned)H.z - (unsigned)D.z) * B.fx_scale[2];
-              hit = m != a && d0 * d0 + d1 * d1 + d2 * d2 < ((H.w & D.w) < 0 ? rl2 : rcl2);
+        __syncwarp();  // the previous window is no longer read
+        stage_window(b, lane, incl, pre, start, c0, nc, stage[w]);
+        if (mine) {
+#pragma unroll 4
+          for (int k = 0; k < nc; ++k) {
+            const int4 D = stage[w][k];
+            const int m = id_of(D.w);
+            const float d0 = (float)(int)((unsigned)C.x - (unsigned)D.x) * B.fx_scale[0];
+            const float d1 = (float)(int)((unsigned)C.y - (unsigned)D.y) * B.fx_scale[1];
+            const float d2 = (float)(int)((unsigned)C.z - (unsigned)D.z) * B.fx_scale[2];
+            if (m != a && d0 * d0 + d1 * d1 + d2 * d2 < ((H & D.w) < 0 ? rl2 : rcl2)) {
+              if (count < s.cap) row[count] = m;
+              ++count;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) {
-              const int p = count + __popc(bal & ((1u << lane) - 1u));
-              if (p < s.cap) b.nbr[(size_t)tt * s.cap + p] = m;
-            }
-            count += __popc(bal);
           }
-          if (lane == 0) hcnt[w][h] = count;
-          __syncwarp();
         }
       }
-      __syncwarp();
-      for (int h = lane; h < nh; h += 32) {
-        const int4 H = home[w][h];
-        const int count = hcnt[w][h];
-        const int tt = hitem[w][h];
+      if (mine) {
         b.nn[tt] = count < s.cap ? count : s.cap;
-        b.com_ref[id_of(H.w)] = make_int4(H.x, H.y, H.z, 0);
+        b.com_ref[a] = make_int4(C.x, C.y, C.z, 0);
         if (count > s.cap) set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, count);
       }
     }
