@@ -667,6 +667,12 @@ def main():
                     help="for --profile: the water-like fluid (64k molecules, or --molecules at its density)")
     ap.add_argument("--molecules", type=int, default=200_000,
                     help="system size for --profile (same density, shape and slab proportions)")
+    ap.add_argument("--save-state", default=None,
+                    help="for --profile: run --equilibrate MD steps from the initial state, save x, v and the "
+                         "thermodynamic-force table to this .npz and exit (so that a profiled process can start "
+                         "from the equilibrated fluid without hundreds of launches before the captured ones)")
+    ap.add_argument("--load-state", default=None, help="for --profile: start from a state saved by --save-state")
+    ap.add_argument("--equilibrate", type=int, default=600, help="for --save-state: MD steps (multiple of 100)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -695,10 +701,27 @@ def main():
             s = inputs.c2_800k() if args.molecules == 200_000 else inputs.scaled_c2(args.molecules)
             x0, v0 = inputs.tetra_state(s)
         sim = adress.AdResS(s, precision=args.precision, device=f"cuda:{local}")
+        if args.save_state:
+            sim.set_state(x0, v0)
+            sim.compute_forces(energies=False)
+            for _ in range(max(1, args.equilibrate // MD_PER_BLOCK)):
+                sim.run(MD_PER_BLOCK, sample_every=SAMPLE_EVERY, tf_update=True, alpha=TF_ALPHA)
+            sim.check()
+            xe, ve, _ = sim.get_state()
+            np.savez(args.save_state, x=xe, v=ve, tf=sim.get_tf())
+            print(json.dumps({"saved": args.save_state, "steps": sim.get_step(), "lists": sim.list_stats()}))
+            sim.close()
+            return 0
+        xi, vi = x0, v0  # the initial state (atomistic samples start from it)
+        if args.load_state:
+            saved = np.load(args.load_state)
+            x0, v0 = saved["x"], saved["v"]
+            sim.set_tf(saved["tf"])
         sim.set_state(x0, v0)
         if args.cg_mode:
-            # the production network: trained on samples of an all-atomistic run
-            feat, t, at = atomistic_samples(s, x0, v0, device=f"cuda:{local}")
+            # the production network: trained on samples of an all-atomistic run from the
+            # initial state (an AdResS state has overlapping atoms in its CG region)
+            feat, t, at = atomistic_samples(s, xi, vi, device=f"cuda:{local}")
             at.close()
             train_network(sim, feat, t)
             sim.set_cg_mode(1)
@@ -759,10 +782,10 @@ def main():
     total_s, ms, clocks = timed(sim, args.steps, args.warmup)
     rebuilds = timed.rebuilds
     # kernels per bench step (one graph): 1 prologue + 99 fused + 1 last + 100 decide
-    # + 10 density samples + 2 for the TF update (update, sample-count reset); 14 kernels
-    # per list rebuild
+    # + 10 density samples + 2 for the TF update (update, sample-count reset); 9 kernels
+    # per list rebuild (count, 2 scan, fill, sort, 2 scan, lists, dense-cell lists)
     per_block = 1 + (MD_PER_BLOCK - 1) + 1 + MD_PER_BLOCK + MD_PER_BLOCK // SAMPLE_EVERY + 2
-    launches = args.steps * per_block + 14 * rebuilds
+    launches = args.steps * per_block + 9 * rebuilds
     value, total_s = job_throughput(total_s, s.N * MD_PER_BLOCK * args.steps, dist, dev)
 
     # ---- live kernel timing (CUDA events on the library's stream) + roofline ----
