@@ -98,7 +98,8 @@ typedef struct {
   double kT, gamma, dt;
   uint64_t seed;
   int64_t replica;
-  /* neighbour lists over molecule centres: cutoff max(rc_cg, rc_at + 2 r_ext) + skin */
+  /* neighbour lists over molecule centres: cutoff max(rc_cg, rc_at + 2 r_ext) + skin between
+   * two high-resolution work items, rc_cg + skin when either is coarse-grained */
   double skin, r_ext;
   int32_t max_neighbors; /* initial list capacity per molecule; 0 = automatic */
   int32_t precision;     /* adress_precision */
@@ -188,8 +189,11 @@ adress_status adress_bind_state(adress_handle h, double* x, double* v, void* f);
  * of that section handled by separate work lists instead of non-uniform domains).
  * Map the bound positions to centres of mass and resolution values, then rebuild the
  * Morton-ordered cell list, the class work lists (high-resolution candidates first,
- * then coarse-grained molecules) and the Verlet lists.  Synchronises: grows the list
- * capacity and rebuilds when a molecule has more neighbours than it holds. */
+ * then coarse-grained molecules) and the Verlet lists (symmetric; a pair with a
+ * coarse-grained item, which has weight 0 until the next build, is listed within
+ * rc_cg + skin, a pair of high-resolution items within max(rc_cg, rc_at + 2 r_ext) + skin).
+ * Synchronises: grows the list capacity and rebuilds when a molecule has more neighbours
+ * than it holds. */
 adress_status adress_build_lists(adress_handle h);
 
 /* Conservative forces of the bound positions (Eq. 1 + bonded + thermodynamic force,
