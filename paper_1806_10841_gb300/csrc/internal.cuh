@@ -40,9 +40,11 @@ struct Ctrl {
   // squared COM displacement since the last build [1], as block maxima spread over
   // kExtSlots slots (block b uses slot b mod kExtSlots); the decide kernel folds and clears them
   unsigned ext_slot[2][kExtSlots];
+  int n_netc;  // candidate pairs of the network CG force from the last list build (Bufs::netc)
 };
 
-// Decision taken after a mapping (see decide_after_map in observe.cu).
+// Arguments of the rebuild decision taken after a mapping (k_decide in observe.cu): force a
+// rebuild, advance the time level, set the graph conditional handle h.
 struct DecideArgs {
   int force, advance, use_h;
   cudaGraphConditionalHandle h;
@@ -201,8 +203,10 @@ struct Bufs {
                     // words 0-4 the ordering (d, s_a, s_b), 5-9 the ordering (d, s_b, s_a)
   int2* pslot;   // [pcap] the pair's two list slots
   int* mirror;   // [M*cap] (CG mode 1) slot of the same pair in the partner's list, from the last build
+  int4* netc;    // [pcap] (CG mode 1) candidate pairs of the last build: slot, mirror slot, a, b
   unsigned* npair;  // pairs written this step
   long long pcap;   // pairs the buffers may hold (the allocation, or a smaller limit the host set)
+  long long ncap;   // candidate records netc may hold (the allocation)
   unsigned wait_polls;  // poll limit of the tcgen05 evaluation's product waits (kMmaWaitPolls)
   // batched replicas (nbox > 1)
   const Box* boxes;    // [nbox]
@@ -278,7 +282,9 @@ cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st);
 // molecule arrays and, in a graph, sets the conditional of the rebuild node.
 cudaError_t launch_decide(const Sys& s, const Bufs& b, DecideArgs da, cudaStream_t st);
 cudaError_t launch_max_nn(const Sys& s, const Bufs& b, cudaStream_t st);
-// Mirror slots of the current lists (Bufs::mirror); launch_rebuild runs it in CG mode 1.
+// Mirror slots of the current lists (Bufs::mirror) and the network force's candidate pairs
+// (Bufs::netc, counted in Ctrl::n_netc, which the caller zeroes); launch_rebuild runs it in
+// CG mode 1.
 cudaError_t launch_mirror(const Sys& s, const Bufs& b, cudaStream_t st);
 // out[i] = sum_{j<i} in[j] for i < n, *total = sum of all (n <= 8M)
 cudaError_t device_exclusive_scan(const int* in, int* out, int n, int* tmp, int* total, cudaStream_t st);

@@ -34,6 +34,7 @@ __global__ void k_rb_count(const __grid_constant__ Sys s, Bufs b) {
   if (a == 0) {
     b.ctrl->n_dense = 0;
     b.ctrl->force_rebuild = 0;
+    b.ctrl->n_netc = 0;
   }
   if (a >= s.M) return;
   const Box& B = box_of(s, b, a);
@@ -383,9 +384,12 @@ __global__ void __launch_bounds__(128) k_rb_mirror(const __grid_constant__ Sys s
   }
 }
 
+cudaError_t launch_net_candidates(const Sys& s, const Bufs& b, cudaStream_t st);
+
 cudaError_t launch_mirror(const Sys& s, const Bufs& b, cudaStream_t st) {
   k_rb_mirror<<<ceil_div((long long)s.M * 4, 128), 128, 0, st>>>(s, b);
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? launch_net_candidates(s, b, st) : e;
 }
 
 // Largest neighbour count of the last build (host-side capacity check only).

@@ -728,12 +728,14 @@ __global__ void k_mlp_collect(const __grid_constant__ Sys s, Bufs b, int pass, c
 // ---------------- pair forces for the dynamics -------------------------------------------
 // Every list slot (t, q) whose pair needs a CG force (COM distance < rc_cg and w_ab < 1, the
 // force kernel's test in its own precision and arithmetic) gets the symmetrised network
-// force in fpair[t cap + q].  Two kernels: k_mlp_feat walks the lists (a thread per work
-// item), takes every such pair once (from the molecule with the smaller id), computes its
-// features, finds the mirror slot in the partner's list and appends both to a pair buffer
-// (one atomic per warp; the buffer order varies between runs, the values do not);
-// k_mlp_eval then evaluates the buffer 16 pairs per warp tile (both orderings as two
-// tensor-core tiles, weights staged in shared memory) and writes the force to both slots.
+// force in fpair[t cap + q].  At each list build k_net_candidates records every pair that may
+// need the network before the next build, once (from the molecule with the smaller id), with
+// its slot and the mirror slot in the partner's list.  Per step k_mlp_feat tests the
+// candidates, computes the features of those that need the network and appends them to a
+// pair buffer (one atomic per warp; the buffer order varies between runs, the values do
+// not); the evaluation kernel (k_mlp_eval_tc on tcgen05, or k_mlp_eval below: 16 pairs per
+// warp tile, both orderings as two tensor-core tiles, weights staged in shared memory) then
+// writes the force to both slots.
 
 // The first molecule's centre (FP64 or fixed-point, by path) is passed in.
 template <bool F64>
@@ -772,90 +774,151 @@ __device__ __forceinline__ bool needs_network(const Sys& s, const Box& X, const 
   }
 }
 
-constexpr int kFeatLanes = 4;  // lanes per work item in k_mlp_feat (a power of two <= 32)
+// Both orderings of a pair's features, normalised (mean, 1/std in sn) and packed as bf16
+// pairs the way the evaluation kernels read their A operands.
+__device__ __forceinline__ void pack_pair_inputs(const float f[9], const float (*sn)[kIn], unsigned* out) {
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int w = 0; w < 5; ++w) {
+      float v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * w + h;
+        const int src = (u == 0 || k == 0) ? k : (k < 5 ? k + 4 : k - 4);
+        v[h] = k < kIn ? (f[src < kIn ? src : 0] - sn[0][k < kIn ? k : 0]) * sn[1][k < kIn ? k : 0] : 0.f;
+      }
+      out[5 * u + w] = pack_bf16(v[0], v[1]);
+    }
+}
 
-template <int NA, bool F64>
-__global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s, Bufs b, const float* __restrict__ norm) {
-  // multiple time stepping: the network gives a slow (CG) force, needed only at outer time
-  // levels; elsewhere no pair is written and the evaluation kernel finds nothing to do
-  if (s.respa_n > 1 && b.ctrl->step % s.respa_n != 0) return;
-  // input normalisation (mean, 1/std) for the network's A operands
-  __shared__ float sn[2][kIn];
-  if (threadIdx.x < kIn) {
-    sn[0][threadIdx.x] = norm[threadIdx.x];
-    sn[1][threadIdx.x] = norm[2 * kIn + 1 + threadIdx.x];
-  }
-  __syncthreads();
-  // kFeatLanes lanes per work item, lane g taking list slots g, g + kFeatLanes, ...; one walk
-  // of the list tests every slot and marks the selected ones in sel (bit j for slot
-  // g + kFeatLanes j; slots past bit 31 are tested again when their features are formed)
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) / kFeatLanes, g = threadIdx.x & (kFeatLanes - 1);
+// A molecule deep in the atomistic region at the list build: it keeps lambda = 1 until the
+// next build (its centre moves by less than skin/2 before then).
+__device__ __forceinline__ bool deep_atomistic(const Sys& s, const Bufs& b, int cur, int a) {
+  if (s.lam_uniform_on) return s.lam_uniform >= 1.0;
+  const double d = s.fp64 ? fabs(b.dxc64[cur][a]) : (double)fabsf(b.molf[cur][a].x);
+  return d < box_of(s, b, a).d_at - 0.5 * s.skin - 1e-3;
+}
+
+// Candidate pairs of the network force, built with the lists (after the mirror slots): every
+// listed slot (t, q) whose molecule pair a = items[t] < m is within rc_cg + skin and is not
+// made of two deep-atomistic molecules.  Until the next build every pair that needs the
+// network (weight below 1, centres within rc_cg) is among them: the centres move by less
+// than skin/2 each, and a pair of deep-atomistic molecules keeps weight 1.  Records (slot,
+// mirror slot, a, m); four lanes per work item, one atomic per warp (the order varies between
+// runs, the set does not).
+template <bool F64>
+__global__ void __launch_bounds__(128) k_net_candidates(const __grid_constant__ Sys s, Bufs b) {
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2, g = threadIdx.x & 3;
   const int lane = threadIdx.x & 31;
   const bool live = t < s.M;
   const int cur = b.ctrl->parity;
   const int a = live ? b.items[t] : 0;
   const int n = live ? b.nn[t] : 0;
   const Box& X = box_of(s, b, a);
-  const Centre<F64> CA = centre_of<F64>(b, cur, a);
+  const bool deep_a = live && deep_atomistic(s, b, cur, a);
   const int* row = b.nbr + (size_t)t * s.cap;
-  unsigned sel = 0u;
-  int cnt = 0;
-  for (int q = g, j = 0; q < n; q += kFeatLanes, ++j) {
-    const int m = row[q];
-    if (m > a && needs_network<F64>(s, X, b, cur, CA, m)) {
-      ++cnt;
-      if (j < 32) sel |= 1u << j;
+  auto candidate = [&](int m) -> bool {
+    if (m <= a || (deep_a && deep_atomistic(s, b, cur, m))) return false;
+    if constexpr (F64) {
+      const double4_32a A = b.com64[cur][a], B = b.com64[cur][m];
+      return pair_r2(minimg_cmp(A.x - B.x, X.L[0], X.halfL[0]), minimg_cmp(A.y - B.y, X.L[1], X.halfL[1]),
+                     minimg_cmp(A.z - B.z, X.L[2], X.halfL[2])) < s.r_cg_list2;
+    } else {
+      const int4 A = b.com_fx[cur][a], B = b.com_fx[cur][m];
+      return pair_r2((float)(int)((unsigned)A.x - (unsigned)B.x) * X.fx_scale[0],
+                     (float)(int)((unsigned)A.y - (unsigned)B.y) * X.fx_scale[1],
+                     (float)(int)((unsigned)A.z - (unsigned)B.z) * X.fx_scale[2]) < s.f.r_cg_list2;
     }
-  }
+  };
+  unsigned long long sel = 0ull;
+  int cnt = 0;
+  for (int q = g, j = 0; q < n; q += 4, ++j)
+    if (candidate(row[q])) {
+      ++cnt;
+      if (j < 64) sel |= 1ull << j;
+    }
   int incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const int v = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += v;
   }
-  unsigned base = 0;
-  if (lane == 31 && incl > 0) base = atomicAdd(b.npair, (unsigned)incl);
+  int base = 0;
+  if (lane == 31 && incl > 0) base = atomicAdd(&b.ctrl->n_netc, incl);
   base = __shfl_sync(0xffffffffu, base, 31);
   long long p = (long long)base + (incl - cnt);
   if (cnt == 0) return;
-  int qx = g + 32 * kFeatLanes;  // where the search for selected slots beyond the mask resumes
+  int qx = g + 256;  // where the search for candidates beyond the mask resumes
   for (int left = cnt; left > 0; --left) {
-    int q, m = -1;
+    int q;
     if (sel) {
-      q = g + kFeatLanes * (__ffs(sel) - 1);
+      q = g + 4 * (__ffsll((long long)sel) - 1);
       sel &= sel - 1;
-      m = row[q];
     } else {
-      for (q = qx; q < n; q += kFeatLanes) {
-        m = row[q];
-        if (m > a && needs_network<F64>(s, X, b, cur, CA, m)) break;
-      }
+      for (q = qx; q < n; q += 4)
+        if (candidate(row[q])) break;
       if (q >= n) return;  // not reached: the first walk counted this slot
-      qx = q + kFeatLanes;
+      qx = q + 4;
     }
-    if (p >= b.pcap) {
+    if (p >= b.ncap) {  // not reached: at most one record per unordered listed pair
       set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, (int)p);
       return;
     }
-    float f[9];
-    pair_features32<NA, F64>(s, b, cur, a, m, f);
-    // both orderings, normalised and packed as the A fragments read them
-    unsigned* out = b.pfrag + p * 10;
-#pragma unroll
-    for (int u = 0; u < 2; ++u)
-#pragma unroll
-      for (int w = 0; w < 5; ++w) {
-        float v[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int k = 2 * w + h;
-          const int src = (u == 0 || k == 0) ? k : (k < 5 ? k + 4 : k - 4);
-          v[h] = k < kIn ? (f[src < kIn ? src : 0] - sn[0][k < kIn ? k : 0]) * sn[1][k < kIn ? k : 0] : 0.f;
-        }
-        out[5 * u + w] = pack_bf16(v[0], v[1]);
-      }
-    b.pslot[p] = make_int2(t * s.cap + q, b.mirror[(size_t)t * s.cap + q]);
+    const size_t slot = (size_t)t * s.cap + q;
+    b.netc[p] = make_int4((int)slot, b.mirror[slot], a, row[q]);
     ++p;
+  }
+}
+
+cudaError_t launch_net_candidates(const Sys& s, const Bufs& b, cudaStream_t st) {
+  const int blocks = ceil_div((long long)s.M * 4, 128);
+  if (s.fp64) k_net_candidates<true><<<blocks, 128, 0, st>>>(s, b);
+  else k_net_candidates<false><<<blocks, 128, 0, st>>>(s, b);
+  return cudaGetLastError();
+}
+
+// Pairs that need the network this step, from the candidates of the last build: the force
+// kernel's test (centres within rc_cg, weight below 1) in its own precision and arithmetic,
+// then the pair's features, normalised bf16 inputs of both orderings and its two list slots
+// appended to the pair buffer (one atomic per warp).  One thread per candidate, persistent grid.
+template <int NA, bool F64>
+__global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s, Bufs b, const float* __restrict__ norm) {
+  // multiple time stepping: the network gives a slow (CG) force, needed only at outer time
+  // levels; elsewhere no pair is written and the evaluation kernel finds nothing to do
+  if (s.respa_n > 1 && b.ctrl->step % s.respa_n != 0) return;
+  __shared__ float sn[2][kIn];
+  if (threadIdx.x < kIn) {
+    sn[0][threadIdx.x] = norm[threadIdx.x];
+    sn[1][threadIdx.x] = norm[2 * kIn + 1 + threadIdx.x];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int cur = b.ctrl->parity;
+  const long long nc = min((long long)b.ctrl->n_netc, b.ncap);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < nc; k0 += stride) {
+    const long long k = k0 + lane;
+    int4 rec = make_int4(0, 0, 0, 0);
+    bool need = false;
+    if (k < nc) {
+      rec = b.netc[k];
+      need = needs_network<F64>(s, box_of(s, b, rec.z), b, cur, centre_of<F64>(b, cur, rec.z), rec.w);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, need);
+    unsigned base = 0;
+    if (lane == 0 && bal) base = atomicAdd(b.npair, (unsigned)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (!need) continue;
+    const long long p = (long long)base + __popc(bal & ((1u << lane) - 1u));
+    if (p >= b.pcap) {
+      set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, (int)p);
+      continue;
+    }
+    float f[9];
+    pair_features32<NA, F64>(s, b, cur, rec.z, rec.w, f);
+    pack_pair_inputs(f, sn, b.pfrag + p * 10);
+    b.pslot[p] = make_int2(rec.x, rec.y);
   }
 }
 
@@ -1120,7 +1183,14 @@ cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* f
   const MlpDev m{a.P, a.W1p, a.W2p, a.W2Tp, a.norm};
   cudaError_t e = cudaMemsetAsync(b.npair, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  const int blocks = ceil_div((long long)s.M * kFeatLanes, 128);
+  // persistent grid for the candidates (their count is on the device)
+  static int blocks = 0;
+  if (!blocks) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    blocks = 16 * sms;
+  }
 #define FEAT(NA_)                                                       \
   (s.fp64 ? k_mlp_feat<NA_, true><<<blocks, 128, 0, st>>>(s, b, a.norm) \
           : k_mlp_feat<NA_, false><<<blocks, 128, 0, st>>>(s, b, a.norm))
