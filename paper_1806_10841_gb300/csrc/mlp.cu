@@ -1183,13 +1183,15 @@ cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* f
   const MlpDev m{a.P, a.W1p, a.W2p, a.W2Tp, a.norm};
   cudaError_t e = cudaMemsetAsync(b.npair, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  // persistent grid for the candidates (their count is on the device)
+  // persistent grid for the candidates (their count is on the device): two full waves of
+  // the 11 blocks per SM that the kernel's 44 registers allow (1, 1.45, 3 and 4 waves
+  // measured slower at 800k atoms)
   static int blocks = 0;
   if (!blocks) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
-    blocks = 16 * sms;
+    blocks = 22 * sms;
   }
 #define FEAT(NA_)                                                       \
   (s.fp64 ? k_mlp_feat<NA_, true><<<blocks, 128, 0, st>>>(s, b, a.norm) \
