@@ -118,7 +118,6 @@ static cudaError_t alloc_pair_buffers(adress_ctx* h) {
   const long long pcap = (long long)h->sys.M * h->sys.cap / 2 + 32;
   cudaError_t e = realloc_owned(h, &b.pfrag, (size_t)pcap * 10 + 4);
   if (e == cudaSuccess) e = realloc_owned(h, &b.pslot, (size_t)pcap + 2);
-  if (e == cudaSuccess) e = realloc_owned(h, &b.mirror, (size_t)h->sys.M * h->sys.cap);
   if (e == cudaSuccess) e = realloc_owned(h, &b.netc, (size_t)pcap);
   if (e == cudaSuccess && !b.npair) e = dalloc(h, &b.npair, 1);
   if (e == cudaSuccess) {
@@ -1475,10 +1474,10 @@ adress_status adress_set_cg_mode(adress_handle h, int32_t mode) {
   }
   if (h->sys.cg_mode != mode) free_graphs(h);
   h->sys.cg_mode = mode;
-  // mirror slots of the lists already built (later builds add them themselves)
+  // candidate pairs of the lists already built (later builds add them themselves)
   if (mode == 1 && h->lists_built) {
     CUDA_OR_FAIL(h, cudaMemsetAsync(&h->buf.ctrl->n_netc, 0, sizeof(int), h->stream));
-    CUDA_OR_FAIL(h, launch_mirror(h->sys, h->buf, h->stream));
+    CUDA_OR_FAIL(h, launch_net_candidates(h->sys, h->buf, h->stream));
   }
   return ADRESS_OK;
 }

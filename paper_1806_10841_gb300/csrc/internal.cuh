@@ -202,8 +202,8 @@ struct Bufs {
   unsigned* pfrag;  // [pcap][10] normalised network inputs of this step's pairs as bf16 pairs:
                     // words 0-4 the ordering (d, s_a, s_b), 5-9 the ordering (d, s_b, s_a)
   int2* pslot;   // [pcap] the pair's two list slots
-  int* mirror;   // [M*cap] (CG mode 1) slot of the same pair in the partner's list, from the last build
-  int4* netc;    // [pcap] (CG mode 1) candidate pairs of the last build: slot, mirror slot, a, b
+  int4* netc;    // [pcap] (CG mode 1) candidate pairs of the last build: slot, slot of the same
+                 // pair in the partner's list, a, b
   unsigned* npair;  // pairs written this step
   long long pcap;   // pairs the buffers may hold (the allocation, or a smaller limit the host set)
   long long ncap;   // candidate records netc may hold (the allocation)
@@ -282,10 +282,10 @@ cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st);
 // molecule arrays and, in a graph, sets the conditional of the rebuild node.
 cudaError_t launch_decide(const Sys& s, const Bufs& b, DecideArgs da, cudaStream_t st);
 cudaError_t launch_max_nn(const Sys& s, const Bufs& b, cudaStream_t st);
-// Mirror slots of the current lists (Bufs::mirror) and the network force's candidate pairs
+// The network force's candidate pairs of the current lists with their mirror slots
 // (Bufs::netc, counted in Ctrl::n_netc, which the caller zeroes); launch_rebuild runs it in
 // CG mode 1.
-cudaError_t launch_mirror(const Sys& s, const Bufs& b, cudaStream_t st);
+cudaError_t launch_net_candidates(const Sys& s, const Bufs& b, cudaStream_t st);
 // out[i] = sum_{j<i} in[j] for i < n, *total = sum of all (n <= 8M)
 cudaError_t device_exclusive_scan(const int* in, int* out, int n, int* tmp, int* total, cudaStream_t st);
 // mode: 0 conservative forces, 1 last step of a run (thermostat + second half kick),

@@ -362,35 +362,7 @@ __global__ void __launch_bounds__(32 * kNbrWarps) k_rb_nbr_dense(const __grid_co
   }
 }
 
-// Mirror slots: for slot (t, q) holding partner m, the slot of molecule items[t] in m's
-// list (the lists are symmetric).  Four lanes per work item.
-__global__ void __launch_bounds__(128) k_rb_mirror(const __grid_constant__ Sys s, Bufs b) {
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 2, g = threadIdx.x & 3;
-  if (t >= s.M) return;
-  const int a = b.items[t], n = b.nn[t];
-  const int* row = b.nbr + (size_t)t * s.cap;
-  for (int q = g; q < n; q += 4) {
-    const int m = row[q];
-    const int tb = b.item_of[m], nb = b.nn[tb];
-    const int* rb = b.nbr + (size_t)tb * s.cap;
-    int found = -1;
-    for (int qq = 0; qq < nb; ++qq)
-      if (rb[qq] == a) {
-        found = qq;
-        break;
-      }
-    if (found < 0) set_error(b.ctrl, ADRESS_ERR_STATE, a);
-    b.mirror[(size_t)t * s.cap + q] = found < 0 ? -1 : tb * s.cap + found;
-  }
-}
-
 cudaError_t launch_net_candidates(const Sys& s, const Bufs& b, cudaStream_t st);
-
-cudaError_t launch_mirror(const Sys& s, const Bufs& b, cudaStream_t st) {
-  k_rb_mirror<<<ceil_div((long long)s.M * 4, 128), 128, 0, st>>>(s, b);
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? launch_net_candidates(s, b, st) : e;
-}
 
 // Largest neighbour count of the last build (host-side capacity check only).
 __global__ void k_max_nn(const __grid_constant__ Sys s, const Bufs b) {
@@ -421,7 +393,7 @@ cudaError_t launch_rebuild(const Sys& s, const Bufs& b, cudaStream_t st) {
   if ((e = exclusive_scan(b.flag, b.pos, s.M, b.scan_tmp, b.pos + s.M, st)) != cudaSuccess) return e;
   k_rb_nbr<<<ceil_div(s.ncell, kNbrWarps), 32 * kNbrWarps, 0, st>>>(s, b);
   k_rb_nbr_dense<<<std::min(ceil_div((long long)s.ncell * kHomeParts, kNbrWarps), 152 * 16), 32 * kNbrWarps, 0, st>>>(s, b);
-  if (s.cg_mode && b.mirror) return launch_mirror(s, b, st);
+  if (s.cg_mode && b.netc) return launch_net_candidates(s, b, st);
   return cudaGetLastError();
 }
 

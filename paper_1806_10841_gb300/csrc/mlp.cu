@@ -800,7 +800,7 @@ __device__ __forceinline__ bool deep_atomistic(const Sys& s, const Bufs& b, int 
   return d < box_of(s, b, a).d_at - 0.5 * s.skin - 1e-3;
 }
 
-// Candidate pairs of the network force, built with the lists (after the mirror slots): every
+// Candidate pairs of the network force, built with the lists: every
 // listed slot (t, q) whose molecule pair a = items[t] < m is within rc_cg + skin and is not
 // made of two deep-atomistic molecules.  Until the next build every pair that needs the
 // network (weight below 1, centres within rc_cg) is among them: the centres move by less
@@ -865,8 +865,17 @@ __global__ void __launch_bounds__(128) k_net_candidates(const __grid_constant__ 
       set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, (int)p);
       return;
     }
-    const size_t slot = (size_t)t * s.cap + q;
-    b.netc[p] = make_int4((int)slot, b.mirror[slot], a, row[q]);
+    // the mirror slot: where a sits in m's list (the lists are symmetric)
+    const int m = row[q], tb = b.item_of[m], nb = b.nn[tb];
+    const int* rb = b.nbr + (size_t)tb * s.cap;
+    int found = -1;
+    for (int qq = 0; qq < nb; ++qq)
+      if (rb[qq] == a) {
+        found = qq;
+        break;
+      }
+    if (found < 0) set_error(b.ctrl, ADRESS_ERR_STATE, a);
+    b.netc[p] = make_int4(t * s.cap + q, found < 0 ? -1 : tb * s.cap + found, a, m);
     ++p;
   }
 }
