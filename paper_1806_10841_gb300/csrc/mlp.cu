@@ -914,6 +914,9 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
       rec = b.netc[k];
       need = needs_network<F64>(s, box_of(s, b, rec.z), b, cur, centre_of<F64>(b, cur, rec.z), rec.w);
     }
+    // the features first, so that their gathers overlap the warp's atomic below
+    float f[9];
+    if (need) pair_features32<NA, F64>(s, b, cur, rec.z, rec.w, f);
     const unsigned bal = __ballot_sync(0xffffffffu, need);
     unsigned base = 0;
     if (lane == 0 && bal) base = atomicAdd(b.npair, (unsigned)__popc(bal));
@@ -924,8 +927,6 @@ __global__ void __launch_bounds__(128) k_mlp_feat(const __grid_constant__ Sys s,
       set_error(b.ctrl, ADRESS_ERR_LIST_OVERFLOW, (int)p);
       continue;
     }
-    float f[9];
-    pair_features32<NA, F64>(s, b, cur, rec.z, rec.w, f);
     pack_pair_inputs(f, sn, b.pfrag + p * 10);
     b.pslot[p] = make_int2(rec.x, rec.y);
   }
@@ -1192,9 +1193,9 @@ cudaError_t mlp_pairs(const Sys& s, const Bufs& b, const MlpDevArgs& a, float* f
   const MlpDev m{a.P, a.W1p, a.W2p, a.W2Tp, a.norm};
   cudaError_t e = cudaMemsetAsync(b.npair, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  // persistent grid for the candidates (their count is on the device): two full waves of
-  // the 11 blocks per SM that the kernel's 44 registers allow (1, 1.45, 3 and 4 waves
-  // measured slower at 800k atoms)
+  // persistent grid for the candidates (their count is on the device): 22 blocks per SM,
+  // about two waves of the 10 that the kernel's 48 registers let reside (11, 16, 20, 33 and
+  // 44 blocks per SM measured slower at 800k atoms)
   static int blocks = 0;
   if (!blocks) {
     int dev = 0, sms = 0;
