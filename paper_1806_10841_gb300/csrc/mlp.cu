@@ -793,11 +793,15 @@ __device__ __forceinline__ void pack_pair_inputs(const float f[9], const float (
 }
 
 // A molecule deep in the atomistic region at the list build: it keeps lambda = 1 until the
-// next build (its centre moves by less than skin/2 before then).
-__device__ __forceinline__ bool deep_atomistic(const Sys& s, const Bufs& b, int cur, int a) {
+// next build (its centre moves by less than skin/2 before then).  thr = d_at - skin/2 - 1e-3
+// of the molecule's box (as float for the FP32 path, whose distances are floats).
+template <bool F64>
+__device__ __forceinline__ bool deep_atomistic(const Sys& s, const Bufs& b, int cur, int a, double thr, float thr_f) {
   if (s.lam_uniform_on) return s.lam_uniform >= 1.0;
-  const double d = s.fp64 ? fabs(b.dxc64[cur][a]) : (double)fabsf(b.molf[cur][a].x);
-  return d < box_of(s, b, a).d_at - 0.5 * s.skin - 1e-3;
+  if constexpr (F64)
+    return fabs(b.dxc64[cur][a]) < thr;
+  else
+    return fabsf(b.molf[cur][a].x) < thr_f;
 }
 
 // Candidate pairs of the network force, built with the lists: every
@@ -816,10 +820,14 @@ __global__ void __launch_bounds__(128) k_net_candidates(const __grid_constant__ 
   const int a = live ? b.items[t] : 0;
   const int n = live ? b.nn[t] : 0;
   const Box& X = box_of(s, b, a);
-  const bool deep_a = live && deep_atomistic(s, b, cur, a);
+  // the threshold once per thread (neighbours share the box of the work item); the FP32
+  // path forms it from float parameters (skin = sqrt(r_cg_list2) - rc_cg), off the FP64 pipe
+  const double thr = F64 ? X.d_at - 0.5 * s.skin - 1e-3 : 0.0;
+  const float thr_f = X.d_at_f - 0.5f * (sqrtf(s.f.r_cg_list2) - sqrtf(s.f.rc_cg2)) - 1e-3f;
+  const bool deep_a = live && deep_atomistic<F64>(s, b, cur, a, thr, thr_f);
   const int* row = b.nbr + (size_t)t * s.cap;
   auto candidate = [&](int m) -> bool {
-    if (m <= a || (deep_a && deep_atomistic(s, b, cur, m))) return false;
+    if (m <= a || (deep_a && deep_atomistic<F64>(s, b, cur, m, thr, thr_f))) return false;
     if constexpr (F64) {
       const double4_32a A = b.com64[cur][a], B = b.com64[cur][m];
       return pair_r2(minimg_cmp(A.x - B.x, X.L[0], X.halfL[0]), minimg_cmp(A.y - B.y, X.L[1], X.halfL[1]),
